@@ -1,0 +1,294 @@
+"""FP64 CPU oracle for the GSta training step.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the package smoke check and the
+benchmark's CPU-baseline leg are the only callers. The CUDA product never
+imports this package, and this package imports nothing from the product.
+
+The arithmetic lives in ``gsta_oracle.c`` (plain loops in double precision);
+this module compiles it with gcc on first use and wraps each function for
+numpy arrays. ``controller.py`` holds the host-side schedule of the method
+(Eq. 5 thresholds, Eq. 7 early stop, plateau learning rate).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gsta_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+N_PARAMS = 59
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE arithmetic: no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+             "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cam(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+        ("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3), ("campos", ctypes.c_double * 3),
+        ("znear", ctypes.c_double), ("dilation", ctypes.c_double), ("bg", ctypes.c_double * 3),
+    ]
+
+
+def make_cam(cam, tile: int = 16, znear: float = 0.2, dilation: float = 0.3, bg=(0.0, 0.0, 0.0)) -> Cam:
+    """Oracle camera from a ``synth.Camera``-like object (duck-typed)."""
+    c = Cam()
+    c.width, c.height, c.tile = int(cam.width), int(cam.height), int(tile)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float64).reshape(9)]
+    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float64).reshape(3)]
+    c.campos[:] = [float(v) for v in np.asarray(cam.campos, np.float64).reshape(3)]
+    c.znear, c.dilation = float(znear), float(dilation)
+    c.bg[:] = [float(v) for v in bg]
+    return c
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_up = ctypes.POINTER(ctypes.c_uint32)
+_bp = ctypes.POINTER(ctypes.c_uint8)
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.or_sh_basis.argtypes = [_dp, _dp]
+            L.or_sh_basis_grad.argtypes = [_dp, _dp]
+            L.or_project.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _dp, _dp, _dp, _dp, _dp, _ip, _ip, _dp]
+            L.or_sort.argtypes = [_i64, _fp, _ip, _fp, _i32, _i32, _i32, _i32, _i64, _up, _up]
+            L.or_sort.restype = _i64
+            L.or_render.argtypes = [_i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp, _ip, _dp]
+            L.or_pixel_trace.argtypes = [_i32, _i32, _i32, _i32, _dp, _dp, _dp, _up, _up, _i32, _ip, _dp, _dp]
+            L.or_pixel_trace.restype = _i32
+            L.or_render_brute.argtypes = [_i64, _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _ip, _ip, _fp, _dp]
+            L.or_loss.argtypes = [_i32, _i32, _dp, _dp, ctypes.c_double, _dp]
+            L.or_loss.restype = ctypes.c_double
+            L.or_render_bwd.argtypes = [_i64, _i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _bp,
+                                        _bp, _dp, _dp, _dp, _dp, _bp]
+            L.or_project_bwd.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _bp, _dp, _dp, _dp, _dp, _dp,
+                                         _dp, _dp]
+            L.or_adam.argtypes = [_i64, _dp, _dp, _dp, _dp, _bp, _dp, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, _i64]
+            L.or_freeze_update.argtypes = [_i64, _fp, _fp, _ip, _bp, ctypes.c_float, ctypes.c_float, _i32, _ip]
+            L.or_freeze_update.restype = _i64
+            L.or_psnr.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp]
+            _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def sh_basis(d) -> np.ndarray:
+    d = _c(d, np.float64)
+    out = np.zeros(16)
+    lib().or_sh_basis(_p(d, _dp), _p(out, _dp))
+    return out
+
+
+def sh_basis_grad(d) -> np.ndarray:
+    d = _c(d, np.float64)
+    out = np.zeros((16, 3))
+    lib().or_sh_basis_grad(_p(d, _dp), _p(out, _dp))
+    return out
+
+
+def project(params, cam: Cam, sh_degree: int = 3, smooth: bool = False) -> dict:
+    """Per-Gaussian projection (Eq. 1) and SH colour."""
+    P = _c(params, np.float64)
+    n = P.shape[0]
+    out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), depth=np.zeros(n), opacity=np.zeros(n),
+               rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
+               margin=np.zeros(n))
+    lib().or_project(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), _p(out["mean2d"], _dp),
+                     _p(out["conic"], _dp), _p(out["depth"], _dp), _p(out["opacity"], _dp), _p(out["rgb"], _dp),
+                     _p(out["radius"], _ip), _p(out["rect"], _ip), _p(out["margin"], _dp))
+    r = out["rect"]
+    out["tiles_touched"] = ((r[:, 2] - r[:, 0]) * (r[:, 3] - r[:, 1])).astype(np.int32)
+    return out
+
+
+def sort(mean2d_f32, radius, depth_f32, W: int, H: int, tile: int = 16, smooth: bool = False,
+         capacity: int | None = None):
+    """Tile/depth order. Returns (vals uint32[P], ranges uint32[tiles, 2])."""
+    m = _c(mean2d_f32, np.float32)
+    r = _c(radius, np.int32)
+    d = _c(depth_f32, np.float32)
+    n = r.shape[0]
+    tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    if capacity is None:
+        capacity = lib().or_sort(n, _p(m, _fp), _p(r, _ip), _p(d, _fp), W, H, tile, int(smooth), 0, None, None)
+        capacity = abs(capacity)
+    vals = np.zeros(max(capacity, 1), np.uint32)
+    ranges = np.zeros((tiles, 2), np.uint32)
+    P = lib().or_sort(n, _p(m, _fp), _p(r, _ip), _p(d, _fp), W, H, tile, int(smooth), capacity, _p(vals, _up),
+                      _p(ranges, _up))
+    if P < 0:
+        raise OverflowError(f"sort needs {-P} entries, capacity {capacity}")
+    return vals[:P], ranges
+
+
+def render(proj: dict, vals, ranges, cam: Cam, smooth: bool = False) -> dict:
+    """Tiled compositing (Eq. 2)."""
+    W, H = cam.width, cam.height
+    bg = np.array(list(cam.bg), np.float64)
+    image = np.zeros((3, H, W))
+    tfin = np.zeros((H, W))
+    nlast = np.zeros((H, W), np.int32)
+    margin = np.zeros((H, W))
+    lib().or_render(W, H, cam.tile, _p(bg, _dp), int(smooth), _p(_c(proj["mean2d"], np.float64), _dp),
+                    _p(_c(proj["conic"], np.float64), _dp), _p(_c(proj["opacity"], np.float64), _dp),
+                    _p(_c(proj["rgb"], np.float64), _dp), _p(_c(vals, np.uint32), _up),
+                    _p(_c(ranges, np.uint32), _up), _p(image, _dp), _p(tfin, _dp), _p(nlast, _ip), _p(margin, _dp))
+    return dict(image=image, t_final=tfin, n_last=nlast, margin=margin)
+
+
+def pixel_trace(proj: dict, vals, ranges, cam: Cam, px: int, py: int, cap: int = 100000):
+    """(list positions, alphas, transmittance in front) of one pixel's contributors."""
+    pos = np.zeros(cap, np.int32)
+    al = np.zeros(cap)
+    tr = np.zeros(cap)
+    k = lib().or_pixel_trace(px, py, cam.width, cam.tile, _p(_c(proj["mean2d"], np.float64), _dp),
+                             _p(_c(proj["conic"], np.float64), _dp), _p(_c(proj["opacity"], np.float64), _dp),
+                             _p(_c(vals, np.uint32), _up), _p(_c(ranges, np.uint32), _up), cap, _p(pos, _ip),
+                             _p(al, _dp), _p(tr, _dp))
+    return pos[:k], al[:k], tr[:k]
+
+
+def render_brute(proj: dict, cam: Cam) -> np.ndarray:
+    W, H = cam.width, cam.height
+    bg = np.array(list(cam.bg), np.float64)
+    n = proj["radius"].shape[0]
+    image = np.zeros((3, H, W))
+    lib().or_render_brute(n, W, H, cam.tile, _p(bg, _dp), _p(_c(proj["mean2d"], np.float64), _dp),
+                          _p(_c(proj["conic"], np.float64), _dp), _p(_c(proj["opacity"], np.float64), _dp),
+                          _p(_c(proj["rgb"], np.float64), _dp), _p(_c(proj["radius"], np.int32), _ip),
+                          _p(_c(proj["rect"], np.int32), _ip), _p(_c(proj["depth"], np.float32), _fp),
+                          _p(image, _dp))
+    return image
+
+
+def loss(image, gt, lam: float = 0.2, grad: bool = True):
+    """Eq. 3. Returns (loss, dL/dimage or None)."""
+    x = _c(image, np.float64)
+    y = _c(gt, np.float64)
+    H, W = x.shape[1], x.shape[2]
+    g = np.zeros_like(x) if grad else None
+    val = lib().or_loss(H, W, _p(x, _dp), _p(y, _dp), lam, _p(g, _dp))
+    return val, g
+
+
+def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=None, smooth: bool = False) -> dict:
+    W, H = cam.width, cam.height
+    n = proj["opacity"].shape[0]
+    bg = np.array(list(cam.bg), np.float64)
+    out = dict(d_mean2d=np.zeros((n, 2)), d_conic=np.zeros((n, 3)), d_opacity=np.zeros(n), d_rgb=np.zeros((n, 3)),
+               tainted=np.zeros(n, np.uint8))
+    fr = None if frozen is None else _c(frozen, np.uint8)
+    am = None if amb is None else _c(amb, np.uint8)
+    lib().or_render_bwd(n, W, H, cam.tile, _p(bg, _dp), int(smooth), _p(_c(proj["mean2d"], np.float64), _dp),
+                        _p(_c(proj["conic"], np.float64), _dp), _p(_c(proj["opacity"], np.float64), _dp),
+                        _p(_c(proj["rgb"], np.float64), _dp), _p(_c(vals, np.uint32), _up),
+                        _p(_c(ranges, np.uint32), _up), _p(_c(dl_dimage, np.float64), _dp), _p(fr, _bp),
+                        _p(am, _bp), _p(out["d_mean2d"], _dp), _p(out["d_conic"], _dp), _p(out["d_opacity"], _dp),
+                        _p(out["d_rgb"], _dp), _p(out["tainted"], _bp))
+    return out
+
+
+def project_bwd(params, cam: Cam, grads2d: dict, frozen=None, sh_degree: int = 3, smooth: bool = False) -> dict:
+    P = _c(params, np.float64)
+    n = P.shape[0]
+    G = np.zeros((n, N_PARAMS))
+    xn = np.zeros(n)
+    rn = np.zeros(n)
+    fr = None if frozen is None else _c(frozen, np.uint8)
+    lib().or_project_bwd(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), _p(fr, _bp),
+                         _p(_c(grads2d["d_mean2d"], np.float64), _dp), _p(_c(grads2d["d_conic"], np.float64), _dp),
+                         _p(_c(grads2d["d_opacity"], np.float64), _dp), _p(_c(grads2d["d_rgb"], np.float64), _dp),
+                         _p(G, _dp), _p(xn, _dp), _p(rn, _dp))
+    return dict(G=G, xyz_norm=xn, rgb_norm=rn)
+
+
+def adam(P, G, M, V, frozen, lr, step: int, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15):
+    """In-place masked Adam on float64 (n, 59) arrays."""
+    for a in (P, M, V):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lr = _c(lr, np.float64)
+    fr = None if frozen is None else _c(frozen, np.uint8)
+    lib().or_adam(P.shape[0], _p(P, _dp), _p(_c(G, np.float64), _dp), _p(M, _dp), _p(V, _dp), _p(fr, _bp),
+                  _p(lr, _dp), b1, b2, eps, step)
+
+
+def freeze_update(acc_xyz, acc_rgb, cnt, frozen, eps_xyz: float, eps_rgb: float, mode: int):
+    """In-place on float32 acc arrays, int32 cnt and uint8 frozen. Returns act (int32, ascending)."""
+    for a, dt in ((acc_xyz, np.float32), (acc_rgb, np.float32), (cnt, np.int32), (frozen, np.uint8)):
+        assert a.dtype == dt and a.flags.c_contiguous
+    n = frozen.shape[0]
+    act = np.zeros(max(n, 1), np.int32)
+    k = lib().or_freeze_update(n, _p(acc_xyz, _fp), _p(acc_rgb, _fp), _p(cnt, _ip), _p(frozen, _bp),
+                               np.float32(eps_xyz), np.float32(eps_rgb), mode, _p(act, _ip))
+    return act[:k]
+
+
+def psnr(images, gts) -> np.ndarray:
+    x = _c(images, np.float64)
+    y = _c(gts, np.float64)
+    S, H, W = x.shape[0], x.shape[2], x.shape[3]
+    out = np.zeros(S)
+    lib().or_psnr(S, H, W, _p(x, _dp), _p(y, _dp), _p(out, _dp))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Whole-step compositions (each stage above, in the paper's order).
+# ---------------------------------------------------------------------------
+
+def forward(params, cam: Cam, sh_degree: int = 3, smooth: bool = False) -> dict:
+    """Projection, per-tile depth order and compositing for one view."""
+    proj = project(params, cam, sh_degree, smooth)
+    vals, ranges = sort(proj["mean2d"].astype(np.float32), proj["radius"], proj["depth"].astype(np.float32),
+                        cam.width, cam.height, cam.tile, smooth)
+    ren = render(proj, vals, ranges, cam, smooth)
+    return dict(proj=proj, vals=vals, ranges=ranges, **ren)
+
+
+def loss_and_grad(params, cam: Cam, gt, frozen=None, sh_degree: int = 3, smooth: bool = False,
+                  lam: float = 0.2) -> dict:
+    """Forward, Eq. 3 loss and the analytic gradient of the loss w.r.t. all 59 parameters."""
+    f = forward(params, cam, sh_degree, smooth)
+    L, dimg = loss(f["image"], gt, lam)
+    g2 = render_bwd(f["proj"], f["vals"], f["ranges"], cam, dimg, frozen, smooth=smooth)
+    pb = project_bwd(params, cam, g2, frozen, sh_degree, smooth)
+    return dict(loss=L, dl_dimage=dimg, grads2d=g2, **pb, fwd=f)
+
+
+def loss_only(params, cam: Cam, gt, sh_degree: int = 3, smooth: bool = False, lam: float = 0.2) -> float:
+    f = forward(params, cam, sh_degree, smooth)
+    return loss(f["image"], gt, lam, grad=False)[0]

@@ -1,0 +1,90 @@
+"""Host-side schedule of GSta, written out plainly (oracle side).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* Eq. 5 dynamic freeze thresholds, read as eps_k = eps_0 * clamp(0.5 + 1.5 k / K, 0.5, 1.5):
+  the literal recursion grows without bound, while Sec. 3.2.1 and Sec. 4.1
+  say the thresholds rise with k and stay within [0.5, 1.5] x their initial
+  values.
+* Sec. 4.1 freeze cadence: the map is updated every 250 iterations inside
+  [3000, min(10000, early-stop iteration)), reset every 2000 iterations, and
+  not updated for 500 iterations after a reset.
+* Eq. 7 early stop: PSNR on the training subset every 1000 iterations; stop
+  when the last two PSNR changes are both below 0.2 dB.
+* Sec. 3.2.3 plateau schedule on the xyz learning rate: decay 0.75,
+  patience 1, threshold read as 1 dB on the PSNR (absolute, mode max).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+
+@dataclasses.dataclass
+class ScheduleConfig:
+    total_iter: int = 30000
+    warmup: int = 3000
+    window_end: int = 10000
+    every: int = 250
+    reset_every: int = 2000
+    wait: int = 500
+    psnr_every: int = 1000
+    eps_psnr: float = 0.2
+    finetune_iters: int = 1000
+    eps0_xyz: float = 3e-5
+    eps0_rgb: float = 1e-4
+    lr_decay: float = 0.75
+    lr_patience: int = 1
+    lr_eps: float = 1.0
+
+
+def threshold(eps0: float, k: int, K: int) -> float:
+    """Eq. 5 under the clamped-linear reading."""
+    f = 0.5 + 1.5 * k / K
+    return eps0 * min(1.5, max(0.5, f))
+
+
+def freeze_action(k: int, cfg: ScheduleConfig, last_reset: int | None, stop_iter: int | None) -> str | None:
+    """What the freeze map does before iteration k: 'update', 'reset', 'clear' (statistics
+    only) or None. ``last_reset`` is the iteration of the previous reset, ``stop_iter`` the
+    early-stop iteration if it has happened."""
+    if k % cfg.every != 0:
+        return None
+    end = cfg.window_end if stop_iter is None else min(cfg.window_end, stop_iter)
+    if k >= end:
+        return None
+    if k < cfg.warmup:
+        return "clear"
+    if k % cfg.reset_every == 0:
+        return "reset"
+    if last_reset is not None and k < last_reset + cfg.wait:
+        return "clear"
+    return "update"
+
+
+def early_stop(psnrs: list[float], eps: float) -> bool:
+    """Eq. 7: both of the two most recent PSNR changes are below eps (signed changes)."""
+    if len(psnrs) < 3:
+        return False
+    return (psnrs[-1] - psnrs[-2]) < eps and (psnrs[-2] - psnrs[-3]) < eps
+
+
+class Plateau:
+    """Decay the learning rate when the PSNR has not improved by more than
+    ``eps`` for more than ``patience`` evaluations."""
+
+    def __init__(self, lr: float, decay: float, patience: int, eps: float):
+        self.lr, self.decay, self.patience, self.eps = lr, decay, patience, eps
+        self.best = -math.inf
+        self.bad = 0
+
+    def step(self, psnr: float) -> float:
+        if psnr > self.best + self.eps:
+            self.best = psnr
+            self.bad = 0
+        else:
+            self.bad += 1
+            if self.bad > self.patience:
+                self.lr *= self.decay
+                self.bad = 0
+        return self.lr

@@ -1,0 +1,901 @@
+/*
+ * gsta_oracle.c -- a plain, slow FP64 CPU statement of one GSta training step
+ * (3-D Gaussian splatting with gradient-norm freezing).
+ *
+ * TEST INFRASTRUCTURE. This library is the parity reference for the CUDA
+ * path. Only the test-suite, the package smoke check and the benchmark's
+ * CPU-baseline leg load it; the product never does. It shares no code,
+ * header, table or constant generator with the CUDA sources.
+ *
+ * Paper: "GSta: Efficient Training Scheme with Siestaed Gaussians for
+ * Monocular 3D Scene Reconstruction" (arXiv 2504.06716).
+ *
+ *   Sec. 3.1, Eq. 1   projected 2-D Gaussian (EWA splatting)   or_project
+ *   Sec. 3.1          SH view-dependent colour                 or_sh_basis
+ *   Sec. 3.1          blending "in a sorted order"             or_sort
+ *   Sec. 3.1, Eq. 2   front-to-back alpha compositing          or_render, or_render_brute
+ *   Sec. 3.1, Eq. 3   L = (1 - 0.2) L1 + 0.2 D-SSIM            or_loss
+ *   Sec. 3.2.4        backward skips frozen Gaussians          or_render_bwd, or_project_bwd
+ *   Sec. 3.2.1, Eq. 4-6  per-Gaussian freeze decision          or_freeze_update
+ *   Sec. 3.2.4        optimiser updates unfrozen Gaussians     or_adam
+ *   Sec. 3.2.2, Eq. 7 PSNR on a training subset                or_psnr
+ *
+ * The paper cites EWA splatting and 3DGS for the renderer and does not write
+ * its internals out. The readings taken here (camera model, dilation,
+ * 3-sigma radius, tile rule, alpha and transmittance cut-offs, SH offset and
+ * clamp, SSIM window) are stated at each function and are shared with the
+ * CUDA path only through their written statement.
+ *
+ * Every computation is a direct loop in double precision. Where a floating
+ * point value decides an integer that the CUDA path must reproduce bit for
+ * bit (the tile rectangle of a Gaussian, the sort key, the freeze test) the
+ * decision is taken in single precision, the precision of the kernels.
+ *
+ * Layouts (all row-major, caller-allocated):
+ *   params  [n][59]  0-2 mean, 3-5 log-scale, 6-9 quaternion (w,x,y,z),
+ *                    10 opacity logit, 11+3c+ch SH coefficient c, channel ch
+ *   mean2d  [n][2], conic [n][3] (a, b, c of [[a,b],[b,c]]), rgb [n][3]
+ *   rect    [n][4]   x0, y0, x1, y1 tile rectangle, half-open
+ *   image   [3][H][W]
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NP 59
+
+typedef struct {
+    int32_t width, height, tile, pad0;
+    double fx, fy, cx, cy;
+    double R[9];      /* world -> camera rotation, row-major */
+    double t[3];      /* world -> camera translation */
+    double campos[3]; /* camera centre, world space */
+    double znear;     /* Gaussians with camera-space z <= znear are culled */
+    double dilation;  /* added to both diagonal entries of the 2-D covariance */
+    double bg[3];     /* background colour */
+} or_camera;
+
+static const double PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------ */
+/* Real spherical harmonics, degree <= 3 (Sec. 3.1: "a set of spherical
+ * harmonics (SH) coefficients (up to 3 bands)").
+ *
+ * Textbook definition, built here from Legendre polynomials:
+ *   Y_l^0   = K_l^0 P_l(z)
+ *   Y_l^{m} = sqrt2 K_l^m cos(m phi) P_l^m(z)        m > 0
+ *   Y_l^{-m}= sqrt2 K_l^m sin(m phi) P_l^m(z)        m > 0
+ *   K_l^m   = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)
+ *   P_l^m(z)= (-1)^m (1-z^2)^{m/2} d^m/dz^m P_l(z)   (Condon-Shortley phase)
+ * With sin^m(theta) e^{i m phi} = (x + i y)^m this is a polynomial in the
+ * unit direction (x, y, z). Coefficient index c = l^2 + l + m.
+ * ------------------------------------------------------------------ */
+
+/* Coefficients of P_l (l <= 3) by Bonnet's recurrence. */
+static void legendre_coeffs(double P[4][4]) {
+    memset(P, 0, sizeof(double) * 16);
+    P[0][0] = 1.0;
+    P[1][1] = 1.0;
+    for (int n = 1; n < 3; ++n) {
+        for (int k = 0; k < 4; ++k) {
+            double v = -n * P[n - 1][k];
+            if (k > 0) v += (2 * n + 1) * P[n][k - 1];
+            P[n + 1][k] = v / (n + 1);
+        }
+    }
+}
+
+static double poly_eval(const double *c, int deg, double z) {
+    double r = 0.0;
+    for (int k = deg; k >= 0; --k) r = r * z + c[k];
+    return r;
+}
+
+static void poly_deriv(const double *c, double *d) {
+    for (int k = 0; k < 3; ++k) d[k] = (k + 1) * c[k + 1];
+    d[3] = 0.0;
+}
+
+static double factorial(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return f;
+}
+
+/* Y[16] and, if dY != NULL, dY[16][3]: the gradient of the polynomial
+ * extension above with respect to (x, y, z). */
+static void sh_eval(const double dir[3], double *Y, double *dY) {
+    double P[4][4];
+    legendre_coeffs(P);
+    double x = dir[0], y = dir[1], z = dir[2];
+    for (int l = 0; l <= 3; ++l) {
+        double Q[4], dQ[4];
+        memcpy(Q, P[l], sizeof(Q));
+        for (int m = 0; m <= l; ++m) {
+            /* Q = d^m P_l / dz^m, dQ = its derivative */
+            poly_deriv(Q, dQ);
+            double K = sqrt((2 * l + 1) / (4.0 * PI) * factorial(l - m) / factorial(l + m));
+            double q = poly_eval(Q, 3, z), dq = poly_eval(dQ, 3, z);
+            if (m == 0) {
+                int c = l * l + l;
+                Y[c] = K * q;
+                if (dY) { dY[3 * c] = 0; dY[3 * c + 1] = 0; dY[3 * c + 2] = K * dq; }
+            } else {
+                /* (x+iy)^m and m (x+iy)^(m-1) */
+                double re = 1, im = 0, pre = 1, pim = 0;
+                for (int k = 0; k < m; ++k) {
+                    if (k == m - 1) { pre = m * re; pim = m * im; }
+                    double nre = re * x - im * y, nim = re * y + im * x;
+                    re = nre; im = nim;
+                }
+                double A = sqrt(2.0) * K * ((m & 1) ? -1.0 : 1.0);
+                int cp = l * l + l + m, cn = l * l + l - m;
+                Y[cp] = A * re * q;
+                Y[cn] = A * im * q;
+                if (dY) {
+                    /* d/dx Re = Re(m w^(m-1)), d/dy Re = -Im(m w^(m-1));
+                       d/dx Im = Im(m w^(m-1)), d/dy Im =  Re(m w^(m-1)) */
+                    dY[3 * cp] = A * pre * q;
+                    dY[3 * cp + 1] = -A * pim * q;
+                    dY[3 * cp + 2] = A * re * dq;
+                    dY[3 * cn] = A * pim * q;
+                    dY[3 * cn + 1] = A * pre * q;
+                    dY[3 * cn + 2] = A * im * dq;
+                }
+            }
+            memcpy(Q, dQ, sizeof(Q));
+        }
+    }
+}
+
+void or_sh_basis(const double *dir, double *Y) { sh_eval(dir, Y, NULL); }
+void or_sh_basis_grad(const double *dir, double *dY) {
+    double Y[16];
+    sh_eval(dir, Y, dY);
+}
+
+/* ------------------------------------------------------------------ */
+/* Small dense helpers.                                                */
+/* ------------------------------------------------------------------ */
+static void matmul(const double *A, const double *B, double *C, int n, int k, int m) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < m; ++j) {
+            double s = 0;
+            for (int r = 0; r < k; ++r) s += A[i * k + r] * B[r * m + j];
+            C[i * m + j] = s;
+        }
+}
+static void transpose(const double *A, double *T, int n, int m) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < m; ++j) T[j * n + i] = A[i * m + j];
+}
+
+/* Rotation matrix of a unit quaternion (w, x, y, z). */
+static void quat_to_rot(const double *q, double *R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* dR/dw, dR/dx, dR/dy, dR/dz of the matrix above. */
+static void quat_to_rot_grad(const double *q, double dR[4][9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double a[4][9] = {
+        {0, -2 * z, 2 * y, 2 * z, 0, -2 * x, -2 * y, 2 * x, 0},
+        {0, 2 * y, 2 * z, 2 * y, -4 * x, -2 * w, 2 * z, 2 * w, -4 * x},
+        {-4 * y, 2 * x, 2 * w, 2 * x, 0, 2 * z, -2 * w, 2 * z, -4 * y},
+        {-4 * z, -2 * w, 2 * x, 2 * w, -4 * z, 2 * y, 2 * x, 2 * y, 0},
+    };
+    memcpy(dR, a, sizeof(a));
+}
+
+/* ------------------------------------------------------------------ */
+/* Projection (Sec. 3.1, Eq. 1).                                        */
+/* ------------------------------------------------------------------ */
+
+/* Tile rectangle of a splat, decided in single precision:
+ *   x0 = floor((mx - r) / T), x1 = floor((mx + r) / T), same for y,
+ * clipped to the grid; half-open output. Returns the tile count. */
+static int32_t tile_rect(float mx, float my, int32_t r, int32_t tile, int32_t tx, int32_t ty, int32_t *rect) {
+    float inv = 1.0f / (float)tile; /* exact: the tile size is a power of two */
+    float fr = (float)r;
+    float x0 = floorf((mx - fr) * inv), x1 = floorf((mx + fr) * inv);
+    float y0 = floorf((my - fr) * inv), y1 = floorf((my + fr) * inv);
+    if (x0 < 0.0f) x0 = 0.0f;
+    if (y0 < 0.0f) y0 = 0.0f;
+    if (x1 > (float)(tx - 1)) x1 = (float)(tx - 1);
+    if (y1 > (float)(ty - 1)) y1 = (float)(ty - 1);
+    if (x0 > x1 || y0 > y1) { rect[0] = rect[1] = rect[2] = rect[3] = 0; return 0; }
+    rect[0] = (int32_t)x0; rect[1] = (int32_t)y0;
+    rect[2] = (int32_t)x1 + 1; rect[3] = (int32_t)y1 + 1;
+    return (rect[2] - rect[0]) * (rect[3] - rect[1]);
+}
+
+static double frac_dist(double v) { /* distance of v to the nearest integer */
+    return fabs(v - floor(v + 0.5));
+}
+
+typedef struct {
+    int visible;
+    double tc[3], s[3], qn[4], qlen, Rq[9], Sigma[9], J[6], Tm[6], cov[4], det, Q[4];
+    double mean2d[2];
+    int clampx, clampy;
+    double cux, cuy;
+    double dir[3], dist, Y[16], dY[48], rgb_raw[3], rgb[3], opacity;
+    int32_t radius, rect[4];
+    double margin;
+} gauss_fwd;
+
+/* One Gaussian through the projection.
+ * Readings (the paper names EWA splatting and 3DGS without their formulas):
+ *  - camera space t = R mu + t_c, culled when t_z <= znear;
+ *  - Sigma = R(q/|q|) diag(exp(2 s)) R^T;
+ *  - J = [[fx/tz, 0, -fx u/tz], [0, fy/tz, -fy v/tz]] with u = tx/tz and
+ *    v = ty/tz clamped to +-1.3 * (W/2)/fx and +-1.3 * (H/2)/fy;
+ *  - 2-D covariance J R_c Sigma R_c^T J^T + dilation * I, culled when det <= 0;
+ *  - 2-D mean (fx tx/tz + cx, fy ty/tz + cy), pixel (i, j) sits at (i, j);
+ *  - radius = ceil(3 sqrt(largest eigenvalue)), tile rectangle as tile_rect;
+ *  - opacity = sigmoid(logit);
+ *  - colour = max(0, sum_c k_c Y_c(d) + 1/2), d = (mu - campos)/|mu - campos|.
+ * smooth != 0 drops every cut-off except the near plane (for finite
+ * differences): no radius, all tiles, no colour clamp. */
+static void project_one(const double *p, const or_camera *cam, int sh_degree, int smooth, gauss_fwd *g) {
+    memset(g, 0, sizeof(*g));
+    g->margin = INFINITY;
+    const double *mu = p;
+    for (int i = 0; i < 3; ++i)
+        g->tc[i] = cam->R[3 * i] * mu[0] + cam->R[3 * i + 1] * mu[1] + cam->R[3 * i + 2] * mu[2] + cam->t[i];
+    if (!smooth) g->margin = fabs(g->tc[2] - cam->znear);
+    if (g->tc[2] <= cam->znear) return;
+    double tz = g->tc[2];
+
+    for (int i = 0; i < 3; ++i) g->s[i] = exp(p[3 + i]);
+    double qq = 0;
+    for (int i = 0; i < 4; ++i) qq += p[6 + i] * p[6 + i];
+    g->qlen = sqrt(qq);
+    for (int i = 0; i < 4; ++i) g->qn[i] = p[6 + i] / g->qlen;
+    quat_to_rot(g->qn, g->Rq);
+    double M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = g->Rq[3 * i + j] * g->s[j];
+    double Mt[9];
+    transpose(M, Mt, 3, 3);
+    matmul(M, Mt, g->Sigma, 3, 3, 3);
+
+    double limx = 1.3 * 0.5 * cam->width / cam->fx, limy = 1.3 * 0.5 * cam->height / cam->fy;
+    double u = g->tc[0] / tz, v = g->tc[1] / tz;
+    g->cux = u; g->cuy = v;
+    if (u > limx) { g->cux = limx; g->clampx = 1; }
+    if (u < -limx) { g->cux = -limx; g->clampx = 1; }
+    if (v > limy) { g->cuy = limy; g->clampy = 1; }
+    if (v < -limy) { g->cuy = -limy; g->clampy = 1; }
+    double *J = g->J;
+    J[0] = cam->fx / tz; J[1] = 0; J[2] = -cam->fx * g->cux / tz;
+    J[3] = 0; J[4] = cam->fy / tz; J[5] = -cam->fy * g->cuy / tz;
+    matmul(J, cam->R, g->Tm, 2, 3, 3);
+    double TS[6], Tt[6];
+    matmul(g->Tm, g->Sigma, TS, 2, 3, 3);
+    transpose(g->Tm, Tt, 2, 3);
+    matmul(TS, Tt, g->cov, 2, 3, 2);
+    g->cov[0] += cam->dilation;
+    g->cov[3] += cam->dilation;
+    g->det = g->cov[0] * g->cov[3] - g->cov[1] * g->cov[2];
+    if (g->det <= 0) return;
+    g->Q[0] = g->cov[3] / g->det; g->Q[1] = -g->cov[1] / g->det;
+    g->Q[2] = -g->cov[2] / g->det; g->Q[3] = g->cov[0] / g->det;
+    g->mean2d[0] = cam->fx * u + cam->cx;
+    g->mean2d[1] = cam->fy * v + cam->cy;
+
+    int32_t tx = (cam->width + cam->tile - 1) / cam->tile, ty = (cam->height + cam->tile - 1) / cam->tile;
+    if (smooth) {
+        g->radius = 1;
+        g->rect[0] = 0; g->rect[1] = 0; g->rect[2] = tx; g->rect[3] = ty;
+    } else {
+        double half = 0.5 * (g->cov[0] + g->cov[3]);
+        double dif = 0.5 * (g->cov[0] - g->cov[3]);
+        double lam = half + sqrt(dif * dif + g->cov[1] * g->cov[1]);
+        double r3 = 3.0 * sqrt(lam);
+        g->radius = (int32_t)ceil(r3);
+        double m = frac_dist(r3);
+        if (m < g->margin) g->margin = m;
+        if (g->radius <= 0) { g->radius = 0; return; }
+        if (tile_rect((float)g->mean2d[0], (float)g->mean2d[1], g->radius, cam->tile, tx, ty, g->rect) == 0) {
+            g->radius = 0;
+            return;
+        }
+        double e[4] = {(g->mean2d[0] - g->radius) / cam->tile, (g->mean2d[0] + g->radius) / cam->tile,
+                       (g->mean2d[1] - g->radius) / cam->tile, (g->mean2d[1] + g->radius) / cam->tile};
+        for (int i = 0; i < 4; ++i) {
+            double dm = frac_dist(e[i]) * cam->tile;
+            if (dm < g->margin) g->margin = dm;
+        }
+    }
+
+    g->opacity = 1.0 / (1.0 + exp(-p[10]));
+    double dv[3] = {mu[0] - cam->campos[0], mu[1] - cam->campos[1], mu[2] - cam->campos[2]};
+    g->dist = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+    for (int i = 0; i < 3; ++i) g->dir[i] = dv[i] / g->dist;
+    sh_eval(g->dir, g->Y, g->dY);
+    int nc = (sh_degree + 1) * (sh_degree + 1);
+    for (int ch = 0; ch < 3; ++ch) {
+        double c = 0.5;
+        for (int k = 0; k < nc; ++k) c += p[11 + 3 * k + ch] * g->Y[k];
+        g->rgb_raw[ch] = c;
+        g->rgb[ch] = (smooth || c > 0) ? c : 0.0;
+    }
+    g->visible = 1;
+}
+
+/* Per-Gaussian projection. margin[i] is the smallest distance (pixels, or
+ * world units for the near plane) of a value that decides an integer
+ * (radius, tile rectangle, culling) to its threshold. */
+void or_project(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
+                double *mean2d, double *conic, double *depth, double *opacity, double *rgb,
+                int32_t *radius, int32_t *rect, double *margin) {
+    for (int64_t i = 0; i < n; ++i) {
+        gauss_fwd g;
+        project_one(P + NP * i, cam, sh_degree, smooth, &g);
+        if (margin) margin[i] = g.margin;
+        if (!g.visible) {
+            mean2d[2 * i] = mean2d[2 * i + 1] = 0;
+            conic[3 * i] = conic[3 * i + 1] = conic[3 * i + 2] = 0;
+            depth[i] = 0; opacity[i] = 0;
+            rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = 0;
+            radius[i] = 0;
+            rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
+            continue;
+        }
+        mean2d[2 * i] = g.mean2d[0]; mean2d[2 * i + 1] = g.mean2d[1];
+        conic[3 * i] = g.Q[0]; conic[3 * i + 1] = g.Q[1]; conic[3 * i + 2] = g.Q[3];
+        depth[i] = g.tc[2];
+        opacity[i] = g.opacity;
+        for (int c = 0; c < 3; ++c) rgb[3 * i + c] = g.rgb[c];
+        radius[i] = g.radius;
+        for (int c = 0; c < 4; ++c) rect[4 * i + c] = g.rect[c];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Depth order per tile (Sec. 3.1: colours "blended in a sorted order"). */
+/* Every (Gaussian, tile of its rectangle) pair becomes one entry with
+ * key = (tile id << 32) | bits(float32 depth); entries are generated in
+ * Gaussian-index order, tiles row-major inside a rectangle, and sorted
+ * stably by key, so equal keys keep ascending Gaussian index.
+ * ------------------------------------------------------------------ */
+typedef struct {
+    uint64_t key;
+    int64_t order;
+    uint32_t val;
+} sort_entry;
+
+static int cmp_entry(const void *a, const void *b) {
+    const sort_entry *x = (const sort_entry *)a, *y = (const sort_entry *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->order < y->order ? -1 : (x->order > y->order);
+}
+
+/* Returns P, the number of entries. Writes vals[P] and ranges[tiles][2]
+ * (start, end) when P <= capacity; otherwise writes nothing and returns -P.
+ * smooth != 0: every Gaussian with radius > 0 covers every tile. */
+int64_t or_sort(int64_t n, const float *mean2d, const int32_t *radius, const float *depth, int32_t W, int32_t H,
+                int32_t tile, int32_t smooth, int64_t capacity, uint32_t *vals, uint32_t *ranges) {
+    int32_t tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
+    int64_t P = 0;
+    int32_t rect[4];
+    for (int64_t i = 0; i < n; ++i) {
+        if (radius[i] <= 0) continue;
+        if (smooth) P += (int64_t)tx * ty;
+        else P += tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect);
+    }
+    if (P > capacity) return -P;
+    sort_entry *e = (sort_entry *)malloc(sizeof(sort_entry) * (P > 0 ? P : 1));
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (radius[i] <= 0) continue;
+        if (smooth) { rect[0] = 0; rect[1] = 0; rect[2] = tx; rect[3] = ty; }
+        else if (tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect) == 0) continue;
+        uint32_t dbits;
+        memcpy(&dbits, &depth[i], 4);
+        for (int32_t y = rect[1]; y < rect[3]; ++y)
+            for (int32_t x = rect[0]; x < rect[2]; ++x) {
+                e[k].key = ((uint64_t)(uint32_t)(y * tx + x) << 32) | dbits;
+                e[k].order = k;
+                e[k].val = (uint32_t)i;
+                ++k;
+            }
+    }
+    qsort(e, (size_t)P, sizeof(sort_entry), cmp_entry);
+    for (int64_t t = 0; t < (int64_t)tx * ty; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
+    for (int64_t j = 0; j < P; ++j) {
+        vals[j] = e[j].val;
+        uint32_t t = (uint32_t)(e[j].key >> 32);
+        if (j == 0 || (uint32_t)(e[j - 1].key >> 32) != t) ranges[2 * t] = (uint32_t)j;
+        if (j == P - 1 || (uint32_t)(e[j + 1].key >> 32) != t) ranges[2 * t + 1] = (uint32_t)(j + 1);
+    }
+    free(e);
+    return P;
+}
+
+/* ------------------------------------------------------------------ */
+/* Compositing (Sec. 3.1, Eq. 2): C = sum_i c_i a_i prod_{j<i} (1 - a_j).  */
+/* Readings: a_i = min(0.99, o_i exp(-0.5 d^T Q d)), d = mean2d - pixel;
+ * a Gaussian with a positive exponent or a_i < 1/255 is skipped; the ray
+ * stops before the Gaussian that would take the transmittance below 1e-4;
+ * the remaining transmittance shows the background. smooth != 0 removes
+ * every cut-off. n_last = number of list entries up to and including the
+ * last one that contributed.                                              */
+/* ------------------------------------------------------------------ */
+#define ALPHA_MIN (1.0 / 255.0)
+#define ALPHA_MAX 0.99
+#define T_MIN 1e-4
+
+typedef struct {
+    int skip, stop;
+    double alpha, G, power, dx, dy, rel_margin;
+    int capped;
+} blend_eval;
+
+static void eval_entry(const double *mean2d, const double *conic, const double *opacity, uint32_t g, double px,
+                       double py, double T, int smooth, blend_eval *e) {
+    e->dx = mean2d[2 * g] - px;
+    e->dy = mean2d[2 * g + 1] - py;
+    double a = conic[3 * g], b = conic[3 * g + 1], c = conic[3 * g + 2];
+    e->power = -0.5 * (a * e->dx * e->dx + c * e->dy * e->dy) - b * e->dx * e->dy;
+    double scale = 0.5 * (fabs(a) * e->dx * e->dx + fabs(c) * e->dy * e->dy) + fabs(b * e->dx * e->dy) + 1e-300;
+    e->rel_margin = fabs(e->power) / scale;
+    e->skip = e->stop = e->capped = 0;
+    if (!smooth && e->power > 0) { e->skip = 1; return; }
+    e->G = exp(e->power);
+    double oG = opacity[g] * e->G;
+    e->alpha = oG;
+    if (!smooth) {
+        double m = fabs(oG - ALPHA_MAX) / ALPHA_MAX;
+        if (m < e->rel_margin) e->rel_margin = m;
+        if (oG > ALPHA_MAX) { e->alpha = ALPHA_MAX; e->capped = 1; }
+        m = fabs(e->alpha - ALPHA_MIN) / ALPHA_MIN;
+        if (m < e->rel_margin) e->rel_margin = m;
+        if (e->alpha < ALPHA_MIN) { e->skip = 1; return; }
+        double tn = T * (1.0 - e->alpha);
+        m = fabs(tn - T_MIN) / T_MIN;
+        if (m < e->rel_margin) e->rel_margin = m;
+        if (tn < T_MIN) e->stop = 1;
+    }
+}
+
+/* Tiled render over the sorted lists. margin[H][W] (may be NULL): the
+ * smallest relative distance of a per-pixel decision (exponent sign, alpha
+ * cap, alpha floor, transmittance floor) to its threshold. */
+void or_render(int32_t W, int32_t H, int32_t tile, const double *bg, int32_t smooth, const double *mean2d,
+               const double *conic, const double *opacity, const double *rgb, const uint32_t *vals,
+               const uint32_t *ranges, double *image, double *t_final, int32_t *n_last, double *margin) {
+    int32_t tx = (W + tile - 1) / tile;
+    for (int32_t py = 0; py < H; ++py)
+        for (int32_t px = 0; px < W; ++px) {
+            int32_t t = (py / tile) * tx + (px / tile);
+            uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+            double T = 1.0, C[3] = {0, 0, 0}, mg = INFINITY;
+            int32_t last = 0;
+            for (uint32_t k = s; k < e; ++k) {
+                uint32_t g = vals[k];
+                blend_eval ev;
+                eval_entry(mean2d, conic, opacity, g, px, py, T, smooth, &ev);
+                if (ev.rel_margin < mg) mg = ev.rel_margin;
+                if (ev.skip) continue;
+                if (ev.stop) break;
+                for (int c = 0; c < 3; ++c) C[c] += rgb[3 * g + c] * ev.alpha * T;
+                T *= 1.0 - ev.alpha;
+                last = (int32_t)(k - s + 1);
+            }
+            int64_t pix = (int64_t)py * W + px;
+            for (int c = 0; c < 3; ++c) image[(int64_t)c * H * W + pix] = C[c] + T * bg[c];
+            t_final[pix] = T;
+            n_last[pix] = last;
+            if (margin) margin[pix] = mg;
+        }
+}
+
+/* Contributors of one pixel in blending order: list position, alpha and
+ * the transmittance in front of each. Returns their number (at most cap). */
+int32_t or_pixel_trace(int32_t px, int32_t py, int32_t W, int32_t tile, const double *mean2d, const double *conic,
+                       const double *opacity, const uint32_t *vals, const uint32_t *ranges, int32_t cap,
+                       int32_t *pos, double *alpha, double *trans) {
+    int32_t tx = (W + tile - 1) / tile;
+    int32_t t = (py / tile) * tx + (px / tile);
+    double T = 1.0;
+    int32_t k = 0;
+    for (uint32_t j = ranges[2 * t]; j < ranges[2 * t + 1] && k < cap; ++j) {
+        blend_eval ev;
+        eval_entry(mean2d, conic, opacity, vals[j], px, py, T, 0, &ev);
+        if (ev.skip) continue;
+        if (ev.stop) break;
+        pos[k] = (int32_t)(j - ranges[2 * t]);
+        alpha[k] = ev.alpha;
+        trans[k] = T;
+        ++k;
+        T *= 1.0 - ev.alpha;
+    }
+    return k;
+}
+
+/* The same image by brute force: for every pixel, all Gaussians whose
+ * tile rectangle holds the pixel's tile, in ascending (float32 depth,
+ * index) order, composited by Eq. 2 with the same cut-offs. */
+typedef struct { float d; int64_t i; } depth_idx;
+static int cmp_depth(const void *a, const void *b) {
+    const depth_idx *x = (const depth_idx *)a, *y = (const depth_idx *)b;
+    if (x->d != y->d) return x->d < y->d ? -1 : 1;
+    return x->i < y->i ? -1 : (x->i > y->i);
+}
+
+void or_render_brute(int64_t n, int32_t W, int32_t H, int32_t tile, const double *bg, const double *mean2d,
+                     const double *conic, const double *opacity, const double *rgb, const int32_t *radius,
+                     const int32_t *rect, const float *depth, double *image) {
+    depth_idx *ord = (depth_idx *)malloc(sizeof(depth_idx) * (n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (radius[i] > 0) { ord[m].d = depth[i]; ord[m].i = i; ++m; }
+    qsort(ord, (size_t)m, sizeof(depth_idx), cmp_depth);
+    for (int32_t py = 0; py < H; ++py)
+        for (int32_t px = 0; px < W; ++px) {
+            int32_t tcx = px / tile, tcy = py / tile;
+            double T = 1.0, C[3] = {0, 0, 0};
+            for (int64_t k = 0; k < m; ++k) {
+                int64_t g = ord[k].i;
+                const int32_t *r = rect + 4 * g;
+                if (tcx < r[0] || tcx >= r[2] || tcy < r[1] || tcy >= r[3]) continue;
+                double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                double pw = -0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) - conic[3 * g + 1] * dx * dy;
+                if (pw > 0) continue;
+                double a = opacity[g] * exp(pw);
+                if (a > ALPHA_MAX) a = ALPHA_MAX;
+                if (a < ALPHA_MIN) continue;
+                if (T * (1 - a) < T_MIN) break;
+                for (int c = 0; c < 3; ++c) C[c] += rgb[3 * g + c] * a * T;
+                T *= 1 - a;
+            }
+            for (int c = 0; c < 3; ++c) image[(int64_t)c * H * W + (int64_t)py * W + px] = C[c] + T * bg[c];
+        }
+    free(ord);
+}
+
+/* ------------------------------------------------------------------ */
+/* Loss (Sec. 3.1, Eq. 3): L = (1 - l) L1 + l (1 - SSIM), l = 0.2.        */
+/* Readings: L1 and SSIM are means over all 3 H W values; SSIM per channel
+ * with an 11x11 Gaussian window (sigma 1.5, normalised to sum 1), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2 (the usual SSIM constants for a unit
+ * dynamic range). The gradient of |x - y| at x = y is taken as 0.
+ * Direct 2-D windows, no separable shortcut.                              */
+/* ------------------------------------------------------------------ */
+static void ssim_window(double w[11][11]) {
+    double g[11], s = 0;
+    for (int i = 0; i < 11; ++i) { g[i] = exp(-((i - 5) * (i - 5)) / (2 * 1.5 * 1.5)); s += g[i]; }
+    for (int i = 0; i < 11; ++i)
+        for (int j = 0; j < 11; ++j) w[i][j] = g[i] * g[j] / (s * s);
+}
+
+double or_loss(int32_t H, int32_t W, const double *image, const double *gt, double lambda, double *dl_dimage) {
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double w[11][11];
+    ssim_window(w);
+    int64_t HW = (int64_t)H * W, N = 3 * HW;
+    double l1 = 0, ssim = 0;
+    double *A = (double *)malloc(sizeof(double) * HW), *B = (double *)malloc(sizeof(double) * HW),
+           *Cm = (double *)malloc(sizeof(double) * HW);
+    for (int ch = 0; ch < 3; ++ch) {
+        const double *x = image + ch * HW, *y = gt + ch * HW;
+        for (int32_t i = 0; i < H; ++i)
+            for (int32_t j = 0; j < W; ++j) {
+                double mx = 0, my = 0, xx = 0, yy = 0, xy = 0;
+                for (int di = -5; di <= 5; ++di)
+                    for (int dj = -5; dj <= 5; ++dj) {
+                        int32_t a = i + di, b = j + dj;
+                        if (a < 0 || a >= H || b < 0 || b >= W) continue;
+                        double wt = w[di + 5][dj + 5], xv = x[(int64_t)a * W + b], yv = y[(int64_t)a * W + b];
+                        mx += wt * xv; my += wt * yv; xx += wt * xv * xv; yy += wt * yv * yv; xy += wt * xv * yv;
+                    }
+                double sx = xx - mx * mx, sy = yy - my * my, sxy = xy - mx * my;
+                double n1 = 2 * mx * my + C1, n2 = 2 * sxy + C2;
+                double d1 = mx * mx + my * my + C1, d2 = sx + sy + C2;
+                double m = n1 * n2 / (d1 * d2);
+                ssim += m;
+                /* partial derivatives of the map value with respect to the
+                   window mean of x, of x^2 and of x*y */
+                int64_t p = (int64_t)i * W + j;
+                A[p] = m * (2 * my / n1 - 2 * my / n2 - 2 * mx / d1 + 2 * mx / d2);
+                B[p] = -m / d2;
+                Cm[p] = 2 * m / n2;
+            }
+        if (dl_dimage) {
+            for (int32_t i = 0; i < H; ++i)
+                for (int32_t j = 0; j < W; ++j) {
+                    double ga = 0, gb = 0, gc = 0;
+                    for (int di = -5; di <= 5; ++di)
+                        for (int dj = -5; dj <= 5; ++dj) {
+                            int32_t a = i + di, b = j + dj;
+                            if (a < 0 || a >= H || b < 0 || b >= W) continue;
+                            double wt = w[di + 5][dj + 5];
+                            int64_t q = (int64_t)a * W + b;
+                            ga += wt * A[q]; gb += wt * B[q]; gc += wt * Cm[q];
+                        }
+                    int64_t p = (int64_t)i * W + j;
+                    double dssim = (ga + 2 * x[p] * gb + y[p] * gc) / N;
+                    double d = x[p] - y[p];
+                    double sg = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);
+                    dl_dimage[ch * HW + p] = (1 - lambda) * sg / N - lambda * dssim;
+                }
+        }
+        for (int64_t p = 0; p < HW; ++p) l1 += fabs(x[p] - y[p]);
+    }
+    free(A); free(B); free(Cm);
+    return (1 - lambda) * l1 / N + lambda * (1 - ssim / N);
+}
+
+/* ------------------------------------------------------------------ */
+/* Rasteriser backward. Sec. 3.2.4: the gradient is not computed for a   */
+/* frozen Gaussian; frozen Gaussians still occlude and so still enter the */
+/* transmittance of the others.                                           */
+/* For every pixel the forward pass is rerun and its contributors kept;
+ * with suffix sums S_k = sum_{i>k} c_i a_i T_i the derivative of Eq. 2 is
+ *   dC/da_k = c_k T_k - (S_k + T_final bg) / (1 - a_k),   dC/dc_k = a_k T_k.
+ * Outputs are accumulated over pixels for unfrozen Gaussians only:
+ *   d_mean2d[n][2], d_conic[n][3] (a, b, c), d_opacity[n], d_rgb[n][3].
+ * amb[H][W] (optional): pixels whose forward decisions are ambiguous;
+ * tainted[n] (optional) is set for every Gaussian evaluated at one.       */
+/* ------------------------------------------------------------------ */
+void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *bg, int32_t smooth,
+                   const double *mean2d, const double *conic, const double *opacity, const double *rgb,
+                   const uint32_t *vals, const uint32_t *ranges, const double *dl_dimage, const uint8_t *frozen,
+                   const uint8_t *amb, double *d_mean2d, double *d_conic, double *d_opacity, double *d_rgb,
+                   uint8_t *tainted) {
+    int32_t tx = (W + tile - 1) / tile;
+    int64_t HW = (int64_t)H * W;
+    memset(d_mean2d, 0, sizeof(double) * 2 * n);
+    memset(d_conic, 0, sizeof(double) * 3 * n);
+    memset(d_opacity, 0, sizeof(double) * n);
+    memset(d_rgb, 0, sizeof(double) * 3 * n);
+    if (tainted) memset(tainted, 0, (size_t)n);
+    int32_t cap = 0;
+    for (int64_t t = 0; t < (int64_t)tx * ((H + tile - 1) / tile); ++t) {
+        int32_t len = (int32_t)(ranges[2 * t + 1] - ranges[2 * t]);
+        if (len > cap) cap = len;
+    }
+    blend_eval *ev = (blend_eval *)malloc(sizeof(blend_eval) * (cap > 0 ? cap : 1));
+    uint32_t *gid = (uint32_t *)malloc(sizeof(uint32_t) * (cap > 0 ? cap : 1));
+    double *Tk = (double *)malloc(sizeof(double) * (cap > 0 ? cap : 1));
+    double *S = (double *)malloc(sizeof(double) * 3 * (cap > 0 ? cap : 1));
+    for (int32_t py = 0; py < H; ++py)
+        for (int32_t px = 0; px < W; ++px) {
+            int32_t t = (py / tile) * tx + (px / tile);
+            uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+            int64_t pix = (int64_t)py * W + px;
+            int ambiguous = amb ? amb[pix] : 0;
+            double T = 1.0;
+            int nc = 0;
+            for (uint32_t k = s; k < e; ++k) {
+                uint32_t g = vals[k];
+                blend_eval b;
+                eval_entry(mean2d, conic, opacity, g, px, py, T, smooth, &b);
+                if (ambiguous && tainted) tainted[g] = 1;
+                if (b.skip) continue;
+                if (b.stop) break;
+                ev[nc] = b; gid[nc] = g; Tk[nc] = T; ++nc;
+                T *= 1.0 - b.alpha;
+            }
+            double Tf = T;
+            double acc[3] = {0, 0, 0};
+            for (int k = nc - 1; k >= 0; --k) {
+                for (int c = 0; c < 3; ++c) S[3 * k + c] = acc[c];
+                for (int c = 0; c < 3; ++c) acc[c] += rgb[3 * gid[k] + c] * ev[k].alpha * Tk[k];
+            }
+            double dC[3];
+            for (int c = 0; c < 3; ++c) dC[c] = dl_dimage[c * HW + pix];
+            for (int k = 0; k < nc; ++k) {
+                uint32_t g = gid[k];
+                if (frozen && frozen[g]) continue;
+                double a = ev[k].alpha, dA = 0;
+                for (int c = 0; c < 3; ++c) {
+                    double dCda = rgb[3 * g + c] * Tk[k] - (S[3 * k + c] + Tf * bg[c]) / (1.0 - a);
+                    dA += dC[c] * dCda;
+                    d_rgb[3 * g + c] += a * Tk[k] * dC[c];
+                }
+                if (ev[k].capped) continue; /* alpha = 0.99 does not depend on o or G */
+                double o = opacity[g], G = ev[k].G;
+                d_opacity[g] += dA * G;
+                double dpow = dA * o * G;
+                double dx = ev[k].dx, dy = ev[k].dy;
+                double qa = conic[3 * g], qb = conic[3 * g + 1], qc = conic[3 * g + 2];
+                d_conic[3 * g] += -0.5 * dx * dx * dpow;
+                d_conic[3 * g + 1] += -dx * dy * dpow;
+                d_conic[3 * g + 2] += -0.5 * dy * dy * dpow;
+                d_mean2d[2 * g] += -(qa * dx + qb * dy) * dpow;
+                d_mean2d[2 * g + 1] += -(qb * dx + qc * dy) * dpow;
+            }
+        }
+    free(ev); free(gid); free(Tk); free(S);
+}
+
+/* ------------------------------------------------------------------ */
+/* Projection backward: chain rule from the 2-D quantities to the 59     */
+/* parameters, for unfrozen visible Gaussians (Sec. 3.2.4). Also returns  */
+/* the two quantities of the freeze test (Sec. 3.2.1):                    */
+/*   xyz_norm = |dL/d mean2d| in normalised device units, i.e. with the   */
+/*              pixel gradient scaled by (W/2, H/2) (the positional        */
+/*              gradient that 3DGS densification thresholds);              */
+/*   rgb_norm = |dL/d k_0| over the 3 channels (the diffuse colour).       */
+/* G is [n][59]; rows of frozen or culled Gaussians are zero.             */
+/* ------------------------------------------------------------------ */
+void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
+                    const uint8_t *frozen, const double *d_mean2d, const double *d_conic, const double *d_opacity,
+                    const double *d_rgb, double *G, double *xyz_norm, double *rgb_norm) {
+    memset(G, 0, sizeof(double) * NP * n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (xyz_norm) xyz_norm[i] = 0;
+        if (rgb_norm) rgb_norm[i] = 0;
+        if (frozen && frozen[i]) continue;
+        const double *p = P + NP * i;
+        double *gp = G + NP * i;
+        gauss_fwd g;
+        project_one(p, cam, sh_degree, smooth, &g);
+        if (!g.visible) continue;
+        const double *dm = d_mean2d + 2 * i, *dq = d_conic + 3 * i, *dc = d_rgb + 3 * i;
+
+        /* colour: c = max(0, sum_k k_c Y_c(d) + 1/2) */
+        int nc = (sh_degree + 1) * (sh_degree + 1);
+        double gc[3], ddir[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ++ch) gc[ch] = (smooth || g.rgb_raw[ch] > 0) ? dc[ch] : 0.0;
+        for (int k = 0; k < nc; ++k)
+            for (int ch = 0; ch < 3; ++ch) {
+                gp[11 + 3 * k + ch] = g.Y[k] * gc[ch];
+                for (int a = 0; a < 3; ++a) ddir[a] += p[11 + 3 * k + ch] * gc[ch] * g.dY[3 * k + a];
+            }
+        double dmu[3], dd = ddir[0] * g.dir[0] + ddir[1] * g.dir[1] + ddir[2] * g.dir[2];
+        for (int a = 0; a < 3; ++a) dmu[a] = (ddir[a] - g.dir[a] * dd) / g.dist;
+
+        /* opacity = sigmoid(logit) */
+        gp[10] = d_opacity[i] * g.opacity * (1 - g.opacity);
+
+        /* conic = inverse of the 2-D covariance: dL/dcov = -Q dL/dQ Q */
+        double GQ[4] = {dq[0], 0.5 * dq[1], 0.5 * dq[1], dq[2]}, tmp[4], Gcov[4];
+        matmul(g.Q, GQ, tmp, 2, 2, 2);
+        matmul(tmp, g.Q, Gcov, 2, 2, 2);
+        for (int a = 0; a < 4; ++a) Gcov[a] = -Gcov[a];
+
+        /* cov = Tm Sigma Tm^T (+ dilation): dSigma = Tm^T Gcov Tm, dTm = 2 Gcov Tm Sigma */
+        double Tt[6], t1[6], GSig[9], t2[6], GTm[6];
+        transpose(g.Tm, Tt, 2, 3);
+        matmul(Tt, Gcov, t1, 3, 2, 2);
+        matmul(t1, g.Tm, GSig, 3, 2, 3);
+        matmul(Gcov, g.Tm, t2, 2, 2, 3);
+        matmul(t2, g.Sigma, GTm, 2, 3, 3);
+        for (int a = 0; a < 6; ++a) GTm[a] *= 2;
+
+        /* Tm = J R_c */
+        double Rct[9], GJ[6];
+        transpose(cam->R, Rct, 3, 3);
+        matmul(GTm, Rct, GJ, 2, 3, 3);
+        double tx = g.tc[0], ty = g.tc[1], tz = g.tc[2];
+        double dtz = GJ[0] * (-cam->fx / (tz * tz)) + GJ[4] * (-cam->fy / (tz * tz)) +
+                     GJ[2] * (cam->fx * g.cux / (tz * tz)) + GJ[5] * (cam->fy * g.cuy / (tz * tz));
+        double dcu = GJ[2] * (-cam->fx / tz), dcv = GJ[5] * (-cam->fy / tz);
+        double du = (g.clampx ? 0.0 : dcu) + cam->fx * dm[0];
+        double dv = (g.clampy ? 0.0 : dcv) + cam->fy * dm[1];
+        double dtc[3] = {du / tz, dv / tz, dtz - du * tx / (tz * tz) - dv * ty / (tz * tz)};
+        for (int a = 0; a < 3; ++a)
+            dmu[a] += cam->R[a] * dtc[0] + cam->R[3 + a] * dtc[1] + cam->R[6 + a] * dtc[2];
+        for (int a = 0; a < 3; ++a) gp[a] = dmu[a];
+
+        /* Sigma = M M^T, M = R_q diag(s) */
+        double M[9], GM[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M[3 * a + b] = g.Rq[3 * a + b] * g.s[b];
+        matmul(GSig, M, GM, 3, 3, 3);
+        for (int a = 0; a < 9; ++a) GM[a] *= 2;
+        double GR[9];
+        for (int b = 0; b < 3; ++b) {
+            double ds = 0;
+            for (int a = 0; a < 3; ++a) {
+                ds += GM[3 * a + b] * g.Rq[3 * a + b];
+                GR[3 * a + b] = GM[3 * a + b] * g.s[b];
+            }
+            gp[3 + b] = ds * g.s[b];
+        }
+        double dR[4][9], dqn[4], qd = 0;
+        quat_to_rot_grad(g.qn, dR);
+        for (int k = 0; k < 4; ++k) {
+            dqn[k] = 0;
+            for (int a = 0; a < 9; ++a) dqn[k] += GR[a] * dR[k][a];
+            qd += dqn[k] * g.qn[k];
+        }
+        for (int k = 0; k < 4; ++k) gp[6 + k] = (dqn[k] - g.qn[k] * qd) / g.qlen;
+
+        if (xyz_norm) {
+            double ex = dm[0] * 0.5 * cam->width, ey = dm[1] * 0.5 * cam->height;
+            xyz_norm[i] = sqrt(ex * ex + ey * ey);
+        }
+        if (rgb_norm) rgb_norm[i] = sqrt(gp[11] * gp[11] + gp[12] * gp[12] + gp[13] * gp[13]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Adam restricted to unfrozen Gaussians (Sec. 3.2.4: the optimiser only  */
+/* updates Gaussians whose gradients were computed). Textbook Adam with   */
+/* bias correction at the global step `step` (>= 1); lr has one entry per  */
+/* parameter group: xyz, scale, rotation, opacity, SH DC, SH rest.         */
+/* Frozen rows of P, M and V are not touched.                             */
+/* ------------------------------------------------------------------ */
+static int param_group(int r) {
+    if (r < 3) return 0;
+    if (r < 6) return 1;
+    if (r < 10) return 2;
+    if (r < 11) return 3;
+    if (r < 14) return 4;
+    return 5;
+}
+
+void or_adam(int64_t n, double *P, const double *G, double *M, double *V, const uint8_t *frozen, const double *lr,
+             double b1, double b2, double eps, int64_t step) {
+    double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
+    for (int64_t i = 0; i < n; ++i) {
+        if (frozen && frozen[i]) continue;
+        for (int r = 0; r < NP; ++r) {
+            int64_t k = NP * i + r;
+            double g = G[k];
+            M[k] = b1 * M[k] + (1 - b1) * g;
+            V[k] = b2 * V[k] + (1 - b2) * g * g;
+            double mh = M[k] / bc1, vh = V[k] / bc2;
+            P[k] -= lr[param_group(r)] * mh / (sqrt(vh) + eps);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Freeze map update (Sec. 3.2.1, Eqs. 4-6; cadence in Sec. 4.1).          */
+/* The gradient norms of each Gaussian are summed over the iterations      */
+/* since the last update in which it was visible (acc_*, cnt). mode:       */
+/*   0 update: freeze_i |= cnt>0 && acc_xyz/cnt < eps_xyz                  */
+/*                               && acc_rgb/cnt < eps_rgb   (Eqs. 4, 6)    */
+/*             (a frozen Gaussian stays frozen: the map accumulates);      */
+/*   1 reset : every Gaussian unfrozen;                                    */
+/*   2 clear : the map is kept.                                            */
+/* Every mode then zeroes the statistics and lists the unfrozen Gaussians  */
+/* in ascending order in act. The average and the comparison are taken in  */
+/* single precision. Returns the number of unfrozen Gaussians.             */
+/* ------------------------------------------------------------------ */
+int64_t or_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen, float eps_xyz,
+                         float eps_rgb, int32_t mode, int32_t *act) {
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mode == 1) frozen[i] = 0;
+        if (mode == 0 && cnt[i] > 0) {
+            volatile float c = (float)cnt[i];
+            volatile float ax = acc_xyz[i] / c, ar = acc_rgb[i] / c;
+            if (ax < eps_xyz && ar < eps_rgb) frozen[i] = 1;
+        }
+        acc_xyz[i] = 0; acc_rgb[i] = 0; cnt[i] = 0;
+        if (!frozen[i]) act[k++] = (int32_t)i;
+    }
+    return k;
+}
+
+/* ------------------------------------------------------------------ */
+/* PSNR (Sec. 3.2.2, Eq. 7 uses it): 10 log10(1 / MSE) with the rendered   */
+/* image clamped to [0, 1], MSE over all 3 H W values; an MSE below 1e-10   */
+/* reads as 1e-10 (100 dB).                                                */
+/* ------------------------------------------------------------------ */
+void or_psnr(int32_t S, int32_t H, int32_t W, const double *images, const double *gts, double *psnr) {
+    int64_t N = 3 * (int64_t)H * W;
+    for (int32_t s = 0; s < S; ++s) {
+        double se = 0;
+        for (int64_t k = 0; k < N; ++k) {
+            double x = images[s * N + k];
+            x = x < 0 ? 0 : (x > 1 ? 1 : x);
+            double d = x - gts[s * N + k];
+            se += d * d;
+        }
+        double mse = se / N;
+        if (mse < 1e-10) mse = 1e-10;
+        psnr[s] = 10.0 * log10(1.0 / mse);
+    }
+}

@@ -1,0 +1,220 @@
+"""Pins of the FP64 oracle's forward path against facts fixed outside the oracle:
+closed forms, quadrature, brute force and invariants. CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2504_06716_gb300 import synth
+
+
+def _cam_on_axis(W=64, H=48, f=80.0, tile=16, dilation=0.0, bg=(0, 0, 0), orc=None):
+    """Camera at the origin looking down +z (identity rotation)."""
+    cam = synth.Camera(W, H, f, f, W / 2.0, H / 2.0, np.eye(3), np.zeros(3), np.zeros(3))
+    return orc.make_cam(cam, tile=tile, dilation=dilation, bg=bg)
+
+
+def _gauss(mean, log_s, quat=(1, 0, 0, 0), logit=0.0, dc=(0.0, 0.0, 0.0)):
+    p = np.zeros(59)
+    p[0:3] = mean
+    p[3:6] = log_s
+    p[6:10] = quat
+    p[10] = logit
+    p[11:14] = dc
+    return p
+
+
+# ----------------------------------------------------------------------------- SH
+
+
+def test_sh_orthonormal_by_quadrature(orc):
+    """The 16 real SH functions are orthonormal on the sphere (Gauss-Legendre in
+    cos(theta) x uniform in phi; exact for these polynomial degrees)."""
+    zs, wz = np.polynomial.legendre.leggauss(12)
+    nphi = 24
+    G = np.zeros((16, 16))
+    for z, w in zip(zs, wz):
+        s = math.sqrt(1 - z * z)
+        for k in range(nphi):
+            phi = 2 * math.pi * k / nphi
+            Y = orc.sh_basis([s * math.cos(phi), s * math.sin(phi), z])
+            G += w * (2 * math.pi / nphi) * np.outer(Y, Y)
+    assert np.abs(G - np.eye(16)).max() < 1e-12
+
+
+def test_sh_band0_constant_and_band1_directions(orc):
+    d = np.array([0.36, -0.48, 0.8])
+    Y = orc.sh_basis(d)
+    assert Y[0] == pytest.approx(1.0 / (2.0 * math.sqrt(math.pi)), abs=1e-15)
+    # band 1 is sqrt(3/(4 pi)) times (-y, z, -x) with the Condon-Shortley phase
+    c1 = math.sqrt(3.0 / (4.0 * math.pi))
+    assert np.allclose(Y[1:4], c1 * np.array([-d[1], d[2], -d[0]]), atol=1e-15)
+    # addition theorem: sum_m Y_lm(d)^2 = (2l+1)/(4 pi) for every band
+    for l in range(4):
+        assert np.sum(Y[l * l:(l + 1) * (l + 1)] ** 2) == pytest.approx((2 * l + 1) / (4 * math.pi), rel=1e-12)
+
+
+def test_sh_gradient_by_finite_differences(orc):
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        d = rng.normal(size=3)
+        dY = orc.sh_basis_grad(d)
+        h = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd = (orc.sh_basis(d + e) - orc.sh_basis(d - e)) / (2 * h)
+            assert np.allclose(dY[:, a], fd, atol=1e-8)
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.2, 0.5, 0.9)])
+def test_single_isotropic_gaussian_closed_form(orc, bg):
+    """One isotropic Gaussian on the optical axis at depth z with scale s and no
+    dilation images as C(u, v) = c a + (1 - a) bg with
+    a = min(0.99, o exp(-((u-cx)^2 + (v-cy)^2) / (2 (f s / z)^2))) wherever
+    a >= 1/255 and the pixel's tile lies within ceil(3 f s / z) of the centre."""
+    W, H, f, z, s, tile = 64, 48, 80.0, 4.0, 0.21, 16  # 3 sigma = 12.6: off the ceil boundary
+    cam = _cam_on_axis(W, H, f, tile, 0.0, bg, orc)
+    dc = np.array([0.7, -0.3, 0.1])
+    logit = 1.3
+    P = _gauss([0, 0, z], [math.log(s)] * 3, quat=(0.3, 0.5, -0.2, 0.7), logit=logit, dc=dc)[None]
+    f_ = orc.forward(P, cam, sh_degree=0)
+    o = 1 / (1 + math.exp(-logit))
+    c = np.maximum(dc / (2 * math.sqrt(math.pi)) + 0.5, 0)
+    sig = f * s / z
+    r = math.ceil(3 * sig)
+    u, v = np.meshgrid(np.arange(W), np.arange(H))
+    a = np.minimum(0.99, o * np.exp(-((u - W / 2) ** 2 + (v - H / 2) ** 2) / (2 * sig * sig)))
+    tx0, tx1 = math.floor((W / 2 - r) / tile), math.floor((W / 2 + r) / tile)
+    ty0, ty1 = math.floor((H / 2 - r) / tile), math.floor((H / 2 + r) / tile)
+    inside = (u // tile >= tx0) & (u // tile <= tx1) & (v // tile >= ty0) & (v // tile <= ty1)
+    a = np.where(inside & (a >= 1 / 255), a, 0.0)
+    want = c[:, None, None] * a + (1 - a) * np.array(bg)[:, None, None]
+    assert f_["proj"]["radius"][0] == r
+    assert np.abs(f_["image"] - want).max() < 1e-12
+    assert np.abs(f_["t_final"] - (1 - a)).max() < 1e-12
+
+
+def test_two_gaussians_blend_front_to_back(orc):
+    """Eq. 2 for two Gaussians on the axis: C = c1 a1 + c2 a2 (1 - a1) with the
+    nearer one first, whatever their index order."""
+    W, H, f = 32, 32, 60.0
+    cam = _cam_on_axis(W, H, f, 16, 0.0, (0, 0, 0), orc)
+    near = _gauss([0, 0, 3.0], [math.log(0.3)] * 3, logit=0.5, dc=(1.0, 0.0, 0.0))
+    far = _gauss([0, 0, 5.0], [math.log(0.5)] * 3, logit=0.8, dc=(0.0, 1.0, 0.0))
+    for order in ([far, near], [near, far]):
+        f_ = orc.forward(np.stack(order), cam, sh_degree=0)
+        u, v = W // 2, H // 2
+        a1 = min(0.99, 1 / (1 + math.exp(-0.5)))
+        a2 = min(0.99, 1 / (1 + math.exp(-0.8)))
+        c1 = np.array([1.0, 0, 0]) / (2 * math.sqrt(math.pi)) + 0.5
+        c2 = np.array([0, 1.0, 0]) / (2 * math.sqrt(math.pi)) + 0.5
+        want = c1 * a1 + c2 * a2 * (1 - a1)
+        assert np.allclose(f_["image"][:, v, u], want, atol=1e-12)
+
+
+def test_anisotropic_projection_closed_form(orc):
+    """An axis-aligned Gaussian straight ahead of the camera projects to
+    J S^2 J^T (+ dilation): variances (f s_x / z)^2 + d and (f s_y / z)^2 + d,
+    no covariance; the conic is their inverse and the mean sits at (cx, cy)."""
+    cam = _cam_on_axis(64, 64, 100.0, 16, 0.3, (0, 0, 0), orc)
+    z, sx, sy = 5.0, 0.3, 0.1
+    P = _gauss([0, 0, z], [math.log(sx), math.log(sy), math.log(0.2)])[None]
+    pr = orc.project(P, cam, 0)
+    vx, vy = (100 * sx / z) ** 2 + 0.3, (100 * sy / z) ** 2 + 0.3
+    assert np.allclose(pr["conic"][0], [1 / vx, 0, 1 / vy], rtol=1e-12, atol=1e-15)
+    assert np.allclose(pr["mean2d"][0], [32, 32], atol=1e-12)
+    assert pr["depth"][0] == pytest.approx(z)
+    assert pr["radius"][0] == math.ceil(3 * math.sqrt(max(vx, vy)))
+
+
+def test_near_plane_and_offscreen_culling(orc):
+    cam = _cam_on_axis(64, 64, 100.0, 16, 0.3, (0, 0, 0), orc)
+    P = np.stack([
+        _gauss([0, 0, 0.1], [-3] * 3),  # in front of the camera but inside the near plane
+        _gauss([0, 0, -2.0], [-3] * 3),  # behind the camera
+        _gauss([50, 0, 2.0], [-3] * 3),  # far off to the side: no tile touched
+        _gauss([0, 0, 2.0], [-3] * 3),  # visible
+    ])
+    pr = orc.project(P, cam, 0)
+    assert list(pr["radius"] > 0) == [False, False, False, True]
+    assert list(pr["tiles_touched"]) == [0, 0, 0, pr["tiles_touched"][3]]
+
+
+# ----------------------------------------------------------------------------- brute force
+
+
+def _random_view(orc, n=300, W=72, H=56, tile=16, seed=3, bg=(0.1, 0.2, 0.3)):
+    g = np.random.default_rng(seed)
+    P = synth.gaussians_uniform(n, seed)
+    P[:, 3:6] += 1.0  # larger splats so that lists overlap heavily
+    P[:, 10] = g.uniform(-1, 3, n)
+    cam = synth.pinhole(W, H, 60.0, (0.3, -0.4, 3.2))
+    return P, orc.make_cam(cam, tile=tile, bg=bg)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tiled_render_equals_brute_force(orc, tile):
+    P, cam = _random_view(orc, tile=tile)
+    f = orc.forward(P, cam)
+    brute = orc.render_brute(f["proj"], cam)
+    assert (f["proj"]["radius"] > 0).sum() > 100
+    assert np.abs(f["image"] - brute).max() < 1e-12
+
+
+def test_sort_lists_match_rectangles_and_depth_order(orc):
+    P, cam = _random_view(orc, n=400, W=100, H=70, tile=16, seed=9)
+    pr = orc.project(P, cam)
+    m32 = pr["mean2d"].astype(np.float32)
+    d32 = pr["depth"].astype(np.float32)
+    vals, ranges = orc.sort(m32, pr["radius"], d32, cam.width, cam.height, cam.tile)
+    tx = (cam.width + 15) // 16
+    ty = (cam.height + 15) // 16
+    assert len(vals) == int(pr["tiles_touched"].sum())
+    # tile ranges partition the entry list in tile order
+    nonempty = ranges[ranges[:, 1] > ranges[:, 0]]
+    assert nonempty[0, 0] == 0 and nonempty[-1, 1] == len(vals)
+    assert np.all(nonempty[1:, 0] == nonempty[:-1, 1])
+    for t in range(tx * ty):
+        x, y = t % tx, t // tx
+        r = pr["rect"]
+        members = np.nonzero((pr["radius"] > 0) & (r[:, 0] <= x) & (x < r[:, 2]) & (r[:, 1] <= y) & (y < r[:, 3]))[0]
+        got = vals[ranges[t, 0]:ranges[t, 1]]
+        want = sorted(members.tolist(), key=lambda i: (float(d32[i]), i))
+        assert got.tolist() == want
+
+
+def test_transmittance_non_increasing_along_rays(orc):
+    P, cam = _random_view(orc, n=600, seed=11)
+    f = orc.forward(P, cam)
+    checked = 0
+    for py in range(0, cam.height, 5):
+        for px in range(0, cam.width, 5):
+            pos, al, tr = orc.pixel_trace(f["proj"], f["vals"], f["ranges"], cam, px, py)
+            if len(al) == 0:
+                continue
+            checked += 1
+            assert np.all(np.diff(tr) <= 0)
+            assert np.all((al >= 1 / 255) & (al <= 0.99))
+            assert tr[-1] * (1 - al[-1]) >= 1e-4
+            assert f["t_final"][py, px] == pytest.approx(tr[-1] * (1 - al[-1]), rel=1e-12)
+            assert f["n_last"][py, px] == pos[-1] + 1
+    assert checked > 50
+
+
+def test_early_termination_by_transmittance(orc):
+    """A stack of Gaussians with alpha = 0.95 at the centre pixel: T runs
+    1, 0.05, 0.0025, 1.25e-4; the fourth layer would take it to 6.25e-6 < 1e-4,
+    so the ray stops before it and exactly three layers contribute."""
+    cam = _cam_on_axis(32, 32, 60.0, 16, 0.0, (0, 0, 0), orc)
+    logit = math.log(0.95 / 0.05)
+    P = np.stack([_gauss([0, 0, 2.0 + 0.5 * k], [math.log(0.5)] * 3, logit=logit, dc=(k, 0, 0)) for k in range(5)])
+    f = orc.forward(P, cam, sh_degree=0)
+    pos, al, tr = orc.pixel_trace(f["proj"], f["vals"], f["ranges"], cam, 16, 16)
+    assert np.allclose(al, [0.95] * 3, rtol=1e-12) and np.allclose(tr, [1.0, 0.05, 0.0025], rtol=1e-12)
+    assert f["t_final"][16, 16] == pytest.approx(1.25e-4, rel=1e-9)
+    c = (np.arange(3) / (2 * math.sqrt(math.pi)) + 0.5) * 0.95 * np.array([1.0, 0.05, 0.0025])
+    assert f["image"][0, 16, 16] == pytest.approx(c.sum(), rel=1e-12)
