@@ -86,7 +86,9 @@ def lib():
             L.or_loss.argtypes = [_i32, _i32, _dp, _dp, ctypes.c_double, _dp]
             L.or_loss.restype = ctypes.c_double
             L.or_render_bwd.argtypes = [_i64, _i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _bp,
-                                        _bp, _dp, _dp, _dp, _dp, _bp]
+                                        _bp, _bp, _dp, _dp, _dp, _dp, _bp]
+            L.or_render_pixels.argtypes = [_i64, _ip, _ip, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp,
+                                           _ip, _dp]
             L.or_project_bwd.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _bp, _dp, _dp, _dp, _dp, _dp,
                                          _dp, _dp]
             L.or_adam.argtypes = [_i64, _dp, _dp, _dp, _dp, _bp, _dp, ctypes.c_double, ctypes.c_double,
@@ -205,7 +207,23 @@ def loss(image, gt, lam: float = 0.2, grad: bool = True):
     return val, g
 
 
-def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=None, smooth: bool = False) -> dict:
+def render_pixels(proj: dict, vals, ranges, cam: Cam, px, py) -> dict:
+    """Eq. 2 at the listed pixels only."""
+    px = _c(px, np.int32)
+    py = _c(py, np.int32)
+    k = px.shape[0]
+    bg = np.array(list(cam.bg), np.float64)
+    out = dict(image=np.zeros((3, k)), t_final=np.zeros(k), n_last=np.zeros(k, np.int32), margin=np.zeros(k))
+    lib().or_render_pixels(k, _p(px, _ip), _p(py, _ip), cam.width, cam.tile, _p(bg, _dp),
+                           _p(_c(proj["mean2d"], np.float64), _dp), _p(_c(proj["conic"], np.float64), _dp),
+                           _p(_c(proj["opacity"], np.float64), _dp), _p(_c(proj["rgb"], np.float64), _dp),
+                           _p(_c(vals, np.uint32), _up), _p(_c(ranges, np.uint32), _up), _p(out["image"], _dp),
+                           _p(out["t_final"], _dp), _p(out["n_last"], _ip), _p(out["margin"], _dp))
+    return out
+
+
+def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=None, smooth: bool = False,
+               tile_mask=None) -> dict:
     W, H = cam.width, cam.height
     n = proj["opacity"].shape[0]
     bg = np.array(list(cam.bg), np.float64)
@@ -213,11 +231,12 @@ def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=N
                tainted=np.zeros(n, np.uint8))
     fr = None if frozen is None else _c(frozen, np.uint8)
     am = None if amb is None else _c(amb, np.uint8)
+    tm = None if tile_mask is None else _c(tile_mask, np.uint8)
     lib().or_render_bwd(n, W, H, cam.tile, _p(bg, _dp), int(smooth), _p(_c(proj["mean2d"], np.float64), _dp),
                         _p(_c(proj["conic"], np.float64), _dp), _p(_c(proj["opacity"], np.float64), _dp),
                         _p(_c(proj["rgb"], np.float64), _dp), _p(_c(vals, np.uint32), _up),
                         _p(_c(ranges, np.uint32), _up), _p(_c(dl_dimage, np.float64), _dp), _p(fr, _bp),
-                        _p(am, _bp), _p(out["d_mean2d"], _dp), _p(out["d_conic"], _dp), _p(out["d_opacity"], _dp),
+                        _p(am, _bp), _p(tm, _bp), _p(out["d_mean2d"], _dp), _p(out["d_conic"], _dp), _p(out["d_opacity"], _dp),
                         _p(out["d_rgb"], _dp), _p(out["tainted"], _bp))
     return out
 

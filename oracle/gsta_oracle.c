@@ -496,6 +496,35 @@ void or_render(int32_t W, int32_t H, int32_t tile, const double *bg, int32_t smo
         }
 }
 
+/* The tiled render of Eq. 2 at a list of pixels only (same rules as
+ * or_render); out [3][npix], t_final [npix], n_last [npix]. */
+void or_render_pixels(int64_t npix, const int32_t *pxs, const int32_t *pys, int32_t W, int32_t tile, const double *bg,
+                      const double *mean2d, const double *conic, const double *opacity, const double *rgb,
+                      const uint32_t *vals, const uint32_t *ranges, double *out, double *t_final, int32_t *n_last,
+                      double *margin) {
+    int32_t tx = (W + tile - 1) / tile;
+    for (int64_t q = 0; q < npix; ++q) {
+        int32_t px = pxs[q], py = pys[q];
+        int32_t t = (py / tile) * tx + (px / tile);
+        double T = 1.0, C[3] = {0, 0, 0}, mg = INFINITY;
+        int32_t last = 0;
+        for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1]; ++k) {
+            blend_eval ev;
+            eval_entry(mean2d, conic, opacity, vals[k], px, py, T, 0, &ev);
+            if (ev.rel_margin < mg) mg = ev.rel_margin;
+            if (ev.skip) continue;
+            if (ev.stop) break;
+            for (int c = 0; c < 3; ++c) C[c] += rgb[3 * vals[k] + c] * ev.alpha * T;
+            T *= 1.0 - ev.alpha;
+            last = (int32_t)(k - ranges[2 * t] + 1);
+        }
+        for (int c = 0; c < 3; ++c) out[c * npix + q] = C[c] + T * bg[c];
+        t_final[q] = T;
+        n_last[q] = last;
+        if (margin) margin[q] = mg;
+    }
+}
+
 /* Contributors of one pixel in blending order: list position, alpha and
  * the transmittance in front of each. Returns their number (at most cap). */
 int32_t or_pixel_trace(int32_t px, int32_t py, int32_t W, int32_t tile, const double *mean2d, const double *conic,
@@ -642,13 +671,16 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
  * Outputs are accumulated over pixels for unfrozen Gaussians only:
  *   d_mean2d[n][2], d_conic[n][3] (a, b, c), d_opacity[n], d_rgb[n][3].
  * amb[H][W] (optional): pixels whose forward decisions are ambiguous;
- * tainted[n] (optional) is set for every Gaussian evaluated at one.       */
+ * tainted[n] (optional) is set for every Gaussian evaluated at one.
+ * tile_mask[tiles] (optional): only pixels of tiles with a non-zero entry
+ * are processed; the gradient of a Gaussian is complete when every tile of
+ * its rectangle is in the mask.                                           */
 /* ------------------------------------------------------------------ */
 void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *bg, int32_t smooth,
                    const double *mean2d, const double *conic, const double *opacity, const double *rgb,
                    const uint32_t *vals, const uint32_t *ranges, const double *dl_dimage, const uint8_t *frozen,
-                   const uint8_t *amb, double *d_mean2d, double *d_conic, double *d_opacity, double *d_rgb,
-                   uint8_t *tainted) {
+                   const uint8_t *amb, const uint8_t *tile_mask, double *d_mean2d, double *d_conic,
+                   double *d_opacity, double *d_rgb, uint8_t *tainted) {
     int32_t tx = (W + tile - 1) / tile;
     int64_t HW = (int64_t)H * W;
     memset(d_mean2d, 0, sizeof(double) * 2 * n);
@@ -668,6 +700,7 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
     for (int32_t py = 0; py < H; ++py)
         for (int32_t px = 0; px < W; ++px) {
             int32_t t = (py / tile) * tx + (px / tile);
+            if (tile_mask && !tile_mask[t]) continue;
             uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
             int64_t pix = (int64_t)py * W + px;
             int ambiguous = amb ? amb[pix] : 0;

@@ -1,0 +1,305 @@
+// Training loss L = (1 - lambda) L1 + lambda (1 - SSIM) and dL/dimage
+// (Sec. 3.1, Eq. 3), and the PSNR of Eq. 7's early-stop check (Sec. 3.2.2).
+//
+// SSIM uses the 11x11 Gaussian window (sigma 1.5) as two 1-D passes in
+// shared memory (Sec. 3.3, "Accelerated SSIM loss calculation"): one kernel
+// builds the five window moments of a 32x32 tile plus its 5-pixel halo and
+// emits the SSIM map's three partial-derivative maps; a second kernel runs
+// the same separable window over those maps (the window is symmetric, so it
+// is its own adjoint) and combines them with the L1 term into dL/dimage.
+// Block partial sums are reduced in a fixed order, so the loss is
+// deterministic.
+#include "common.cuh"
+
+namespace gs {
+
+__device__ uint32_t g_loss_flags;
+
+namespace {
+
+constexpr int kT = 32;            // output tile edge
+constexpr int kR = 5;             // window radius
+constexpr int kE = kT + 2 * kR;   // tile edge with halo
+constexpr int kLossThreads = 256;
+
+struct Win {
+    float w[11];
+};
+
+__device__ __forceinline__ float ld_or_zero(const float *p, int y, int x, int H, int W) {
+    return (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(p + (int64_t)y * W + x) : 0.f;
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restrict__ img,
+                                                          const float *__restrict__ gt, int H, int W, Win win,
+                                                          float *__restrict__ mapA, float *__restrict__ mapB,
+                                                          float *__restrict__ mapC, float2 *__restrict__ part) {
+    __shared__ float sx[kE][kE + 1], sy[kE][kE + 1];
+    __shared__ float h[5][kE][kT + 1];
+    __shared__ float red[2][kLossThreads / 32];
+    const int ch = blockIdx.z;
+    const int64_t HW = (int64_t)H * W;
+    const float *x = img + ch * HW, *y = gt + ch * HW;
+    const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
+    for (int k = threadIdx.x; k < kE * kE; k += kLossThreads) {
+        int r = k / kE, c = k % kE;
+        sx[r][c] = ld_or_zero(x, oy + r, ox + c, H, W);
+        sy[r][c] = ld_or_zero(y, oy + r, ox + c, H, W);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kE * kT; k += kLossThreads) {
+        int r = k / kT, c = k % kT;
+        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+#pragma unroll
+        for (int q = 0; q < 11; ++q) {
+            float xv = sx[r][c + q], yv = sy[r][c + q], w = win.w[q];
+            a += w * xv;
+            b += w * yv;
+            aa += w * xv * xv;
+            bb += w * yv * yv;
+            ab += w * xv * yv;
+        }
+        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = aa; h[3][r][c] = bb; h[4][r][c] = ab;
+    }
+    __syncthreads();
+    const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
+    float l1 = 0.f, ss = 0.f;
+    for (int k = threadIdx.x; k < kT * kT; k += kLossThreads) {
+        int r = k / kT, c = k % kT;
+        int gy = blockIdx.y * kT + r, gx = blockIdx.x * kT + c;
+        if (gy >= H || gx >= W) continue;
+        float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+#pragma unroll
+        for (int q = 0; q < 11; ++q) {
+            float w = win.w[q];
+            mx += w * h[0][r + q][c];
+            my += w * h[1][r + q][c];
+            xx += w * h[2][r + q][c];
+            yy += w * h[3][r + q][c];
+            xy += w * h[4][r + q][c];
+        }
+        float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
+        float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
+        float d1 = mx * mx + my * my + C1, d2 = vx + vy + C2;
+        float m = (n1 * n2) / (d1 * d2);
+        ss += m;
+        l1 += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
+        // partials of the map value w.r.t. the window means of x, x^2 and x*y
+        int64_t p = ch * HW + (int64_t)gy * W + gx;
+        mapA[p] = m * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
+        mapB[p] = -m / d2;
+        mapC[p] = 2.f * m / n2;
+    }
+    // block sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        l1 += __shfl_xor_sync(kFull, l1, o);
+        ss += __shfl_xor_sync(kFull, ss, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = l1; red[1][threadIdx.x >> 5] = ss; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < kLossThreads / 32; ++w) { a += red[0][w]; b += red[1][w]; }
+        int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        part[blk] = make_float2(a, b);
+    }
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restrict__ img,
+                                                          const float *__restrict__ gt, int H, int W, Win win,
+                                                          float lambda, const float *__restrict__ mapA,
+                                                          const float *__restrict__ mapB,
+                                                          const float *__restrict__ mapC, float *__restrict__ dl) {
+    __shared__ float sm[3][kE][kE + 1];
+    __shared__ float h[3][kE][kT + 1];
+    const int ch = blockIdx.z;
+    const int64_t HW = (int64_t)H * W;
+    const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
+    const float *a = mapA + ch * HW, *b = mapB + ch * HW, *c = mapC + ch * HW;
+    for (int k = threadIdx.x; k < kE * kE; k += kLossThreads) {
+        int r = k / kE, q = k % kE;
+        sm[0][r][q] = ld_or_zero(a, oy + r, ox + q, H, W);
+        sm[1][r][q] = ld_or_zero(b, oy + r, ox + q, H, W);
+        sm[2][r][q] = ld_or_zero(c, oy + r, ox + q, H, W);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kE * kT; k += kLossThreads) {
+        int r = k / kT, q = k % kT;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < 11; ++t) {
+            float w = win.w[t];
+            s0 += w * sm[0][r][q + t];
+            s1 += w * sm[1][r][q + t];
+            s2 += w * sm[2][r][q + t];
+        }
+        h[0][r][q] = s0; h[1][r][q] = s1; h[2][r][q] = s2;
+    }
+    __syncthreads();
+    const float invN = 1.f / (3.f * (float)HW);
+    for (int k = threadIdx.x; k < kT * kT; k += kLossThreads) {
+        int r = k / kT, q = k % kT;
+        int gy = blockIdx.y * kT + r, gx = blockIdx.x * kT + q;
+        if (gy >= H || gx >= W) continue;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < 11; ++t) {
+            float w = win.w[t];
+            s0 += w * h[0][r + t][q];
+            s1 += w * h[1][r + t][q];
+            s2 += w * h[2][r + t][q];
+        }
+        int64_t p = ch * HW + (int64_t)gy * W + gx;
+        float xv = __ldg(img + p), yv = __ldg(gt + p);
+        float d = xv - yv;
+        float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        float dssim = s0 + 2.f * xv * s1 + yv * s2;
+        dl[p] = ((1.f - lambda) * sg - lambda * dssim) * invN;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_loss_final(const float2 *__restrict__ part, int nparts, int64_t N,
+                                                     float lambda, float *__restrict__ loss) {
+    __shared__ double r1[32], r2[32];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += 1024) {
+        float2 v = part[k];
+        a += (double)v.x;
+        b += (double)v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(kFull, a, o);
+        b += __shfl_xor_sync(kFull, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = a; r2[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double l1 = 0.0, ss = 0.0;
+        for (int w = 0; w < 32; ++w) { l1 += r1[w]; ss += r2[w]; }
+        double L = (1.0 - lambda) * l1 / (double)N + lambda * (1.0 - ss / (double)N);
+        float Lf = (float)L;
+        if (!isfinite(Lf)) atomicOr(&g_loss_flags, GS_FLAG_NONFINITE);
+        *loss = Lf;
+    }
+}
+
+// ---- PSNR ----
+constexpr int kPsnrThreads = 256;
+constexpr int kPsnrBlocks = 64;  // partial sums per image
+
+__global__ void __launch_bounds__(kPsnrThreads) k_psnr_partial(const float *__restrict__ img,
+                                                              const float *__restrict__ gt, int64_t N,
+                                                              float *__restrict__ part) {
+    __shared__ float red[kPsnrThreads / 32];
+    const int s = blockIdx.y;
+    const float *x = img + s * N, *y = gt + s * N;
+    float acc = 0.f;
+    for (int64_t k = (int64_t)blockIdx.x * kPsnrThreads + threadIdx.x; k < N; k += (int64_t)kPsnrBlocks * kPsnrThreads) {
+        float v = fminf(fmaxf(__ldg(x + k), 0.f), 1.f) - __ldg(y + k);
+        acc += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f;
+        for (int w = 0; w < kPsnrThreads / 32; ++w) a += red[w];
+        part[(int64_t)s * kPsnrBlocks + blockIdx.x] = a;
+    }
+}
+
+__global__ void k_psnr_final(const float *__restrict__ part, int64_t N, float *__restrict__ psnr) {
+    const int s = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    double se = 0.0;
+    for (int b = 0; b < kPsnrBlocks; ++b) se += (double)part[(int64_t)s * kPsnrBlocks + b];
+    double mse = se / (double)N;
+    if (mse < 1e-10) mse = 1e-10;
+    psnr[s] = (float)(10.0 * log10(1.0 / mse));
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct LossGrid {
+    dim3 grid;
+    int nparts;
+};
+
+inline LossGrid loss_grid(int H, int W) {
+    LossGrid g;
+    g.grid = dim3((unsigned)((W + kT - 1) / kT), (unsigned)((H + kT - 1) / kT), 3);
+    g.nparts = (int)(g.grid.x * g.grid.y * g.grid.z);
+    return g;
+}
+
+Win make_window() {
+    Win w;
+    double g[11], s = 0.0;
+    for (int i = 0; i < 11; ++i) {
+        g[i] = exp(-(double)((i - 5) * (i - 5)) / (2.0 * 1.5 * 1.5));
+        s += g[i];
+    }
+    for (int i = 0; i < 11; ++i) w.w[i] = (float)(g[i] / s);
+    return w;
+}
+
+}  // namespace
+
+uint32_t take_loss_flags() {
+    uint32_t f = 0, z = 0;
+    cudaMemcpyFromSymbol(&f, g_loss_flags, sizeof(f));
+    cudaMemcpyToSymbol(g_loss_flags, &z, sizeof(z));
+    return f;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_loss_workspace_bytes(int32_t H, int32_t W) {
+    if (H <= 0 || W <= 0) return 0;
+    size_t maps = 3 * (size_t)3 * H * W * sizeof(float);
+    return align256(maps) + align256(sizeof(float2) * (size_t)loss_grid(H, W).nparts);
+}
+
+extern "C" int gs_loss(const float *image, const float *gt, int32_t H, int32_t W, float lambda, void *ws,
+                       size_t ws_bytes, float *loss_dev, float *dl_dimage, gs_stream_t stream) {
+    if (H <= 0 || W <= 0 || H > 16384 || W > 16384 || !(lambda >= 0.f && lambda <= 1.f)) return GS_ERR_INVALID_ARG;
+    if (!image || !gt || !ws || !loss_dev || !dl_dimage) return GS_ERR_INVALID_ARG;
+    if (ws_bytes < gs_loss_workspace_bytes(H, W) || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    const int64_t HW = (int64_t)H * W;
+    float *mapA = static_cast<float *>(ws);
+    float *mapB = mapA + 3 * HW, *mapC = mapB + 3 * HW;
+    float2 *part = reinterpret_cast<float2 *>(static_cast<char *>(ws) + align256(9 * (size_t)HW * sizeof(float)));
+    LossGrid g = loss_grid(H, W);
+    Win win = make_window();
+    k_ssim_fwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, mapA, mapB, mapC, part);
+    k_ssim_bwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, lambda, mapA, mapB, mapC, dl_dimage);
+    k_loss_final<<<1, 1024, 0, s>>>(part, g.nparts, 3 * HW, lambda, loss_dev);
+    note_launches(3);
+    return launch_status();
+}
+
+extern "C" size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W) {
+    (void)H; (void)W;
+    if (S <= 0) return 0;
+    return align256(sizeof(float) * (size_t)S * kPsnrBlocks);
+}
+
+extern "C" int gs_psnr(const float *images, const float *gts, int32_t S, int32_t H, int32_t W, void *ws,
+                       size_t ws_bytes, float *psnr_dev, gs_stream_t stream) {
+    if (S < 0 || H <= 0 || W <= 0) return GS_ERR_INVALID_ARG;
+    if (S == 0) return GS_OK;
+    if (!images || !gts || !ws || !psnr_dev || ws_bytes < gs_psnr_workspace_bytes(S, H, W)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    const int64_t N = 3 * (int64_t)H * W;
+    float *part = static_cast<float *>(ws);
+    k_psnr_partial<<<dim3(kPsnrBlocks, (unsigned)S), kPsnrThreads, 0, s>>>(images, gts, N, part);
+    k_psnr_final<<<(unsigned)S, 32, 0, s>>>(part, N, psnr_dev);
+    note_launches(2);
+    return launch_status();
+}

@@ -1,0 +1,176 @@
+// Freeze map and active list (Sec. 3.2.1, Eqs. 4-6) and Adam restricted to
+// the unfrozen Gaussians (Sec. 3.2.4).
+//
+// The freeze update is a stream compaction: each Gaussian's new state is
+// decided in place, per-block counts are scanned, and the unfrozen indices
+// are written in ascending order. Adam then runs over that compacted list
+// only; with the 256-byte parameter rows, every active Gaussian is 15 whole
+// 16-byte vectors of P, G, m and v, so the traffic is proportional to the
+// number of unfrozen Gaussians whatever the freeze pattern.
+#include "common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kFB = 1024;  // Gaussians per freeze block
+
+__device__ __forceinline__ bool decide(int mode, uint8_t fr, float ax, float ar, int32_t c, float ex, float er) {
+    if (mode == 1) return false;
+    if (fr) return true;
+    if (mode == 0 && c > 0) {
+        float cf = (float)c;
+        return __fdiv_rn(ax, cf) < ex && __fdiv_rn(ar, cf) < er;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kFB) k_freeze_mark(int64_t n, float *__restrict__ acc_xyz,
+                                                    float *__restrict__ acc_rgb, int32_t *__restrict__ cnt,
+                                                    uint8_t *__restrict__ frozen, float ex, float er, int mode,
+                                                    int32_t *__restrict__ part) {
+    int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    int active = 0;
+    if (i < n) {
+        bool f = decide(mode, frozen[i], acc_xyz[i], acc_rgb[i], cnt[i], ex, er);
+        frozen[i] = f ? 1 : 0;
+        acc_xyz[i] = 0.f;
+        acc_rgb[i] = 0.f;
+        cnt[i] = 0;
+        active = !f;
+    }
+    int c = __syncthreads_count(active);
+    if (threadIdx.x == 0) part[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(1024) k_freeze_scan(int32_t *__restrict__ part, int nb,
+                                                      int32_t *__restrict__ n_active) {
+    __shared__ int ws[32];
+    int carry = 0;
+    for (int base = 0; base < nb; base += 1024) {
+        int j = base + threadIdx.x;
+        int v = j < nb ? part[j] : 0, tot;
+        int ex = block_exclusive_scan(v, ws, &tot);
+        if (j < nb) part[j] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *n_active = carry;
+}
+
+__global__ void __launch_bounds__(kFB) k_freeze_emit(int64_t n, const uint8_t *__restrict__ frozen,
+                                                    const int32_t *__restrict__ part, int32_t *__restrict__ act) {
+    __shared__ int ws[32];
+    int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    int a = (i < n) && !frozen[i];
+    int tot;
+    int r = block_exclusive_scan(a, ws, &tot);
+    if (a) act[part[blockIdx.x] + r] = (int32_t)i;
+}
+
+struct AdamArgs {
+    float lr[64];  // per float of a row (group rate; 0 for padding)
+    float b1, b2, eps, step_size_scale, inv_sqrt_bc2;
+};
+
+constexpr int kChunks = 15;  // 16-byte vectors per row holding the 59 parameters
+
+__global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float *__restrict__ G,
+                                              float *__restrict__ m, float *__restrict__ v,
+                                              const int32_t *__restrict__ act, const int32_t *__restrict__ n_active,
+                                              AdamArgs a) {
+    const int64_t total = (int64_t)(*n_active) * kChunks;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx / kChunks;
+        const int c = (int)(idx - k * kChunks);
+        const int64_t off = (int64_t)act[k] * kRow + 4 * c;
+        float4 p4 = *reinterpret_cast<float4 *>(P + off);
+        const float4 g4 = __ldg(reinterpret_cast<const float4 *>(G + off));
+        float4 m4 = *reinterpret_cast<float4 *>(m + off);
+        float4 v4 = *reinterpret_cast<float4 *>(v + off);
+        float pp[4] = {p4.x, p4.y, p4.z, p4.w}, gg[4] = {g4.x, g4.y, g4.z, g4.w};
+        float mm[4] = {m4.x, m4.y, m4.z, m4.w}, vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float g = gg[e];
+            mm[e] = a.b1 * mm[e] + (1.f - a.b1) * g;
+            vv[e] = a.b2 * vv[e] + (1.f - a.b2) * g * g;
+            const float lr = a.lr[4 * c + e];
+            pp[e] -= lr * a.step_size_scale * mm[e] / (sqrtf(vv[e]) * a.inv_sqrt_bc2 + a.eps);
+        }
+        *reinterpret_cast<float4 *>(P + off) = make_float4(pp[0], pp[1], pp[2], pp[3]);
+        *reinterpret_cast<float4 *>(m + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
+        *reinterpret_cast<float4 *>(v + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int g_num_sms = 0;
+
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_num_sms = v > 0 ? v : 152;
+    }
+    return g_num_sms;
+}
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_freeze_workspace_bytes(int64_t n) {
+    if (n < 0) return 0;
+    int64_t nb = (n + kFB - 1) / kFB;
+    return align256(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+}
+
+extern "C" int gs_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen,
+                                float eps_xyz, float eps_rgb, int32_t mode, int32_t *act, int32_t *n_active_dev,
+                                void *ws, size_t ws_bytes, gs_stream_t stream) {
+    if (n < 0 || n > INT32_MAX || mode < 0 || mode > 2 || !n_active_dev) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!acc_xyz || !acc_rgb || !cnt || !frozen || !act)) return GS_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < gs_freeze_workspace_bytes(n)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    int nb = (int)((n + kFB - 1) / kFB);
+    int32_t *part = static_cast<int32_t *>(ws);
+    if (nb > 0)
+        k_freeze_mark<<<nb, kFB, 0, s>>>(n, acc_xyz, acc_rgb, cnt, frozen, eps_xyz, eps_rgb, mode, part);
+    k_freeze_scan<<<1, 1024, 0, s>>>(part, nb, n_active_dev);
+    if (nb > 0) k_freeze_emit<<<nb, kFB, 0, s>>>(n, frozen, part, act);
+    note_launches(nb > 0 ? 3 : 1);
+    return launch_status();
+}
+
+extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
+                              const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
+                              int64_t step, gs_stream_t stream) {
+    if (n < 0 || step < 1 || !lr || !n_active_dev) return GS_ERR_INVALID_ARG;
+    if (!(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps >= 0.f)) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    if (!P || !G || !m || !v || !act) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(m) |
+         reinterpret_cast<uintptr_t>(v)) & 15)
+        return GS_ERR_INVALID_ARG;
+    AdamArgs a;
+    static const int group_of[64] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5,
+                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5,
+                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, -1};
+    for (int f = 0; f < 64; ++f) a.lr[f] = group_of[f] >= 0 ? lr[group_of[f]] : 0.f;
+    double bc1 = 1.0 - pow((double)b1, (double)step), bc2 = 1.0 - pow((double)b2, (double)step);
+    a.b1 = b1;
+    a.b2 = b2;
+    a.eps = eps;
+    a.step_size_scale = (float)(1.0 / bc1);
+    a.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
+    const int64_t max_items = n * kChunks;
+    int64_t blocks = (max_items + 255) / 256;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a);
+    note_launches(1);
+    return launch_status();
+}

@@ -1,0 +1,269 @@
+"""Thin ctypes binding of ``libgsta.so`` (declared in ``include/gsta.h``).
+
+Argument marshalling only: every function here takes torch tensors (or raw
+integers), checks dtype/device/contiguity, and passes ``data_ptr()`` values
+and the current CUDA stream to the C entry point of the same name. All
+arithmetic runs in the CUDA kernels behind the C ABI. A missing library or a
+non-zero status raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsta.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gsta.h")
+
+ROW = 64       # floats per parameter row
+SPLAT = 12     # floats per splat record
+GRAD2D = 12    # floats per raster-gradient row
+
+GS_FLAG_CAPACITY, GS_FLAG_NONFINITE, GS_FLAG_TIMEOUT = 1, 2, 4
+
+
+class GsError(RuntimeError):
+    def __init__(self, name: str, status: int, text: str):
+        super().__init__(f"{name} failed: {text} (status {status})")
+        self.status = status
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+        ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("campos", ctypes.c_float * 3),
+        ("znear", ctypes.c_float), ("dilation", ctypes.c_float), ("bg", ctypes.c_float * 3),
+    ]
+
+    @property
+    def tiles(self) -> int:
+        return ((self.width + self.tile - 1) // self.tile) * ((self.height + self.tile - 1) // self.tile)
+
+
+def camera(cam, tile: int = 16, znear: float = 0.2, dilation: float = 0.3, bg=(0.0, 0.0, 0.0)) -> GsCamera:
+    """A ``GsCamera`` from any object with width, height, fx, fy, cx, cy, R, t, campos."""
+    c = GsCamera()
+    c.width, c.height, c.tile = int(cam.width), int(cam.height), int(tile)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.R[:] = [float(v) for v in np.asarray(cam.R, np.float64).reshape(9)]
+    c.t[:] = [float(v) for v in np.asarray(cam.t, np.float64).reshape(3)]
+    c.campos[:] = [float(v) for v in np.asarray(cam.campos, np.float64).reshape(3)]
+    c.znear, c.dilation = float(znear), float(dilation)
+    c.bg[:] = [float(v) for v in bg]
+    return c
+
+
+_P = ctypes.c_void_p
+_I64, _I32, _F32, _SZ, _U32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t, ctypes.c_uint32
+_CAM = ctypes.POINTER(GsCamera)
+
+_SIGS = {
+    "gs_project": ([_P, _I64, _I32, _CAM, _P, _P], _I32),
+    "gs_sort_workspace_bytes": ([_I64, _I64, _I32, _I32, _I32], _SZ),
+    "gs_sort": ([_P, _I64, _CAM, _P, _SZ, _I64, _P, _P, _P, _P], _I32),
+    "gs_render_fwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P], _I32),
+    "gs_loss_workspace_bytes": ([_I32, _I32], _SZ),
+    "gs_loss": ([_P, _P, _I32, _I32, _F32, _P, _SZ, _P, _P, _P], _I32),
+    "gs_raster_bwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_project_bwd": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_render_bwd": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_freeze_workspace_bytes": ([_I64], _SZ),
+    "gs_freeze_update": ([_I64, _P, _P, _P, _P, _F32, _F32, _I32, _P, _P, _P, _SZ, _P], _I32),
+    "gs_adam_masked": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_float), _F32, _F32, _F32, _I64, _P],
+                       _I32),
+    "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
+    "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
+    "gs_get_device_error": ([ctypes.POINTER(ctypes.c_uint32), _P], _I32),
+    "gs_status_string": ([_I32], ctypes.c_char_p),
+    "gs_launch_count": ([], ctypes.c_uint64),
+    "gs_version": ([], _I32),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(name: str, status: int):
+    if status != 0:
+        raise GsError(name, status, load().gs_status_string(status).decode())
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------- entry points (same names as the C ABI)
+
+
+def gs_project(P, n: int, sh_degree: int, cam: GsCamera, splats, stream=None):
+    import torch
+
+    _check("gs_project", load().gs_project(_ptr(P, torch.float32, "P"), n, sh_degree, ctypes.byref(cam),
+                                           _ptr(splats, torch.float32, "splats"), _stream(stream)))
+
+
+def gs_sort_workspace_bytes(n: int, capacity: int, cam: GsCamera) -> int:
+    return int(load().gs_sort_workspace_bytes(n, capacity, cam.width, cam.height, cam.tile))
+
+
+def gs_sort(splats, n: int, cam: GsCamera, ws, capacity: int, vals, ranges, count, stream=None):
+    import torch
+
+    _check("gs_sort", load().gs_sort(_ptr(splats, torch.float32, "splats"), n, ctypes.byref(cam),
+                                     _ptr(ws, torch.uint8, "ws"), ws.numel(), capacity,
+                                     _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+                                     _ptr(count, torch.int64, "count"), _stream(stream)))
+
+
+def gs_render_fwd(splats, vals, ranges, cam: GsCamera, image, t_final, n_last, stream=None):
+    import torch
+
+    _check("gs_render_fwd", load().gs_render_fwd(_ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"),
+                                                 _ptr(ranges, torch.int32, "ranges"), ctypes.byref(cam),
+                                                 _ptr(image, torch.float32, "image"),
+                                                 _ptr(t_final, torch.float32, "t_final"),
+                                                 _ptr(n_last, torch.int32, "n_last"), _stream(stream)))
+
+
+def gs_loss_workspace_bytes(H: int, W: int) -> int:
+    return int(load().gs_loss_workspace_bytes(H, W))
+
+
+def gs_loss(image, gt, H: int, W: int, lam: float, ws, loss, dl_dimage, stream=None):
+    import torch
+
+    _check("gs_loss", load().gs_loss(_ptr(image, torch.float32, "image"), _ptr(gt, torch.float32, "gt"), H, W, lam,
+                                     _ptr(ws, torch.uint8, "ws"), ws.numel(), _ptr(loss, torch.float32, "loss"),
+                                     _ptr(dl_dimage, torch.float32, "dl_dimage"), _stream(stream)))
+
+
+def gs_raster_bwd(splats, vals, ranges, cam: GsCamera, t_final, n_last, dl_dimage, frozen, grad2d, stream=None):
+    import torch
+
+    _check("gs_raster_bwd", load().gs_raster_bwd(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), _ptr(t_final, torch.float32, "t_final"), _ptr(n_last, torch.int32, "n_last"),
+        _ptr(dl_dimage, torch.float32, "dl_dimage"), _ptr(frozen, torch.uint8, "frozen"),
+        _ptr(grad2d, torch.float32, "grad2d"), _stream(stream)))
+
+
+def gs_project_bwd(P, n: int, sh_degree: int, cam: GsCamera, splats, act, n_active, grad2d, G, acc_xyz=None,
+                   acc_rgb=None, cnt=None, stream=None):
+    import torch
+
+    _check("gs_project_bwd", load().gs_project_bwd(
+        _ptr(P, torch.float32, "P"), n, sh_degree, ctypes.byref(cam), _ptr(splats, torch.float32, "splats"),
+        _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(grad2d, torch.float32, "grad2d"),
+        _ptr(G, torch.float32, "G"), _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _stream(stream)))
+
+
+def gs_render_bwd(P, n: int, sh_degree: int, cam: GsCamera, splats, vals, ranges, t_final, n_last, dl_dimage, frozen,
+                  act, n_active, grad2d, G, acc_xyz=None, acc_rgb=None, cnt=None, stream=None):
+    import torch
+
+    _check("gs_render_bwd", load().gs_render_bwd(
+        _ptr(P, torch.float32, "P"), n, sh_degree, ctypes.byref(cam), _ptr(splats, torch.float32, "splats"),
+        _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"), _ptr(t_final, torch.float32, "t_final"),
+        _ptr(n_last, torch.int32, "n_last"), _ptr(dl_dimage, torch.float32, "dl_dimage"),
+        _ptr(frozen, torch.uint8, "frozen"), _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
+        _ptr(grad2d, torch.float32, "grad2d"), _ptr(G, torch.float32, "G"), _ptr(acc_xyz, torch.float32, "acc_xyz"),
+        _ptr(acc_rgb, torch.float32, "acc_rgb"), _ptr(cnt, torch.int32, "cnt"), _stream(stream)))
+
+
+def gs_freeze_workspace_bytes(n: int) -> int:
+    return int(load().gs_freeze_workspace_bytes(n))
+
+
+def gs_freeze_update(n: int, acc_xyz, acc_rgb, cnt, frozen, eps_xyz: float, eps_rgb: float, mode: int, act, n_active,
+                     ws, stream=None):
+    import torch
+
+    _check("gs_freeze_update", load().gs_freeze_update(
+        n, _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _ptr(frozen, torch.uint8, "frozen"), eps_xyz, eps_rgb, mode,
+        _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(ws, torch.uint8, "ws"),
+        ws.numel(), _stream(stream)))
+
+
+def gs_adam_masked(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, eps: float, step: int, stream=None):
+    import torch
+
+    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
+    _check("gs_adam_masked", load().gs_adam_masked(
+        _ptr(P, torch.float32, "P"), _ptr(G, torch.float32, "G"), _ptr(m, torch.float32, "m"),
+        _ptr(v, torch.float32, "v"), n, _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
+        lr6, b1, b2, eps, step, _stream(stream)))
+
+
+def gs_psnr_workspace_bytes(S: int, H: int, W: int) -> int:
+    return int(load().gs_psnr_workspace_bytes(S, H, W))
+
+
+def gs_psnr(images, gts, S: int, H: int, W: int, ws, psnr, stream=None):
+    import torch
+
+    _check("gs_psnr", load().gs_psnr(_ptr(images, torch.float32, "images"), _ptr(gts, torch.float32, "gts"), S, H, W,
+                                     _ptr(ws, torch.uint8, "ws"), ws.numel(), _ptr(psnr, torch.float32, "psnr"),
+                                     _stream(stream)))
+
+
+def gs_get_device_error(stream=None) -> int:
+    """Synchronises the stream, returns and clears the device error bits."""
+    flags = ctypes.c_uint32(0)
+    st = load().gs_get_device_error(ctypes.byref(flags), _stream(stream))
+    if st not in (0, 6):
+        _check("gs_get_device_error", st)
+    return int(flags.value)
+
+
+def gs_status_string(status: int) -> str:
+    return load().gs_status_string(status).decode()
+
+
+def gs_launch_count() -> int:
+    return int(load().gs_launch_count())
+
+
+def gs_version() -> int:
+    return int(load().gs_version())

@@ -1,0 +1,139 @@
+"""Device-resident state and the composition of one GSta training step.
+
+Nothing here computes: it allocates the caller-owned buffers the C ABI
+expects (PyTorch is the allocator) and calls the entry points in the order
+of Algorithm 1 -- rasterise (project, sort, composite), loss, backward with
+frozen Gaussians skipped, masked Adam -- plus the freeze-map update and the
+PSNR check at the cadence the host controller decides.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import lib
+
+# Learning rates per parameter group: xyz, scale, rotation, opacity, SH DC, SH rest.
+# Sec. 4.1: the vanilla 3DGS rates except opacity 0.025; the vanilla values are
+# not printed in the paper and are taken from common 3DGS practice: xyz
+# 1.6e-4 x scene extent, scale 5e-3, rotation 1e-3, SH DC 2.5e-3, SH rest 2.5e-3/20.
+def default_lrs(scene_extent: float) -> list[float]:
+    return [1.6e-4 * scene_extent, 5e-3, 1e-3, 0.025, 2.5e-3, 2.5e-3 / 20.0]
+
+
+def pack_params(p59: np.ndarray, device="cuda") -> torch.Tensor:
+    """(N, 59) array -> (N, 64) float32 device tensor with zero padding."""
+    n = p59.shape[0]
+    out = torch.zeros((n, lib.ROW), dtype=torch.float32)
+    out[:, :59] = torch.from_numpy(np.ascontiguousarray(p59, dtype=np.float32))
+    return out.to(device)
+
+
+@dataclasses.dataclass
+class View:
+    """Per-resolution buffers of one rendered view."""
+    cam: lib.GsCamera
+    image: torch.Tensor
+    t_final: torch.Tensor
+    n_last: torch.Tensor
+    dl: torch.Tensor
+    loss: torch.Tensor
+    loss_ws: torch.Tensor
+    vals: torch.Tensor
+    ranges: torch.Tensor
+    count: torch.Tensor
+    sort_ws: torch.Tensor
+    capacity: int
+
+
+class Model:
+    """Gaussian parameters, Adam moments, freeze state and per-step scratch on one GPU."""
+
+    def __init__(self, params59: np.ndarray, sh_degree: int = 3, device="cuda"):
+        self.device = torch.device(device)
+        self.n = int(params59.shape[0])
+        self.sh_degree = sh_degree
+        n = self.n
+        f32 = dict(dtype=torch.float32, device=self.device)
+        self.P = pack_params(params59, self.device)
+        self.G = torch.zeros((n, lib.ROW), **f32)
+        self.m = torch.zeros((n, lib.ROW), **f32)
+        self.v = torch.zeros((n, lib.ROW), **f32)
+        self.splats = torch.zeros((n, lib.SPLAT), **f32)
+        self.grad2d = torch.zeros((n, lib.GRAD2D), **f32)
+        self.frozen = torch.zeros(n, dtype=torch.uint8, device=self.device)
+        self.act = torch.arange(n, dtype=torch.int32, device=self.device)
+        self.n_active = torch.tensor([n], dtype=torch.int32, device=self.device)
+        self.acc_xyz = torch.zeros(n, **f32)
+        self.acc_rgb = torch.zeros(n, **f32)
+        self.cnt = torch.zeros(n, dtype=torch.int32, device=self.device)
+        self.freeze_ws = torch.zeros(max(lib.gs_freeze_workspace_bytes(n), 256), dtype=torch.uint8, device=self.device)
+        self.step_count = 0
+
+    # ---- views ----
+    def make_view(self, cam: lib.GsCamera, capacity: int) -> View:
+        H, W = cam.height, cam.width
+        dev = self.device
+        return View(
+            cam=cam,
+            image=torch.zeros((3, H, W), dtype=torch.float32, device=dev),
+            t_final=torch.zeros((H, W), dtype=torch.float32, device=dev),
+            n_last=torch.zeros((H, W), dtype=torch.int32, device=dev),
+            dl=torch.zeros((3, H, W), dtype=torch.float32, device=dev),
+            loss=torch.zeros(1, dtype=torch.float32, device=dev),
+            loss_ws=torch.zeros(lib.gs_loss_workspace_bytes(H, W), dtype=torch.uint8, device=dev),
+            vals=torch.zeros(max(capacity, 1), dtype=torch.int32, device=dev),
+            ranges=torch.zeros((cam.tiles, 2), dtype=torch.int32, device=dev),
+            count=torch.zeros(1, dtype=torch.int64, device=dev),
+            sort_ws=torch.zeros(lib.gs_sort_workspace_bytes(self.n, capacity, cam), dtype=torch.uint8, device=dev),
+            capacity=capacity,
+        )
+
+    def retarget(self, view: View, cam: lib.GsCamera) -> View:
+        """Same buffers, another camera of the same resolution and tile size."""
+        assert (cam.width, cam.height, cam.tile) == (view.cam.width, view.cam.height, view.cam.tile)
+        view.cam = cam
+        return view
+
+    # ---- step pieces ----
+    def rasterize(self, view: View, stream=None):
+        lib.gs_project(self.P, self.n, self.sh_degree, view.cam, self.splats, stream)
+        lib.gs_sort(self.splats, self.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count,
+                    stream)
+        lib.gs_render_fwd(self.splats, view.vals, view.ranges, view.cam, view.image, view.t_final, view.n_last, stream)
+
+    def loss(self, view: View, gt: torch.Tensor, lam: float = 0.2, stream=None):
+        lib.gs_loss(view.image, gt, view.cam.height, view.cam.width, lam, view.loss_ws, view.loss, view.dl, stream)
+
+    def backward(self, view: View, stats: bool = True, stream=None):
+        lib.gs_render_bwd(self.P, self.n, self.sh_degree, view.cam, self.splats, view.vals, view.ranges, view.t_final,
+                          view.n_last, view.dl, self.frozen, self.act, self.n_active, self.grad2d, self.G,
+                          self.acc_xyz if stats else None, self.acc_rgb if stats else None,
+                          self.cnt if stats else None, stream)
+
+    def adam(self, lrs, b1=0.9, b2=0.999, eps=1e-15, stream=None):
+        self.step_count += 1
+        lib.gs_adam_masked(self.P, self.G, self.m, self.v, self.n, self.act, self.n_active, lrs, b1, b2, eps,
+                           self.step_count, stream)
+
+    def train_step(self, view: View, gt: torch.Tensor, lrs, stream=None):
+        """One iteration of Algorithm 1's inner body on the current freeze map."""
+        self.rasterize(view, stream)
+        self.loss(view, gt, stream=stream)
+        self.backward(view, stream=stream)
+        self.adam(lrs, stream=stream)
+
+    def freeze_update(self, eps_xyz: float, eps_rgb: float, mode: int, stream=None):
+        lib.gs_freeze_update(self.n, self.acc_xyz, self.acc_rgb, self.cnt, self.frozen, eps_xyz, eps_rgb, mode,
+                             self.act, self.n_active, self.freeze_ws, stream)
+
+    def measure_capacity(self, cams, slack: float = 1.25) -> int:
+        """Largest entry count over ``cams`` (one projection + sort each), times ``slack``."""
+        worst = 0
+        for cam in cams:
+            lib.gs_project(self.P, self.n, self.sh_degree, cam, self.splats)
+            tt = self.splats[:, 11].contiguous().view(torch.int32)
+            worst = max(worst, int(tt.to(torch.int64).sum().item()))
+        return int(worst * slack) + 1024

@@ -1,0 +1,123 @@
+"""Host-side GSta controller: freeze thresholds, freeze cadence, early stop
+and the plateau learning-rate schedule (Algorithm 1's scalar logic).
+
+Readings of the paper taken here:
+* Eq. 5 -- thresholds rise linearly with the iteration and stay within
+  [0.5, 1.5] x their initial values (Sec. 3.2.1, Sec. 4.1):
+  eps_k = eps_0 * min(1.5, max(0.5, 0.5 + 1.5 k / K)).
+* Sec. 4.1 -- the map is updated every 250 iterations inside
+  [3000, min(10000, early-stop iteration)); reset every 2000 iterations and
+  left alone for 500 iterations after a reset; the gradient statistics are
+  restarted at every 250-iteration boundary, so each update averages the
+  iterations since the previous boundary.
+* Eq. 7 -- PSNR of a fixed training subset every 1000 iterations while the
+  freezing phase lasts; stop when the last two changes are both < 0.2 dB;
+  then all Gaussians are unfrozen for a finetuning stage of K_f iterations,
+  after which training ends.
+* Sec. 3.2.3 -- the xyz learning rate decays by 0.75 when the PSNR has not
+  risen by more than 1 dB for more than one evaluation.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+FREEZE_UPDATE, FREEZE_RESET, FREEZE_CLEAR = 0, 1, 2
+
+
+@dataclasses.dataclass
+class GStaConfig:
+    total_iter: int = 30000
+    warmup: int = 3000
+    window_end: int = 10000
+    every: int = 250
+    reset_every: int = 2000
+    wait: int = 500
+    psnr_every: int = 1000
+    eps_psnr: float = 0.2
+    finetune_iters: int = 1000
+    eps0_xyz: float = 3e-5
+    eps0_rgb: float = 1e-4
+    lr_decay: float = 0.75
+    lr_patience: int = 1
+    lr_eps: float = 1.0
+    freezing: bool = True  # False: plain 3DGS training (no freezing, no early stop)
+
+    @staticmethod
+    def tiny() -> "GStaConfig":
+        """The schedule scaled to a 200-iteration run."""
+        return GStaConfig(total_iter=200, warmup=20, window_end=150, every=10, reset_every=80, wait=20, psnr_every=20,
+                          finetune_iters=20)
+
+
+class GStaController:
+    def __init__(self, cfg: GStaConfig, lr_xyz: float):
+        self.cfg = cfg
+        self.lr_xyz = lr_xyz
+        self._best = float("-inf")
+        self._bad = 0
+        self.psnrs: list[float] = []
+        self.last_reset: int | None = None
+        self.stop_iter: int | None = None
+        self.finetune_left: int | None = None
+
+    def thresholds(self, k: int) -> tuple[float, float]:
+        c = self.cfg
+        s = min(1.5, max(0.5, 0.5 + 1.5 * k / c.total_iter))
+        return c.eps0_xyz * s, c.eps0_rgb * s
+
+    def freeze_mode(self, k: int) -> int | None:
+        """Freeze-map action before iteration k (None: nothing)."""
+        c = self.cfg
+        if not c.freezing or self.finetune_left is not None or k % c.every:
+            return None
+        end = c.window_end if self.stop_iter is None else min(c.window_end, self.stop_iter)
+        if k >= end:
+            return None
+        if k < c.warmup:
+            return FREEZE_CLEAR
+        if k % c.reset_every == 0:
+            self.last_reset = k
+            return FREEZE_RESET
+        if self.last_reset is not None and k - self.last_reset < c.wait:
+            return FREEZE_CLEAR
+        return FREEZE_UPDATE
+
+    def wants_psnr(self, k: int) -> bool:
+        c = self.cfg
+        return c.freezing and self.finetune_left is None and k > 0 and k % c.psnr_every == 0 and k <= c.window_end
+
+    def report_psnr(self, k: int, psnr: float) -> bool:
+        """Record a subset PSNR; returns True when early stop fires (Eq. 7)."""
+        c = self.cfg
+        self.psnrs.append(psnr)
+        if psnr > self._best + c.lr_eps:
+            self._best, self._bad = psnr, 0
+        else:
+            self._bad += 1
+            if self._bad > c.lr_patience:
+                self.lr_xyz *= c.lr_decay
+                self._bad = 0
+        p = self.psnrs
+        if len(p) >= 3 and p[-1] - p[-2] < c.eps_psnr and p[-2] - p[-3] < c.eps_psnr:
+            self.stop_iter = k
+            self.finetune_left = c.finetune_iters
+            return True
+        return False
+
+    def finished(self, k: int) -> bool:
+        """Training ends after the finetuning stage (entered on early stop or at total_iter)."""
+        if self.finetune_left is not None:
+            return self.finetune_left <= 0
+        return False
+
+    def after_step(self, k: int) -> bool:
+        """Advance the finetuning countdown; at total_iter without early stop, enter finetuning.
+        Returns True when the map must be reset (all Gaussians unfrozen)."""
+        c = self.cfg
+        if self.finetune_left is not None:
+            self.finetune_left -= 1
+            return False
+        if c.freezing and k + 1 >= c.total_iter:
+            self.finetune_left = c.finetune_iters
+            return True
+        return False

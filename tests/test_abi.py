@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/gsta.h declares. No compute calls here (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gsta.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def cdll():
+    from paper_2504_06716_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared()
+    for want in ["gs_project", "gs_sort", "gs_render_fwd", "gs_render_bwd", "gs_freeze_update", "gs_adam_masked",
+                 "gs_psnr", "gs_loss"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(cdll):
+    L, path = cdll
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\s(gs_[a-z0-9_]+)$", out, flags=re.M))
+    assert set(_declared()) <= exported
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2504_06716_gb300 import lib
+
+    assert set(_declared()) == set(lib._SIGS)
+    for name in _declared():
+        assert callable(getattr(lib, name))
+
+
+def test_status_strings_and_version(cdll):
+    L, _ = cdll
+    L.gs_status_string.restype = ctypes.c_char_p
+    assert L.gs_status_string(0) == b"ok"
+    assert L.gs_status_string(3) == b"sort capacity exceeded"
+    assert L.gs_version() >= 100
+
+
+def test_host_validation_rejects_bad_arguments_without_launching(cdll):
+    """Validation runs on the host before any CUDA call, so it is testable here."""
+    from paper_2504_06716_gb300 import lib
+
+    lib.load()
+    L = lib._lib
+    cam = lib.GsCamera()
+    cam.width, cam.height, cam.tile, cam.fx, cam.fy = 64, 64, 16, 50.0, 50.0
+    # null parameter pointer with n > 0
+    assert L.gs_project(None, 10, 3, ctypes.byref(cam), None, None) == 1
+    # bad SH degree
+    assert L.gs_project(None, 0, 4, ctypes.byref(cam), None, None) == 1
+    # tile size that is not 8, 16 or 32
+    bad = lib.GsCamera()
+    ctypes.pointer(bad)[0] = cam
+    bad.tile = 12
+    assert L.gs_project(None, 0, 3, ctypes.byref(bad), None, None) == 1
+    # n = 0 is a valid empty call and launches nothing
+    assert L.gs_project(None, 0, 3, ctypes.byref(cam), None, None) == 0
+    # workspace too small for the sort
+    assert L.gs_sort(None, 0, ctypes.byref(cam), None, 0, 0, None, None, None, None) == 1
+    # unknown freeze mode
+    assert L.gs_freeze_update(0, None, None, None, None, 1.0, 1.0, 7, None, None, None, 0, None) == 1
+    # Adam step must be >= 1
+    lr = (ctypes.c_float * 6)(*([1e-3] * 6))
+    assert L.gs_adam_masked(None, None, None, None, 0, None, None, lr, 0.9, 0.999, 1e-15, 0, None) == 1
+    # loss weight outside [0, 1]
+    assert L.gs_loss(None, None, 8, 8, 1.5, None, 0, None, None, None) == 1
+    assert L.gs_sort_workspace_bytes(1000, 4000, 64, 64, 16) > 0
+    assert L.gs_loss_workspace_bytes(8, 8) > 0

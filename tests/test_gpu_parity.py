@@ -1,0 +1,457 @@
+"""Stage-by-stage parity of the CUDA path (through the C ABI) with the FP64
+oracle, at sizes the oracle finishes in seconds that span many tiles and
+ragged tails. Integer outputs (sort order, tile ranges, freeze map, active
+list) must match bit for bit; floating outputs within the stated tolerances
+(1e-4 relative on images, 1e-3 relative on gradients)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2504_06716_gb300 import lib, synth  # noqa: E402
+
+import parity_util as pu  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_06716_gb300 import build
+
+    build.build()
+    oracle.build()
+    lib.load()
+
+
+def _scene(kind: str):
+    """(params (n,59) float32-valued, cameras) for a parity workload."""
+    if kind == "tiny":  # the 2,000-Gaussian, 128x128 workload
+        s = synth.tiny_scene()
+        return pu.f32(s.init), s.cameras
+    if kind == "ragged":  # ragged image (100x75) and Gaussian count
+        P = synth.gaussians_uniform(1733, 17)
+        P[:, 3:6] += 0.8
+        cams = synth.circle_cameras(3, 3.5, 100, 75, 55.0)
+        return pu.f32(P), cams
+    if kind == "surface":  # surface mix at a mid resolution
+        s = synth.surface_scene(6000, 10, 8, 320, 214, seed=5)
+        return pu.f32(s.init), s.cameras
+    raise KeyError(kind)
+
+
+def _gpu_project(P, gcam, deg=3):
+    n = P.shape[0]
+    Pt = torch.from_numpy(pu.pack64(P)).to(DEV)
+    spl = torch.zeros((n, 12), dtype=torch.float32, device=DEV)
+    lib.gs_project(Pt, n, deg, gcam, spl)
+    torch.cuda.synchronize()
+    return spl.cpu().numpy()
+
+
+def _gpu_sort(rec, gcam, capacity=None):
+    n = rec.shape[0]
+    if capacity is None:
+        capacity = int(rec[:, 11].view(np.int32).astype(np.int64).sum()) + 7
+    spl = torch.from_numpy(rec).to(DEV)
+    ws = torch.zeros(lib.gs_sort_workspace_bytes(n, capacity, gcam), dtype=torch.uint8, device=DEV)
+    vals = torch.full((max(capacity, 1),), -1, dtype=torch.int32, device=DEV)
+    ranges = torch.full((gcam.tiles, 2), -1, dtype=torch.int32, device=DEV)
+    count = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lib.gs_sort(spl, n, gcam, ws, capacity, vals, ranges, count)
+    flags = lib.gs_get_device_error()
+    P = int(count.item())
+    return vals.cpu().numpy().view(np.uint32), ranges.cpu().numpy().view(np.uint32), P, flags, spl
+
+
+def _gpu_render(spl_t, vals_np, ranges_np, gcam):
+    H, W = gcam.height, gcam.width
+    vals = torch.from_numpy(vals_np.view(np.int32).copy()).to(DEV)
+    ranges = torch.from_numpy(ranges_np.view(np.int32).copy()).to(DEV)
+    img = torch.zeros((3, H, W), device=DEV)
+    tf = torch.zeros((H, W), device=DEV)
+    nl = torch.zeros((H, W), dtype=torch.int32, device=DEV)
+    lib.gs_render_fwd(spl_t, vals, ranges, gcam, img, tf, nl)
+    torch.cuda.synchronize()
+    return img.cpu().numpy(), tf.cpu().numpy(), nl.cpu().numpy(), vals, ranges
+
+
+# ----------------------------------------------------------------------------- A1 projection
+
+
+@pytest.mark.parametrize("kind", ["tiny", "ragged", "surface"])
+def test_project_matches_oracle(kind):
+    P, cams = _scene(kind)
+    for cam in cams[:4]:
+        ocam, gcam = pu.cameras(cam)
+        want = oracle.project(P, ocam)
+        got = _gpu_project(P, gcam)
+        safe = want["margin"] > pu.PROJ_MARGIN
+        rad = got[:, 10].view(np.int32)
+        tt = got[:, 11].view(np.int32)
+        assert safe.mean() > 0.95
+        assert np.array_equal(rad[safe], want["radius"][safe])
+        assert np.array_equal(tt[safe], want["tiles_touched"][safe])
+        vis = safe & (want["radius"] > 0)
+        assert vis.sum() > 50
+        assert np.abs(got[vis, 0:2] - want["mean2d"][vis]).max() < 1e-3
+        scale = np.maximum(np.abs(want["conic"][vis, 0]), np.abs(want["conic"][vis, 2]))[:, None]
+        assert (np.abs(got[vis, 2:5] - want["conic"][vis]) / scale).max() < 1e-4
+        assert np.allclose(got[vis, 5], want["opacity"][vis], rtol=1e-6, atol=0)
+        assert np.abs(got[vis, 6:9] - want["rgb"][vis]).max() < 1e-5
+        assert np.allclose(got[vis, 9], want["depth"][vis], rtol=1e-6, atol=0)
+        # culled Gaussians are all-zero records
+        culled = safe & (want["radius"] == 0)
+        assert np.all(got[culled] == 0)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_project_lower_sh_degrees(deg):
+    P, cams = _scene("tiny")
+    ocam, gcam = pu.cameras(cams[1])
+    want = oracle.project(P, ocam, sh_degree=deg)
+    got = _gpu_project(P, gcam, deg)
+    vis = (want["margin"] > pu.PROJ_MARGIN) & (want["radius"] > 0)
+    assert np.abs(got[vis, 6:9] - want["rgb"][vis]).max() < 1e-5
+
+
+def test_project_empty_and_all_culled():
+    _, gcam = pu.cameras(synth.tiny_scene().cameras[0])
+    spl = torch.zeros((1, 12), device=DEV)
+    lib.gs_project(torch.zeros((1, 64), device=DEV), 0, 3, gcam, spl)  # n = 0
+    P = np.zeros((5, 59))
+    P[:, 0:3] = [100.0, 100.0, 100.0]  # behind / far outside every camera
+    P[:, 6] = 1.0
+    got = _gpu_project(pu.f32(P), gcam)
+    assert np.all(got == 0)
+
+
+# ----------------------------------------------------------------------------- A2 sort (bit-exact)
+
+
+def _oracle_sort(rec, ocam, capacity=None):
+    return oracle.sort(rec[:, 0:2], rec[:, 10].view(np.int32), rec[:, 9], ocam.width, ocam.height, ocam.tile,
+                       capacity=capacity)
+
+
+@pytest.mark.parametrize("kind,tile", [("tiny", 16), ("ragged", 8), ("ragged", 32), ("surface", 16), ("surface", 8)])
+def test_sort_bit_exact(kind, tile):
+    P, cams = _scene(kind)
+    ocam, gcam = pu.cameras(cams[0], tile=tile)
+    rec = pu.records_from_oracle(oracle.project(P, ocam))
+    want_vals, want_ranges = _oracle_sort(rec, ocam)
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam)
+    assert flags == 0
+    assert Pn == len(want_vals) > 0
+    assert np.array_equal(vals[:Pn], want_vals)
+    assert np.array_equal(ranges, want_ranges)
+
+
+def test_sort_ties_keep_index_order():
+    """Many Gaussians with bit-identical depth on overlapping tiles: the order
+    inside a tile must be ascending index (the stable-sort tie break)."""
+    g = np.random.default_rng(0)
+    n = 5000
+    rec = np.zeros((n, 12), np.float32)
+    rec[:, 0] = g.uniform(0, 200, n)
+    rec[:, 1] = g.uniform(0, 120, n)
+    rec[:, 9] = g.choice(np.array([1.5, 2.25, 3.0, 7.0], np.float32), n)
+    rad = g.integers(1, 30, n).astype(np.int32)
+    rad[::7] = 0  # some culled
+    rec[:, 10] = rad.view(np.float32)
+    cam = synth.pinhole(200, 120, 60.0, (0, -3, 0.5))
+    ocam, gcam = pu.cameras(cam, tile=16)
+    tiles = np.zeros(n, np.int32)
+    for i in range(n):  # tiles touched by the float32 rectangle rule of the oracle
+        if rad[i] > 0:
+            v, _ = oracle.sort(rec[i:i + 1, 0:2], rad[i:i + 1], rec[i:i + 1, 9], 200, 120, 16)
+            tiles[i] = len(v)
+    rad[tiles == 0] = 0
+    rec[:, 10] = rad.view(np.float32)
+    rec[:, 11] = tiles.view(np.float32)
+    want_vals, want_ranges = _oracle_sort(rec, ocam)
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam)
+    assert flags == 0 and Pn == len(want_vals)
+    assert np.array_equal(vals[:Pn], want_vals)
+    assert np.array_equal(ranges, want_ranges)
+
+
+def test_sort_empty_input():
+    P = np.zeros((300, 59))
+    P[:, 2] = -50.0  # behind the camera
+    P[:, 6] = 1.0
+    ocam, gcam = pu.cameras(synth.pinhole(64, 64, 60.0, (0, -3, 0.5)))
+    rec = pu.records_from_oracle(oracle.project(pu.f32(P), ocam))
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam, capacity=16)
+    assert Pn == 0 and flags == 0
+    assert np.all(ranges == 0)
+
+
+def test_sort_capacity_overflow_is_flagged_and_clipped():
+    P, cams = _scene("tiny")
+    ocam, gcam = pu.cameras(cams[0])
+    rec = pu.records_from_oracle(oracle.project(P, ocam))
+    want_vals, _ = _oracle_sort(rec, ocam)
+    cap = len(want_vals) // 2
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam, capacity=cap)
+    assert flags & lib.GS_FLAG_CAPACITY
+    assert Pn == len(want_vals)
+    assert ranges.max() <= cap
+    # the device flag is sticky until read, and reading clears it
+    assert lib.gs_get_device_error() == 0
+
+
+# ----------------------------------------------------------------------------- A3 render forward
+
+
+@pytest.mark.parametrize("kind,tile,bg", [("tiny", 16, (0, 0, 0)), ("ragged", 8, (0.2, 0.4, 0.6)),
+                                          ("ragged", 32, (0, 0, 0)), ("surface", 16, (0.1, 0.1, 0.1))])
+def test_render_forward_matches_oracle(kind, tile, bg):
+    P, cams = _scene(kind)
+    ocam, gcam = pu.cameras(cams[0], tile=tile, bg=bg)
+    rec = pu.records_from_oracle(oracle.project(P, ocam))
+    proj = pu.proj_from_records(rec)
+    vals, ranges, Pn, flags, spl = _gpu_sort(rec, gcam)
+    want = oracle.render(proj, vals[:Pn], ranges, ocam)
+    img, tf, nl, _, _ = _gpu_render(spl, vals[:Pn], ranges, gcam)
+    ok = want["margin"] > pu.PIXEL_MARGIN
+    assert ok.mean() > 0.99
+    assert np.array_equal(nl[ok], want["n_last"][ok])
+    good, worst = pu.close(img, want["image"], 1e-4, 1.0, np.broadcast_to(ok, img.shape))
+    assert good, worst
+    good, worst = pu.close(tf, want["t_final"], 1e-4, 1e-3, ok)
+    assert good, worst
+    # pixels with an ambiguous decision must still hold a valid composite
+    assert np.all(np.isfinite(img)) and np.all((tf >= 1e-4 * 0.99) & (tf <= 1.0))
+
+
+# ----------------------------------------------------------------------------- A4 loss
+
+
+def _gpu_loss(x, y, lam=0.2):
+    H, W = x.shape[1], x.shape[2]
+    xt = torch.from_numpy(x.astype(np.float32)).to(DEV)
+    yt = torch.from_numpy(y.astype(np.float32)).to(DEV)
+    ws = torch.zeros(lib.gs_loss_workspace_bytes(H, W), dtype=torch.uint8, device=DEV)
+    loss = torch.zeros(1, device=DEV)
+    dl = torch.zeros_like(xt)
+    lib.gs_loss(xt, yt, H, W, lam, ws, loss, dl)
+    torch.cuda.synchronize()
+    return float(loss.item()), dl.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,W", [(37, 53), (128, 128), (75, 100)])
+def test_loss_matches_oracle(H, W):
+    g = np.random.default_rng(H * W)
+    x = pu.f32(g.uniform(0, 1, (3, H, W)))
+    y = pu.f32(np.clip(x + g.normal(0, 0.1, x.shape), 0, 1))
+    Lw, dw = oracle.loss(x, y)
+    Lg, dg = _gpu_loss(x, y)
+    assert Lg == pytest.approx(Lw, rel=1e-5)
+    scale = np.abs(dw).mean()
+    good, worst = pu.close(dg, dw, 1e-3, scale)
+    assert good, worst
+
+
+def test_loss_on_rendered_images():
+    """Smooth rendered content (small local variance) is the hard case for the
+    float32 window moments."""
+    P, cams = _scene("tiny")
+    s = synth.tiny_scene()
+    ocam, _ = pu.cameras(cams[2])
+    x = pu.f32(oracle.forward(P, ocam)["image"])
+    y = pu.f32(oracle.forward(pu.f32(s.gt), ocam)["image"])
+    Lw, dw = oracle.loss(x, y)
+    Lg, dg = _gpu_loss(x, y)
+    assert Lg == pytest.approx(Lw, rel=1e-5)
+    good, worst = pu.close(dg, dw, 1e-3, np.abs(dw).mean())
+    assert good, worst
+
+
+def test_loss_identical_images():
+    x = pu.f32(np.random.default_rng(2).uniform(0, 1, (3, 40, 30)))
+    Lg, dg = _gpu_loss(x, x)
+    assert abs(Lg) < 1e-6
+    assert np.abs(dg).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------- A5/A6 backward
+
+
+def _stage_inputs(kind, tile=16, bg=(0, 0, 0), cam_index=0, frozen_frac=0.3, seed=0):
+    P, cams = _scene(kind)
+    ocam, gcam = pu.cameras(cams[cam_index], tile=tile, bg=bg)
+    rec = pu.records_from_oracle(oracle.project(P, ocam))
+    proj = pu.proj_from_records(rec)
+    vals, ranges, Pn, _, spl = _gpu_sort(rec, gcam)
+    fw = oracle.render(proj, vals[:Pn], ranges, ocam)
+    g = np.random.default_rng(seed)
+    gt = pu.f32(np.clip(fw["image"] + g.normal(0, 0.05, fw["image"].shape), 0, 1))
+    _, dl = oracle.loss(fw["image"], gt)
+    dl = pu.f32(dl)
+    frozen = (g.uniform(0, 1, P.shape[0]) < frozen_frac).astype(np.uint8)
+    return dict(P=P, ocam=ocam, gcam=gcam, rec=rec, proj=proj, vals=vals[:Pn], ranges=ranges, spl=spl, fw=fw, dl=dl,
+                frozen=frozen, gt=gt)
+
+
+def _gpu_raster_bwd(st):
+    n = st["P"].shape[0]
+    _, tf, nl, vals, ranges = _gpu_render(st["spl"], st["vals"], st["ranges"], st["gcam"])
+    tft = torch.from_numpy(tf).to(DEV)
+    nlt = torch.from_numpy(nl).to(DEV)
+    dlt = torch.from_numpy(st["dl"].astype(np.float32)).to(DEV)
+    fr = torch.from_numpy(st["frozen"]).to(DEV)
+    g2 = torch.zeros((n, 12), device=DEV)
+    lib.gs_raster_bwd(st["spl"], vals, ranges, st["gcam"], tft, nlt, dlt, fr, g2)
+    torch.cuda.synchronize()
+    return g2.cpu().numpy(), tf, nl
+
+
+@pytest.mark.parametrize("kind,tile,bg", [("tiny", 16, (0, 0, 0)), ("ragged", 8, (0.3, 0.2, 0.1)),
+                                          ("surface", 16, (0, 0, 0)), ("ragged", 32, (0, 0, 0))])
+def test_raster_backward_matches_oracle(kind, tile, bg):
+    st = _stage_inputs(kind, tile, bg)
+    g2, _, _ = _gpu_raster_bwd(st)
+    amb = (st["fw"]["margin"] <= pu.PIXEL_MARGIN).astype(np.uint8)
+    want = oracle.render_bwd(st["proj"], st["vals"], st["ranges"], st["ocam"], st["dl"], st["frozen"], amb)
+    fr = st["frozen"] == 1
+    assert np.all(g2[fr] == 0), "frozen Gaussians must receive nothing"
+    ok = ~fr & (want["tainted"] == 0)
+    assert ok.sum() > 0.5 * (~fr).sum()
+    cols = [(want["d_mean2d"], g2[:, 0:2]), (want["d_conic"], g2[:, 2:5]), (want["d_opacity"][:, None], g2[:, 5:6]),
+            (want["d_rgb"], g2[:, 6:9])]
+    for w, g in cols:
+        floor = 1e-2 * np.abs(w[ok]).max()
+        good, worst = pu.close(g[ok], w[ok], 1e-3, floor)
+        assert good, worst
+    assert np.all(g2[:, 9:] == 0)
+
+
+def test_project_backward_matches_oracle():
+    st = _stage_inputs("tiny", frozen_frac=0.25, seed=3)
+    n = st["P"].shape[0]
+    g = np.random.default_rng(4)
+    # raster gradients for every Gaussian, given to both sides identically
+    g2 = pu.f32(g.normal(0, 1e-3, (n, 12)))
+    g2[:, 9:] = 0
+    grads2d = dict(d_mean2d=g2[:, 0:2], d_conic=g2[:, 2:5], d_opacity=g2[:, 5], d_rgb=g2[:, 6:9])
+    act = np.nonzero(st["frozen"] == 0)[0].astype(np.int32)
+    want = oracle.project_bwd(st["P"], st["ocam"], grads2d, st["frozen"])
+    Pt = torch.from_numpy(pu.pack64(st["P"])).to(DEV)
+    spl = torch.zeros((n, 12), device=DEV)
+    lib.gs_project(Pt, n, 3, st["gcam"], spl)
+    g2t = torch.from_numpy(g2.astype(np.float32)).to(DEV)
+    G = torch.full((n, 64), 7.0, device=DEV)
+    actt = torch.from_numpy(act).to(DEV)
+    nact = torch.tensor([len(act)], dtype=torch.int32, device=DEV)
+    ax = torch.zeros(n, device=DEV)
+    ar = torch.zeros(n, device=DEV)
+    cn = torch.zeros(n, dtype=torch.int32, device=DEV)
+    lib.gs_project_bwd(Pt, n, 3, st["gcam"], spl, actt, nact, g2t, G, ax, ar, cn)
+    torch.cuda.synchronize()
+    G = G.cpu().numpy()
+    g2_after = g2t.cpu().numpy()
+    vis_gpu = spl.cpu().numpy()[:, 10].view(np.int32) > 0
+    proj = oracle.project(st["P"], st["ocam"])
+    safe = proj["margin"] > pu.PROJ_MARGIN
+    fr = st["frozen"] == 1
+    assert np.all(G[fr] == 7.0), "rows of frozen Gaussians are not touched"
+    a = ~fr & safe
+    assert np.all(G[a & ~vis_gpu][:, :] == 0)
+    groups = [slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11), slice(11, 14), slice(14, 59)]
+    av = a & vis_gpu
+    for sl in groups:
+        w = want["G"][av, sl]
+        good, worst = pu.close(G[av, sl], w, 1e-3, 1e-2 * np.abs(w).max())
+        assert good, (sl, worst)
+    assert np.all(G[a, 59:] == 0)
+    # raster gradients of processed Gaussians are consumed (zeroed)
+    assert np.all(g2_after[av] == 0) and np.array_equal(g2_after[fr], g2[fr].astype(np.float32))
+    # freeze statistics
+    ax, ar, cn = ax.cpu().numpy(), ar.cpu().numpy(), cn.cpu().numpy()
+    assert np.array_equal(cn[a], av[a].astype(np.int32))
+    assert np.allclose(ax[av], want["xyz_norm"][av], rtol=1e-5, atol=1e-12)
+    assert np.allclose(ar[av], want["rgb_norm"][av], rtol=1e-5, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- A7 freeze update (bit-exact)
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 1024, 4099, 200003])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_freeze_update_bit_exact(n, mode):
+    g = np.random.default_rng(n + 31 * mode)
+    acc_x = (g.exponential(3e-5, n) * g.integers(0, 4, n)).astype(np.float32)
+    acc_r = (g.exponential(1e-4, n) * g.integers(0, 4, n)).astype(np.float32)
+    cnt = g.integers(0, 4, n).astype(np.int32)
+    frozen = (g.uniform(0, 1, n) < 0.2).astype(np.uint8)
+    ex, er = np.float32(4e-5), np.float32(1.1e-4)
+    t = [torch.from_numpy(a.copy()).to(DEV) for a in (acc_x, acc_r, cnt, frozen)]
+    act = torch.full((max(n, 1),), -1, dtype=torch.int32, device=DEV)
+    na = torch.zeros(1, dtype=torch.int32, device=DEV)
+    ws = torch.zeros(lib.gs_freeze_workspace_bytes(n), dtype=torch.uint8, device=DEV)
+    lib.gs_freeze_update(n, *t, float(ex), float(er), mode, act, na, ws)
+    want_act = oracle.freeze_update(acc_x, acc_r, cnt, frozen, ex, er, mode)
+    k = int(na.item())
+    assert k == len(want_act)
+    assert np.array_equal(act.cpu().numpy()[:k], want_act)
+    assert np.array_equal(t[3].cpu().numpy(), frozen)
+    assert not t[0].any() and not t[1].any() and not t[2].any()
+
+
+# ----------------------------------------------------------------------------- A8 masked Adam
+
+
+def test_adam_masked_matches_oracle_and_skips_frozen():
+    g = np.random.default_rng(8)
+    n = 3001
+    P = g.normal(size=(n, 59)).astype(np.float32)
+    M = g.normal(0, 1e-3, (n, 59)).astype(np.float32)
+    V = g.uniform(0, 1e-5, (n, 59)).astype(np.float32)
+    G = g.normal(0, 1e-3, (n, 59)).astype(np.float32)
+    frozen = (g.uniform(0, 1, n) < 0.4).astype(np.uint8)
+    act = np.nonzero(frozen == 0)[0].astype(np.int32)
+    lr = [1.6e-4 * 4.4, 5e-3, 1e-3, 0.025, 2.5e-3, 1.25e-4]
+    step = 17
+    Pt, Mt, Vt, Gt = (torch.from_numpy(pu.pack64(a)).to(DEV) for a in (P, M, V, G))
+    lib.gs_adam_masked(Pt, Gt, Mt, Vt, n, torch.from_numpy(act).to(DEV),
+                       torch.tensor([len(act)], dtype=torch.int32, device=DEV), lr, 0.9, 0.999, 1e-15, step)
+    torch.cuda.synchronize()
+    Po, Mo, Vo = (P.astype(np.float64), M.astype(np.float64), V.astype(np.float64))
+    oracle.adam(Po, G.astype(np.float64), Mo, Vo, frozen, np.array(lr), step, eps=1e-15)
+    Pg, Mg, Vg = (t.cpu().numpy()[:, :59] for t in (Pt, Mt, Vt))
+    fr = frozen == 1
+    assert np.array_equal(Pg[fr], P[fr]) and np.array_equal(Mg[fr], M[fr]) and np.array_equal(Vg[fr], V[fr])
+    a = ~fr
+    assert np.allclose(Mg[a], Mo[a], rtol=1e-5, atol=1e-12)
+    assert np.allclose(Vg[a], Vo[a], rtol=1e-5, atol=1e-15)
+    # the update itself within 1e-4 relative of the oracle's, plus float32 rounding of p
+    dg, dw = Pg[a] - P[a], Po[a] - P[a]
+    assert np.all(np.abs(dg - dw) <= 1e-4 * np.abs(dw) + 2 * np.spacing(np.abs(P[a]).astype(np.float32)))
+    assert np.all(Pt.cpu().numpy()[:, 59:] == 0)
+
+
+# ----------------------------------------------------------------------------- A9 PSNR
+
+
+def test_psnr_matches_oracle():
+    g = np.random.default_rng(9)
+    S, H, W = 4, 57, 91
+    gt = pu.f32(g.uniform(0, 1, (S, 3, H, W)))
+    img = pu.f32(gt + g.normal(0, 0.05, gt.shape))
+    img[1] = gt[1]  # identical: 100 dB floor
+    img[2] += 0.7  # mostly clamped
+    want = oracle.psnr(img, gt)
+    it = torch.from_numpy(img.astype(np.float32)).to(DEV)
+    gtt = torch.from_numpy(gt.astype(np.float32)).to(DEV)
+    ws = torch.zeros(lib.gs_psnr_workspace_bytes(S, H, W), dtype=torch.uint8, device=DEV)
+    out = torch.zeros(S, device=DEV)
+    lib.gs_psnr(it, gtt, S, H, W, ws, out)
+    got = out.cpu().numpy()
+    assert got[1] == pytest.approx(100.0, abs=1e-4)
+    assert np.allclose(got, want, rtol=1e-5, atol=1e-4)
