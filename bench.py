@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Training throughput of the GSta hot path on one GB300.
+
+Workload (synthetic stand-in for the paper's Mip-NeRF 360 scenes): 1,000,000
+Gaussians sampled on a sphere + ground plane + 20 boxes, SH degree 3, 200
+cameras on a hemisphere at 1237x822, targets rendered from a 1.5M-Gaussian
+ground-truth set. A step is one training iteration of Algorithm 1: the
+freeze-map action and subset-PSNR check at their cadence, projection, sort,
+compositing, loss, backward with frozen Gaussians skipped, masked Adam.
+
+The model is first trained (untimed) through the GSta schedule up to
+iteration 4750 -- past warmup, a reset and an update -- so the timed
+iterations run on the freeze map the method itself produced; warm-up and
+timed iterations continue the same schedule.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per GPU, launched with torchrun);
+the path has no exchange step, so no collective is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="surface-1M-1237x822", n_init=1_000_000, n_gt=1_500_000, views=200, width=1237, height=822,
+                tile=16, sh_degree=3)
+METRIC = "train it/s (GSta freezing, 1M Gaussians, 1237x822)"
+PEAKS_FALLBACK = dict(hbm_gbs=6800.0, sm_max_mhz=2070.0)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- CPU (oracle) leg
+
+
+def oracle_sample_step(scene, frac: float, rng_seed: int = 0) -> dict:
+    """One oracle training step on a bounded sample of the workload.
+
+    The sample is a centred crop of one training view covering `frac` of its
+    pixels, with the Gaussians visible in it: the oracle runs its full step
+    there (projection, sort, compositing, loss, backward, Adam on those
+    Gaussians). Culling and Adam of the Gaussians outside the crop are timed
+    on a random `frac` share of them. The step time of the whole view is the
+    sample's time divided by `frac`."""
+    import numpy as np
+
+    import oracle
+    from paper_2504_06716_gb300 import synth
+
+    cam = scene.cameras[scene.train_views[0]]
+    W, H = cam.width, cam.height
+    s = float(np.sqrt(frac))
+    cw, ch = max(16, int(round(W * s))), max(16, int(round(H * s)))
+    x0, y0 = (W - cw) // 2, (H - ch) // 2
+    crop = synth.Camera(cw, ch, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, cam.R, cam.t, cam.campos)
+    ocam = oracle.make_cam(crop)
+    true_frac = cw * ch / float(W * H)
+    P = scene.init
+    rng = np.random.default_rng(rng_seed)
+    if not hasattr(scene, "_crop_vis"):  # which Gaussians the crop sees (setup, untimed)
+        scene._crop_vis = np.nonzero(oracle.project(P, ocam)["radius"] > 0)[0]
+    vis = scene._crop_vis
+    sub = np.ascontiguousarray(P[vis])
+    others = np.setdiff1d(np.arange(P.shape[0]), vis)
+    pick = rng.choice(others, size=max(1, int(len(others) * true_frac)), replace=False)
+    gt = rng.uniform(0, 1, (3, ch, cw))
+    M = np.zeros_like(sub)
+    V = np.zeros_like(sub)
+    t0 = time.perf_counter()
+    res = oracle.loss_and_grad(sub, ocam, gt)
+    oracle.adam(sub, res["G"], M, V, None, np.full(6, 1e-3), step=1)
+    oracle.project(np.ascontiguousarray(P[pick]), ocam)
+    Po = np.ascontiguousarray(P[pick])
+    oracle.adam(Po, np.zeros_like(Po), np.zeros_like(Po), np.zeros_like(Po), None, np.full(6, 1e-3), step=1)
+    dt = time.perf_counter() - t0
+    return dict(seconds=dt, frac=true_frac, crop=(cw, ch), gaussians=int(len(vis)), step_s=dt / true_frac)
+
+
+def cpu_baseline(scene, frac: float = 0.45) -> dict:
+    r = oracle_sample_step(scene, frac)
+    return dict(value=1.0 / r["step_s"], unit="it/s", cores=1, kind="oracle",
+                sample=(f"one oracle step on a centred {r['crop'][0]}x{r['crop'][1]} crop ({r['frac']:.3f} of the "
+                        f"view, {r['gaussians']} visible Gaussians) plus culling and Adam of the same share of the "
+                        f"other Gaussians, {r['seconds']:.1f} s on 1 core, divided by the share"))
+
+
+def reference_arm(args):
+    """The oracle as the reference implementation: K timed steps, each a bounded
+    sample of the workload sized so the whole run takes a few minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2504_06716_gb300 import synth
+
+    scene = synth.surface_scene(WORKLOAD["n_init"], 10, WORKLOAD["views"], WORKLOAD["width"], WORKLOAD["height"])
+    budget = 150.0
+    full_step_s = 70.0  # oracle seconds for one whole step of this workload (measured; sets the share)
+    frac = min(0.12, max(0.002, budget / max(1, args.steps + args.warmup) / full_step_s))
+    for i in range(args.warmup):
+        oracle_sample_step(scene, frac, i)
+    times, samples = [], []
+    for i in range(args.steps):
+        r = oracle_sample_step(scene, frac, 1000 + i)
+        times.append(r["step_s"])
+        samples.append(r["seconds"])
+    its = len(times) / sum(times)
+    line = dict(impl="reference", metric=METRIC, value=its, unit="it/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000.0 / its, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD["workload"], gaussians=WORKLOAD["n_init"],
+                            resolution=f"{WORKLOAD['width']}x{WORKLOAD['height']}", sh_degree=3),
+                cpu_baseline=dict(value=its, unit="it/s", cores=1, kind="oracle",
+                                  sample=f"each step: oracle on a centred crop of {frac:.4f} of a view "
+                                         f"({statistics.mean(samples):.2f} s), time divided by the share"),
+                e2e=dict(value=its, unit="it/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2504_06716_gb300 import lib, pipeline, synth
+    from paper_2504_06716_gb300.schedule import GStaConfig
+    from paper_2504_06716_gb300.train import Trainer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib.load()
+
+    W_, H_ = WORKLOAD["width"], WORKLOAD["height"]
+    scene = synth.surface_scene(WORKLOAD["n_init"], WORKLOAD["n_gt"], WORKLOAD["views"], W_, H_)
+    tr = Trainer(scene, GStaConfig(), tile=WORKLOAD["tile"])
+    m = tr.model
+    # untimed pre-training through the schedule (warmup, calibration, reset, first updates)
+    while tr.k < args.start_iter:
+        tr.iteration(allow_early_stop=False)
+    for _ in range(args.warmup):
+        tr.iteration(allow_early_stop=False)
+    torch.cuda.synchronize()
+    if lib.gs_get_device_error():
+        raise RuntimeError("device error flags set during pre-training")
+
+    stream = torch.cuda.current_stream()
+    # dominant kernel (rasteriser backward) timed live inside the timed region
+    raster_ev = []
+    orig_backward = m.backward
+
+    def backward_split(view, stats=True, stream=None):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lib.gs_raster_bwd(m.splats, view.vals, view.ranges, view.cam, view.t_final, view.n_last, view.dl, m.frozen,
+                          m.grad2d)
+        e1.record()
+        raster_ev.append((e0, e1, tr.order[tr.k]))
+        lib.gs_project_bwd(m.P, m.n, m.sh_degree, view.cam, m.splats, m.act, m.n_active, m.grad2d, m.G,
+                           m.acc_xyz if stats else None, m.acc_rgb if stats else None, m.cnt if stats else None)
+
+    m.backward = backward_split
+    active_before = int(m.n_active.item())
+    k_start = tr.k
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lib.gs_launch_count()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            tr.iteration(allow_early_stop=False)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    launches = lib.gs_launch_count() - launches0
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    m.backward = orig_backward
+    active_after = int(m.n_active.item())
+    flags = lib.gs_get_device_error()
+    its = args.steps * world / (ms / 1000.0)
+
+    # ---- per-stage split (fwd / bwd ms) on the same state, untimed above ----
+    stages = stage_split(tr, 20)
+
+    # ---- plain 3DGS on the same state: all Gaussians active ----
+    plain = plain_rate(tr, max(50, min(args.steps, 300)))
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_kind = _peaks()
+    rb_ms = [a.elapsed_time(b) for a, b, _ in raster_ev]
+    rb_mean = sum(rb_ms) / len(rb_ms)
+    pairs = pairs_per_launch(tr, [v for _, _, v in raster_ev])
+    clk_summary = clk.summary()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lane-instructions per second, in T/s
+    achieved = pairs * RASTER_BWD_OPS_PER_PAIR / (rb_mean / 1e3) / 1e12
+    roofline = dict(bound="alu", kernel="k_raster_bwd", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
+                    frac=achieved / alu_peak, traffic=None,
+                    work_per_unit=f"{RASTER_BWD_OPS_PER_PAIR} FP32 lane-instructions per (pixel, splat) pair up to the"
+                                  f" pixel's last contributor; {pairs:.3e} pairs per launch",
+                    peak_source=f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock of "
+                                f"{peak_kind} peaks file)",
+                    mean_launch_ms=rb_mean)
+    adam = stages.get("adam_roofline")
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = e2e_rate(tr, max(30, min(args.steps, 200)))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene)
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=its, unit="it/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                    data="synthetic",
+                    config=dict(workload=WORKLOAD["workload"], gaussians=WORKLOAD["n_init"],
+                                resolution=f"{W_}x{H_}", sh_degree=3, tile=WORKLOAD["tile"], views=WORKLOAD["views"],
+                                start_iter=k_start, active_gaussians_start=active_before,
+                                active_gaussians_end=active_after, thresholds_eps0=list(tr.eps0),
+                                l2="working set (P, G, m, v = 1 GB) larger than L2; no flush",
+                                parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+                    fwd_ms=stages["fwd_ms"], bwd_ms=stages["bwd_ms"], stage_ms=stages["stage_ms"],
+                    plain_its=plain["its"], plain_stage_ms=plain["stage_ms"], gsta_speedup_vs_plain=its / world /
+                    plain["its"],
+                    roofline=roofline, roofline_adam=adam, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
+                    clocks=clk_summary, device_flags=flags)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# Algorithmic FP32 work of the rasteriser backward per (pixel, splat) pair, counted
+# from its formula: offset (2), exponent (8), exp and opacity (3), alpha floor/cap
+# tests (3), transmittance recovery (2), colour-behind update (9), dL/dalpha (10),
+# colour gradient (4), opacity/exponent gradient (3), conic and mean gradients (12).
+RASTER_BWD_OPS_PER_PAIR = 56
+
+
+def pairs_per_launch(tr, views) -> float:
+    """Sum over pixels of the list position of the last contributor, averaged
+    over the views of the timed launches (re-rendered after timing)."""
+    import torch
+
+    m, view = tr.model, tr.view
+    tot = 0
+    sample = views[:: max(1, len(views) // 16)]
+    for v in sample:
+        m.retarget(view, tr.cams[v])
+        m.rasterize(view)
+        tot += int(view.n_last.to(torch.int64).sum().item())
+    return tot / len(sample)
+
+
+def stage_split(tr, n) -> dict:
+    import torch
+
+    from paper_2504_06716_gb300 import lib
+
+    m, view = tr.model, tr.view
+    names = ["project", "sort", "render", "loss", "raster_bwd", "project_bwd", "adam"]
+    acc = {k: 0.0 for k in names}
+    lrs = list(tr.lrs)
+    for i in range(n):
+        v = tr.order[tr.k + i]
+        m.retarget(view, tr.cams[v])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        ev[0].record()
+        lib.gs_project(m.P, m.n, m.sh_degree, view.cam, m.splats)
+        ev[1].record()
+        lib.gs_sort(m.splats, m.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count)
+        ev[2].record()
+        lib.gs_render_fwd(m.splats, view.vals, view.ranges, view.cam, view.image, view.t_final, view.n_last)
+        ev[3].record()
+        m.loss(view, tr.targets[v])
+        ev[4].record()
+        lib.gs_raster_bwd(m.splats, view.vals, view.ranges, view.cam, view.t_final, view.n_last, view.dl, m.frozen,
+                          m.grad2d)
+        ev[5].record()
+        lib.gs_project_bwd(m.P, m.n, m.sh_degree, view.cam, m.splats, m.act, m.n_active, m.grad2d, m.G, m.acc_xyz,
+                           m.acc_rgb, m.cnt)
+        ev[6].record()
+        m.adam(lrs)
+        ev[7].record()
+        torch.cuda.synchronize()
+        for j, k in enumerate(names):
+            acc[k] += ev[j].elapsed_time(ev[j + 1])
+    st = {k: v / n for k, v in acc.items()}
+    peaks, kind = _peaks()
+    n_act = int(m.n_active.item())
+    adam_bytes = n_act * 15 * 16 * 7  # read P, G, m, v and write P, m, v: 15 16-byte vectors each
+    adam_gbs = adam_bytes / (st["adam"] / 1e3) / 1e9
+    return dict(stage_ms=st, fwd_ms=st["project"] + st["sort"] + st["render"],
+                bwd_ms=st["loss"] + st["raster_bwd"] + st["project_bwd"],
+                adam_roofline=dict(bound="hbm", kernel="k_adam", achieved=adam_gbs, peak=peaks["hbm_gbs"],
+                                   unit="GB/s", frac=adam_gbs / peaks["hbm_gbs"], traffic=None,
+                                   bytes_per_active_gaussian=15 * 16 * 7, active=n_act, peak_source=kind))
+
+
+def plain_rate(tr, n) -> dict:
+    """Plain 3DGS iterations (no freezing) from the current state."""
+    import torch
+
+    m = tr.model
+    saved = (m.frozen.clone(), m.act.clone(), m.n_active.clone())
+    m.freeze_update(0.0, 0.0, 1)
+    for i in range(5):
+        v = tr.order[i]
+        m.retarget(tr.view, tr.cams[v])
+        m.train_step(tr.view, tr.targets[v], tr.lrs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(n):
+        v = tr.order[i]
+        m.retarget(tr.view, tr.cams[v])
+        m.train_step(tr.view, tr.targets[v], tr.lrs)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = stage_split(tr, 10)["stage_ms"]
+    m.frozen.copy_(saved[0])
+    m.act.copy_(saved[1])
+    m.n_active.copy_(saved[2])
+    return dict(its=n / (ms / 1e3), stage_ms=st)
+
+
+def e2e_rate(tr, n) -> dict:
+    """Same iterations through the public API with host buffers: each step copies
+    its target image from pinned host memory and reads the loss back."""
+    import torch
+
+    m, view = tr.model, tr.view
+    views = [tr.order[i] for i in range(n)]
+    host = {v: tr.targets[v].cpu().pin_memory() for v in set(views)}
+    dev = torch.empty_like(tr.targets[views[0]])
+    loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for v in views:
+        dev.copy_(host[v], non_blocking=True)
+        m.retarget(view, tr.cams[v])
+        m.train_step(view, dev, tr.lrs)
+        loss_host.copy_(view.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    dt = time.perf_counter() - t0
+    return dict(value=n / dt, unit="it/s", h2d_bytes_per_step=int(dev.numel() * 4), d2h_bytes_per_step=4,
+                note="host-pinned target upload and loss read-back every step; freeze map as in the timed region")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["gsta", "reference"], default="gsta")
+    ap.add_argument("--start-iter", type=int, default=4750)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()
