@@ -192,6 +192,27 @@ int gs_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, ui
                      float eps_rgb, int32_t mode, int32_t *act, int32_t *n_active_dev, void *ws, size_t ws_bytes,
                      gs_stream_t stream);
 
+/* gs_freeze_update without a workspace argument. The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * where they make the call -- for example a host that owns every device
+ * buffer and hands this library only the inputs and outputs, or a loop that
+ * must not call cudaMalloc because an allocation can synchronise the whole
+ * device. Its scratch (one count per 1024 Gaussians) is a fixed 256 KB array
+ * inside the library that every GPU which loads the library keeps until the
+ * process exits; it allows n <= 67,108,864 and returns GS_ERR_INVALID_ARG for
+ * more. The first call on a device, made with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. All calls share the one array: each call writes
+ * every entry it reads before reading it, so nothing has to be cleared
+ * between calls, but calls whose executions overlap on the GPU (other
+ * streams, other host threads) race on it and must be ordered by the caller.
+ * Allocates nothing (no cudaMalloc, no library allocator). Arguments,
+ * results and errors are those of gs_freeze_update; GS_ERR_CUDA also if the
+ * address lookup fails. */
+int gs_freeze_update_noalloc(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen,
+                             float eps_xyz, float eps_rgb, int32_t mode, int32_t *act, int32_t *n_active_dev,
+                             gs_stream_t stream);
+
 /* Sec. 3.2.4 (the optimiser only updates Gaussians that are not frozen).
  * Adam at global step `step` >= 1 for the rows act[0 .. *n_active_dev) of
  * P, with gradient G and moments m, v (all [n][64]):

@@ -174,3 +174,57 @@ extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int6
     note_launches(1);
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// gs_freeze_update_noalloc: the same freeze update with its scratch (one count
+// per block of 1024 Gaussians) in a fixed array inside the library, for
+// callers that cannot allocate device memory where they call it.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gs {
+namespace {
+
+constexpr int kNoAllocBlocks = 65536;  // 256 KB of counts: n <= 65536 * 1024
+static __device__ __align__(256) int32_t g_freeze_scratch[kNoAllocBlocks];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_scratch_mu;
+int32_t *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_freeze_scratch on the current device, looked up once per
+// device. Returns nullptr if the lookup fails.
+int32_t *scratch_on_current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_freeze_scratch) != cudaSuccess) return nullptr;
+        g_scratch_ptr[dev] = static_cast<int32_t *>(p);
+    }
+    return g_scratch_ptr[dev];
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_freeze_update_noalloc(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen,
+                                        float eps_xyz, float eps_rgb, int32_t mode, int32_t *act,
+                                        int32_t *n_active_dev, gs_stream_t stream) {
+    if (n < 0 || n > (int64_t)kNoAllocBlocks * kFB || mode < 0 || mode > 2 || !n_active_dev)
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!acc_xyz || !acc_rgb || !cnt || !frozen || !act)) return GS_ERR_INVALID_ARG;
+    int32_t *part = scratch_on_current_device();
+    if (!part) return GS_ERR_CUDA;
+    // Every count the scan reads is written by k_freeze_mark in the same call,
+    // so nothing left in the array by an earlier call needs clearing.
+    cudaStream_t s = as_stream(stream);
+    int nb = (int)((n + kFB - 1) / kFB);
+    if (nb > 0)
+        k_freeze_mark<<<nb, kFB, 0, s>>>(n, acc_xyz, acc_rgb, cnt, frozen, eps_xyz, eps_rgb, mode, part);
+    k_freeze_scan<<<1, 1024, 0, s>>>(part, nb, n_active_dev);
+    if (nb > 0) k_freeze_emit<<<nb, kFB, 0, s>>>(n, frozen, part, act);
+    note_launches(nb > 0 ? 3 : 1);
+    return launch_status();
+}

@@ -73,6 +73,7 @@ _SIGS = {
     "gs_render_bwd": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "gs_freeze_workspace_bytes": ([_I64], _SZ),
     "gs_freeze_update": ([_I64, _P, _P, _P, _P, _F32, _F32, _I32, _P, _P, _P, _SZ, _P], _I32),
+    "gs_freeze_update_noalloc": ([_I64, _P, _P, _P, _P, _F32, _F32, _I32, _P, _P, _P], _I32),
     "gs_adam_masked": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_float), _F32, _F32, _F32, _I64, _P],
                        _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
@@ -224,6 +225,17 @@ def gs_freeze_update(n: int, acc_xyz, acc_rgb, cnt, frozen, eps_xyz: float, eps_
         _ptr(cnt, torch.int32, "cnt"), _ptr(frozen, torch.uint8, "frozen"), eps_xyz, eps_rgb, mode,
         _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(ws, torch.uint8, "ws"),
         ws.numel(), _stream(stream)))
+
+
+def gs_freeze_update_noalloc(n: int, acc_xyz, acc_rgb, cnt, frozen, eps_xyz: float, eps_rgb: float, mode: int, act,
+                             n_active, stream=None):
+    """gs_freeze_update with the library's fixed scratch array instead of a workspace."""
+    import torch
+
+    _check("gs_freeze_update_noalloc", load().gs_freeze_update_noalloc(
+        n, _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _ptr(frozen, torch.uint8, "frozen"), eps_xyz, eps_rgb, mode,
+        _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _stream(stream)))
 
 
 def gs_adam_masked(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, eps: float, step: int, stream=None):
