@@ -210,6 +210,11 @@ def gpu_arm(args):
 
     W_, H_ = WORKLOAD["width"], WORKLOAD["height"]
     scene = synth.surface_scene(WORKLOAD["n_init"], WORKLOAD["n_gt"], WORKLOAD["views"], W_, H_)
+    if args.views < WORKLOAD["views"]:  # smaller profiling case: fewer targets on the device
+        keep = set(scene.train_views[:args.views])
+        scene.train_views = sorted(keep)
+        scene.test_views = scene.test_views[:2]
+        scene.subset_views = scene.train_views[:2]
     tr = Trainer(scene, GStaConfig(), tile=WORKLOAD["tile"])
     m = tr.model
     # untimed pre-training through the schedule (warmup, calibration, reset, first updates)
@@ -247,11 +252,13 @@ def gpu_arm(args):
     with ClockSampler(local) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
         t0.record(stream)
         for _ in range(args.steps):
             tr.iteration(allow_early_stop=False)
         t1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = lib.gs_launch_count() - launches0
     ms = t0.elapsed_time(t1)
     if world > 1:
@@ -441,6 +448,8 @@ def main():
     ap.add_argument("--impl", choices=["gsta", "reference"], default="gsta")
     ap.add_argument("--start-iter", type=int, default=4750)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--views", type=int, default=WORKLOAD["views"],
+                    help="train on the first N training views only (smaller device footprint for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -51,17 +51,20 @@ class View:
 class Model:
     """Gaussian parameters, Adam moments, freeze state and per-step scratch on one GPU."""
 
-    def __init__(self, params59: np.ndarray, sh_degree: int = 3, device="cuda"):
+    def __init__(self, params59: np.ndarray, sh_degree: int = 3, device="cuda", trainable: bool = True):
         self.device = torch.device(device)
         self.n = int(params59.shape[0])
         self.sh_degree = sh_degree
         n = self.n
         f32 = dict(dtype=torch.float32, device=self.device)
         self.P = pack_params(params59, self.device)
+        self.splats = torch.zeros((n, lib.SPLAT), **f32)
+        self.step_count = 0
+        if not trainable:  # render-only (targets): no gradients, moments or freeze state
+            return
         self.G = torch.zeros((n, lib.ROW), **f32)
         self.m = torch.zeros((n, lib.ROW), **f32)
         self.v = torch.zeros((n, lib.ROW), **f32)
-        self.splats = torch.zeros((n, lib.SPLAT), **f32)
         self.grad2d = torch.zeros((n, lib.GRAD2D), **f32)
         self.frozen = torch.zeros(n, dtype=torch.uint8, device=self.device)
         self.act = torch.arange(n, dtype=torch.int32, device=self.device)
@@ -70,10 +73,9 @@ class Model:
         self.acc_rgb = torch.zeros(n, **f32)
         self.cnt = torch.zeros(n, dtype=torch.int32, device=self.device)
         self.freeze_ws = torch.zeros(max(lib.gs_freeze_workspace_bytes(n), 256), dtype=torch.uint8, device=self.device)
-        self.step_count = 0
 
     # ---- views ----
-    def make_view(self, cam: lib.GsCamera, capacity: int) -> View:
+    def make_view(self, cam: lib.GsCamera, capacity: int, trainable: bool = True) -> View:
         H, W = cam.height, cam.width
         dev = self.device
         return View(
@@ -81,9 +83,10 @@ class Model:
             image=torch.zeros((3, H, W), dtype=torch.float32, device=dev),
             t_final=torch.zeros((H, W), dtype=torch.float32, device=dev),
             n_last=torch.zeros((H, W), dtype=torch.int32, device=dev),
-            dl=torch.zeros((3, H, W), dtype=torch.float32, device=dev),
+            dl=torch.zeros((3, H, W) if trainable else (1,), dtype=torch.float32, device=dev),
             loss=torch.zeros(1, dtype=torch.float32, device=dev),
-            loss_ws=torch.zeros(lib.gs_loss_workspace_bytes(H, W), dtype=torch.uint8, device=dev),
+            loss_ws=torch.zeros(lib.gs_loss_workspace_bytes(H, W) if trainable else 1, dtype=torch.uint8,
+                                device=dev),
             vals=torch.zeros(max(capacity, 1), dtype=torch.int32, device=dev),
             ranges=torch.zeros((cam.tiles, 2), dtype=torch.int32, device=dev),
             count=torch.zeros(1, dtype=torch.int64, device=dev),

@@ -39,9 +39,9 @@ class Trainer:
         self.device = torch.device(device)
         # targets rendered from the ground-truth set
         gt_views = sorted(set(scene.train_views) | set(scene.test_views))
-        gtm = pipeline.Model(scene.gt, device=self.device)
+        gtm = pipeline.Model(scene.gt, device=self.device, trainable=False)
         gcap = gtm.measure_capacity([self.cams[v] for v in gt_views])
-        gv = gtm.make_view(self.cams[gt_views[0]], gcap)
+        gv = gtm.make_view(self.cams[gt_views[0]], gcap, trainable=False)
         self.targets = {}
         for v in gt_views:
             gtm.retarget(gv, self.cams[v])
