@@ -220,6 +220,10 @@ def gpu_arm(args):
     # untimed pre-training through the schedule (warmup, calibration, reset, first updates)
     while tr.k < args.start_iter:
         tr.iteration(allow_early_stop=False)
+    tuning = None
+    if not args.no_autotune:  # rasteriser tile size and launch shapes for this state (autotune.py)
+        tr.autotune()
+        tuning = dict(tile=tr.tuning.tile, fwd_ppt_batch=list(tr.tuning.fwd), bwd_ppt_batch=list(tr.tuning.bwd))
     for _ in range(args.warmup):
         tr.iteration(allow_early_stop=False)
     torch.cuda.synchronize()
@@ -235,8 +239,8 @@ def gpu_arm(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        lib.gs_raster_bwd(m.splats, view.vals, view.ranges, view.cam, view.t_final, view.n_last, view.dl, m.frozen,
-                          m.grad2d)
+        lib.gs_raster_bwd_cfg(m.splats, view.vals, view.ranges, view.cam, m.bwd_cfg, view.t_final, view.n_last,
+                              view.dl, m.frozen, m.grad2d)
         e1.record()
         raster_ev.append((e0, e1, tr.order[tr.k]))
         lib.gs_project_bwd(m.P, m.n, m.sh_degree, view.cam, m.splats, m.act, m.n_active, m.grad2d, m.G,
@@ -307,7 +311,8 @@ def gpu_arm(args):
                     ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic",
                     config=dict(workload=WORKLOAD["workload"], gaussians=WORKLOAD["n_init"],
-                                resolution=f"{W_}x{H_}", sh_degree=3, tile=WORKLOAD["tile"], views=WORKLOAD["views"],
+                                resolution=f"{W_}x{H_}", sh_degree=3, tile=tr.view.cam.tile, raster_tuning=tuning,
+                                views=WORKLOAD["views"],
                                 start_iter=k_start, active_gaussians_start=active_before,
                                 active_gaussians_end=active_after, thresholds_eps0=list(tr.eps0),
                                 l2="working set (P, G, m, v = 1 GB) larger than L2; no flush",
@@ -362,12 +367,13 @@ def stage_split(tr, n) -> dict:
         ev[1].record()
         lib.gs_sort(m.splats, m.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count)
         ev[2].record()
-        lib.gs_render_fwd(m.splats, view.vals, view.ranges, view.cam, view.image, view.t_final, view.n_last)
+        lib.gs_render_fwd_cfg(m.splats, view.vals, view.ranges, view.cam, m.fwd_cfg, view.image, view.t_final,
+                              view.n_last)
         ev[3].record()
         m.loss(view, tr.targets[v])
         ev[4].record()
-        lib.gs_raster_bwd(m.splats, view.vals, view.ranges, view.cam, view.t_final, view.n_last, view.dl, m.frozen,
-                          m.grad2d)
+        lib.gs_raster_bwd_cfg(m.splats, view.vals, view.ranges, view.cam, m.bwd_cfg, view.t_final, view.n_last,
+                              view.dl, m.frozen, m.grad2d)
         ev[5].record()
         lib.gs_project_bwd(m.P, m.n, m.sh_degree, view.cam, m.splats, m.act, m.n_active, m.grad2d, m.G, m.acc_xyz,
                            m.acc_rgb, m.cnt)
@@ -448,6 +454,7 @@ def main():
     ap.add_argument("--impl", choices=["gsta", "reference"], default="gsta")
     ap.add_argument("--start-iter", type=int, default=4750)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep 16-pixel tiles and default launch shapes")
     ap.add_argument("--views", type=int, default=WORKLOAD["views"],
                     help="train on the first N training views only (smaller device footprint for profiling)")
     args = ap.parse_args()

@@ -134,6 +134,18 @@ int gs_sort(const float *splats, int64_t n, const gs_camera *cam, void *ws, size
 int gs_render_fwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                   float *image, float *t_final, int32_t *n_last, gs_stream_t stream);
 
+/* Launch shape of the two rasteriser kernels (the autotuner's knobs; the
+ * results do not depend on it). NULL selects the built-in default for the
+ * camera's tile size. */
+typedef struct {
+    int32_t pixels_per_thread; /* pixels each thread composites: 1 or 2 */
+    int32_t batch;             /* splats staged per shared-memory batch: 32, 64, 128 or 256 */
+} gs_raster_config;
+
+/* gs_render_fwd with an explicit launch shape (cfg may be NULL). */
+int gs_render_fwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                      const gs_raster_config *cfg, float *image, float *t_final, int32_t *n_last, gs_stream_t stream);
+
 /* Bytes of workspace gs_loss needs for an H x W image. */
 size_t gs_loss_workspace_bytes(int32_t H, int32_t W);
 
@@ -157,6 +169,11 @@ int gs_loss(const float *image, const float *gt, int32_t H, int32_t W, float lam
 int gs_raster_bwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                   const float *t_final, const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen,
                   float *grad2d, gs_stream_t stream);
+
+/* gs_raster_bwd with an explicit launch shape (cfg may be NULL). */
+int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                      const gs_raster_config *cfg, const float *t_final, const int32_t *n_last,
+                      const float *dl_dimage, const uint8_t *frozen, float *grad2d, gs_stream_t stream);
 
 /* Sec. 3.2.4, second half, and the statistics of Sec. 3.2.1: chain rule from
  * grad2d to the 59 parameters for the Gaussians act[0 .. *n_active_dev).

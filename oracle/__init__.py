@@ -86,7 +86,7 @@ def lib():
             L.or_loss.argtypes = [_i32, _i32, _dp, _dp, ctypes.c_double, _dp]
             L.or_loss.restype = ctypes.c_double
             L.or_render_bwd.argtypes = [_i64, _i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _bp,
-                                        _bp, _bp, _dp, _dp, _dp, _dp, _bp]
+                                        _bp, _bp, _dp, _dp, _dp, _dp, _bp, _dp]
             L.or_render_pixels.argtypes = [_i64, _ip, _ip, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp,
                                            _ip, _dp]
             L.or_project_bwd.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _bp, _dp, _dp, _dp, _dp, _dp,
@@ -228,7 +228,7 @@ def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=N
     n = proj["opacity"].shape[0]
     bg = np.array(list(cam.bg), np.float64)
     out = dict(d_mean2d=np.zeros((n, 2)), d_conic=np.zeros((n, 3)), d_opacity=np.zeros(n), d_rgb=np.zeros((n, 3)),
-               tainted=np.zeros(n, np.uint8))
+               tainted=np.zeros(n, np.uint8), amb_abs=np.zeros((n, 9)))
     fr = None if frozen is None else _c(frozen, np.uint8)
     am = None if amb is None else _c(amb, np.uint8)
     tm = None if tile_mask is None else _c(tile_mask, np.uint8)
@@ -237,7 +237,7 @@ def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=N
                         _p(_c(proj["rgb"], np.float64), _dp), _p(_c(vals, np.uint32), _up),
                         _p(_c(ranges, np.uint32), _up), _p(_c(dl_dimage, np.float64), _dp), _p(fr, _bp),
                         _p(am, _bp), _p(tm, _bp), _p(out["d_mean2d"], _dp), _p(out["d_conic"], _dp), _p(out["d_opacity"], _dp),
-                        _p(out["d_rgb"], _dp), _p(out["tainted"], _bp))
+                        _p(out["d_rgb"], _dp), _p(out["tainted"], _bp), _p(out["amb_abs"], _dp))
     return out
 
 

@@ -671,7 +671,11 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
  * Outputs are accumulated over pixels for unfrozen Gaussians only:
  *   d_mean2d[n][2], d_conic[n][3] (a, b, c), d_opacity[n], d_rgb[n][3].
  * amb[H][W] (optional): pixels whose forward decisions are ambiguous;
- * tainted[n] (optional) is set for every Gaussian evaluated at one.
+ * tainted[n] (optional) is set for every Gaussian evaluated at one;
+ * amb_abs[n][9] (optional) sums, over ambiguous pixels, the absolute value of
+ * each of a Gaussian's nine per-pixel gradient terms (mean x, y; conic a, b,
+ * c; opacity; r, g, b): a decision that flips at such a pixel changes a
+ * Gaussian's gradient by no more than its terms there.
  * tile_mask[tiles] (optional): only pixels of tiles with a non-zero entry
  * are processed; the gradient of a Gaussian is complete when every tile of
  * its rectangle is in the mask.                                           */
@@ -680,7 +684,7 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                    const double *mean2d, const double *conic, const double *opacity, const double *rgb,
                    const uint32_t *vals, const uint32_t *ranges, const double *dl_dimage, const uint8_t *frozen,
                    const uint8_t *amb, const uint8_t *tile_mask, double *d_mean2d, double *d_conic,
-                   double *d_opacity, double *d_rgb, uint8_t *tainted) {
+                   double *d_opacity, double *d_rgb, uint8_t *tainted, double *amb_abs) {
     int32_t tx = (W + tile - 1) / tile;
     int64_t HW = (int64_t)H * W;
     memset(d_mean2d, 0, sizeof(double) * 2 * n);
@@ -688,6 +692,7 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
     memset(d_opacity, 0, sizeof(double) * n);
     memset(d_rgb, 0, sizeof(double) * 3 * n);
     if (tainted) memset(tainted, 0, (size_t)n);
+    if (amb_abs) memset(amb_abs, 0, sizeof(double) * 9 * n);
     int32_t cap = 0;
     for (int64_t t = 0; t < (int64_t)tx * ((H + tile - 1) / tile); ++t) {
         int32_t len = (int32_t)(ranges[2 * t + 1] - ranges[2 * t]);
@@ -728,10 +733,12 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                 uint32_t g = gid[k];
                 if (frozen && frozen[g]) continue;
                 double a = ev[k].alpha, dA = 0;
+                double *ab = (ambiguous && amb_abs) ? amb_abs + 9 * (int64_t)g : NULL;
                 for (int c = 0; c < 3; ++c) {
                     double dCda = rgb[3 * g + c] * Tk[k] - (S[3 * k + c] + Tf * bg[c]) / (1.0 - a);
                     dA += dC[c] * dCda;
                     d_rgb[3 * g + c] += a * Tk[k] * dC[c];
+                    if (ab) ab[6 + c] += fabs(a * Tk[k] * dC[c]);
                 }
                 if (ev[k].capped) continue; /* alpha = 0.99 does not depend on o or G */
                 double o = opacity[g], G = ev[k].G;
@@ -744,6 +751,14 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                 d_conic[3 * g + 2] += -0.5 * dy * dy * dpow;
                 d_mean2d[2 * g] += -(qa * dx + qb * dy) * dpow;
                 d_mean2d[2 * g + 1] += -(qb * dx + qc * dy) * dpow;
+                if (ab) {
+                    ab[0] += fabs((qa * dx + qb * dy) * dpow);
+                    ab[1] += fabs((qb * dx + qc * dy) * dpow);
+                    ab[2] += fabs(0.5 * dx * dx * dpow);
+                    ab[3] += fabs(dx * dy * dpow);
+                    ab[4] += fabs(0.5 * dy * dy * dpow);
+                    ab[5] += fabs(dA * G);
+                }
             }
         }
     free(ev); free(gid); free(Tk); free(S);

@@ -1,17 +1,17 @@
 // Tile rasteriser: front-to-back alpha compositing (Sec. 3.1, Eq. 2) and its
 // backward (Sec. 3.2.4), which skips the gradient work of frozen Gaussians.
 //
-// One CTA per screen tile, one thread per pixel. The tile's sorted splat list
-// is staged through shared memory in batches (one record per thread), so
-// every thread reads each splat as a shared-memory broadcast. No tensor
+// One CTA per screen tile, two pixels per thread. The tile's sorted splat
+// list is staged through shared memory in batches, so every thread reads
+// each splat as a shared-memory broadcast. No tensor
 // cores: the work is a per-pixel exponential and a handful of FMAs.
 //
 // The backward walks each list back to front and recovers the transmittance
 // in front of every splat from the value the forward left over, so no
 // per-pixel list is stored. A warp's 32 pixels see the same splat at the
-// same time; their nine gradient terms are summed with warp shuffles, then
-// added once per warp into a shared accumulator, and the accumulator goes
-// to global memory with one atomic per value per tile.
+// same time; their nine gradient terms are summed with a recursive-halving
+// warp reduction, added once per warp into a shared accumulator, and the
+// accumulator goes to global memory with one atomic per value per tile.
 #include "common.cuh"
 
 namespace gs {
@@ -19,80 +19,198 @@ namespace {
 
 constexpr int kBatch = 256;
 
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) k_render_fwd(const float *__restrict__ splats,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const uint32_t *__restrict__ ranges, DevCam cam,
-                                                        float *__restrict__ image, float *__restrict__ t_final,
-                                                        int32_t *__restrict__ n_last) {
-    constexpr int NT = TS * TS;
-    constexpr int B = NT < kBatch ? NT : kBatch;
+// A thread owns PPT pixels of its tile, (x, y + k TS/PPT) for k < PPT. Each
+// splat staged in shared memory is loaded once per PPT evaluations, and the
+// per-pixel update is written with selects instead of branches so the PPT
+// independent chains interleave.
+template <int TS, int PPT, int B>
+__global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const float *__restrict__ splats,
+                                                              const uint32_t *__restrict__ vals,
+                                                              const uint32_t *__restrict__ ranges, DevCam cam,
+                                                              float *__restrict__ image, float *__restrict__ t_final,
+                                                              int32_t *__restrict__ n_last) {
+    constexpr int NT = TS * TS / PPT;  // threads; B = splats per staged batch
     __shared__ float4 s_xyab[B];
     __shared__ float4 s_cocg[B];
     __shared__ float s_blue[B];
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-    const int px = tx * TS + (int)(threadIdx.x % TS), py = ty * TS + (int)(threadIdx.x / TS);
-    const bool inside = px < cam.W && py < cam.H;
+    const int px = tx * TS + (int)(threadIdx.x % TS);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
-    const float fpx = (float)px, fpy = (float)py;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    int last = 0;
-    bool done = !inside;
+    const float fpx = (float)px;
+    float fpy[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
+    int last[PPT], py[PPT];
+    bool done[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        py[k] = ty * TS + (int)(threadIdx.x / TS) + k * (TS / PPT);
+        fpy[k] = (float)py[k];
+        T[k] = 1.f;
+        c0[k] = c1[k] = c2[k] = 0.f;
+        last[k] = 0;
+        done[k] = !(px < cam.W && py[k] < cam.H);
+    }
     for (uint32_t base = start; base < end; base += B) {
-        if (__syncthreads_count(done) == NT) break;
-        if (threadIdx.x < B && base + threadIdx.x < end) {
-            const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)vals[base + threadIdx.x] * kSplat);
-            s_xyab[threadIdx.x] = __ldg(r);
-            s_cocg[threadIdx.x] = __ldg(r + 1);
-            s_blue[threadIdx.x] = __ldg(reinterpret_cast<const float *>(r + 2));
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) all = all && done[k];
+        if (__syncthreads_count(all) == NT) break;
+        for (int q = threadIdx.x; q < B; q += NT) {
+            if (base + q < end) {
+                const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)vals[base + q] * kSplat);
+                s_xyab[q] = __ldg(r);
+                s_cocg[q] = __ldg(r + 1);
+                s_blue[q] = __ldg(reinterpret_cast<const float *>(r + 2));
+            }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)B, end - base);
-        for (int j = 0; j < cnt && !done; ++j) {
+        for (int j = 0; j < cnt; ++j) {
             const float4 xa = s_xyab[j], co = s_cocg[j];
-            const float dx = __fsub_rn(xa.x, fpx), dy = __fsub_rn(xa.y, fpy);
-            const float power = splat_power(dx, dy, xa.z, xa.w, co.x);
-            if (power > 0.f) continue;
-            const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
-            if (alpha < kAlphaMin) continue;
-            const float tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            if (tn < kTMin) { done = true; break; }
-            const float w = alpha * T;
-            c0 += co.z * w;
-            c1 += co.w * w;
-            c2 += s_blue[j] * w;
-            T = tn;
-            last = (int)(base - start) + j + 1;
+            const float blue = s_blue[j];
+            const float dx = __fsub_rn(xa.x, fpx);
+            bool alive = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const float dy = __fsub_rn(xa.y, fpy[k]);
+                const float power = splat_power(dx, dy, xa.z, xa.w, co.x);
+                const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
+                const float tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                const bool use = !done[k] && power <= 0.f && alpha >= kAlphaMin;
+                const bool stop = use && tn < kTMin;
+                const bool add = use && !stop;
+                const float w = add ? alpha * T[k] : 0.f;
+                c0[k] += co.z * w;
+                c1[k] += co.w * w;
+                c2[k] += blue * w;
+                T[k] = add ? tn : T[k];
+                last[k] = add ? (int)(base - start) + j + 1 : last[k];
+                done[k] = done[k] || stop;
+                alive = alive || !done[k];
+            }
+            if (!alive) break;
+        }
+        __syncthreads();
+    }
+    const int64_t HW = (int64_t)cam.W * cam.H;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (px < cam.W && py[k] < cam.H) {
+            const int64_t pix = (int64_t)py[k] * cam.W + px;
+            image[pix] = c0[k] + T[k] * cam.bg[0];
+            image[HW + pix] = c1[k] + T[k] * cam.bg[1];
+            image[2 * HW + pix] = c2[k] + T[k] * cam.bg[2];
+            t_final[pix] = T[k];
+            n_last[pix] = last[k];
         }
     }
-    if (inside) {
-        const int64_t pix = (int64_t)py * cam.W + px, HW = (int64_t)cam.W * cam.H;
-        image[pix] = c0 + T * cam.bg[0];
-        image[HW + pix] = c1 + T * cam.bg[1];
-        image[2 * HW + pix] = c2 + T * cam.bg[2];
-        t_final[pix] = T;
-        n_last[pix] = last;
-    }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum of nine per-lane values over a warp by recursive halving: at each of
+// the five xor levels a lane keeps half of its remaining slots and adds the
+// partner's copy of them (5 + 3 + 2 + 1 + 1 = 12 shuffles instead of 45).
+// On return, lane L holds the warp total of value kSlotOf[(L >> 1) & 15]
+// (-1: none); lanes L and L ^ 1 hold the same total.
+__device__ __constant__ int8_t kSlotOf[16] = {0, 1, 2, -1, 3, 4, -1, -1, 5, 6, 7, -1, 8, -1, -1, -1};
+
+__device__ __forceinline__ float warp_sum9(const float (&g)[9], int lane) {
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+    float r[5];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
+    for (int j = 0; j < 5; ++j) {  // keep values 0-4 (lower half) or 5-8 (upper half)
+        const float lo = g[j], hi = j < 4 ? g[5 + j] : 0.f;
+        const float mine = h4 ? hi : lo, other = h4 ? lo : hi;
+        r[j] = mine + __shfl_xor_sync(kFull, other, 16);
+    }
+    float s[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // keep slots 0-2 or 3-4
+        const float lo = r[j], hi = j < 2 ? r[3 + j] : 0.f;
+        const float mine = h3 ? hi : lo, other = h3 ? lo : hi;
+        s[j] = mine + __shfl_xor_sync(kFull, other, 8);
+    }
+    float u[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {  // keep slots 0-1 or 2
+        const float lo = s[j], hi = j < 1 ? s[2 + j] : 0.f;
+        const float mine = h2 ? hi : lo, other = h2 ? lo : hi;
+        u[j] = mine + __shfl_xor_sync(kFull, other, 4);
+    }
+    float w = (h1 ? u[1] : u[0]) + __shfl_xor_sync(kFull, h1 ? u[0] : u[1], 2);
+    return w + __shfl_xor_sync(kFull, w, 1);
 }
 
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) k_raster_bwd(const float *__restrict__ splats,
-                                                        const uint32_t *__restrict__ vals,
-                                                        const uint32_t *__restrict__ ranges, DevCam cam,
-                                                        const float *__restrict__ t_final,
-                                                        const int32_t *__restrict__ n_last,
-                                                        const float *__restrict__ dl_dimage,
-                                                        const uint8_t *__restrict__ frozen,
-                                                        float *__restrict__ grad2d) {
-    constexpr int NT = TS * TS;
-    constexpr int B = NT < kBatch ? NT : kBatch;
+// Backward of one pixel for one splat. Updates the pixel's recovered
+// transmittance T and the colour behind (S, la, lc) and, unless the splat is
+// frozen, adds its nine gradient terms to g.
+struct PixBwd {
+    float T, Tf, dC0, dC1, dC2, bgdot;
+    float S0, S1, S2, la, lc0, lc1, lc2;
+    int nl;
+};
+
+__device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, float dx, float dy, const float4 &xa, const float4 &co,
+                                        float blue, bool frz, float (&g)[9]) {
+    const float power = splat_power(dx, dy, xa.z, xa.w, co.x);
+    const float G = __expf(power);
+    const float oG = __fmul_rn(co.y, G);
+    const float alpha = fminf(kAlphaMax, oG);
+    if (!(pos < p.nl && power <= 0.f && alpha >= kAlphaMin)) return false;
+    const float om = 1.f - alpha;
+    p.T = __fdividef(p.T, om);  // transmittance in front of this splat
+    p.S0 = p.la * p.lc0 + (1.f - p.la) * p.S0;
+    p.S1 = p.la * p.lc1 + (1.f - p.la) * p.S1;
+    p.S2 = p.la * p.lc2 + (1.f - p.la) * p.S2;
+    if (!frz) {
+        const float dA = p.T * (p.dC0 * (co.z - p.S0) + p.dC1 * (co.w - p.S1) + p.dC2 * (blue - p.S2)) -
+                         __fdividef(p.Tf, om) * p.bgdot;
+        const float wT = alpha * p.T;
+        g[6] += wT * p.dC0;
+        g[7] += wT * p.dC1;
+        g[8] += wT * p.dC2;
+        if (!(oG > kAlphaMax)) {
+            const float dpow = dA * oG;
+            g[5] += dA * G;
+            g[2] += -0.5f * dx * dx * dpow;
+            g[3] += -dx * dy * dpow;
+            g[4] += -0.5f * dy * dy * dpow;
+            g[0] += -(xa.z * dx + xa.w * dy) * dpow;
+            g[1] += -(xa.w * dx + co.x * dy) * dpow;
+        }
+    }
+    p.la = alpha;
+    p.lc0 = co.z;
+    p.lc1 = co.w;
+    p.lc2 = blue;
+    return true;
+}
+
+__device__ __forceinline__ void pix_load(PixBwd &p, bool inside, int64_t pix, int64_t HW, const float *t_final,
+                                         const int32_t *n_last, const float *dl, const DevCam &cam) {
+    p.T = 1.f; p.dC0 = p.dC1 = p.dC2 = 0.f; p.nl = 0;
+    if (inside) {
+        p.T = t_final[pix];
+        p.nl = n_last[pix];
+        p.dC0 = dl[pix];
+        p.dC1 = dl[HW + pix];
+        p.dC2 = dl[2 * HW + pix];
+    }
+    p.Tf = p.T;
+    p.bgdot = cam.bg[0] * p.dC0 + cam.bg[1] * p.dC1 + cam.bg[2] * p.dC2;
+    p.S0 = p.S1 = p.S2 = 0.f;
+    p.la = p.lc0 = p.lc1 = p.lc2 = 0.f;
+}
+
+template <int TS, int PPT, int B>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__restrict__ splats,
+                                                              const uint32_t *__restrict__ vals,
+                                                              const uint32_t *__restrict__ ranges, DevCam cam,
+                                                              const float *__restrict__ t_final,
+                                                              const int32_t *__restrict__ n_last,
+                                                              const float *__restrict__ dl_dimage,
+                                                              const uint8_t *__restrict__ frozen,
+                                                              float *__restrict__ grad2d) {
+    constexpr int NT = TS * TS / PPT;
     __shared__ float4 s_xyab[B];
     __shared__ float4 s_cocg[B];
     __shared__ float s_blue[B];
@@ -102,129 +220,144 @@ __global__ void __launch_bounds__(TS * TS) k_raster_bwd(const float *__restrict_
     __shared__ int s_maxlast;
     const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-    const int px = tx * TS + (int)(threadIdx.x % TS), py = ty * TS + (int)(threadIdx.x / TS);
-    const bool inside = px < cam.W && py < cam.H;
+    const int px = tx * TS + (int)(threadIdx.x % TS);
     const uint32_t start = ranges[2 * tile];
-    const float fpx = (float)px, fpy = (float)py;
-    const int64_t pix = (int64_t)py * cam.W + px, HW = (int64_t)cam.W * cam.H;
-
-    float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f;
-    int nl = 0;
-    if (inside) {
-        T = t_final[pix];
-        nl = n_last[pix];
-        dC0 = dl_dimage[pix];
-        dC1 = dl_dimage[HW + pix];
-        dC2 = dl_dimage[2 * HW + pix];
+    const float fpx = (float)px;
+    const int64_t HW = (int64_t)cam.W * cam.H;
+    PixBwd p[PPT];
+    float fpy[PPT];
+    int nlmax = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        const int py = ty * TS + (int)(threadIdx.x / TS) + k * (TS / PPT);
+        fpy[k] = (float)py;
+        pix_load(p[k], px < cam.W && py < cam.H, (int64_t)py * cam.W + px, HW, t_final, n_last, dl_dimage, cam);
+        nlmax = max(nlmax, p[k].nl);
     }
-    const float Tf = T;
-    const float bgdot = cam.bg[0] * dC0 + cam.bg[1] * dC1 + cam.bg[2] * dC2;
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;  // colour behind the current splat, per unit transmittance
-    float la = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;  // alpha and colour of the splat behind
-
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
-    if (nl > 0) atomicMax(&s_maxlast, nl);
+    if (nlmax > 0) atomicMax(&s_maxlast, nlmax);
     __syncthreads();
     const uint32_t rend = start + (uint32_t)s_maxlast;
     const int lane = threadIdx.x & 31;
+    const int slot = kSlotOf[(lane >> 1) & 15];
+    const bool writer = slot >= 0 && !(lane & 1);
 
     for (int64_t bend = rend; bend > (int64_t)start; bend -= B) {
         const int64_t bstart = bend - B > (int64_t)start ? bend - B : (int64_t)start;
         const int cnt = (int)(bend - bstart);
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t g = vals[bstart + threadIdx.x];
-            const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
-            s_xyab[threadIdx.x] = __ldg(r);
-            s_cocg[threadIdx.x] = __ldg(r + 1);
-            s_blue[threadIdx.x] = __ldg(reinterpret_cast<const float *>(r + 2));
-            s_gid[threadIdx.x] = g;
-            s_frz[threadIdx.x] = frozen ? (int)frozen[g] : 0;
-        }
-        if ((int)threadIdx.x < B) {
+        for (int q = threadIdx.x; q < B; q += NT) {
+            if (q < cnt) {
+                const uint32_t g = vals[bstart + q];
+                const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
+                s_xyab[q] = __ldg(r);
+                s_cocg[q] = __ldg(r + 1);
+                s_blue[q] = __ldg(reinterpret_cast<const float *>(r + 2));
+                s_gid[q] = g;
+                s_frz[q] = frozen ? (int)frozen[g] : 0;
+            }
 #pragma unroll
-            for (int q = 0; q < 9; ++q) s_acc[q][threadIdx.x] = 0.f;
+            for (int k = 0; k < 9; ++k) s_acc[k][q] = 0.f;
         }
         __syncthreads();
         for (int j = cnt - 1; j >= 0; --j) {
             const int pos = (int)(bstart - (int64_t)start) + j;  // position in the tile list
             const float4 xa = s_xyab[j], co = s_cocg[j];
             const float blue = s_blue[j];
-            const float dx = __fsub_rn(xa.x, fpx), dy = __fsub_rn(xa.y, fpy);
-            const float power = splat_power(dx, dy, xa.z, xa.w, co.x);
-            const float G = __expf(power);
-            const float oG = __fmul_rn(co.y, G);
-            const float alpha = fminf(kAlphaMax, oG);
-            const bool contrib = pos < nl && power <= 0.f && alpha >= kAlphaMin;
-            float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f, g6 = 0.f, g7 = 0.f, g8 = 0.f;
-            if (contrib) {
-                const float om = 1.f - alpha;
-                T = __fdividef(T, om);  // transmittance in front of this splat
-                S0 = la * lc0 + (1.f - la) * S0;
-                S1 = la * lc1 + (1.f - la) * S1;
-                S2 = la * lc2 + (1.f - la) * S2;
-                if (!s_frz[j]) {
-                    const float dA = T * (dC0 * (co.z - S0) + dC1 * (co.w - S1) + dC2 * (blue - S2)) -
-                                     __fdividef(Tf, om) * bgdot;
-                    const float wT = alpha * T;
-                    g6 = wT * dC0;
-                    g7 = wT * dC1;
-                    g8 = wT * dC2;
-                    if (!(oG > kAlphaMax)) {
-                        const float dpow = dA * oG;
-                        g5 = dA * G;
-                        g2 = -0.5f * dx * dx * dpow;
-                        g3 = -dx * dy * dpow;
-                        g4 = -0.5f * dy * dy * dpow;
-                        g0 = -(xa.z * dx + xa.w * dy) * dpow;
-                        g1 = -(xa.w * dx + co.x * dy) * dpow;
-                    }
-                }
-                la = alpha;
-                lc0 = co.z;
-                lc1 = co.w;
-                lc2 = blue;
-            }
-            if (!s_frz[j] && __any_sync(kFull, contrib)) {
-                g0 = warp_sum(g0); g1 = warp_sum(g1); g2 = warp_sum(g2);
-                g3 = warp_sum(g3); g4 = warp_sum(g4); g5 = warp_sum(g5);
-                g6 = warp_sum(g6); g7 = warp_sum(g7); g8 = warp_sum(g8);
-                if (lane == 0) {
-                    atomicAdd(&s_acc[0][j], g0); atomicAdd(&s_acc[1][j], g1); atomicAdd(&s_acc[2][j], g2);
-                    atomicAdd(&s_acc[3][j], g3); atomicAdd(&s_acc[4][j], g4); atomicAdd(&s_acc[5][j], g5);
-                    atomicAdd(&s_acc[6][j], g6); atomicAdd(&s_acc[7][j], g7); atomicAdd(&s_acc[8][j], g8);
-                }
+            const bool frz = s_frz[j] != 0;
+            const float dx = __fsub_rn(xa.x, fpx);
+            float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool c = false;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) c |= pix_bwd(p[k], pos, dx, __fsub_rn(xa.y, fpy[k]), xa, co, blue, frz, g);
+            if (!frz && __any_sync(kFull, c)) {
+                const float tot = warp_sum9(g, lane);
+                if (writer) atomicAdd(&s_acc[slot][j], tot);
             }
         }
         __syncthreads();
-        if ((int)threadIdx.x < cnt && !s_frz[threadIdx.x]) {
-            float *dst = grad2d + (int64_t)s_gid[threadIdx.x] * kG2d;
+        for (int q = threadIdx.x; q < cnt; q += NT) {
+            if (!s_frz[q]) {
+                float *dst = grad2d + (int64_t)s_gid[q] * kG2d;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                const float v = s_acc[q][threadIdx.x];
-                if (v != 0.f) atomicAdd(dst + q, v);
+                for (int k = 0; k < 9; ++k) {
+                    const float v = s_acc[k][q];
+                    if (v != 0.f) atomicAdd(dst + k, v);
+                }
             }
         }
         __syncthreads();
     }
 }
 
-template <int TS>
-int launch_fwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const DevCam &dc, float *image,
-               float *t_final, int32_t *n_last, cudaStream_t s) {
-    k_render_fwd<TS><<<dc.tiles_x * dc.tiles_y, TS * TS, 0, s>>>(splats, vals, ranges, dc, image, t_final, n_last);
+// Launch shape used when the caller gives none: pixels per thread and batch
+// size of each kernel by tile size (timed on GB300; the autotuner may pick
+// another per workload).
+inline void default_config(int tile, bool bwd, int &ppt, int &batch) {
+    if (tile == 8) { ppt = 1; batch = 64; return; }
+    if (tile == 16) { ppt = bwd ? 2 : 1; batch = 256; return; }
+    ppt = 2;
+    batch = 256;
+}
+
+struct FwdArgs {
+    const float *splats;
+    const uint32_t *vals, *ranges;
+    DevCam cam;
+    float *image, *t_final;
+    int32_t *n_last;
+};
+
+struct BwdArgs {
+    const float *splats;
+    const uint32_t *vals, *ranges;
+    DevCam cam;
+    const float *t_final;
+    const int32_t *n_last;
+    const float *dl;
+    const uint8_t *frozen;
+    float *grad2d;
+};
+
+template <int TS, int PPT, int B>
+void launch(const FwdArgs &a, cudaStream_t s) {
+    k_render_fwd<TS, PPT, B><<<a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, 0, s>>>(a.splats, a.vals, a.ranges, a.cam,
+                                                                                    a.image, a.t_final, a.n_last);
+}
+
+template <int TS, int PPT, int B>
+void launch(const BwdArgs &a, cudaStream_t s) {
+    k_raster_bwd<TS, PPT, B><<<a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, 0, s>>>(
+        a.splats, a.vals, a.ranges, a.cam, a.t_final, a.n_last, a.dl, a.frozen, a.grad2d);
+}
+
+template <int TS, int PPT, class A>
+void by_batch(int batch, const A &a, cudaStream_t s) {
+    switch (batch) {
+        case 32: launch<TS, PPT, 32>(a, s); break;
+        case 64: launch<TS, PPT, 64>(a, s); break;
+        case 128: launch<TS, PPT, 128>(a, s); break;
+        default: launch<TS, PPT, 256>(a, s); break;
+    }
+}
+
+template <class A>
+int dispatch(int tile, int ppt, int batch, const A &a, cudaStream_t s) {
+    switch (tile * 10 + ppt) {
+        case 81: by_batch<8, 1>(batch, a, s); break;
+        case 82: by_batch<8, 2>(batch, a, s); break;
+        case 161: by_batch<16, 1>(batch, a, s); break;
+        case 162: by_batch<16, 2>(batch, a, s); break;
+        case 321: by_batch<32, 1>(batch, a, s); break;
+        default: by_batch<32, 2>(batch, a, s); break;
+    }
     note_launches(1);
     return launch_status();
 }
 
-template <int TS>
-int launch_bwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const DevCam &dc,
-               const float *t_final, const int32_t *n_last, const float *dl, const uint8_t *frozen, float *grad2d,
-               cudaStream_t s) {
-    k_raster_bwd<TS><<<dc.tiles_x * dc.tiles_y, TS * TS, 0, s>>>(splats, vals, ranges, dc, t_final, n_last, dl,
-                                                                  frozen, grad2d);
-    note_launches(1);
-    return launch_status();
+inline bool config_ok(const gs_raster_config *c) {
+    return !c || ((c->pixels_per_thread == 1 || c->pixels_per_thread == 2) &&
+                  (c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256));
 }
 
 }  // namespace
@@ -232,29 +365,39 @@ int launch_bwd(const float *splats, const uint32_t *vals, const uint32_t *ranges
 
 using namespace gs;
 
+extern "C" int gs_render_fwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                 const gs_camera *cam, const gs_raster_config *cfg, float *image, float *t_final,
+                                 int32_t *n_last, gs_stream_t stream) {
+    if (!camera_ok(cam) || !config_ok(cfg) || !ranges || !image || !t_final || !n_last) return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
+    FwdArgs a{splats, vals, ranges, make_cam(cam), image, t_final, n_last};
+    int ppt, batch;
+    default_config(a.cam.tile, false, ppt, batch);
+    if (cfg) { ppt = cfg->pixels_per_thread; batch = cfg->batch; }
+    return dispatch(a.cam.tile, ppt, batch, a, as_stream(stream));
+}
+
 extern "C" int gs_render_fwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                              float *image, float *t_final, int32_t *n_last, gs_stream_t stream) {
-    if (!camera_ok(cam) || !ranges || !image || !t_final || !n_last) return GS_ERR_INVALID_ARG;
+    return gs_render_fwd_cfg(splats, vals, ranges, cam, nullptr, image, t_final, n_last, stream);
+}
+
+extern "C" int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                 const gs_camera *cam, const gs_raster_config *cfg, const float *t_final,
+                                 const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen, float *grad2d,
+                                 gs_stream_t stream) {
+    if (!camera_ok(cam) || !config_ok(cfg) || !ranges || !t_final || !n_last || !dl_dimage || !grad2d)
+        return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
-    DevCam dc = make_cam(cam);
-    cudaStream_t s = as_stream(stream);
-    switch (dc.tile) {
-        case 8: return launch_fwd<8>(splats, vals, ranges, dc, image, t_final, n_last, s);
-        case 16: return launch_fwd<16>(splats, vals, ranges, dc, image, t_final, n_last, s);
-        default: return launch_fwd<32>(splats, vals, ranges, dc, image, t_final, n_last, s);
-    }
+    BwdArgs a{splats, vals, ranges, make_cam(cam), t_final, n_last, dl_dimage, frozen, grad2d};
+    int ppt, batch;
+    default_config(a.cam.tile, true, ppt, batch);
+    if (cfg) { ppt = cfg->pixels_per_thread; batch = cfg->batch; }
+    return dispatch(a.cam.tile, ppt, batch, a, as_stream(stream));
 }
 
 extern "C" int gs_raster_bwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                              const float *t_final, const int32_t *n_last, const float *dl_dimage,
                              const uint8_t *frozen, float *grad2d, gs_stream_t stream) {
-    if (!camera_ok(cam) || !ranges || !t_final || !n_last || !dl_dimage || !grad2d) return GS_ERR_INVALID_ARG;
-    if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
-    DevCam dc = make_cam(cam);
-    cudaStream_t s = as_stream(stream);
-    switch (dc.tile) {
-        case 8: return launch_bwd<8>(splats, vals, ranges, dc, t_final, n_last, dl_dimage, frozen, grad2d, s);
-        case 16: return launch_bwd<16>(splats, vals, ranges, dc, t_final, n_last, dl_dimage, frozen, grad2d, s);
-        default: return launch_bwd<32>(splats, vals, ranges, dc, t_final, n_last, dl_dimage, frozen, grad2d, s);
-    }
+    return gs_raster_bwd_cfg(splats, vals, ranges, cam, nullptr, t_final, n_last, dl_dimage, frozen, grad2d, stream);
 }

@@ -31,6 +31,16 @@ class GsError(RuntimeError):
         self.status = status
 
 
+class GsRasterConfig(ctypes.Structure):
+    _fields_ = [("pixels_per_thread", ctypes.c_int32), ("batch", ctypes.c_int32)]
+
+
+def raster_config(pixels_per_thread: int, batch: int) -> GsRasterConfig:
+    c = GsRasterConfig()
+    c.pixels_per_thread, c.batch = int(pixels_per_thread), int(batch)
+    return c
+
+
 class GsCamera(ctypes.Structure):
     _fields_ = [
         ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("tile", ctypes.c_int32), ("pad0", ctypes.c_int32),
@@ -66,6 +76,8 @@ _SIGS = {
     "gs_sort_workspace_bytes": ([_I64, _I64, _I32, _I32, _I32], _SZ),
     "gs_sort": ([_P, _I64, _CAM, _P, _SZ, _I64, _P, _P, _P, _P], _I32),
     "gs_render_fwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P], _I32),
+    "gs_render_fwd_cfg": ([_P, _P, _P, _CAM, ctypes.POINTER(GsRasterConfig), _P, _P, _P, _P], _I32),
+    "gs_raster_bwd_cfg": ([_P, _P, _P, _CAM, ctypes.POINTER(GsRasterConfig), _P, _P, _P, _P, _P, _P], _I32),
     "gs_loss_workspace_bytes": ([_I32, _I32], _SZ),
     "gs_loss": ([_P, _P, _I32, _I32, _F32, _P, _SZ, _P, _P, _P], _I32),
     "gs_raster_bwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P, _P, _P], _I32),
@@ -164,6 +176,26 @@ def gs_render_fwd(splats, vals, ranges, cam: GsCamera, image, t_final, n_last, s
                                                  _ptr(image, torch.float32, "image"),
                                                  _ptr(t_final, torch.float32, "t_final"),
                                                  _ptr(n_last, torch.int32, "n_last"), _stream(stream)))
+
+
+def gs_render_fwd_cfg(splats, vals, ranges, cam: GsCamera, cfg, image, t_final, n_last, stream=None):
+    import torch
+
+    _check("gs_render_fwd_cfg", load().gs_render_fwd_cfg(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), None if cfg is None else ctypes.byref(cfg), _ptr(image, torch.float32, "image"),
+        _ptr(t_final, torch.float32, "t_final"), _ptr(n_last, torch.int32, "n_last"), _stream(stream)))
+
+
+def gs_raster_bwd_cfg(splats, vals, ranges, cam: GsCamera, cfg, t_final, n_last, dl_dimage, frozen, grad2d,
+                      stream=None):
+    import torch
+
+    _check("gs_raster_bwd_cfg", load().gs_raster_bwd_cfg(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), None if cfg is None else ctypes.byref(cfg), _ptr(t_final, torch.float32, "t_final"),
+        _ptr(n_last, torch.int32, "n_last"), _ptr(dl_dimage, torch.float32, "dl_dimage"),
+        _ptr(frozen, torch.uint8, "frozen"), _ptr(grad2d, torch.float32, "grad2d"), _stream(stream)))
 
 
 def gs_loss_workspace_bytes(H: int, W: int) -> int:

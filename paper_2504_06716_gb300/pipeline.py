@@ -60,6 +60,8 @@ class Model:
         self.P = pack_params(params59, self.device)
         self.splats = torch.zeros((n, lib.SPLAT), **f32)
         self.step_count = 0
+        self.fwd_cfg = None  # rasteriser launch shapes (None: library defaults); see autotune.py
+        self.bwd_cfg = None
         if not trainable:  # render-only (targets): no gradients, moments or freeze state
             return
         self.G = torch.zeros((n, lib.ROW), **f32)
@@ -105,16 +107,23 @@ class Model:
         lib.gs_project(self.P, self.n, self.sh_degree, view.cam, self.splats, stream)
         lib.gs_sort(self.splats, self.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count,
                     stream)
-        lib.gs_render_fwd(self.splats, view.vals, view.ranges, view.cam, view.image, view.t_final, view.n_last, stream)
+        lib.gs_render_fwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.fwd_cfg, view.image, view.t_final,
+                              view.n_last, stream)
 
     def loss(self, view: View, gt: torch.Tensor, lam: float = 0.2, stream=None):
         lib.gs_loss(view.image, gt, view.cam.height, view.cam.width, lam, view.loss_ws, view.loss, view.dl, stream)
 
     def backward(self, view: View, stats: bool = True, stream=None):
-        lib.gs_render_bwd(self.P, self.n, self.sh_degree, view.cam, self.splats, view.vals, view.ranges, view.t_final,
-                          view.n_last, view.dl, self.frozen, self.act, self.n_active, self.grad2d, self.G,
-                          self.acc_xyz if stats else None, self.acc_rgb if stats else None,
-                          self.cnt if stats else None, stream)
+        """gs_render_bwd, as its two halves so that the tuned launch shape applies."""
+        lib.gs_raster_bwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.bwd_cfg, view.t_final, view.n_last,
+                              view.dl, self.frozen, self.grad2d, stream)
+        lib.gs_project_bwd(self.P, self.n, self.sh_degree, view.cam, self.splats, self.act, self.n_active, self.grad2d,
+                           self.G, self.acc_xyz if stats else None, self.acc_rgb if stats else None,
+                           self.cnt if stats else None, stream)
+
+    def apply_tuning(self, tuning):
+        self.fwd_cfg = lib.raster_config(*tuning.fwd)
+        self.bwd_cfg = lib.raster_config(*tuning.bwd)
 
     def adam(self, lrs, b1=0.9, b2=0.999, eps=1e-15, stream=None):
         self.step_count += 1

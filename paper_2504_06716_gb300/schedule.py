@@ -41,6 +41,9 @@ class GStaConfig:
     lr_patience: int = 1
     lr_eps: float = 1.0
     freezing: bool = True  # False: plain 3DGS training (no freezing, no early stop)
+    # plain 3DGS decays the xyz rate exponentially to 1/100 over the run
+    # (Sec. 3.2.3 describes the vanilla decay that GSta's plateau schedule replaces)
+    plain_lr_final_ratio: float = 0.01
 
     @staticmethod
     def tiny() -> "GStaConfig":
@@ -81,6 +84,15 @@ class GStaController:
         if self.last_reset is not None and k - self.last_reset < c.wait:
             return FREEZE_CLEAR
         return FREEZE_UPDATE
+
+    def lr_xyz_at(self, k: int) -> float:
+        """xyz learning rate for iteration k: the plateau schedule under GSta,
+        vanilla exponential decay for plain training."""
+        c = self.cfg
+        if c.freezing:
+            return self.lr_xyz
+        t = min(1.0, max(0.0, k / c.total_iter))
+        return self.lr_xyz * c.plain_lr_final_ratio ** t
 
     def wants_psnr(self, k: int) -> bool:
         c = self.cfg

@@ -25,7 +25,7 @@ import time
 import numpy as np
 import torch
 
-from . import lib, pipeline, synth
+from . import autotune, lib, pipeline, synth
 from .schedule import FREEZE_RESET, FREEZE_UPDATE, GStaConfig, GStaController
 
 
@@ -63,6 +63,38 @@ class Trainer:
         self.calibrated = False
         self.events: list[tuple[int, str, float]] = []
         self.k = 0
+        self.capacity_check_every = 100
+        self.overflows = 0
+
+    def check_capacity(self, headroom: float = 0.8, grow: float = 1.5):
+        """Read the sort's entry count and the device error word (one sync) and
+        grow the sort buffers before the count reaches the capacity. An
+        overflow that already happened (truncated lists) is counted."""
+        P = int(self.view.count.item())
+        flags = lib.gs_get_device_error()
+        if flags & lib.GS_FLAG_CAPACITY:
+            self.overflows += 1
+            self.events.append((self.k, "capacity_overflow", float(P)))
+        if flags & ~lib.GS_FLAG_CAPACITY:
+            raise RuntimeError(f"device error flags {flags:#x} at iteration {self.k}")
+        if P > headroom * self.view.capacity:
+            cam = self.view.cam
+            self.view = self.model.make_view(cam, int(max(P, self.view.capacity) * grow) + 1024)
+            self.events.append((self.k, "capacity", float(self.view.capacity)))
+
+    def autotune(self, n_views: int = 2) -> autotune.RasterTuning:
+        """Pick the rasteriser tile size and launch shapes on the current state
+        (autotune.py) and switch every camera and buffer to them."""
+        views = [self.order[(self.k + i) % len(self.order)] for i in range(n_views)]
+        res = autotune.tune(self.model, [self.cams[v] for v in views], [self.targets[v] for v in views],
+                            n_views=n_views)
+        self.cams = [autotune.retile(c, res.tile) for c in self.cams]
+        vis = sorted(set(self.scene.train_views) | set(self.scene.test_views))
+        cap = self.model.measure_capacity([self.cams[v] for v in vis])
+        self.view = self.model.make_view(self.cams[self.scene.train_views[0]], cap)
+        self.model.apply_tuning(res)
+        self.tuning = res
+        return res
 
     # ---- measurements ----
     def psnr_of(self, views) -> float:
@@ -124,11 +156,13 @@ class Trainer:
         v = self.order[k]
         m.retarget(self.view, self.cams[v])
         lrs = list(self.lrs)
-        lrs[0] = c.lr_xyz
+        lrs[0] = c.lr_xyz_at(k)
         m.train_step(self.view, self.targets[v], lrs)
         if c.after_step(k):
             m.freeze_update(0.0, 0.0, FREEZE_RESET)
         self.k += 1
+        if self.k % self.capacity_check_every == 0:
+            self.check_capacity()
 
     def finished(self) -> bool:
         c = self.ctrl
@@ -142,6 +176,21 @@ def run(args) -> dict:
     scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
     cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters)
     tr = Trainer(scene, cfg)
+    tuning = None
+    if args.autotune:
+        for _ in range(args.tune_after):
+            tr.iteration()
+        tuning = dict(tile=tr.autotune().tile, fwd=tr.tuning.fwd, bwd=tr.tuning.bwd)
+        tr2 = Trainer.__new__(Trainer)  # restart training from the initial state with the tuned shapes
+        tr2.__dict__.update(tr.__dict__)
+        tr2.model = pipeline.Model(scene.init, device=tr.device)
+        tr2.model.apply_tuning(tr.tuning)
+        vis = sorted(set(scene.train_views) | set(scene.test_views))
+        tr2.view = tr2.model.make_view(tr2.cams[scene.train_views[0]], tr2.model.measure_capacity(
+            [tr2.cams[v] for v in vis]))
+        tr2.ctrl = GStaController(cfg, tr.lrs[0])
+        tr2.k, tr2.calibrated, tr2.eps0, tr2.events, tr2.overflows = 0, False, (cfg.eps0_xyz, cfg.eps0_rgb), [], 0
+        tr = tr2
     evals = []
     t0 = time.perf_counter()
     eval_every = args.eval_every
@@ -156,7 +205,8 @@ def run(args) -> dict:
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
     out = dict(arm=args.arm, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(), evals=evals,
-               events=tr.events, eps0=tr.eps0, device_flags=lib.gs_get_device_error())
+               events=tr.events, eps0=tr.eps0, tuning=tuning, overflows=tr.overflows,
+               final_capacity=tr.view.capacity, device_flags=lib.gs_get_device_error())
     return out
 
 
@@ -170,6 +220,8 @@ def main():
     ap.add_argument("--height", type=int, default=822)
     ap.add_argument("--iters", type=int, default=30000)
     ap.add_argument("--eval-every", type=int, default=1000)
+    ap.add_argument("--autotune", action="store_true", help="tune the rasteriser launch shape first")
+    ap.add_argument("--tune-after", type=int, default=300, help="iterations trained before tuning (then restarted)")
     args = ap.parse_args()
     print(json.dumps(run(args)))
 

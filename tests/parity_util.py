@@ -18,6 +18,13 @@ PIXEL_MARGIN = 1e-5
 # Same for the integer decisions of the projection (radius, tile rectangle,
 # near plane), in pixels / world units.
 PROJ_MARGIN = 1e-3
+# When the CUDA path also computes the projection itself, its alpha values
+# differ from the oracle's by up to ~5e-5 relative (float32 2-D means and
+# conics); decisions within this margin may go either way.
+E2E_PIXEL_MARGIN = 2e-4
+
+GRAD2D_KEYS = [("d_mean2d", 0), ("d_mean2d", 1), ("d_conic", 0), ("d_conic", 1), ("d_conic", 2), ("d_opacity", None),
+               ("d_rgb", 0), ("d_rgb", 1), ("d_rgb", 2)]
 
 
 def f32(x):
@@ -74,6 +81,49 @@ def close(got, want, rtol, floor, mask=None):
     if mask is not None:
         err = err[mask]
         lim = lim[mask]
+    if err.size == 0:
+        return True, 0.0
+    ratio = float((err / np.maximum(lim, 1e-300)).max())
+    return ratio <= 1.0, ratio
+
+
+def grad2d_matrix(bwd: dict) -> np.ndarray:
+    """Oracle raster gradients as an [n][9] array in the grad2d column order."""
+    n = bwd["d_opacity"].shape[0]
+    out = np.zeros((n, 9))
+    for k, (key, col) in enumerate(GRAD2D_KEYS):
+        out[:, k] = bwd[key] if col is None else bwd[key][:, col]
+    return out
+
+
+def param_bound(P, ocam, amb_abs, frozen=None, sh_degree=3):
+    """Bound on |change of the 59-parameter gradient| caused by raster-gradient
+    changes of at most amb_abs[n][9]: sum_k |J[:, k]| amb_abs[k], with the
+    columns of the (per-Gaussian) projection Jacobian J obtained from the
+    oracle's projection backward on unit raster gradients."""
+    n = P.shape[0]
+    bound = np.zeros((n, 59))
+    if not np.any(amb_abs):
+        return bound
+    for k, (key, col) in enumerate(GRAD2D_KEYS):
+        g2 = dict(d_mean2d=np.zeros((n, 2)), d_conic=np.zeros((n, 3)), d_opacity=np.zeros(n), d_rgb=np.zeros((n, 3)))
+        if col is None:
+            g2[key][:] = 1.0
+        else:
+            g2[key][:, col] = 1.0
+        Jk = oracle.project_bwd(P, ocam, g2, frozen, sh_degree)["G"]
+        bound += np.abs(Jk) * amb_abs[:, k:k + 1]
+    return bound
+
+
+def close_bound(got, want, rtol, floor, extra, mask=None):
+    """|got - want| <= rtol * (|want| + floor) + extra; returns (ok, worst ratio)."""
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    err = np.abs(got - want)
+    lim = rtol * (np.abs(want) + floor) + extra
+    if mask is not None:
+        err, lim = err[mask], lim[mask]
     if err.size == 0:
         return True, 0.0
     ratio = float((err / np.maximum(lim, 1e-300)).max())

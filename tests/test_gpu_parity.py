@@ -321,14 +321,14 @@ def test_raster_backward_matches_oracle(kind, tile, bg):
     want = oracle.render_bwd(st["proj"], st["vals"], st["ranges"], st["ocam"], st["dl"], st["frozen"], amb)
     fr = st["frozen"] == 1
     assert np.all(g2[fr] == 0), "frozen Gaussians must receive nothing"
-    ok = ~fr & (want["tainted"] == 0)
-    assert ok.sum() > 0.5 * (~fr).sum()
-    cols = [(want["d_mean2d"], g2[:, 0:2]), (want["d_conic"], g2[:, 2:5]), (want["d_opacity"][:, None], g2[:, 5:6]),
-            (want["d_rgb"], g2[:, 6:9])]
-    for w, g in cols:
-        floor = 1e-2 * np.abs(w[ok]).max()
-        good, worst = pu.close(g[ok], w[ok], 1e-3, floor)
-        assert good, worst
+    a = ~fr
+    W9 = pu.grad2d_matrix(want)
+    # a decision that flips at an ambiguous pixel moves a Gaussian's gradient by
+    # at most its own terms there (want["amb_abs"])
+    for cols in (slice(0, 2), slice(2, 5), slice(5, 6), slice(6, 9)):
+        w = W9[a, cols]
+        good, worst = pu.close_bound(g2[a, cols], w, 1e-3, 1e-2 * np.abs(w).max(), want["amb_abs"][a, cols])
+        assert good, (cols, worst)
     assert np.all(g2[:, 9:] == 0)
 
 
@@ -465,3 +465,36 @@ def test_psnr_matches_oracle():
     got = out.cpu().numpy()
     assert got[1] == pytest.approx(100.0, abs=1e-4)
     assert np.allclose(got, want, rtol=1e-5, atol=1e-4)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_every_launch_shape_gives_the_same_result(tile):
+    """Pixels per thread and batch size change only the launch shape: the
+    forward is bit-identical and the backward equal up to atomic reordering."""
+    st = _stage_inputs("ragged" if tile != 16 else "surface", tile)
+    n = st["P"].shape[0]
+    gcam = st["gcam"]
+    vals = torch.from_numpy(st["vals"].view(np.int32).copy()).to(DEV)
+    ranges = torch.from_numpy(st["ranges"].view(np.int32).copy()).to(DEV)
+    H, W = gcam.height, gcam.width
+    dlt = torch.from_numpy(st["dl"].astype(np.float32)).to(DEV)
+    fr = torch.from_numpy(st["frozen"]).to(DEV)
+    ref = None
+    for ppt in (1, 2):
+        for batch in (32, 64, 128, 256):
+            cfg = lib.raster_config(ppt, batch)
+            img = torch.zeros((3, H, W), device=DEV)
+            tf = torch.zeros((H, W), device=DEV)
+            nl = torch.zeros((H, W), dtype=torch.int32, device=DEV)
+            lib.gs_render_fwd_cfg(st["spl"], vals, ranges, gcam, cfg, img, tf, nl)
+            g2 = torch.zeros((n, 12), device=DEV)
+            lib.gs_raster_bwd_cfg(st["spl"], vals, ranges, gcam, cfg, tf, nl, dlt, fr, g2)
+            torch.cuda.synchronize()
+            out = (img.cpu().numpy(), tf.cpu().numpy(), nl.cpu().numpy(), g2.cpu().numpy())
+            if ref is None:
+                ref = out
+                continue
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+            assert np.array_equal(out[2], ref[2])
+            good, worst = pu.close(out[3], ref[3], 1e-4, 1e-3 * np.abs(ref[3]).max())
+            assert good, (ppt, batch, worst)
