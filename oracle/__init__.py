@@ -96,6 +96,19 @@ def lib():
             L.or_freeze_update.argtypes = [_i64, _fp, _fp, _ip, _bp, ctypes.c_float, ctypes.c_float, _i32, _ip]
             L.or_freeze_update.restype = _i64
             L.or_psnr.argtypes = [_i32, _i32, _i32, _dp, _dp, _dp]
+            L.or_mlp_nparams.restype = _i32
+            L.or_freeze_apply.argtypes = [_i64, _fp, ctypes.c_float, _bp, _ip]
+            L.or_freeze_apply.restype = _i64
+            L.or_bf16.argtypes = [ctypes.c_double]
+            L.or_bf16.restype = ctypes.c_double
+            L.or_pred_history.argtypes = [_i64, _fp, _fp, _ip, _bp, _dp]
+            L.or_pred_features.argtypes = [_i64, _dp, _fp, _fp, _ip, _dp, _i32, _i32, ctypes.c_double,
+                                           ctypes.c_double, _dp]
+            L.or_mlp_forward.argtypes = [_i64, _dp, _dp, _i32, _dp]
+            L.or_mlp_loss_grad.argtypes = [_i64, _dp, _dp, _dp, _dp, _i32, _dp, _dp]
+            L.or_mlp_loss_grad.restype = ctypes.c_double
+            L.or_mlp_adam.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, _i64]
             _lib = L
     return _lib
 
@@ -311,3 +324,74 @@ def loss_and_grad(params, cam: Cam, gt, frozen=None, sh_degree: int = 3, smooth:
 def loss_only(params, cam: Cam, gt, sh_degree: int = 3, smooth: bool = False, lam: float = 0.2) -> float:
     f = forward(params, cam, sh_degree, smooth)
     return loss(f["image"], gt, lam, grad=False)[0]
+
+
+# ---------------------------------------------------------------------------
+# Learned freeze predictor (not in the paper; the reference for its kernels).
+# ---------------------------------------------------------------------------
+MLP_IN, MLP_H = 16, 64
+MLP_OFF = dict(W1=0, b1=1024, W2=1088, b2=5184, W3=5248, b3=5312)
+
+
+def mlp_nparams() -> int:
+    return int(lib().or_mlp_nparams())
+
+
+def bf16(x) -> np.ndarray:
+    """Round-to-nearest-even bfloat16 of float32(x), element-wise."""
+    f = np.asarray(x, np.float32).copy()
+    b = f.view(np.uint32)
+    b += np.uint32(0x7FFF) + ((b >> 16) & np.uint32(1))
+    b &= np.uint32(0xFFFF0000)
+    return b.view(np.float32).astype(np.float64)
+
+
+def pred_history(acc_xyz, acc_rgb, cnt, frozen, state):
+    """In-place update of the [n][12] float64 predictor state at a statistics boundary."""
+    assert state.dtype == np.float64 and state.flags.c_contiguous
+    fr = None if frozen is None else _c(frozen, np.uint8)
+    lib().or_pred_history(state.shape[0], _p(_c(acc_xyz, np.float32), _fp), _p(_c(acc_rgb, np.float32), _fp),
+                          _p(_c(cnt, np.int32), _ip), _p(fr, _bp), _p(state, _dp))
+
+
+def pred_features(P, acc_xyz, acc_rgb, cnt, state, k: int, K: int, eps_xyz: float, eps_rgb: float) -> np.ndarray:
+    P = _c(P, np.float64)
+    n = P.shape[0]
+    X = np.zeros((n, MLP_IN))
+    lib().or_pred_features(n, _p(P, _dp), _p(_c(acc_xyz, np.float32), _fp), _p(_c(acc_rgb, np.float32), _fp),
+                           _p(_c(cnt, np.int32), _ip), _p(_c(state, np.float64), _dp), k, K, eps_xyz, eps_rgb,
+                           _p(X, _dp))
+    return X
+
+
+def mlp_forward(X, prm, round_bf16: bool = True) -> np.ndarray:
+    X = _c(X, np.float64)
+    p = np.zeros(X.shape[0])
+    lib().or_mlp_forward(X.shape[0], _p(X, _dp), _p(_c(prm, np.float64), _dp), int(round_bf16), _p(p, _dp))
+    return p
+
+
+def mlp_loss_grad(X, y, prm, w=None, round_bf16: bool = True, with_abs: bool = False):
+    """(loss, gradient) or, with ``with_abs``, (loss, gradient, sum of |per-row terms|)."""
+    X = _c(X, np.float64)
+    g = np.zeros(mlp_nparams())
+    a = np.zeros(mlp_nparams()) if with_abs else None
+    wv = None if w is None else _c(w, np.float64)
+    L = lib().or_mlp_loss_grad(X.shape[0], _p(X, _dp), _p(_c(y, np.float64), _dp), _p(wv, _dp),
+                               _p(_c(prm, np.float64), _dp), int(round_bf16), _p(g, _dp), _p(a, _dp))
+    return (L, g, a) if with_abs else (L, g)
+
+
+def mlp_adam(prm, grad, m, v, lr: float, step: int, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+    for a in (prm, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().or_mlp_adam(_p(prm, _dp), _p(_c(grad, np.float64), _dp), _p(m, _dp), _p(v, _dp), lr, b1, b2, eps, step)
+
+
+def freeze_apply(prob, tau: float, frozen):
+    """In-place frozen |= prob > tau (uint8 frozen); returns the active list."""
+    assert frozen.dtype == np.uint8 and frozen.flags.c_contiguous
+    n = frozen.shape[0]
+    act = np.zeros(max(n, 1), np.int32)
+    k = lib().or_freeze_apply(n, _p(_c(prob, np.float32), _fp), np.float32(tau), _p(frozen, _bp), _p(act, _ip))
+    return act[:k]

@@ -947,3 +947,195 @@ void or_psnr(int32_t S, int32_t H, int32_t W, const double *images, const double
         psnr[s] = 10.0 * log10(1.0 / mse);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned freeze predictor. The paper has no learned component: this is */
+/* the plain statement of the predictor the CUDA path builds (features,  */
+/* 16 -> 64 -> 64 -> 1 MLP, weighted BCE, Adam), used as its reference.  */
+/* ------------------------------------------------------------------ */
+#define MLP_IN 16
+#define MLP_H 64
+#define OFF_W1 0                      /* [16][64], input-major */
+#define OFF_B1 (OFF_W1 + MLP_IN * MLP_H)
+#define OFF_W2 (OFF_B1 + MLP_H)       /* [64][64], input-major */
+#define OFF_B2 (OFF_W2 + MLP_H * MLP_H)
+#define OFF_W3 (OFF_B2 + MLP_H)       /* [64] */
+#define OFF_B3 (OFF_W3 + MLP_H)
+#define MLP_NPARAM (OFF_B3 + 1)       /* 5313 */
+
+int32_t or_mlp_nparams(void) { return MLP_NPARAM; }
+
+/* Round to bfloat16 (8-bit mantissa) by round-to-nearest-even on the
+ * float32 value: add 0x7fff plus the lowest kept bit, drop 16 bits. */
+double or_bf16(double x) {
+    float f = (float)x;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b += 0x7fffu + ((b >> 16) & 1u);
+    b &= 0xffff0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+/* Per-Gaussian predictor state, [n][12]: 0-3 history of the xyz norm EMA
+ * (most recent first), 4-7 the same for rgb, 8 xyz EMA, 9 rgb EMA,
+ * 10 visible iterations so far, 11 boundaries spent frozen.
+ * At every statistics boundary (every 250 iterations, before the statistics
+ * are cleared): if the Gaussian was visible (cnt > 0) each EMA becomes
+ * 0.5 EMA + 0.5 (acc / cnt) and views += cnt; frozen += frozen[i]; then each
+ * history shifts by one and takes the EMA at its front. */
+void or_pred_history(int64_t n, const float *acc_xyz, const float *acc_rgb, const int32_t *cnt, const uint8_t *frozen,
+                     double *state) {
+    for (int64_t i = 0; i < n; ++i) {
+        double *s = state + 12 * i;
+        if (cnt[i] > 0) {
+            s[8] = 0.5 * s[8] + 0.5 * ((double)acc_xyz[i] / cnt[i]);
+            s[9] = 0.5 * s[9] + 0.5 * ((double)acc_rgb[i] / cnt[i]);
+            s[10] += cnt[i];
+        }
+        if (frozen && frozen[i]) s[11] += 1;
+        for (int j = 3; j > 0; --j) { s[j] = s[j - 1]; s[4 + j] = s[4 + j - 1]; }
+        s[0] = s[8];
+        s[4] = s[9];
+    }
+}
+
+static double log_ratio(double v, double eps) {
+    double r = log10((v > 1e-30 ? v : 1e-30) / eps);
+    return r < -8 ? -8 : (r > 8 ? 8 : r);
+}
+
+/* The 16 features of Gaussian i at iteration k of K, with thresholds
+ * eps_xyz, eps_rgb: 0-3 log10(history_xyz / eps_xyz), 4-7 the same for rgb
+ * (each clamped to [-8, 8], norms below 1e-30 read as 1e-30), 8 opacity
+ * sigmoid(logit), 9 largest and 10 smallest log-scale, 11 ln(1 + views),
+ * 12 k / K, 13-14 log10 of the current window's average norm over its
+ * threshold (0 visible iterations read as a norm of 0), 15 min(frozen
+ * boundaries, 8) / 8. */
+void or_pred_features(int64_t n, const double *P, const float *acc_xyz, const float *acc_rgb, const int32_t *cnt,
+                      const double *state, int32_t k, int32_t K, double eps_xyz, double eps_rgb, double *X) {
+    for (int64_t i = 0; i < n; ++i) {
+        const double *s = state + 12 * i, *p = P + NP * i;
+        double *x = X + MLP_IN * i;
+        for (int j = 0; j < 4; ++j) {
+            x[j] = log_ratio(s[j], eps_xyz);
+            x[4 + j] = log_ratio(s[4 + j], eps_rgb);
+        }
+        x[8] = 1.0 / (1.0 + exp(-p[10]));
+        double mx = p[3], mn = p[3];
+        for (int j = 4; j < 6; ++j) { if (p[j] > mx) mx = p[j]; if (p[j] < mn) mn = p[j]; }
+        x[9] = mx;
+        x[10] = mn;
+        x[11] = log(1.0 + s[10]);
+        x[12] = (double)k / K;
+        double ax = cnt[i] > 0 ? (double)acc_xyz[i] / cnt[i] : 0.0, ar = cnt[i] > 0 ? (double)acc_rgb[i] / cnt[i] : 0.0;
+        x[13] = log_ratio(ax, eps_xyz);
+        x[14] = log_ratio(ar, eps_rgb);
+        x[15] = (s[11] < 8 ? s[11] : 8) / 8.0;
+    }
+}
+
+/* Forward of one row: a1 = X W1 + b1, h1 = relu(a1), a2 = h1 W2 + b2,
+ * h2 = relu(a2), z = h2 . W3 + b3. With round != 0 the inputs X, the
+ * weights W1, W2, W3 and h1 (the second layer's input) are rounded to
+ * bfloat16 first; biases are not. */
+static double mlp_row(const double *xin, const double *prm, int round, double *xr, double *a1, double *h1r, double *a2,
+                      double *h2) {
+    for (int c = 0; c < MLP_IN; ++c) xr[c] = round ? or_bf16(xin[c]) : xin[c];
+    for (int j = 0; j < MLP_H; ++j) {
+        double s = prm[OFF_B1 + j];
+        for (int c = 0; c < MLP_IN; ++c) {
+            double w = prm[OFF_W1 + c * MLP_H + j];
+            s += xr[c] * (round ? or_bf16(w) : w);
+        }
+        a1[j] = s;
+        double h = s > 0 ? s : 0;
+        h1r[j] = round ? or_bf16(h) : h;
+    }
+    double z = prm[OFF_B3];
+    for (int j = 0; j < MLP_H; ++j) {
+        double s = prm[OFF_B2 + j];
+        for (int c = 0; c < MLP_H; ++c) {
+            double w = prm[OFF_W2 + c * MLP_H + j];
+            s += h1r[c] * (round ? or_bf16(w) : w);
+        }
+        a2[j] = s;
+        h2[j] = s > 0 ? s : 0;
+        double w3 = prm[OFF_W3 + j];
+        z += h2[j] * (round ? or_bf16(w3) : w3);
+    }
+    return z;
+}
+
+/* p[i] = sigmoid(z) of every row. */
+void or_mlp_forward(int64_t n, const double *X, const double *prm, int32_t round, double *p) {
+    double xr[MLP_IN], a1[MLP_H], h1[MLP_H], a2[MLP_H], h2[MLP_H];
+    for (int64_t i = 0; i < n; ++i) {
+        double z = mlp_row(X + MLP_IN * i, prm, round, xr, a1, h1, a2, h2);
+        p[i] = 1.0 / (1.0 + exp(-z));
+    }
+}
+
+/* Weighted binary cross-entropy L = sum_i w_i (softplus(z_i) - y_i z_i) /
+ * sum_i w_i (w = NULL: all 1) and its gradient over the 5313 parameters
+ * (added into grad). The gradient passes through the bfloat16 roundings as
+ * the identity. abs_grad (optional) receives the sum of the absolute values
+ * of the per-row terms of each gradient entry (the scale of its rounding
+ * error in finite precision). Returns L. */
+#define ADDG(k, v) do { double v_ = (v); grad[k] += v_; if (abs_grad) abs_grad[k] += fabs(v_); } while (0)
+double or_mlp_loss_grad(int64_t n, const double *X, const double *y, const double *w, const double *prm,
+                        int32_t round, double *grad, double *abs_grad) {
+    double xr[MLP_IN], a1[MLP_H], h1[MLP_H], a2[MLP_H], h2[MLP_H], dh2[MLP_H], dh1[MLP_H];
+    double wsum = 0, L = 0;
+    for (int64_t i = 0; i < n; ++i) wsum += w ? w[i] : 1.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double wi = (w ? w[i] : 1.0) / wsum;
+        double z = mlp_row(X + MLP_IN * i, prm, round, xr, a1, h1, a2, h2);
+        double sp = z > 0 ? z + log1p(exp(-z)) : log1p(exp(z));
+        L += wi * (sp - y[i] * z);
+        double dz = wi * (1.0 / (1.0 + exp(-z)) - y[i]);
+        ADDG(OFF_B3, dz);
+        for (int j = 0; j < MLP_H; ++j) {
+            double w3 = prm[OFF_W3 + j];
+            ADDG(OFF_W3 + j, dz * h2[j]);
+            dh2[j] = a2[j] > 0 ? dz * (round ? or_bf16(w3) : w3) : 0.0;
+            ADDG(OFF_B2 + j, dh2[j]);
+        }
+        for (int c = 0; c < MLP_H; ++c) {
+            double s = 0;
+            for (int j = 0; j < MLP_H; ++j) {
+                double w2 = prm[OFF_W2 + c * MLP_H + j];
+                ADDG(OFF_W2 + c * MLP_H + j, h1[c] * dh2[j]);
+                s += dh2[j] * (round ? or_bf16(w2) : w2);
+            }
+            dh1[c] = a1[c] > 0 ? s : 0.0;
+            ADDG(OFF_B1 + c, dh1[c]);
+        }
+        for (int c = 0; c < MLP_IN; ++c)
+            for (int j = 0; j < MLP_H; ++j) ADDG(OFF_W1 + c * MLP_H + j, xr[c] * dh1[j]);
+    }
+    return L;
+}
+#undef ADDG
+
+/* One Adam step on the predictor's parameters (textbook, bias-corrected). */
+void or_mlp_adam(double *prm, const double *grad, double *m, double *v, double lr, double b1, double b2, double eps,
+                 int64_t step) {
+    double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
+    for (int k = 0; k < MLP_NPARAM; ++k) {
+        m[k] = b1 * m[k] + (1 - b1) * grad[k];
+        v[k] = b2 * v[k] + (1 - b2) * grad[k] * grad[k];
+        prm[k] -= lr * (m[k] / bc1) / (sqrt(v[k] / bc2) + eps);
+    }
+}
+
+/* Predicted freezing: frozen |= prob > tau; the unfrozen indices in
+ * ascending order go to act. Statistics are not touched. Returns their count. */
+int64_t or_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen, int32_t *act) {
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (prob[i] > tau) frozen[i] = 1;
+        if (!frozen[i]) act[k++] = (int32_t)i;
+    }
+    return k;
+}
