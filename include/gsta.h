@@ -175,6 +175,35 @@ int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t 
                       const gs_raster_config *cfg, const float *t_final, const int32_t *n_last,
                       const float *dl_dimage, const uint8_t *frozen, float *grad2d, gs_stream_t stream);
 
+/* One rendering job of a batch: a view of one scene (all pointers device,
+ * the camera by value). Used by the batch calls below. */
+typedef struct {
+    const float *splats;     /* [n][12] of the job's scene, projected for this view */
+    const uint32_t *vals;    /* the view's sorted lists (gs_sort) */
+    const uint32_t *ranges;  /* [tiles][2] */
+    float *image;            /* [3][H][W] out (forward) */
+    float *t_final;          /* [H][W] out (forward), in (backward) */
+    int32_t *n_last;         /* [H][W] out (forward), in (backward) */
+    const float *dl_dimage;  /* [3][H][W] in (backward) */
+    const uint8_t *frozen;   /* [n] or NULL (backward) */
+    float *grad2d;           /* [n][12] accumulated (backward) */
+    gs_camera cam;
+} gs_raster_job;
+
+/* gs_render_fwd for n_jobs jobs in ONE persistent launch: resident CTAs take
+ * (job, tile) items from a device counter (queue_dev, one uint32 of device
+ * memory, reset by the call) until all jobs are done, so jobs of uneven cost
+ * balance without one launch per job. jobs_dev is a DEVICE array; every job
+ * must have this width, height and tile. Results equal gs_render_fwd per
+ * job. Errors: INVALID_ARG, CUDA. */
+int gs_render_fwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
+                        const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream);
+
+/* gs_raster_bwd for n_jobs jobs in one persistent launch, as above. Jobs of
+ * one scene may share grad2d (their terms add up). */
+int gs_raster_bwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
+                        const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream);
+
 /* Sec. 3.2.4, second half, and the statistics of Sec. 3.2.1: chain rule from
  * grad2d to the 59 parameters for the Gaussians act[0 .. *n_active_dev).
  * Writes full rows of G [n][64] for those Gaussians (zeros if culled in this
@@ -186,6 +215,13 @@ int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t 
 int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
                    const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, float *acc_xyz,
                    float *acc_rgb, int32_t *cnt, gs_stream_t stream);
+
+/* gs_project_bwd that ADDS its gradient rows into G instead of writing them
+ * (several views of one scene in one optimiser step: call gs_project_bwd for
+ * the first view, this for the others). */
+int gs_project_bwd_accum(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
+                         const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, float *acc_xyz,
+                         float *acc_rgb, int32_t *cnt, gs_stream_t stream);
 
 /* gs_raster_bwd followed by gs_project_bwd on the same stream. */
 int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
@@ -241,6 +277,76 @@ int gs_freeze_update_noalloc(int64_t n, float *acc_xyz, float *acc_rgb, int32_t 
 int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
                    const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps, int64_t step,
                    gs_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Learned freeze predictor. The paper has no learned component: these
+ * calls build a small network that proposes Gaussians the gradient-norm
+ * rule (Sec. 3.2.1, Eqs. 4-6) is about to freeze, so they can be frozen
+ * earlier; the rule stays in force and judges the proposals.
+ * --------------------------------------------------------------------- */
+#define GS_MLP_IN 16
+#define GS_MLP_HIDDEN 64
+#define GS_MLP_PARAMS 5313 /* W1[16][64] b1[64] W2[64][64] b2[64] W3[64] b3 */
+#define GS_MLP_WEIGHTS 5184 /* bf16 copies of W1, W2, W3 */
+
+/* Statistics boundary update of the predictor state state[n][12] (float32):
+ * 0-3 xyz-norm EMA history (newest first), 4-7 rgb history, 8 xyz EMA,
+ * 9 rgb EMA, 10 visible iterations, 11 boundaries spent frozen. For each
+ * Gaussian with cnt > 0: EMA = 0.5 EMA + 0.5 acc/cnt, views += cnt; frozen
+ * count += frozen[i] (frozen may be NULL); the histories shift and take the
+ * EMA at the front. Call before gs_freeze_update clears the statistics.
+ * Errors: INVALID_ARG, CUDA. */
+int gs_pred_history(int64_t n, const float *acc_xyz, const float *acc_rgb, const int32_t *cnt, const uint8_t *frozen,
+                    float *state, gs_stream_t stream);
+
+/* The 16 predictor features of every Gaussian, as bfloat16 X[n][16]:
+ * 0-3 and 4-7 log10(history / eps_xyz | eps_rgb) clamped to [-8, 8] (norms
+ * floored at 1e-30), 8 sigmoid(opacity logit), 9 largest and 10 smallest
+ * log-scale, 11 ln(1 + visible iterations), 12 k / K, 13-14 log10 of the
+ * current window's average norms over the thresholds (0 if never visible),
+ * 15 min(boundaries spent frozen, 8) / 8. P [n][64], state [n][12].
+ * Errors: INVALID_ARG, CUDA. */
+int gs_pred_features(int64_t n, const float *P, const float *acc_xyz, const float *acc_rgb, const int32_t *cnt,
+                     const float *state, int32_t k, int32_t K, float eps_xyz, float eps_rgb, uint16_t *X,
+                     gs_stream_t stream);
+
+/* Inference p[i] = sigmoid(relu(relu(X W1 + b1) W2 + b2) . W3 + b3) on the
+ * tensor cores (bf16 inputs X[n][16] and weights wb[5184], the first hidden
+ * layer rounded to bf16, float32 accumulation; biases from params[5313]).
+ * Errors: INVALID_ARG, CUDA. */
+int gs_mlp_fwd(int64_t n, const uint16_t *X, const uint16_t *wb, const float *params, float *p, gs_stream_t stream);
+
+/* Gradient of the weighted binary cross-entropy
+ *   L = inv_wsum * sum_i w_i (softplus(z_i) - y_i z_i)   (w NULL: all 1)
+ * over the 5313 parameters, ADDED into grad[5313] (zero it first); the loss
+ * is added into *loss_dev if loss_dev is not NULL. The forward is the
+ * inference above computed in float32; gradients pass through the bf16
+ * roundings as the identity. Errors: INVALID_ARG, CUDA. */
+int gs_mlp_grad(int64_t n, const uint16_t *X, const float *y, const float *w, float inv_wsum, const uint16_t *wb,
+                const float *params, float *grad, float *loss_dev, gs_stream_t stream);
+
+/* Adam step on the float32 parameters (bias-corrected at `step` >= 1) that
+ * also refreshes the bf16 weight copies wb. Errors: INVALID_ARG, CUDA. */
+int gs_mlp_adam(float *params, const float *grad, float *m, float *v, uint16_t *wb, float lr, float b1, float b2,
+                float eps, int64_t step, gs_stream_t stream);
+
+/* wb = bf16(W1, W2, W3) of params. Errors: INVALID_ARG, CUDA. */
+int gs_mlp_refresh(const float *params, uint16_t *wb, gs_stream_t stream);
+
+/* Freezes every Gaussian with prob[i] > tau (the map only grows; the
+ * statistics are not touched) and rebuilds act / n_active_dev as
+ * gs_freeze_update does. Workspace as gs_freeze_workspace_bytes(n).
+ * Errors: INVALID_ARG, CUDA. */
+int gs_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen, int32_t *act, int32_t *n_active_dev,
+                    void *ws, size_t ws_bytes, gs_stream_t stream);
+
+/* gs_adam_masked with the step counter in device memory: *step_dev is
+ * advanced by one and the bias correction taken at the new value, so a
+ * captured CUDA graph can replay the update step after step. scratch_dev:
+ * two floats of device memory. Errors: INVALID_ARG, CUDA. */
+int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
+                           const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
+                           int64_t *step_dev, float *scratch_dev, gs_stream_t stream);
 
 /* Bytes of workspace gs_psnr needs for S images of H x W. */
 size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W);

@@ -34,7 +34,7 @@ inline bool camera_ok(const gs_camera *c) {
     return true;
 }
 
-inline DevCam make_cam(const gs_camera *c) {
+__host__ __device__ inline DevCam make_cam(const gs_camera *c) {
     DevCam d;
     d.W = c->width;
     d.H = c->height;

@@ -66,6 +66,21 @@ __global__ void __launch_bounds__(kFB) k_freeze_emit(int64_t n, const uint8_t *_
     if (a) act[part[blockIdx.x] + r] = (int32_t)i;
 }
 
+// Freezes every Gaussian whose predicted probability exceeds tau (the map
+// only grows); the gradient statistics are left to the rule.
+__global__ void __launch_bounds__(kFB) k_freeze_mark_pred(int64_t n, const float *__restrict__ prob, float tau,
+                                                         uint8_t *__restrict__ frozen, int32_t *__restrict__ part) {
+    int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    int active = 0;
+    if (i < n) {
+        const bool f = frozen[i] || prob[i] > tau;
+        frozen[i] = f ? 1 : 0;
+        active = !f;
+    }
+    int c = __syncthreads_count(active);
+    if (threadIdx.x == 0) part[blockIdx.x] = c;
+}
+
 struct AdamArgs {
     float lr[64];  // per float of a row (group rate; 0 for padding)
     float b1, b2, eps, step_size_scale, inv_sqrt_bc2;
@@ -73,10 +88,23 @@ struct AdamArgs {
 
 constexpr int kChunks = 15;  // 16-byte vectors per row holding the 59 parameters
 
+// Step counter kept on the device (for CUDA-graph replay): advances it and
+// stores 1 / (1 - b1^t) and 1 / sqrt(1 - b2^t) for the update that follows.
+__global__ void k_adam_step(int64_t *__restrict__ step, float b1, float b2, float *__restrict__ scales) {
+    const int64_t t = *step + 1;
+    *step = t;
+    scales[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    scales[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, (double)t)));
+}
+
 __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float *__restrict__ G,
                                               float *__restrict__ m, float *__restrict__ v,
                                               const int32_t *__restrict__ act, const int32_t *__restrict__ n_active,
-                                              AdamArgs a) {
+                                              AdamArgs a, const float *__restrict__ scales) {
+    if (scales) {
+        a.step_size_scale = scales[0];
+        a.inv_sqrt_bc2 = scales[1];
+    }
     const int64_t total = (int64_t)(*n_active) * kChunks;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -145,6 +173,21 @@ extern "C" int gs_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32
     return launch_status();
 }
 
+extern "C" int gs_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen, int32_t *act,
+                               int32_t *n_active_dev, void *ws, size_t ws_bytes, gs_stream_t stream) {
+    if (n < 0 || n > INT32_MAX || !n_active_dev || !(tau >= 0.f && tau <= 1.f)) return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!prob || !frozen || !act)) return GS_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < gs_freeze_workspace_bytes(n)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    int nb = (int)((n + kFB - 1) / kFB);
+    int32_t *part = static_cast<int32_t *>(ws);
+    if (nb > 0) k_freeze_mark_pred<<<nb, kFB, 0, s>>>(n, prob, tau, frozen, part);
+    k_freeze_scan<<<1, 1024, 0, s>>>(part, nb, n_active_dev);
+    if (nb > 0) k_freeze_emit<<<nb, kFB, 0, s>>>(n, frozen, part, act);
+    note_launches(nb > 0 ? 3 : 1);
+    return launch_status();
+}
+
 extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
                               const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
                               int64_t step, gs_stream_t stream) {
@@ -170,8 +213,39 @@ extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int6
     int64_t blocks = (max_items + 255) / 256;
     int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a);
+    k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a, nullptr);
     note_launches(1);
+    return launch_status();
+}
+
+extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
+                                      const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
+                                      int64_t *step_dev, float *scratch_dev, gs_stream_t stream) {
+    if (n < 0 || !lr || !n_active_dev || !step_dev || !scratch_dev) return GS_ERR_INVALID_ARG;
+    if (!(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps >= 0.f)) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    if (!P || !G || !m || !v || !act) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(G) | reinterpret_cast<uintptr_t>(m) |
+         reinterpret_cast<uintptr_t>(v)) & 15)
+        return GS_ERR_INVALID_ARG;
+    AdamArgs a;
+    static const int group_of[64] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5,
+                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5,
+                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, -1};
+    for (int f = 0; f < 64; ++f) a.lr[f] = group_of[f] >= 0 ? lr[group_of[f]] : 0.f;
+    a.b1 = b1;
+    a.b2 = b2;
+    a.eps = eps;
+    a.step_size_scale = 1.f;
+    a.inv_sqrt_bc2 = 1.f;
+    cudaStream_t s = as_stream(stream);
+    k_adam_step<<<1, 1, 0, s>>>(step_dev, b1, b2, scratch_dev);
+    const int64_t max_items = n * kChunks;
+    int64_t blocks = (max_items + 255) / 256;
+    int64_t cap = (int64_t)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    k_adam<<<(unsigned)blocks, 256, 0, s>>>(P, G, m, v, act, n_active_dev, a, scratch_dev);
+    note_launches(2);
     return launch_status();
 }
 

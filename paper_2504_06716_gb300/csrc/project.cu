@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P
     o[2] = make_float4(rgb[2], g.tz, __int_as_float(radius), __int_as_float(tiles));
 }
 
-// Backward of the projection for act[0 .. *n_active). See gs_project_bwd.
+// Backward of the projection for act[0 .. *n_active). See gs_project_bwd;
+// with ACC the gradient rows are added to G instead of written.
+template <bool ACC>
 __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, DevCam cam,
                                                      const float *__restrict__ splats, const int32_t *__restrict__ act,
                                                      const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
@@ -229,8 +231,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
     const int radius = __float_as_int(__ldg(splats + i * kSplat + 10));
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (radius <= 0) {
+        if (!ACC) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) gout[c] = z4;
+            for (int c = 0; c < 16; ++c) gout[c] = z4;
+        }
         return;
     }
     float4 *g2p = reinterpret_cast<float4 *>(grad2d + i * kG2d);
@@ -380,7 +384,14 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
 #pragma unroll
     for (int f = 59; f < 64; ++f) grow[f] = 0.f;
 #pragma unroll
-    for (int c = 0; c < 16; ++c) gout[c] = make_float4(grow[4 * c], grow[4 * c + 1], grow[4 * c + 2], grow[4 * c + 3]);
+    for (int c = 0; c < 16; ++c) {
+        float4 v = make_float4(grow[4 * c], grow[4 * c + 1], grow[4 * c + 2], grow[4 * c + 3]);
+        if (ACC) {
+            const float4 o = gout[c];
+            v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+        }
+        gout[c] = v;
+    }
 
     if (cnt) {
         float ex = dmx * 0.5f * (float)cam.W, ey = dmy * 0.5f * (float)cam.H;
@@ -406,9 +417,10 @@ extern "C" int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs
     return launch_status();
 }
 
-extern "C" int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
-                              const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d,
-                              float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt, gs_stream_t stream) {
+template <bool ACC>
+static int project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
+                       const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, float *acc_xyz,
+                       float *acc_rgb, int32_t *cnt, gs_stream_t stream) {
     if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam)) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !splats || !act || !n_active_dev || !grad2d || !G) return GS_ERR_INVALID_ARG;
@@ -417,8 +429,24 @@ extern "C" int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, cons
     if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(splats) | reinterpret_cast<uintptr_t>(grad2d) |
          reinterpret_cast<uintptr_t>(G)) & 15)
         return GS_ERR_INVALID_ARG;
-    k_project_bwd<<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, make_cam(cam), splats, act,
-                                                                    n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt);
+    k_project_bwd<ACC><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, make_cam(cam), splats, act,
+                                                                         n_active_dev, grad2d, G, acc_xyz, acc_rgb,
+                                                                         cnt);
     note_launches(1);
     return launch_status();
+}
+
+extern "C" int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
+                              const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d,
+                              float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt, gs_stream_t stream) {
+    return project_bwd<false>(P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt,
+                              stream);
+}
+
+extern "C" int gs_project_bwd_accum(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
+                                    const float *splats, const int32_t *act, const int32_t *n_active_dev,
+                                    float *grad2d, float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt,
+                                    gs_stream_t stream) {
+    return project_bwd<true>(P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt,
+                             stream);
 }

@@ -14,26 +14,26 @@
 // accumulator goes to global memory with one atomic per value per tile.
 #include "common.cuh"
 
+static_assert(sizeof(gs_camera) == 112, "gs_camera layout");
+static_assert(sizeof(gs_raster_job) == 184, "gs_raster_job layout");
+
 namespace gs {
 namespace {
 
-constexpr int kBatch = 256;
 
 // A thread owns PPT pixels of its tile, (x, y + k TS/PPT) for k < PPT. Each
 // splat staged in shared memory is loaded once per PPT evaluations, and the
 // per-pixel update is written with selects instead of branches so the PPT
 // independent chains interleave.
 template <int TS, int PPT, int B>
-__global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const float *__restrict__ splats,
-                                                              const uint32_t *__restrict__ vals,
-                                                              const uint32_t *__restrict__ ranges, DevCam cam,
-                                                              float *__restrict__ image, float *__restrict__ t_final,
-                                                              int32_t *__restrict__ n_last) {
+__device__ __forceinline__ void render_tile(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
+                                            const uint32_t *__restrict__ ranges, const DevCam &cam,
+                                            float *__restrict__ image, float *__restrict__ t_final,
+                                            int32_t *__restrict__ n_last, int tile) {
     constexpr int NT = TS * TS / PPT;  // threads; B = splats per staged batch
     __shared__ float4 s_xyab[B];
     __shared__ float4 s_cocg[B];
     __shared__ float s_blue[B];
-    const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (int)(threadIdx.x % TS);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
@@ -104,6 +104,15 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const float *__res
             n_last[pix] = last[k];
         }
     }
+}
+
+template <int TS, int PPT, int B>
+__global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const float *__restrict__ splats,
+                                                              const uint32_t *__restrict__ vals,
+                                                              const uint32_t *__restrict__ ranges, DevCam cam,
+                                                              float *__restrict__ image, float *__restrict__ t_final,
+                                                              int32_t *__restrict__ n_last) {
+    render_tile<TS, PPT, B>(splats, vals, ranges, cam, image, t_final, n_last, blockIdx.x);
 }
 
 // Sum of nine per-lane values over a warp by recursive halving: at each of
@@ -202,14 +211,11 @@ __device__ __forceinline__ void pix_load(PixBwd &p, bool inside, int64_t pix, in
 }
 
 template <int TS, int PPT, int B>
-__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__restrict__ splats,
-                                                              const uint32_t *__restrict__ vals,
-                                                              const uint32_t *__restrict__ ranges, DevCam cam,
-                                                              const float *__restrict__ t_final,
-                                                              const int32_t *__restrict__ n_last,
-                                                              const float *__restrict__ dl_dimage,
-                                                              const uint8_t *__restrict__ frozen,
-                                                              float *__restrict__ grad2d) {
+__device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
+                                                const uint32_t *__restrict__ ranges, const DevCam &cam,
+                                                const float *__restrict__ t_final, const int32_t *__restrict__ n_last,
+                                                const float *__restrict__ dl_dimage, const uint8_t *__restrict__ frozen,
+                                                float *__restrict__ grad2d, int tile) {
     constexpr int NT = TS * TS / PPT;
     __shared__ float4 s_xyab[B];
     __shared__ float4 s_cocg[B];
@@ -218,7 +224,6 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__res
     __shared__ int s_frz[B];
     __shared__ float s_acc[9][B];
     __shared__ int s_maxlast;
-    const int tile = blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (int)(threadIdx.x % TS);
     const uint32_t start = ranges[2 * tile];
@@ -290,6 +295,54 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__res
     }
 }
 
+template <int TS, int PPT, int B>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__restrict__ splats,
+                                                              const uint32_t *__restrict__ vals,
+                                                              const uint32_t *__restrict__ ranges, DevCam cam,
+                                                              const float *__restrict__ t_final,
+                                                              const int32_t *__restrict__ n_last,
+                                                              const float *__restrict__ dl_dimage,
+                                                              const uint8_t *__restrict__ frozen,
+                                                              float *__restrict__ grad2d) {
+    raster_bwd_tile<TS, PPT, B>(splats, vals, ranges, cam, t_final, n_last, dl_dimage, frozen, grad2d, blockIdx.x);
+}
+
+// ---- many views of many scenes in one persistent launch ----
+// CTAs pull (job, tile) items from a device counter until the batch is done,
+// so jobs of uneven cost (scenes of different sizes) share the GPU without a
+// per-job launch. Every job of a batch has the same image size and tile.
+__device__ __forceinline__ int next_item(uint32_t *queue, int *s_item) {
+    __syncthreads();  // every thread is done with the previous item's shared memory
+    if (threadIdx.x == 0) *s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    return *s_item;
+}
+
+template <int TS, int PPT, int B>
+__global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd_batch(const gs_raster_job *__restrict__ jobs,
+                                                                    int tiles_per_job, int total,
+                                                                    uint32_t *__restrict__ queue) {
+    __shared__ int s_item;
+    for (int item = next_item(queue, &s_item); item < total; item = next_item(queue, &s_item)) {
+        const gs_raster_job &j = jobs[item / tiles_per_job];
+        const DevCam cam = make_cam(&j.cam);
+        render_tile<TS, PPT, B>(j.splats, j.vals, j.ranges, cam, j.image, j.t_final, j.n_last, item % tiles_per_job);
+    }
+}
+
+template <int TS, int PPT, int B>
+__global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd_batch(const gs_raster_job *__restrict__ jobs,
+                                                                    int tiles_per_job, int total,
+                                                                    uint32_t *__restrict__ queue) {
+    __shared__ int s_item;
+    for (int item = next_item(queue, &s_item); item < total; item = next_item(queue, &s_item)) {
+        const gs_raster_job &j = jobs[item / tiles_per_job];
+        const DevCam cam = make_cam(&j.cam);
+        raster_bwd_tile<TS, PPT, B>(j.splats, j.vals, j.ranges, cam, j.t_final, j.n_last, j.dl_dimage, j.frozen,
+                                    j.grad2d, item % tiles_per_job);
+    }
+}
+
 // Launch shape used when the caller gives none: pixels per thread and batch
 // size of each kernel by tile size (timed on GB300; the autotuner may pick
 // another per workload).
@@ -329,6 +382,35 @@ template <int TS, int PPT, int B>
 void launch(const BwdArgs &a, cudaStream_t s) {
     k_raster_bwd<TS, PPT, B><<<a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, 0, s>>>(
         a.splats, a.vals, a.ranges, a.cam, a.t_final, a.n_last, a.dl, a.frozen, a.grad2d);
+}
+
+struct BatchArgs {
+    const gs_raster_job *jobs;
+    int tiles_per_job, total;
+    uint32_t *queue;
+    bool bwd;
+};
+
+template <class K>
+int resident_ctas(K kernel, int threads) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (sms > 0 ? sms : 152) * per_sm;
+}
+
+template <int TS, int PPT, int B>
+void launch(const BatchArgs &a, cudaStream_t s) {
+    constexpr int NT = TS * TS / PPT;
+    if (a.bwd) {
+        const int grid = resident_ctas(k_raster_bwd_batch<TS, PPT, B>, NT);
+        k_raster_bwd_batch<TS, PPT, B><<<grid, NT, 0, s>>>(a.jobs, a.tiles_per_job, a.total, a.queue);
+    } else {
+        const int grid = resident_ctas(k_render_fwd_batch<TS, PPT, B>, NT);
+        k_render_fwd_batch<TS, PPT, B><<<grid, NT, 0, s>>>(a.jobs, a.tiles_per_job, a.total, a.queue);
+    }
 }
 
 template <int TS, int PPT, class A>
@@ -400,4 +482,30 @@ extern "C" int gs_raster_bwd(const float *splats, const uint32_t *vals, const ui
                              const float *t_final, const int32_t *n_last, const float *dl_dimage,
                              const uint8_t *frozen, float *grad2d, gs_stream_t stream) {
     return gs_raster_bwd_cfg(splats, vals, ranges, cam, nullptr, t_final, n_last, dl_dimage, frozen, grad2d, stream);
+}
+
+static int batch_common(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
+                        const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream, bool bwd) {
+    if (!jobs_dev || !queue_dev || n_jobs < 0 || width <= 0 || height <= 0 || !tile_ok(tile) || !config_ok(cfg))
+        return GS_ERR_INVALID_ARG;
+    if (n_jobs == 0) return GS_OK;
+    const int64_t tiles = (int64_t)((width + tile - 1) / tile) * ((height + tile - 1) / tile);
+    if (tiles * n_jobs > INT32_MAX) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(queue_dev, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    BatchArgs a{jobs_dev, (int)tiles, (int)(tiles * n_jobs), queue_dev, bwd};
+    int ppt, batch;
+    default_config(tile, bwd, ppt, batch);
+    if (cfg) { ppt = cfg->pixels_per_thread; batch = cfg->batch; }
+    return dispatch(tile, ppt, batch, a, s);
+}
+
+extern "C" int gs_render_fwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height,
+                                   int32_t tile, const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream) {
+    return batch_common(jobs_dev, n_jobs, width, height, tile, cfg, queue_dev, stream, false);
+}
+
+extern "C" int gs_raster_bwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height,
+                                   int32_t tile, const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream) {
+    return batch_common(jobs_dev, n_jobs, width, height, tile, cfg, queue_dev, stream, true);
 }

@@ -82,12 +82,24 @@ _SIGS = {
     "gs_loss": ([_P, _P, _I32, _I32, _F32, _P, _SZ, _P, _P, _P], _I32),
     "gs_raster_bwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P, _P, _P], _I32),
     "gs_project_bwd": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_project_bwd_accum": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_render_fwd_batch": ([_P, _I32, _I32, _I32, _I32, ctypes.POINTER(GsRasterConfig), _P, _P], _I32),
+    "gs_raster_bwd_batch": ([_P, _I32, _I32, _I32, _I32, ctypes.POINTER(GsRasterConfig), _P, _P], _I32),
     "gs_render_bwd": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
     "gs_freeze_workspace_bytes": ([_I64], _SZ),
     "gs_freeze_update": ([_I64, _P, _P, _P, _P, _F32, _F32, _I32, _P, _P, _P, _SZ, _P], _I32),
     "gs_freeze_update_noalloc": ([_I64, _P, _P, _P, _P, _F32, _F32, _I32, _P, _P, _P], _I32),
     "gs_adam_masked": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_float), _F32, _F32, _F32, _I64, _P],
                        _I32),
+    "gs_pred_history": ([_I64, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_pred_features": ([_I64, _P, _P, _P, _P, _P, _I32, _I32, _F32, _F32, _P, _P], _I32),
+    "gs_mlp_fwd": ([_I64, _P, _P, _P, _P, _P], _I32),
+    "gs_mlp_grad": ([_I64, _P, _P, _P, _F32, _P, _P, _P, _P, _P], _I32),
+    "gs_mlp_adam": ([_P, _P, _P, _P, _P, _F32, _F32, _F32, _F32, _I64, _P], _I32),
+    "gs_mlp_refresh": ([_P, _P, _P], _I32),
+    "gs_freeze_apply": ([_I64, _P, _F32, _P, _P, _P, _P, _SZ, _P], _I32),
+    "gs_adam_masked_devstep": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_float), _F32, _F32, _F32, _P,
+                                _P, _P], _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
     "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
     "gs_get_device_error": ([ctypes.POINTER(ctypes.c_uint32), _P], _I32),
@@ -231,6 +243,41 @@ def gs_project_bwd(P, n: int, sh_degree: int, cam: GsCamera, splats, act, n_acti
         _ptr(cnt, torch.int32, "cnt"), _stream(stream)))
 
 
+def gs_project_bwd_accum(P, n: int, sh_degree: int, cam: GsCamera, splats, act, n_active, grad2d, G, acc_xyz=None,
+                         acc_rgb=None, cnt=None, stream=None):
+    import torch
+
+    _check("gs_project_bwd_accum", load().gs_project_bwd_accum(
+        _ptr(P, torch.float32, "P"), n, sh_degree, ctypes.byref(cam), _ptr(splats, torch.float32, "splats"),
+        _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(grad2d, torch.float32, "grad2d"),
+        _ptr(G, torch.float32, "G"), _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _stream(stream)))
+
+
+class GsRasterJob(ctypes.Structure):
+    _fields_ = [("splats", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
+                ("image", ctypes.c_void_p), ("t_final", ctypes.c_void_p), ("n_last", ctypes.c_void_p),
+                ("dl_dimage", ctypes.c_void_p), ("frozen", ctypes.c_void_p), ("grad2d", ctypes.c_void_p),
+                ("cam", GsCamera)]
+
+
+def gs_render_fwd_batch(jobs_dev, n_jobs: int, width: int, height: int, tile: int, cfg, queue, stream=None):
+    """jobs_dev: uint8 device tensor holding n_jobs GsRasterJob records."""
+    import torch
+
+    _check("gs_render_fwd_batch", load().gs_render_fwd_batch(
+        _ptr(jobs_dev, torch.uint8, "jobs"), n_jobs, width, height, tile, None if cfg is None else ctypes.byref(cfg),
+        _ptr(queue, torch.int32, "queue"), _stream(stream)))
+
+
+def gs_raster_bwd_batch(jobs_dev, n_jobs: int, width: int, height: int, tile: int, cfg, queue, stream=None):
+    import torch
+
+    _check("gs_raster_bwd_batch", load().gs_raster_bwd_batch(
+        _ptr(jobs_dev, torch.uint8, "jobs"), n_jobs, width, height, tile, None if cfg is None else ctypes.byref(cfg),
+        _ptr(queue, torch.int32, "queue"), _stream(stream)))
+
+
 def gs_render_bwd(P, n: int, sh_degree: int, cam: GsCamera, splats, vals, ranges, t_final, n_last, dl_dimage, frozen,
                   act, n_active, grad2d, G, acc_xyz=None, acc_rgb=None, cnt=None, stream=None):
     import torch
@@ -278,6 +325,80 @@ def gs_adam_masked(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, 
         _ptr(P, torch.float32, "P"), _ptr(G, torch.float32, "G"), _ptr(m, torch.float32, "m"),
         _ptr(v, torch.float32, "v"), n, _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
         lr6, b1, b2, eps, step, _stream(stream)))
+
+
+def gs_adam_masked_devstep(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, eps: float, step_dev,
+                           scratch, stream=None):
+    import torch
+
+    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
+    _check("gs_adam_masked_devstep", load().gs_adam_masked_devstep(
+        _ptr(P, torch.float32, "P"), _ptr(G, torch.float32, "G"), _ptr(m, torch.float32, "m"),
+        _ptr(v, torch.float32, "v"), n, _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
+        lr6, b1, b2, eps, _ptr(step_dev, torch.int64, "step"), _ptr(scratch, torch.float32, "scratch"),
+        _stream(stream)))
+
+
+MLP_PARAMS, MLP_WEIGHTS = 5313, 5184
+
+
+def gs_pred_history(n: int, acc_xyz, acc_rgb, cnt, frozen, state, stream=None):
+    import torch
+
+    _check("gs_pred_history", load().gs_pred_history(
+        n, _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _ptr(frozen, torch.uint8, "frozen"), _ptr(state, torch.float32, "state"),
+        _stream(stream)))
+
+
+def gs_pred_features(n: int, P, acc_xyz, acc_rgb, cnt, state, k: int, K: int, eps_xyz: float, eps_rgb: float, X,
+                     stream=None):
+    import torch
+
+    _check("gs_pred_features", load().gs_pred_features(
+        n, _ptr(P, torch.float32, "P"), _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _ptr(state, torch.float32, "state"), k, K, eps_xyz, eps_rgb,
+        _ptr(X, torch.bfloat16, "X"), _stream(stream)))
+
+
+def gs_mlp_fwd(n: int, X, wb, params, p, stream=None):
+    import torch
+
+    _check("gs_mlp_fwd", load().gs_mlp_fwd(n, _ptr(X, torch.bfloat16, "X"), _ptr(wb, torch.bfloat16, "wb"),
+                                           _ptr(params, torch.float32, "params"), _ptr(p, torch.float32, "p"),
+                                           _stream(stream)))
+
+
+def gs_mlp_grad(n: int, X, y, w, inv_wsum: float, wb, params, grad, loss=None, stream=None):
+    import torch
+
+    _check("gs_mlp_grad", load().gs_mlp_grad(
+        n, _ptr(X, torch.bfloat16, "X"), _ptr(y, torch.float32, "y"), _ptr(w, torch.float32, "w"), inv_wsum,
+        _ptr(wb, torch.bfloat16, "wb"), _ptr(params, torch.float32, "params"), _ptr(grad, torch.float32, "grad"),
+        _ptr(loss, torch.float32, "loss"), _stream(stream)))
+
+
+def gs_mlp_adam(params, grad, m, v, wb, lr: float, b1: float, b2: float, eps: float, step: int, stream=None):
+    import torch
+
+    _check("gs_mlp_adam", load().gs_mlp_adam(
+        _ptr(params, torch.float32, "params"), _ptr(grad, torch.float32, "grad"), _ptr(m, torch.float32, "m"),
+        _ptr(v, torch.float32, "v"), _ptr(wb, torch.bfloat16, "wb"), lr, b1, b2, eps, step, _stream(stream)))
+
+
+def gs_mlp_refresh(params, wb, stream=None):
+    import torch
+
+    _check("gs_mlp_refresh", load().gs_mlp_refresh(_ptr(params, torch.float32, "params"),
+                                                   _ptr(wb, torch.bfloat16, "wb"), _stream(stream)))
+
+
+def gs_freeze_apply(n: int, prob, tau: float, frozen, act, n_active, ws, stream=None):
+    import torch
+
+    _check("gs_freeze_apply", load().gs_freeze_apply(
+        n, _ptr(prob, torch.float32, "prob"), tau, _ptr(frozen, torch.uint8, "frozen"), _ptr(act, torch.int32, "act"),
+        _ptr(n_active, torch.int32, "n_active"), _ptr(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
 
 
 def gs_psnr_workspace_bytes(S: int, H: int, W: int) -> int:

@@ -65,6 +65,97 @@ class Trainer:
         self.k = 0
         self.capacity_check_every = 100
         self.overflows = 0
+        # learned freeze predictor (predictor.py): state, logging, application
+        self.pred_state = None
+        self.log = None
+        self.predictor = None
+        self.pred_tau, self.pred_every = 0.9, 100
+        self.pred_count = 0
+        self.shadow = False  # evaluation: judge newly frozen Gaussians on their unmasked gradients
+        self.shadow_checked = {"rule": 0, "pred": 0}
+        self.shadow_false = {"rule": 0, "pred": 0}
+        self._shadow_sets = {}
+
+    def enable_predictor_state(self):
+        n, dev = self.model.n, self.device
+        self.pred_state = torch.zeros((n, 12), dtype=torch.float32, device=dev)
+        self.pred_X = torch.zeros((n, 16), dtype=torch.bfloat16, device=dev)
+        self.pred_p = torch.zeros(n, dtype=torch.float32, device=dev)
+
+    def _features(self, k: int, ex: float, er: float):
+        m = self.model
+        lib.gs_pred_features(m.n, m.P, m.acc_xyz, m.acc_rgb, m.cnt, self.pred_state, k, self.cfg.total_iter, ex, er,
+                             self.pred_X)
+        return self.pred_X
+
+    def _predictor_due(self, k: int) -> bool:
+        c, cfg = self.ctrl, self.cfg
+        if self.predictor is None or not cfg.freezing or c.finetune_left is not None or k % self.pred_every:
+            return False
+        end = cfg.window_end if c.stop_iter is None else min(cfg.window_end, c.stop_iter)
+        if k < cfg.warmup or k >= end:
+            return False
+        return c.last_reset is None or k - c.last_reset >= cfg.wait
+
+    def _apply_predictor(self, k: int):
+        m = self.model
+        ex, er = self.thresholds(k)
+        X = self._features(k, ex, er)
+        self.predictor.predict(X, self.pred_p)
+        before = m.frozen.clone() if self.shadow else None
+        n0 = int(m.n_active.item())
+        lib.gs_freeze_apply(m.n, self.pred_p, self.pred_tau, m.frozen, m.act, m.n_active, m.freeze_ws)
+        self.pred_count += n0 - int(m.n_active.item())
+        if self.shadow:
+            self._track("pred", (m.frozen == 1) & (before == 0))
+
+    def _track(self, source: str, newly):
+        cur = self._shadow_sets.get(source)
+        self._shadow_sets[source] = newly if cur is None else (cur | newly)
+
+    def _shadow_backward(self):
+        """Evaluation only: the unmasked gradient statistics of the Gaussians the
+        predictor froze in this window (no update is applied)."""
+        m, v = self.model, self.view
+        if not hasattr(self, "_sh"):
+            n = m.n
+            self._sh = dict(g2d=torch.zeros_like(m.grad2d), G=torch.zeros_like(m.G),
+                            ax=torch.zeros(n, device=self.device), ar=torch.zeros(n, device=self.device),
+                            cnt=torch.zeros(n, dtype=torch.int32, device=self.device))
+        sh = self._sh
+        union = None
+        for mask in self._shadow_sets.values():
+            union = mask if union is None else (union | mask)
+        idx = torch.nonzero(union).flatten().to(torch.int32)
+        if idx.numel() == 0:
+            return
+        sh["g2d"].zero_()
+        lib.gs_raster_bwd_cfg(m.splats, v.vals, v.ranges, v.cam, m.bwd_cfg, v.t_final, v.n_last, v.dl, None,
+                              sh["g2d"])
+        lib.gs_project_bwd(m.P, m.n, m.sh_degree, v.cam, m.splats, idx,
+                           torch.tensor([idx.numel()], dtype=torch.int32, device=self.device), sh["g2d"], sh["G"],
+                           sh["ax"], sh["ar"], sh["cnt"])
+
+    def _close_shadow_window(self, ex: float, er: float):
+        """At a statistics boundary: a Gaussian frozen during the window just ended
+        counts as a false freeze if its unmasked averages over that window would
+        not have passed the rule (Eq. 4/6)."""
+        if self._shadow_sets and hasattr(self, "_sh"):
+            sh = self._sh
+            c = sh["cnt"].clamp(min=1).float()
+            over = (sh["ax"] / c >= ex) | (sh["ar"] / c >= er)
+            for src, mask in self._shadow_sets.items():
+                seen = mask & (sh["cnt"] > 0)
+                self.shadow_checked[src] += int(seen.sum().item())
+                self.shadow_false[src] += int((seen & over).sum().item())
+            sh["ax"].zero_()
+            sh["ar"].zero_()
+            sh["cnt"].zero_()
+        self._shadow_sets = {}
+
+    def false_freeze_rate(self, source: str = "pred") -> float | None:
+        n = self.shadow_checked[source]
+        return self.shadow_false[source] / n if n else None
 
     def check_capacity(self, headroom: float = 0.8, grow: float = 1.5):
         """Read the sort's entry count and the device error word (one sync) and
@@ -143,7 +234,23 @@ class Trainer:
             if mode == FREEZE_UPDATE:
                 self._maybe_calibrate(k)
             ex, er = self.thresholds(k)
+            if self.pred_state is not None:
+                if self.log is not None and mode == FREEZE_UPDATE:
+                    self.log.features.append((k, self._features(k, ex, er).clone()))
+                if self.shadow:
+                    self._close_shadow_window(ex, er)
+                lib.gs_pred_history(m.n, m.acc_xyz, m.acc_rgb, m.cnt, m.frozen, self.pred_state)
+            before = m.frozen.clone() if (self.shadow and mode == FREEZE_UPDATE) else None
             m.freeze_update(ex, er, mode)
+            if before is not None:
+                self._track("rule", (m.frozen == 1) & (before == 0))
+            if self.log is not None:
+                if mode == FREEZE_UPDATE:
+                    self.log.frozen_after.append((k, m.frozen.cpu().numpy()))
+                elif mode == FREEZE_RESET:
+                    self.log.resets.append(k)
+        elif self._predictor_due(k):
+            self._apply_predictor(k)
         if c.wants_psnr(k):
             p = self.psnr_of(self.scene.subset_views)
             stop = c.report_psnr(k, p)
@@ -158,6 +265,8 @@ class Trainer:
         lrs = list(self.lrs)
         lrs[0] = c.lr_xyz_at(k)
         m.train_step(self.view, self.targets[v], lrs)
+        if self.shadow and self._shadow_sets:
+            self._shadow_backward()
         if c.after_step(k):
             m.freeze_update(0.0, 0.0, FREEZE_RESET)
         self.k += 1
@@ -175,7 +284,7 @@ def run(args) -> dict:
     torch.cuda.set_device(0)
     scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
     cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters)
-    tr = Trainer(scene, cfg)
+    tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
     tuning = None
     if args.autotune:
         for _ in range(args.tune_after):
@@ -204,7 +313,7 @@ def run(args) -> dict:
             t0 = time.perf_counter() - el  # held-out evaluation is not training time
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
-    out = dict(arm=args.arm, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(), evals=evals,
+    out = dict(arm=args.arm, calibrate=not args.no_calibrate, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(), evals=evals,
                events=tr.events, eps0=tr.eps0, tuning=tuning, overflows=tr.overflows,
                final_capacity=tr.view.capacity, device_flags=lib.gs_get_device_error())
     return out
@@ -221,6 +330,7 @@ def main():
     ap.add_argument("--iters", type=int, default=30000)
     ap.add_argument("--eval-every", type=int, default=1000)
     ap.add_argument("--autotune", action="store_true", help="tune the rasteriser launch shape first")
+    ap.add_argument("--no-calibrate", action="store_true", help="use the paper's initial thresholds as they are")
     ap.add_argument("--tune-after", type=int, default=300, help="iterations trained before tuning (then restarted)")
     args = ap.parse_args()
     print(json.dumps(run(args)))
