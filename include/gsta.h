@@ -70,6 +70,7 @@ typedef enum {
 #define GS_FLAG_CAPACITY 1u
 #define GS_FLAG_NONFINITE 2u
 #define GS_FLAG_TIMEOUT 4u
+#define GS_FLAG_BADJOB 8u /* a batch job whose camera differs from the batch's size or tile */
 
 typedef void *gs_stream_t; /* a cudaStream_t */
 
@@ -194,8 +195,10 @@ typedef struct {
  * (job, tile) items from a device counter (queue_dev, one uint32 of device
  * memory, reset by the call) until all jobs are done, so jobs of uneven cost
  * balance without one launch per job. jobs_dev is a DEVICE array; every job
- * must have this width, height and tile. Results equal gs_render_fwd per
- * job. Errors: INVALID_ARG, CUDA. */
+ * must have this width, height and tile (a job that does not is skipped and
+ * raises GS_FLAG_BADJOB). Results equal gs_render_fwd per job. The grid is
+ * the number of CTAs that fit on the device at once. Errors: INVALID_ARG,
+ * CUDA. */
 int gs_render_fwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
                         const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream);
 
@@ -340,12 +343,15 @@ int gs_mlp_refresh(const float *params, uint16_t *wb, gs_stream_t stream);
 int gs_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen, int32_t *act, int32_t *n_active_dev,
                     void *ws, size_t ws_bytes, gs_stream_t stream);
 
-/* gs_adam_masked with the step counter in device memory: *step_dev is
- * advanced by one and the bias correction taken at the new value, so a
- * captured CUDA graph can replay the update step after step. scratch_dev:
- * two floats of device memory. Errors: INVALID_ARG, CUDA. */
+/* gs_adam_masked with the step counter and the six group learning rates in
+ * device memory: *step_dev is advanced by one and the bias correction taken
+ * at the new value, and the rates are read from lr_dev [6] (same order as
+ * gs_adam_masked's lr) when the kernel runs, so a captured CUDA graph can
+ * replay the update step after step while the host changes the rates
+ * between replays. scratch_dev: two floats of device memory.
+ * Errors: INVALID_ARG, CUDA. */
 int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
-                           const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
+                           const int32_t *n_active_dev, const float *lr_dev, float b1, float b2, float eps,
                            int64_t *step_dev, float *scratch_dev, gs_stream_t stream);
 
 /* Bytes of workspace gs_psnr needs for S images of H x W. */

@@ -8,6 +8,7 @@ static std::atomic<unsigned long long> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 uint32_t take_sort_flags();
 uint32_t take_loss_flags();
+uint32_t take_render_flags();
 }  // namespace gs
 
 using namespace gs;
@@ -26,7 +27,7 @@ extern "C" int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const
 extern "C" int gs_get_device_error(uint32_t *flags_host, gs_stream_t stream) {
     if (!flags_host) return GS_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return GS_ERR_CUDA;
-    uint32_t f = take_sort_flags() | take_loss_flags();
+    uint32_t f = take_sort_flags() | take_loss_flags() | take_render_flags();
     if (cudaGetLastError() != cudaSuccess) return GS_ERR_CUDA;
     *flags_host = f;
     return f ? GS_ERR_DEVICE_FLAG : GS_OK;

@@ -97,13 +97,24 @@ __global__ void k_adam_step(int64_t *__restrict__ step, float b1, float b2, floa
     scales[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, (double)t)));
 }
 
+// Parameter group of float f of a row: xyz, scale, rotation, opacity, SH DC,
+// SH rest; -1 for the padding floats 59-63.
+__device__ __forceinline__ int lr_group(int f) {
+    return f < 3 ? 0 : f < 6 ? 1 : f < 10 ? 2 : f < 11 ? 3 : f < 14 ? 4 : f < 59 ? 5 : -1;
+}
+
 __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float *__restrict__ G,
                                               float *__restrict__ m, float *__restrict__ v,
                                               const int32_t *__restrict__ act, const int32_t *__restrict__ n_active,
-                                              AdamArgs a, const float *__restrict__ scales) {
+                                              AdamArgs a, const float *__restrict__ scales,
+                                              const float *__restrict__ lr_dev) {
     if (scales) {
         a.step_size_scale = scales[0];
         a.inv_sqrt_bc2 = scales[1];
+    }
+    if (lr_dev) {  // group rates from device memory (changed between graph replays)
+#pragma unroll
+        for (int f = 0; f < 64; ++f) a.lr[f] = lr_group(f) >= 0 ? lr_dev[lr_group(f)] : 0.f;
     }
     const int64_t total = (int64_t)(*n_active) * kChunks;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -213,15 +224,15 @@ extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int6
     int64_t blocks = (max_items + 255) / 256;
     int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a, nullptr);
+    k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a, nullptr, nullptr);
     note_launches(1);
     return launch_status();
 }
 
 extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
-                                      const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
+                                      const int32_t *n_active_dev, const float *lr_dev, float b1, float b2, float eps,
                                       int64_t *step_dev, float *scratch_dev, gs_stream_t stream) {
-    if (n < 0 || !lr || !n_active_dev || !step_dev || !scratch_dev) return GS_ERR_INVALID_ARG;
+    if (n < 0 || !lr_dev || !n_active_dev || !step_dev || !scratch_dev) return GS_ERR_INVALID_ARG;
     if (!(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps >= 0.f)) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !G || !m || !v || !act) return GS_ERR_INVALID_ARG;
@@ -229,10 +240,7 @@ extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float 
          reinterpret_cast<uintptr_t>(v)) & 15)
         return GS_ERR_INVALID_ARG;
     AdamArgs a;
-    static const int group_of[64] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5,
-                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5,
-                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, -1};
-    for (int f = 0; f < 64; ++f) a.lr[f] = group_of[f] >= 0 ? lr[group_of[f]] : 0.f;
+    for (int f = 0; f < 64; ++f) a.lr[f] = 0.f;  // taken from lr_dev on the device
     a.b1 = b1;
     a.b2 = b2;
     a.eps = eps;
@@ -244,7 +252,7 @@ extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float 
     int64_t blocks = (max_items + 255) / 256;
     int64_t cap = (int64_t)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    k_adam<<<(unsigned)blocks, 256, 0, s>>>(P, G, m, v, act, n_active_dev, a, scratch_dev);
+    k_adam<<<(unsigned)blocks, 256, 0, s>>>(P, G, m, v, act, n_active_dev, a, scratch_dev, lr_dev);
     note_launches(2);
     return launch_status();
 }

@@ -387,8 +387,9 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
     for (int c = 0; c < 16; ++c) {
         float4 v = make_float4(grow[4 * c], grow[4 * c + 1], grow[4 * c + 2], grow[4 * c + 3]);
         if (ACC) {
-            const float4 o = gout[c];
-            v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+            const float4 o = gout[c];  // a plain add, never fused with the product before it
+            v.x = __fadd_rn(v.x, o.x); v.y = __fadd_rn(v.y, o.y);
+            v.z = __fadd_rn(v.z, o.z); v.w = __fadd_rn(v.w, o.w);
         }
         gout[c] = v;
     }

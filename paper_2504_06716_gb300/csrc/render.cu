@@ -318,26 +318,39 @@ __device__ __forceinline__ int next_item(uint32_t *queue, int *s_item) {
     return *s_item;
 }
 
+__device__ uint32_t g_render_flags;
+
+// A job whose camera does not have the batch's image size and tile would
+// index its tile ranges and images with the wrong grid: it is skipped and
+// GS_FLAG_BADJOB raised (uniform across the CTA: every thread reads the same job).
+__device__ __forceinline__ bool job_ok(const DevCam &cam, int W, int H, int TS) {
+    if (cam.W == W && cam.H == H && cam.tile == TS) return true;
+    if (threadIdx.x == 0) atomicOr(&g_render_flags, GS_FLAG_BADJOB);
+    return false;
+}
+
 template <int TS, int PPT, int B>
 __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd_batch(const gs_raster_job *__restrict__ jobs,
-                                                                    int tiles_per_job, int total,
+                                                                    int W, int H, int tiles_per_job, int total,
                                                                     uint32_t *__restrict__ queue) {
     __shared__ int s_item;
     for (int item = next_item(queue, &s_item); item < total; item = next_item(queue, &s_item)) {
         const gs_raster_job &j = jobs[item / tiles_per_job];
         const DevCam cam = make_cam(&j.cam);
+        if (!job_ok(cam, W, H, TS)) continue;
         render_tile<TS, PPT, B>(j.splats, j.vals, j.ranges, cam, j.image, j.t_final, j.n_last, item % tiles_per_job);
     }
 }
 
 template <int TS, int PPT, int B>
 __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd_batch(const gs_raster_job *__restrict__ jobs,
-                                                                    int tiles_per_job, int total,
+                                                                    int W, int H, int tiles_per_job, int total,
                                                                     uint32_t *__restrict__ queue) {
     __shared__ int s_item;
     for (int item = next_item(queue, &s_item); item < total; item = next_item(queue, &s_item)) {
         const gs_raster_job &j = jobs[item / tiles_per_job];
         const DevCam cam = make_cam(&j.cam);
+        if (!job_ok(cam, W, H, TS)) continue;
         raster_bwd_tile<TS, PPT, B>(j.splats, j.vals, j.ranges, cam, j.t_final, j.n_last, j.dl_dimage, j.frozen,
                                     j.grad2d, item % tiles_per_job);
     }
@@ -386,7 +399,7 @@ void launch(const BwdArgs &a, cudaStream_t s) {
 
 struct BatchArgs {
     const gs_raster_job *jobs;
-    int tiles_per_job, total;
+    int W, H, tiles_per_job, total;
     uint32_t *queue;
     bool bwd;
 };
@@ -406,10 +419,10 @@ void launch(const BatchArgs &a, cudaStream_t s) {
     constexpr int NT = TS * TS / PPT;
     if (a.bwd) {
         const int grid = resident_ctas(k_raster_bwd_batch<TS, PPT, B>, NT);
-        k_raster_bwd_batch<TS, PPT, B><<<grid, NT, 0, s>>>(a.jobs, a.tiles_per_job, a.total, a.queue);
+        k_raster_bwd_batch<TS, PPT, B><<<grid, NT, 0, s>>>(a.jobs, a.W, a.H, a.tiles_per_job, a.total, a.queue);
     } else {
         const int grid = resident_ctas(k_render_fwd_batch<TS, PPT, B>, NT);
-        k_render_fwd_batch<TS, PPT, B><<<grid, NT, 0, s>>>(a.jobs, a.tiles_per_job, a.total, a.queue);
+        k_render_fwd_batch<TS, PPT, B><<<grid, NT, 0, s>>>(a.jobs, a.W, a.H, a.tiles_per_job, a.total, a.queue);
     }
 }
 
@@ -493,7 +506,7 @@ static int batch_common(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t w
     if (tiles * n_jobs > INT32_MAX) return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     if (cudaMemsetAsync(queue_dev, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-    BatchArgs a{jobs_dev, (int)tiles, (int)(tiles * n_jobs), queue_dev, bwd};
+    BatchArgs a{jobs_dev, width, height, (int)tiles, (int)(tiles * n_jobs), queue_dev, bwd};
     int ppt, batch;
     default_config(tile, bwd, ppt, batch);
     if (cfg) { ppt = cfg->pixels_per_thread; batch = cfg->batch; }
@@ -509,3 +522,12 @@ extern "C" int gs_raster_bwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs
                                    int32_t tile, const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream) {
     return batch_common(jobs_dev, n_jobs, width, height, tile, cfg, queue_dev, stream, true);
 }
+
+namespace gs {
+uint32_t take_render_flags() {
+    uint32_t f = 0, z = 0;
+    cudaMemcpyFromSymbol(&f, g_render_flags, sizeof(f));
+    cudaMemcpyToSymbol(g_render_flags, &z, sizeof(z));
+    return f;
+}
+}  // namespace gs

@@ -22,7 +22,7 @@ ROW = 64       # floats per parameter row
 SPLAT = 12     # floats per splat record
 GRAD2D = 12    # floats per raster-gradient row
 
-GS_FLAG_CAPACITY, GS_FLAG_NONFINITE, GS_FLAG_TIMEOUT = 1, 2, 4
+GS_FLAG_CAPACITY, GS_FLAG_NONFINITE, GS_FLAG_TIMEOUT, GS_FLAG_BADJOB = 1, 2, 4, 8
 
 
 class GsError(RuntimeError):
@@ -98,7 +98,7 @@ _SIGS = {
     "gs_mlp_adam": ([_P, _P, _P, _P, _P, _F32, _F32, _F32, _F32, _I64, _P], _I32),
     "gs_mlp_refresh": ([_P, _P, _P], _I32),
     "gs_freeze_apply": ([_I64, _P, _F32, _P, _P, _P, _P, _SZ, _P], _I32),
-    "gs_adam_masked_devstep": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(ctypes.c_float), _F32, _F32, _F32, _P,
+    "gs_adam_masked_devstep": ([_P, _P, _P, _P, _I64, _P, _P, _P, _F32, _F32, _F32, _P,
                                 _P, _P], _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
     "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
@@ -327,16 +327,16 @@ def gs_adam_masked(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, 
         lr6, b1, b2, eps, step, _stream(stream)))
 
 
-def gs_adam_masked_devstep(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, eps: float, step_dev,
+def gs_adam_masked_devstep(P, G, m, v, n: int, act, n_active, lr_dev, b1: float, b2: float, eps: float, step_dev,
                            scratch, stream=None):
+    """lr_dev: float32 device tensor of the six group rates."""
     import torch
 
-    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
     _check("gs_adam_masked_devstep", load().gs_adam_masked_devstep(
         _ptr(P, torch.float32, "P"), _ptr(G, torch.float32, "G"), _ptr(m, torch.float32, "m"),
         _ptr(v, torch.float32, "v"), n, _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
-        lr6, b1, b2, eps, _ptr(step_dev, torch.int64, "step"), _ptr(scratch, torch.float32, "scratch"),
-        _stream(stream)))
+        _ptr(lr_dev, torch.float32, "lr_dev"), b1, b2, eps, _ptr(step_dev, torch.int64, "step"),
+        _ptr(scratch, torch.float32, "scratch"), _stream(stream)))
 
 
 MLP_PARAMS, MLP_WEIGHTS = 5313, 5184

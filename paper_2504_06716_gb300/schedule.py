@@ -21,6 +21,8 @@ from __future__ import annotations
 
 import dataclasses
 
+import numpy as np
+
 FREEZE_UPDATE, FREEZE_RESET, FREEZE_CLEAR = 0, 1, 2
 
 
@@ -133,3 +135,24 @@ class GStaController:
             self.finetune_left = c.finetune_iters
             return True
         return False
+
+
+def calibrate_eps0(cfg: GStaConfig, ctrl: GStaController, k: int, acc_xyz: np.ndarray, acc_rgb: np.ndarray,
+                   cnt: np.ndarray):
+    """Threshold calibration at the first freeze update (a reading, not in the
+    paper: its initial thresholds were chosen by inspecting gradient magnitudes
+    of real scenes, Sec. 4.1). If the configured thresholds at iteration k would
+    freeze fewer than 5% or more than 95% of the visible Gaussians, returns
+    ((eps0_xyz, eps0_rgb), frac) with initial values that put the threshold at
+    iteration k on the 30th percentile of the averaged norms; else None."""
+    vis = cnt > 0
+    if vis.sum() == 0:
+        return None
+    ax = acc_xyz[vis] / cnt[vis]
+    ar = acc_rgb[vis] / cnt[vis]
+    ex, er = ctrl.thresholds(k)
+    frac = float(np.mean((ax < ex) & (ar < er)))
+    if 0.05 <= frac <= 0.95:
+        return None
+    scale = ex / cfg.eps0_xyz
+    return (float(np.percentile(ax, 30)) / scale, float(np.percentile(ar, 30)) / scale), frac

@@ -26,7 +26,7 @@ import numpy as np
 import torch
 
 from . import autotune, lib, pipeline, synth
-from .schedule import FREEZE_RESET, FREEZE_UPDATE, GStaConfig, GStaController
+from .schedule import FREEZE_RESET, FREEZE_UPDATE, GStaConfig, GStaController, calibrate_eps0
 
 
 class Trainer:
@@ -207,19 +207,11 @@ class Trainer:
             return
         self.calibrated = True
         m = self.model
-        cnt = m.cnt.cpu().numpy()
-        vis = cnt > 0
-        if vis.sum() == 0:
-            return
-        ax = m.acc_xyz.cpu().numpy()[vis] / cnt[vis]
-        ar = m.acc_rgb.cpu().numpy()[vis] / cnt[vis]
-        ex, er = self.ctrl.thresholds(k)
-        frac = float(np.mean((ax < ex) & (ar < er)))
-        if 0.05 <= frac <= 0.95:
-            return
-        scale = ex / self.cfg.eps0_xyz
-        self.eps0 = (float(np.percentile(ax, 30)) / scale, float(np.percentile(ar, 30)) / scale)
-        self.events.append((k, "calibrated", frac))
+        res = calibrate_eps0(self.cfg, self.ctrl, k, m.acc_xyz.cpu().numpy(), m.acc_rgb.cpu().numpy(),
+                             m.cnt.cpu().numpy())
+        if res is not None:
+            self.eps0 = res[0]
+            self.events.append((k, "calibrated", res[1]))
 
     def thresholds(self, k: int) -> tuple[float, float]:
         ex, er = self.ctrl.thresholds(k)
