@@ -250,12 +250,12 @@ def _close_training(pa, pb, steps, lrs):
             assert float((d > 1e-2 * lr).float().mean()) < 0.01, (lo, float((d > 1e-2 * lr).float().mean()))
 
 
-def test_graph_replay_trains_like_eager_and_like_per_job_launches():
+def test_graph_replay_trains_like_eager_serial_and_per_job_launches():
     from paper_2504_06716_gb300 import pipeline
 
     steps = 24
     runs = {}
-    for mode in ("graph", "batched", "per_job"):
+    for mode in ("graph", "batched", "serial", "per_job"):
         torch.manual_seed(0)
         bt = _tiny_batch()
         launches = [bt.step(mode) for _ in range(steps)]
@@ -267,6 +267,7 @@ def test_graph_replay_trains_like_eager_and_like_per_job_launches():
     lrs = pipeline.default_lrs(4.4)
     _close_training(runs["graph"][0], runs["batched"][0], steps, lrs)
     _close_training(runs["per_job"][0], runs["batched"][0], steps, lrs)
+    _close_training(runs["serial"][0], runs["batched"][0], steps, lrs)
 
 
 def test_batch_trains_scenes_to_completion_and_they_leave_the_batch():
