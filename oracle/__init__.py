@@ -85,10 +85,14 @@ def lib():
             L.or_render_brute.argtypes = [_i64, _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _ip, _ip, _fp, _dp]
             L.or_loss.argtypes = [_i32, _i32, _dp, _dp, ctypes.c_double, _dp]
             L.or_loss.restype = ctypes.c_double
+            L.or_loss_window.argtypes = [_i32, _i32, _dp, _dp, ctypes.c_double, _i32, _i32, _i32, _i32]
+            L.or_loss_window.restype = ctypes.c_double
             L.or_render_bwd.argtypes = [_i64, _i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _bp,
                                         _bp, _bp, _dp, _dp, _dp, _dp, _bp, _dp]
             L.or_render_pixels.argtypes = [_i64, _ip, _ip, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp,
                                            _ip, _dp]
+            L.or_render_pixels_locked.argtypes = [_i64, _ip, _ip, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _up, _up,
+                                                  _i32, _i64, _bp, _dp]
             L.or_project_bwd.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _bp, _dp, _dp, _dp, _dp, _dp,
                                          _dp, _dp]
             L.or_adam.argtypes = [_i64, _dp, _dp, _dp, _dp, _bp, _dp, ctypes.c_double, ctypes.c_double,
@@ -218,6 +222,35 @@ def loss(image, gt, lam: float = 0.2, grad: bool = True):
     g = np.zeros_like(x) if grad else None
     val = lib().or_loss(H, W, _p(x, _dp), _p(y, _dp), lam, _p(g, _dp))
     return val, g
+
+
+def loss_window(image, gt, x0: int, y0: int, x1: int, y1: int, lam: float = 0.2) -> float:
+    """The window [x0, x1) x [y0, y1)'s share of Eq. 3 (see or_loss_window)."""
+    x = _c(image, np.float64)
+    y = _c(gt, np.float64)
+    H, W = x.shape[1], x.shape[2]
+    return lib().or_loss_window(H, W, _p(x, _dp), _p(y, _dp), lam, x0, y0, x1, y1)
+
+
+def render_pixels_locked(proj: dict, vals, ranges, cam: Cam, px, py, dec=None):
+    """or_render_pixels_locked: with dec None, renders and records the
+    decisions (returns image, dec); with dec given, replays them."""
+    px = _c(px, np.int32)
+    py = _c(py, np.int32)
+    k = px.shape[0]
+    r = _c(ranges, np.uint32).reshape(-1, 2)
+    stride = int(max(1, (r[:, 1] - r[:, 0]).max()))
+    mode = 0 if dec is None else 1
+    if dec is None:
+        dec = np.zeros((k, stride), np.uint8)
+    bg = np.array(list(cam.bg), np.float64)
+    image = np.zeros((3, k))
+    lib().or_render_pixels_locked(k, _p(px, _ip), _p(py, _ip), cam.width, cam.tile, _p(bg, _dp),
+                                  _p(_c(proj["mean2d"], np.float64), _dp), _p(_c(proj["conic"], np.float64), _dp),
+                                  _p(_c(proj["opacity"], np.float64), _dp), _p(_c(proj["rgb"], np.float64), _dp),
+                                  _p(_c(vals, np.uint32), _up), _p(r, _up), mode, stride, _p(dec, _bp),
+                                  _p(image, _dp))
+    return image, dec
 
 
 def render_pixels(proj: dict, vals, ranges, cam: Cam, px, py) -> dict:

@@ -525,6 +525,54 @@ void or_render_pixels(int64_t npix, const int32_t *pxs, const int32_t *pys, int3
     }
 }
 
+/* Test support for finite differences of the piecewise-smooth loss: the
+ * render of or_render_pixels with every discrete decision held fixed.
+ * mode 0 (record) renders as or_render_pixels and writes, for pixel q and
+ * position k of its tile's list, dec[q * stride + k] = 0 skipped, 1 blended,
+ * 2 blended at the alpha cap, 3 the ray stopped before this entry (later
+ * positions are not visited). mode 1 (replay) takes those decisions instead
+ * of making them, on the same lists, so the result is a smooth function of
+ * the per-Gaussian values near the recorded point: its derivative is the one
+ * the analytic backward computes. stride >= the longest visited list. */
+void or_render_pixels_locked(int64_t npix, const int32_t *pxs, const int32_t *pys, int32_t W, int32_t tile,
+                             const double *bg, const double *mean2d, const double *conic, const double *opacity,
+                             const double *rgb, const uint32_t *vals, const uint32_t *ranges, int32_t mode,
+                             int64_t stride, uint8_t *dec, double *out) {
+    int32_t tx = (W + tile - 1) / tile;
+    for (int64_t q = 0; q < npix; ++q) {
+        int32_t px = pxs[q], py = pys[q];
+        int32_t t = (py / tile) * tx + (px / tile);
+        uint8_t *d = dec + q * stride;
+        double T = 1.0, C[3] = {0, 0, 0};
+        for (uint32_t k = ranges[2 * t]; k < ranges[2 * t + 1]; ++k) {
+            int64_t pos = k - ranges[2 * t];
+            uint32_t g = vals[k];
+            double alpha;
+            if (mode == 0) {
+                blend_eval ev;
+                eval_entry(mean2d, conic, opacity, g, px, py, T, 0, &ev);
+                if (ev.skip) { d[pos] = 0; continue; }
+                if (ev.stop) { d[pos] = 3; break; }
+                d[pos] = ev.capped ? 2 : 1;
+                alpha = ev.alpha;
+            } else {
+                if (d[pos] == 0) continue;
+                if (d[pos] == 3) break;
+                if (d[pos] == 2) {
+                    alpha = ALPHA_MAX;
+                } else {
+                    double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                    double a = conic[3 * g], b = conic[3 * g + 1], c = conic[3 * g + 2];
+                    alpha = opacity[g] * exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy);
+                }
+            }
+            for (int c = 0; c < 3; ++c) C[c] += rgb[3 * g + c] * alpha * T;
+            T *= 1.0 - alpha;
+        }
+        for (int c = 0; c < 3; ++c) out[c * npix + q] = C[c] + T * bg[c];
+    }
+}
+
 /* Contributors of one pixel in blending order: list position, alpha and
  * the transmittance in front of each. Returns their number (at most cap). */
 int32_t or_pixel_trace(int32_t px, int32_t py, int32_t W, int32_t tile, const double *mean2d, const double *conic,
@@ -604,8 +652,32 @@ static void ssim_window(double w[11][11]) {
         for (int j = 0; j < 11; ++j) w[i][j] = g[i] * g[j] / (s * s);
 }
 
-double or_loss(int32_t H, int32_t W, const double *image, const double *gt, double lambda, double *dl_dimage) {
+/* SSIM map value of one channel at pixel (i, j): Gaussian-weighted window
+ * means of x, y, x^2, y^2, xy over the 11x11 neighbourhood inside the image
+ * (zero padding), then the usual luminance x contrast-structure ratio. */
+typedef struct { double m, mx, my, n1, n2, d1, d2; } ssim_px;
+
+static ssim_px ssim_at(const double *x, const double *y, int32_t H, int32_t W, int32_t i, int32_t j,
+                       double w[11][11]) {
     const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    double mx = 0, my = 0, xx = 0, yy = 0, xy = 0;
+    for (int di = -5; di <= 5; ++di)
+        for (int dj = -5; dj <= 5; ++dj) {
+            int32_t a = i + di, b = j + dj;
+            if (a < 0 || a >= H || b < 0 || b >= W) continue;
+            double wt = w[di + 5][dj + 5], xv = x[(int64_t)a * W + b], yv = y[(int64_t)a * W + b];
+            mx += wt * xv; my += wt * yv; xx += wt * xv * xv; yy += wt * yv * yv; xy += wt * xv * yv;
+        }
+    double sx = xx - mx * mx, sy = yy - my * my, sxy = xy - mx * my;
+    ssim_px r;
+    r.mx = mx; r.my = my;
+    r.n1 = 2 * mx * my + C1; r.n2 = 2 * sxy + C2;
+    r.d1 = mx * mx + my * my + C1; r.d2 = sx + sy + C2;
+    r.m = r.n1 * r.n2 / (r.d1 * r.d2);
+    return r;
+}
+
+double or_loss(int32_t H, int32_t W, const double *image, const double *gt, double lambda, double *dl_dimage) {
     double w[11][11];
     ssim_window(w);
     int64_t HW = (int64_t)H * W, N = 3 * HW;
@@ -616,18 +688,8 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
         const double *x = image + ch * HW, *y = gt + ch * HW;
         for (int32_t i = 0; i < H; ++i)
             for (int32_t j = 0; j < W; ++j) {
-                double mx = 0, my = 0, xx = 0, yy = 0, xy = 0;
-                for (int di = -5; di <= 5; ++di)
-                    for (int dj = -5; dj <= 5; ++dj) {
-                        int32_t a = i + di, b = j + dj;
-                        if (a < 0 || a >= H || b < 0 || b >= W) continue;
-                        double wt = w[di + 5][dj + 5], xv = x[(int64_t)a * W + b], yv = y[(int64_t)a * W + b];
-                        mx += wt * xv; my += wt * yv; xx += wt * xv * xv; yy += wt * yv * yv; xy += wt * xv * yv;
-                    }
-                double sx = xx - mx * mx, sy = yy - my * my, sxy = xy - mx * my;
-                double n1 = 2 * mx * my + C1, n2 = 2 * sxy + C2;
-                double d1 = mx * mx + my * my + C1, d2 = sx + sy + C2;
-                double m = n1 * n2 / (d1 * d2);
+                ssim_px r = ssim_at(x, y, H, W, i, j, w);
+                double m = r.m, mx = r.mx, my = r.my, n1 = r.n1, n2 = r.n2, d1 = r.d1, d2 = r.d2;
                 ssim += m;
                 /* partial derivatives of the map value with respect to the
                    window mean of x, of x^2 and of x*y */
@@ -659,6 +721,30 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
     }
     free(A); free(B); free(Cm);
     return (1 - lambda) * l1 / N + lambda * (1 - ssim / N);
+}
+
+/* The part of the Eq. 3 loss owed to the pixels of the window
+ * [x0, x1) x [y0, y1) of an H x W image, all three channels:
+ *   (1 - lambda)/N sum |x - y|  -  lambda/N sum SSIM(p),   N = 3 H W,
+ * so that or_loss = lambda + the sum of this over any partition of the image
+ * into windows. The SSIM value of a window pixel reads the image up to 5
+ * pixels around it (zero padding at the image border); a change confined to
+ * a region changes only the window terms of the pixels within 5 of it. */
+double or_loss_window(int32_t H, int32_t W, const double *image, const double *gt, double lambda, int32_t x0,
+                      int32_t y0, int32_t x1, int32_t y1) {
+    double w[11][11];
+    ssim_window(w);
+    int64_t HW = (int64_t)H * W, N = 3 * HW;
+    double l1 = 0, ssim = 0;
+    for (int ch = 0; ch < 3; ++ch) {
+        const double *x = image + ch * HW, *y = gt + ch * HW;
+        for (int32_t i = y0; i < y1; ++i)
+            for (int32_t j = x0; j < x1; ++j) {
+                ssim += ssim_at(x, y, H, W, i, j, w).m;
+                l1 += fabs(x[(int64_t)i * W + j] - y[(int64_t)i * W + j]);
+            }
+    }
+    return (1 - lambda) * l1 / N - lambda * ssim / N;
 }
 
 /* ------------------------------------------------------------------ */

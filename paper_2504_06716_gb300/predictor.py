@@ -149,11 +149,38 @@ def evaluate(scene, cfg, predictor: FreezePredictor | None, tau: float, every: i
     return out
 
 
+FLOPS_PER_ROW = 2 * (N_IN * N_H + N_H * N_H + N_H)  # 10,368: the three layers' multiply-adds
+BYTES_PER_ROW = 2 * N_IN + 4  # bf16 features in, float32 probability out
+
+
+def bench_inference(n: int, reps: int = 20) -> dict:
+    """Device time of gs_mlp_fwd on n rows of seeded features (CUDA events on
+    the launching stream, after a warm-up; n x 32 B of features exceed L2 for
+    n in the millions)."""
+    g = torch.Generator(device="cpu").manual_seed(5)
+    X = torch.randn((n, N_IN), generator=g).to(torch.bfloat16).cuda()
+    pred = FreezePredictor()
+    p = torch.empty(n, device="cuda")
+    for _ in range(3):
+        pred.predict(X, p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        pred.predict(X, p)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return dict(rows=n, ms=ms, tflops=FLOPS_PER_ROW * n / (ms * 1e-3) / 1e12,
+                gbs=BYTES_PER_ROW * n / (ms * 1e-3) / 1e9)
+
+
 def main():
     from . import synth
     from .schedule import GStaConfig
 
     ap = argparse.ArgumentParser(description="train the freeze predictor on tiny-scene runs and compare")
+    ap.add_argument("--bench-inference", type=int, default=0, help="only time inference on this many rows")
     ap.add_argument("--train-seeds", default="0,1,2,3,4,5")
     ap.add_argument("--eval-seed", type=int, default=9)
     ap.add_argument("--tau", default="0.9,0.97")
@@ -161,6 +188,9 @@ def main():
     ap.add_argument("--balance", type=int, default=1)
     args = ap.parse_args()
     torch.cuda.set_device(0)
+    if args.bench_inference:
+        print(json.dumps(bench_inference(args.bench_inference)))
+        return
     cfg = GStaConfig.tiny()
     logs = []
     for s in [int(x) for x in args.train_seeds.split(",")]:

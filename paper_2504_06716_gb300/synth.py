@@ -232,6 +232,22 @@ def surface_scene(n_init: int, n_gt: int, n_views: int, width: int, height: int,
     )
 
 
+def smooth_image(height: int, width: int, seed: int, terms: int = 6) -> np.ndarray:
+    """(3, height, width) float64 target image in [0, 1]: per channel a sum of
+    ``terms`` random plane waves (wavelengths 8 to 128 pixels), rescaled."""
+    g = _rng(seed)
+    yy, xx = np.meshgrid(np.arange(height), np.arange(width), indexing="ij")
+    out = np.zeros((3, height, width))
+    for c in range(3):
+        for _ in range(terms):
+            k = 2 * math.pi / g.uniform(8.0, 128.0)
+            a = g.uniform(0.0, 2 * math.pi)
+            out[c] += g.uniform(0.2, 1.0) * np.sin(k * (math.cos(a) * xx + math.sin(a) * yy) + g.uniform(0, 2 * math.pi))
+        lo, hi = out[c].min(), out[c].max()
+        out[c] = (out[c] - lo) / max(hi - lo, 1e-12)
+    return out
+
+
 def view_order(n_iters: int, train_views: list[int], seed: int) -> list[int]:
     """Training view per iteration: a fresh seeded permutation of the training views each epoch."""
     g = _rng(seed)

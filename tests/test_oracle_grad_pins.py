@@ -140,6 +140,31 @@ def test_loss_gradient_by_central_differences(orc):
         assert grad[c, i, j] == pytest.approx(fd, rel=1e-5, abs=1e-11)
 
 
+def test_loss_windows_partition_the_loss(orc):
+    """lambda + the window shares over any partition of the image = Eq. 3."""
+    g = np.random.default_rng(4)
+    x, y = g.uniform(0, 1, (3, 23, 31)), g.uniform(0, 1, (3, 23, 31))
+    total = orc.loss(x, y, grad=False)[0]
+    xs, ys = [0, 7, 8, 20, 31], [0, 5, 17, 23]
+    parts = sum(orc.loss_window(x, y, xs[a], ys[b], xs[a + 1], ys[b + 1])
+                for a in range(len(xs) - 1) for b in range(len(ys) - 1))
+    assert 0.2 + parts == pytest.approx(total, rel=1e-13)
+
+
+def test_loss_window_captures_a_local_change(orc):
+    """A change confined to a region moves the loss exactly as much as the
+    share of the window 5 pixels around that region."""
+    g = np.random.default_rng(5)
+    x, y = g.uniform(0, 1, (3, 40, 50)), g.uniform(0, 1, (3, 40, 50))
+    x2 = x.copy()
+    x2[:, 12:19, 30:36] += g.normal(0, 0.1, (3, 7, 6))
+    d_full = orc.loss(x2, y, grad=False)[0] - orc.loss(x, y, grad=False)[0]
+    d_win = orc.loss_window(x2, y, 25, 7, 41, 24) - orc.loss_window(x, y, 25, 7, 41, 24)
+    assert d_win == pytest.approx(d_full, rel=1e-9, abs=1e-15)
+    d_small = orc.loss_window(x2, y, 26, 8, 40, 23) - orc.loss_window(x, y, 26, 8, 40, 23)
+    assert abs(d_small - d_full) > 1e-9  # one pixel less is not enough
+
+
 # ----------------------------------------------------------------------------- Adam
 
 
