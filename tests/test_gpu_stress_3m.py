@@ -9,8 +9,9 @@ every other Gaussian must get an exactly zero gradient). Checked:
 
 * the crop image and the loss against the oracle;
 * the full 59-parameter gradient of every Gaussian against the oracle's
-  analytic gradient (same tolerances and ambiguity bounds as the smaller
-  end-to-end tests);
+  analytic gradient (the ambiguity bounds of the smaller end-to-end tests,
+  tolerances widened by what float32 2-D means above 1024 px cost, derived
+  below);
 * central finite differences of the FP64 oracle loss, h = 1e-3, on 64
   random parameters of each type (mean, log-scale, rotation, opacity, SH)
   among the Gaussians that contribute to the crop. The loss is piecewise
@@ -39,7 +40,32 @@ pytestmark = pytest.mark.gpu
 
 N, W, H, TILE = 3_000_000, 1920, 1080, 16
 X0, Y0, CS = 832, 416, 256  # the centred 256x256 crop, aligned to 32
+# Pixel decisions within this relative distance of their threshold may go
+# either way on the GPU here. Its 2-D means are float32 values near 1000-1900
+# px, spaced 1.2e-4 px apart (twice the spacing below 1024 px), so a mean is
+# off by up to ~2.4e-4 px; the exponent of a splat changes by |Q d| per pixel
+# of offset, at most ~6 per px at the alpha floor for the smallest splats
+# (sigma ~0.55 px, the 0.3 px^2 dilation) -- up to ~1.4e-3 relative.
+STRESS_PIXEL_MARGIN = 2e-3
+# The same offset changes every alpha by up to that relative amount, not only
+# near decisions, so pixel values carry up to ~1.4e-3 relative error (1e-4
+# suffices at the smaller sizes of the other tests, where means stay below
+# 1024 px and splats are larger) and the gradient terms built on them a
+# little more.
+STRESS_IMAGE_RTOL = 2e-3
+STRESS_GRAD_RTOL = 3e-3
+# A gradient is a sum of per-pixel terms that cancel (a mean's most of all);
+# relative errors of the terms up to ~1.4e-3 make errors of the sum scale with
+# the sum of the terms' absolute values, which the oracle reports.
+STRESS_TERM_RTOL = 2e-3
 TYPES = {"mean": (0, 3), "log_scale": (3, 6), "rotation": (6, 10), "opacity": (10, 11), "sh": (11, 59)}
+
+
+def _crop_set(proj):
+    """Indices of the Gaussians whose tile rectangle meets the crop."""
+    R = proj["rect"]
+    return np.nonzero((proj["radius"] > 0) & (R[:, 0] < (X0 + CS) // TILE) & (R[:, 2] > X0 // TILE)
+                      & (R[:, 1] < (Y0 + CS) // TILE) & (R[:, 3] > Y0 // TILE))[0]
 
 
 @pytest.fixture(scope="module")
@@ -56,21 +82,39 @@ def case():
     P = pu.f32(synth.gaussians_surface(N, 30))
     proj = oracle.project(P, ocam)
     nudge = np.random.default_rng(32)
-    for _ in range(20):  # keep every projection decision out of float32's reach
+    forward = np.asarray(cam.R, np.float64)[2]  # the view axis in world space
+    for _ in range(30):
+        # (1) projection decisions within float32's reach (radius, tile
+        # rectangle, near plane): a rectangle edge sits at mean +- radius, so
+        # move the mean a little, and the scale
         bad = np.nonzero(proj["margin"] <= pu.PROJ_MARGIN)[0]
-        if len(bad) == 0:
+        # (2) depth order: the GPU's float32 depth may differ from the
+        # oracle's by an ulp or two, so two overlapping Gaussians that close
+        # in depth may blend in either order; move one of each pair along the
+        # view axis
+        S = _crop_set(proj)
+        d = proj["depth"][S].astype(np.float32)
+        order = np.argsort(d, kind="stable")
+        R = proj["rect"][S][order]
+        ds = d[order]
+        near = np.zeros(len(S), bool)
+        for k in (1, 2, 3):
+            close = np.abs(ds[k:] - ds[:-k]) <= 3 * np.spacing(np.abs(ds[k:]))
+            ov = (R[k:, 0] < R[:-k, 2]) & (R[k:, 2] > R[:-k, 0]) & (R[k:, 1] < R[:-k, 3]) & (R[k:, 3] > R[:-k, 1])
+            near[k:] |= close & ov
+        tie = S[order[near]]
+        if len(bad) == 0 and len(tie) == 0:
             break
-        # a tile-rectangle edge sits at mean +- radius: move the mean a little, and the scale
         P[bad, 0:3] = pu.f32(P[bad, 0:3] + nudge.normal(0.0, 2e-4, (len(bad), 3)))
         P[bad, 3:6] = pu.f32(P[bad, 3:6] + 3e-3)
-        sub = oracle.project(P[bad], ocam)
+        P[tie, 0:3] = pu.f32(P[tie, 0:3] + nudge.uniform(2e-5, 6e-5, (len(tie), 1)) * forward)
+        moved = np.union1d(bad, tie)
+        sub = oracle.project(P[moved], ocam)
         for k in proj:
-            proj[k][bad] = sub[k]
+            proj[k][moved] = sub[k]
     else:
         raise AssertionError("nudge failed")
-    R = proj["rect"]
-    S = np.nonzero((proj["radius"] > 0) & (R[:, 0] < (X0 + CS) // TILE) & (R[:, 2] > X0 // TILE)
-                   & (R[:, 1] < (Y0 + CS) // TILE) & (R[:, 3] > Y0 // TILE))[0]
+    S = _crop_set(proj)
     gt = synth.smooth_image(CS, CS, 31)
 
     # GPU: the full-size forward and backward through the autograd wrappers
@@ -98,7 +142,7 @@ def case():
     dl = np.zeros((3, H, W))
     dl[:, Y0:Y0 + CS, X0:X0 + CS] = dimg
     amb = np.zeros((H, W), np.uint8)
-    amb[Y0:Y0 + CS, X0:X0 + CS] = (ren["margin"] <= pu.E2E_PIXEL_MARGIN).reshape(CS, CS)
+    amb[Y0:Y0 + CS, X0:X0 + CS] = (ren["margin"] <= STRESS_PIXEL_MARGIN).reshape(CS, CS)
     tx = (W + TILE - 1) // TILE
     tile_mask = np.zeros(tx * ((H + TILE - 1) // TILE), np.uint8)
     for ty in range(Y0 // TILE, (Y0 + CS) // TILE):
@@ -106,16 +150,24 @@ def case():
     rb = oracle.render_bwd(projS, vals, ranges, ocam, dl, amb=amb, tile_mask=tile_mask)
     GS = oracle.project_bwd(PS, ocam, rb)["G"]
     bound = pu.param_bound(PS, ocam, rb["amb_abs"])
+    every = np.zeros((H, W), np.uint8)
+    every[Y0:Y0 + CS, X0:X0 + CS] = 1
+    abs_terms = pu.param_bound(PS, ocam, oracle.render_bwd(projS, vals, ranges, ocam, dl, amb=every,
+                                                           tile_mask=tile_mask)["amb_abs"])
     return dict(cam=cam, ocam=ocam, P=P, S=S, PS=PS, projS=projS, gt=gt, G=G, gpu_crop=gpu_crop, gpu_loss=gpu_loss,
-                img=img, L=L, amb=amb[Y0:Y0 + CS, X0:X0 + CS].astype(bool), GS=GS, bound=bound)
+                img=img, L=L, amb=amb[Y0:Y0 + CS, X0:X0 + CS].astype(bool), margin=ren["margin"].reshape(CS, CS),
+                GS=GS, bound=bound, abs_terms=abs_terms)
 
 
 def test_crop_image_and_loss_match_oracle(case):
     c = case
     assert len(c["S"]) > 20000
     ok = ~np.broadcast_to(c["amb"], c["img"].shape)
-    assert pu.close(c["gpu_crop"], c["img"], 1e-4, 1.0, mask=ok)[0]
-    assert c["amb"].mean() < 0.02  # ambiguous pixels are rare and only checked for validity
+    err = np.abs(c["gpu_crop"] - c["img"]) / (STRESS_IMAGE_RTOL * (np.abs(c["img"]) + 1.0))
+    bad = (err > 1) & ok
+    assert not bad.any(), dict(pixels=int(bad.any(axis=0).sum()), worst=float(err[ok].max()),
+                               margins=np.sort(c["margin"][bad.any(axis=0)])[:10].tolist())
+    assert c["amb"].mean() < 0.1  # ambiguous pixels are only checked for validity
     assert np.isfinite(c["gpu_crop"]).all() and (c["gpu_crop"] >= 0).all()
     assert c["gpu_loss"] == pytest.approx(c["L"], rel=1e-4)
 
@@ -130,8 +182,24 @@ def test_full_gradient_matches_oracle_on_the_crop(case):
     GS, bound = c["GS"], c["bound"]
     for name, (lo, hi) in TYPES.items():
         w = GS[:, lo:hi]
-        good, worst = pu.close_bound(G[S, lo:hi], w, 1e-3, 1e-2 * np.abs(w).max(), bound[:, lo:hi])
-        assert good, (name, worst)
+        extra = bound[:, lo:hi] + STRESS_TERM_RTOL * c["abs_terms"][:, lo:hi]
+        good, worst = pu.close_bound(G[S, lo:hi], w, STRESS_GRAD_RTOL, 1e-2 * np.abs(w).max(), extra)
+        if not good:
+            err = np.abs(G[S, lo:hi] - w)
+            lim = STRESS_GRAD_RTOL * (np.abs(w) + 1e-2 * np.abs(w).max()) + extra
+            r = (err / lim).max(axis=1)
+            top = np.argsort(-r)[:5]
+            d = c["projS"]["depth"].astype(np.float32)
+            R = c["projS"]["rect"]
+            info = []
+            for i in top:
+                ov = (R[:, 0] < R[i, 2]) & (R[:, 2] > R[i, 0]) & (R[:, 1] < R[i, 3]) & (R[:, 3] > R[i, 1])
+                ov[i] = False
+                gap = float(np.abs(d[ov] - d[i]).min()) if ov.any() else None
+                info.append(dict(i=int(i), ratio=float(r[i]), got=G[S[i], lo:hi].tolist(), want=w[i].tolist(),
+                                 extra=extra[i].tolist(), rect=R[i].tolist(), depth=float(d[i]), gap=gap,
+                                 radius=int(c["projS"]["radius"][i])))
+            raise AssertionError((name, worst, info))
 
 
 def test_central_differences_on_64_parameters_per_type(case):
