@@ -77,7 +77,7 @@ def lib():
             L.or_sh_basis.argtypes = [_dp, _dp]
             L.or_sh_basis_grad.argtypes = [_dp, _dp]
             L.or_project.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _dp, _dp, _dp, _dp, _dp, _ip, _ip, _dp]
-            L.or_sort.argtypes = [_i64, _fp, _ip, _fp, _i32, _i32, _i32, _i32, _i64, _up, _up]
+            L.or_sort.argtypes = [_i64, _fp, _fp, _fp, _ip, _fp, _i32, _i32, _i32, _i32, _i64, _up, _up]
             L.or_sort.restype = _i64
             L.or_render.argtypes = [_i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp, _ip, _dp]
             L.or_pixel_trace.argtypes = [_i32, _i32, _i32, _i32, _dp, _dp, _dp, _up, _up, _i32, _ip, _dp, _dp]
@@ -154,24 +154,42 @@ def project(params, cam: Cam, sh_degree: int = 3, smooth: bool = False) -> dict:
     return out
 
 
-def sort(mean2d_f32, radius, depth_f32, W: int, H: int, tile: int = 16, smooth: bool = False,
-         capacity: int | None = None):
-    """Tile/depth order. Returns (vals uint32[P], ranges uint32[tiles, 2])."""
+def sort(mean2d_f32, conic_f32, opacity_f32, radius, depth_f32, W: int, H: int, tile: int = 16,
+         smooth: bool = False, capacity: int | None = None):
+    """Tile/depth order of single-precision splats (mean2d [n][2], conic [n][3],
+    opacity [n], radius [n], depth [n]). Returns (vals uint32[P], ranges
+    uint32[tiles, 2])."""
     m = _c(mean2d_f32, np.float32)
+    q = _c(conic_f32, np.float32)
+    o = _c(opacity_f32, np.float32)
     r = _c(radius, np.int32)
     d = _c(depth_f32, np.float32)
     n = r.shape[0]
     tiles = ((W + tile - 1) // tile) * ((H + tile - 1) // tile)
+    args = (_p(m, _fp), _p(q, _fp), _p(o, _fp), _p(r, _ip), _p(d, _fp), W, H, tile, int(smooth))
     if capacity is None:
-        capacity = lib().or_sort(n, _p(m, _fp), _p(r, _ip), _p(d, _fp), W, H, tile, int(smooth), 0, None, None)
-        capacity = abs(capacity)
+        capacity = abs(lib().or_sort(n, *args, 0, None, None))
     vals = np.zeros(max(capacity, 1), np.uint32)
     ranges = np.zeros((tiles, 2), np.uint32)
-    P = lib().or_sort(n, _p(m, _fp), _p(r, _ip), _p(d, _fp), W, H, tile, int(smooth), capacity, _p(vals, _up),
-                      _p(ranges, _up))
+    P = lib().or_sort(n, *args, capacity, _p(vals, _up), _p(ranges, _up))
     if P < 0:
         raise OverflowError(f"sort needs {-P} entries, capacity {capacity}")
     return vals[:P], ranges
+
+
+def sort_proj(proj: dict, W: int, H: int, tile: int = 16, smooth: bool = False, capacity: int | None = None):
+    """sort() of a projection's values rounded to single precision."""
+    return sort(proj["mean2d"].astype(np.float32), proj["conic"].astype(np.float32),
+                proj["opacity"].astype(np.float32), proj["radius"], proj["depth"].astype(np.float32), W, H, tile,
+                smooth, capacity)
+
+
+def sort_records(rec, W: int, H: int, tile: int = 16, capacity: int | None = None):
+    """sort() of float32 splat records [n][12] (the C-ABI layout: mean 0-1,
+    conic 2-4, opacity 5, depth 9, radius bits 10)."""
+    rec = np.ascontiguousarray(rec, np.float32)
+    return sort(rec[:, 0:2], rec[:, 2:5], rec[:, 5], rec[:, 10].view(np.int32), rec[:, 9], W, H, tile,
+                capacity=capacity)
 
 
 def render(proj: dict, vals, ranges, cam: Cam, smooth: bool = False) -> dict:
@@ -338,8 +356,7 @@ def psnr(images, gts) -> np.ndarray:
 def forward(params, cam: Cam, sh_degree: int = 3, smooth: bool = False) -> dict:
     """Projection, per-tile depth order and compositing for one view."""
     proj = project(params, cam, sh_degree, smooth)
-    vals, ranges = sort(proj["mean2d"].astype(np.float32), proj["radius"], proj["depth"].astype(np.float32),
-                        cam.width, cam.height, cam.tile, smooth)
+    vals, ranges = sort_proj(proj, cam.width, cam.height, cam.tile, smooth)
     ren = render(proj, vals, ranges, cam, smooth)
     return dict(proj=proj, vals=vals, ranges=ranges, **ren)
 

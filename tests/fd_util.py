@@ -79,8 +79,7 @@ def local_fd(task):
             pr = {key: v.copy() for key, v in base.items()}
             for key in pr:
                 pr[key][k] = pert[key][row]
-            vals, ranges = oracle.sort(pr["mean2d"].astype(np.float32), pr["radius"], pr["depth"].astype(np.float32),
-                                       ocam.width, ocam.height, tile)
+            vals, ranges = oracle.sort_proj(pr, ocam.width, ocam.height, tile)
             ren = oracle.render_pixels(pr, vals, ranges, ocam, px, py)
             img = np.zeros((3, cs, cs))
             img[:, py - y0, px - x0] = ren["image"]
@@ -104,8 +103,7 @@ def _local_fd_locked(i, j, hs):
     sub = np.nonzero((proj["radius"] > 0) & (R[:, 0] < t1x) & (R[:, 2] > t0x) & (R[:, 1] < t1y) & (R[:, 3] > t0y))[0]
     k = int(np.nonzero(sub == i)[0][0])
     base = {key: proj[key][sub].copy() for key in ("mean2d", "conic", "depth", "opacity", "rgb", "radius")}
-    vals, ranges = oracle.sort(base["mean2d"].astype(np.float32), base["radius"], base["depth"].astype(np.float32),
-                               ocam.width, ocam.height, tile)
+    vals, ranges = oracle.sort_proj(base, ocam.width, ocam.height, tile)
     yy, xx = np.meshgrid(np.arange(w2[1], w2[3]), np.arange(w2[0], w2[2]), indexing="ij")
     px, py = xx.ravel(), yy.ravel()
     _, dec = oracle.render_pixels_locked(base, vals, ranges, ocam, px, py)

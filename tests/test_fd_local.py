@@ -13,8 +13,7 @@ import parity_util as pu
 def _crop_loss(P, ocam, crop, gt):
     x0, y0, cs = crop
     f = oracle.project(P, ocam)
-    vals, ranges = oracle.sort(f["mean2d"].astype(np.float32), f["radius"], f["depth"].astype(np.float32), ocam.width,
-                               ocam.height, ocam.tile)
+    vals, ranges = oracle.sort_proj(f, ocam.width, ocam.height, ocam.tile)
     yy, xx = np.meshgrid(np.arange(y0, y0 + cs), np.arange(x0, x0 + cs), indexing="ij")
     ren = oracle.render_pixels(f, vals, ranges, ocam, xx.ravel(), yy.ravel())
     return oracle.loss(ren["image"].reshape(3, cs, cs), gt, grad=False)[0]
@@ -66,8 +65,7 @@ def _small_case():
 
 def test_locked_render_records_and_replays_the_plain_render(orc):
     cam, ocam, P, proj, crop, gt = _small_case()
-    vals, ranges = oracle.sort(proj["mean2d"].astype(np.float32), proj["radius"], proj["depth"].astype(np.float32),
-                               ocam.width, ocam.height, 16)
+    vals, ranges = oracle.sort_proj(proj, ocam.width, ocam.height, 16)
     x0, y0, cs = crop
     yy, xx = np.meshgrid(np.arange(y0, y0 + cs), np.arange(x0, x0 + cs), indexing="ij")
     plain = oracle.render_pixels(proj, vals, ranges, ocam, xx.ravel(), yy.ravel())["image"]
@@ -83,8 +81,7 @@ def test_locked_fd_equals_the_analytic_gradient(orc):
     analytic gradient (cut-offs on) for every kind of parameter."""
     cam, ocam, P, proj, crop, gt = _small_case()
     x0, y0, cs = crop
-    vals, ranges = oracle.sort(proj["mean2d"].astype(np.float32), proj["radius"], proj["depth"].astype(np.float32),
-                               ocam.width, ocam.height, 16)
+    vals, ranges = oracle.sort_proj(proj, ocam.width, ocam.height, 16)
     yy, xx = np.meshgrid(np.arange(y0, y0 + cs), np.arange(x0, x0 + cs), indexing="ij")
     img = oracle.render_pixels(proj, vals, ranges, ocam, xx.ravel(), yy.ravel())["image"].reshape(3, cs, cs)
     _, dimg = oracle.loss(img, gt)

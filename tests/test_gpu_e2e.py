@@ -151,8 +151,7 @@ def mid_sorted(mid):
 
 
 def test_fullsize_sort_bit_exact(mid, mid_sorted):
-    want_vals, want_ranges = oracle.sort(mid["rec"][:, 0:2], mid["rec"][:, 10].view(np.int32), mid["rec"][:, 9],
-                                         1237, 822, 16)
+    want_vals, want_ranges = oracle.sort_records(mid["rec"], 1237, 822, 16)
     P = mid_sorted["count"]
     assert P == len(want_vals) > 3_000_000
     assert np.array_equal(mid_sorted["vals"].cpu().numpy()[:P].view(np.uint32), want_vals)

@@ -135,8 +135,7 @@ def test_project_empty_and_all_culled():
 
 
 def _oracle_sort(rec, ocam, capacity=None):
-    return oracle.sort(rec[:, 0:2], rec[:, 10].view(np.int32), rec[:, 9], ocam.width, ocam.height, ocam.tile,
-                       capacity=capacity)
+    return oracle.sort_records(rec, ocam.width, ocam.height, ocam.tile, capacity=capacity)
 
 
 @pytest.mark.parametrize("kind,tile", [("tiny", 16), ("ragged", 8), ("ragged", 32), ("surface", 16), ("surface", 8)])
@@ -164,12 +163,16 @@ def test_sort_ties_keep_index_order():
     rad = g.integers(1, 30, n).astype(np.int32)
     rad[::7] = 0  # some culled
     rec[:, 10] = rad.view(np.float32)
+    # isotropic splats whose 3-sigma circle has the radius, opaque enough to be listed
+    sig = np.maximum(rad, 1).astype(np.float32) / 3.0
+    rec[:, 2] = rec[:, 4] = 1.0 / (sig * sig)
+    rec[:, 5] = 0.9
     cam = synth.pinhole(200, 120, 60.0, (0, -3, 0.5))
     ocam, gcam = pu.cameras(cam, tile=16)
     tiles = np.zeros(n, np.int32)
-    for i in range(n):  # tiles touched by the float32 rectangle rule of the oracle
+    for i in range(n):  # tiles listing the splat by the oracle's rule
         if rad[i] > 0:
-            v, _ = oracle.sort(rec[i:i + 1, 0:2], rad[i:i + 1], rec[i:i + 1, 9], 200, 120, 16)
+            v, _ = oracle.sort_records(rec[i:i + 1], 200, 120, 16)
             tiles[i] = len(v)
     rad[tiles == 0] = 0
     rec[:, 10] = rad.view(np.float32)
@@ -228,6 +231,41 @@ def test_render_forward_matches_oracle(kind, tile, bg):
     assert good, worst
     # pixels with an ambiguous decision must still hold a valid composite
     assert np.all(np.isfinite(img)) and np.all((tf >= 1e-4 * 0.99) & (tf <= 1.0))
+
+
+@pytest.mark.parametrize("kind,tile", [("tiny", 16), ("surface", 8)])
+def test_pair_counts_match_oracle_decisions(kind, tile):
+    """gs_raster_pair_counts (measurement support) against the oracle's own
+    record of every decision up to each pixel's last contributor."""
+    P, cams = _scene(kind)
+    ocam, gcam = pu.cameras(cams[0], tile=tile)
+    rec = pu.records_from_oracle(oracle.project(P, ocam))
+    proj = pu.proj_from_records(rec)
+    vals, ranges, Pn, flags, spl = _gpu_sort(rec, gcam)
+    want = oracle.render(proj, vals[:Pn], ranges, ocam)
+    _, _, nl, vt, rt = _gpu_render(spl, vals[:Pn], ranges, gcam)
+    frozen = (np.random.default_rng(7).uniform(size=P.shape[0]) < 0.3).astype(np.uint8)
+    counts = torch.zeros(3, dtype=torch.int64, device=DEV)
+    lib.gs_raster_pair_counts(spl, vt, rt, gcam, torch.from_numpy(nl).to(DEV), torch.from_numpy(frozen).to(DEV),
+                              counts)
+    got = counts.cpu().numpy()
+    H, W = ocam.height, ocam.width
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    _, dec = oracle.render_pixels_locked(proj, vals[:Pn], ranges, ocam, xx.ravel(), yy.ravel())
+    tiles = (yy // tile) * ((W + tile - 1) // tile) + xx // tile
+    starts = ranges[tiles.ravel(), 0].astype(np.int64)
+    nlo = want["n_last"].ravel()
+    pos = np.arange(dec.shape[1])[None, :]
+    inside = pos < nlo[:, None]
+    g = vals[np.minimum(starts[:, None] + pos, max(Pn - 1, 0))]
+    blended = inside & ((dec == 1) | (dec == 2))
+    want_c = np.array([(blended & (frozen[g] == 0)).sum(), (blended & (frozen[g] == 1)).sum(),
+                       (inside & (dec == 0)).sum()])
+    # pixels whose decisions are within float32 reach may count either way
+    amb = (want["margin"] <= pu.PIXEL_MARGIN).ravel()
+    slack = int(nlo[amb].sum() + nl.ravel()[amb].sum())
+    assert np.abs(got - want_c).sum() <= slack, (got, want_c, slack)
+    assert got.sum() == nl.astype(np.int64).sum()
 
 
 # ----------------------------------------------------------------------------- A4 loss

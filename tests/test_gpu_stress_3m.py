@@ -133,8 +133,7 @@ def case():
     # oracle on the set S
     projS = {k: v[S] for k, v in proj.items()}
     PS = P[S]
-    vals, ranges = oracle.sort(projS["mean2d"].astype(np.float32), projS["radius"], projS["depth"].astype(np.float32),
-                               W, H, TILE)
+    vals, ranges = oracle.sort_proj(projS, W, H, TILE)
     yy, xx = np.meshgrid(np.arange(Y0, Y0 + CS), np.arange(X0, X0 + CS), indexing="ij")
     ren = oracle.render_pixels(projS, vals, ranges, ocam, xx.ravel(), yy.ravel())
     img = ren["image"].reshape(3, CS, CS)

@@ -165,26 +165,55 @@ def test_tiled_render_equals_brute_force(orc, tile):
     assert np.abs(f["image"] - brute).max() < 1e-12
 
 
-def test_sort_lists_match_rectangles_and_depth_order(orc):
+def _box_min_q(m, Q, x, y, tile):
+    """Double-precision minimum of the conic's quadratic form over the box of
+    pixel centres of tile (x, y), by dense sampling plus the clamped mean
+    (an independent check of the oracle's closed form)."""
+    a, b, c = Q
+    xs = np.linspace(x * tile, x * tile + tile - 1, 4 * tile)
+    ys = np.linspace(y * tile, y * tile + tile - 1, 4 * tile)
+    X, Y = np.meshgrid(xs, ys)
+    dx, dy = X - m[0], Y - m[1]
+    q = (a * dx * dx + 2 * b * dx * dy + c * dy * dy).min()
+    cx, cy = np.clip(m[0], xs[0], xs[-1]), np.clip(m[1], ys[0], ys[-1])
+    if cx == m[0] and cy == m[1]:
+        q = 0.0
+    return q
+
+
+def test_sort_lists_match_tile_rule_and_depth_order(orc):
+    """Each tile lists, in (float32 depth, index) order, the splats of its
+    3-sigma rectangle whose alpha can reach 1/255 somewhere in the tile:
+    min over the tile of q = d^T Q d at most 2 ln(255 o) (plus a 1e-3 relative
+    margin). Splats left out must be beyond that by the margin's width; the
+    tiles a splat is listed in never hold a pixel beyond its rectangle."""
     P, cam = _random_view(orc, n=400, W=100, H=70, tile=16, seed=9)
     pr = orc.project(P, cam)
-    m32 = pr["mean2d"].astype(np.float32)
     d32 = pr["depth"].astype(np.float32)
-    vals, ranges = orc.sort(m32, pr["radius"], d32, cam.width, cam.height, cam.tile)
+    vals, ranges = orc.sort_proj(pr, cam.width, cam.height, cam.tile)
     tx = (cam.width + 15) // 16
     ty = (cam.height + 15) // 16
-    assert len(vals) == int(pr["tiles_touched"].sum())
     # tile ranges partition the entry list in tile order
     nonempty = ranges[ranges[:, 1] > ranges[:, 0]]
     assert nonempty[0, 0] == 0 and nonempty[-1, 1] == len(vals)
     assert np.all(nonempty[1:, 0] == nonempty[:-1, 1])
+    r = pr["rect"]
+    tau = 2 * np.log(np.maximum(255 * pr["opacity"], 1e-300))
+    dropped = 0
     for t in range(tx * ty):
         x, y = t % tx, t // tx
-        r = pr["rect"]
         members = np.nonzero((pr["radius"] > 0) & (r[:, 0] <= x) & (x < r[:, 2]) & (r[:, 1] <= y) & (y < r[:, 3]))[0]
-        got = vals[ranges[t, 0]:ranges[t, 1]]
-        want = sorted(members.tolist(), key=lambda i: (float(d32[i]), i))
-        assert got.tolist() == want
+        got = vals[ranges[t, 0]:ranges[t, 1]].tolist()
+        assert set(got) <= set(members.tolist())
+        assert got == sorted(got, key=lambda i: (float(d32[i]), i))
+        for i in members:
+            qmin = _box_min_q(pr["mean2d"][i], pr["conic"][i], x, y, 16)
+            if i in got:
+                assert qmin <= tau[i] + 2e-3 * (1 + abs(tau[i])) + 1e-3
+            else:
+                dropped += 1
+                assert qmin >= tau[i] + 0.5e-3 * (1 + abs(tau[i])) - 1e-3 or tau[i] < 0
+    assert dropped > 0 and len(vals) > 0
 
 
 def test_transmittance_non_increasing_along_rays(orc):
