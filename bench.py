@@ -285,15 +285,19 @@ def gpu_arm(args):
     peaks, peak_kind = _peaks()
     rb_ms = [a.elapsed_time(b) for a, b, _ in raster_ev]
     rb_mean = sum(rb_ms) / len(rb_ms)
-    pairs = pairs_per_launch(tr, [v for _, _, v in raster_ev])
+    pc = pair_counts(tr, [v for _, _, v in raster_ev])
     clk_summary = clk.summary()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lane-instructions per second, in T/s
-    achieved = pairs * RASTER_BWD_OPS_PER_PAIR / (rb_mean / 1e3) / 1e12
+    ops = OPS_BLENDED_ACTIVE * pc[0] + OPS_BLENDED_FROZEN * pc[1] + OPS_SKIPPED * pc[2]
+    achieved = ops / (rb_mean / 1e3) / 1e12
     roofline = dict(bound="alu", kernel="k_raster_bwd", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
                     frac=achieved / alu_peak, traffic=None,
-                    work_per_unit=f"{RASTER_BWD_OPS_PER_PAIR} FP32 lane-instructions per (pixel, splat) pair up to the"
-                                  f" pixel's last contributor; {pairs:.3e} pairs per launch",
+                    work_per_unit=f"FP32 lane-instructions per (pixel, splat) pair over each pixel's list up to its"
+                                  f" last contributor: {OPS_BLENDED_ACTIVE} blended by an unfrozen splat,"
+                                  f" {OPS_BLENDED_FROZEN} by a frozen one, {OPS_SKIPPED} skipped; per launch"
+                                  f" {pc[0]:.3e} / {pc[1]:.3e} / {pc[2]:.3e} pairs (gs_raster_pair_counts,"
+                                  f" freeze map at the end of the timed region)",
                     peak_source=f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock of "
                                 f"{peak_kind} peaks file)",
                     mean_launch_ms=rb_mean)
@@ -328,25 +332,31 @@ def gpu_arm(args):
 
 
 # Algorithmic FP32 work of the rasteriser backward per (pixel, splat) pair, counted
-# from its formula: offset (2), exponent (8), exp and opacity (3), alpha floor/cap
-# tests (3), transmittance recovery (2), colour-behind update (9), dL/dalpha (10),
-# colour gradient (4), opacity/exponent gradient (3), conic and mean gradients (12).
-RASTER_BWD_OPS_PER_PAIR = 56
+# from its formula. Every pair: offset (2), exponent (8), exp and opacity (3),
+# alpha floor/cap tests (3) = 16, all a skipped pair costs. A blended pair adds the
+# transmittance recovery (2) and the colour-behind update (9) = 27, all a frozen
+# splat's pair costs (no gradient, Sec. 3.2.4); an unfrozen splat's pair adds
+# dL/dalpha (10), colour gradient (4), opacity/exponent gradient (3), conic and
+# mean gradients (12) = 56.
+OPS_SKIPPED, OPS_BLENDED_FROZEN, OPS_BLENDED_ACTIVE = 16, 27, 56
 
 
-def pairs_per_launch(tr, views) -> float:
-    """Sum over pixels of the list position of the last contributor, averaged
-    over the views of the timed launches (re-rendered after timing)."""
+def pair_counts(tr, views) -> list[float]:
+    """(blended by an unfrozen splat, blended by a frozen splat, skipped) pairs
+    per launch, averaged over the views of the timed launches (re-rendered
+    after timing, on the final freeze map)."""
     import torch
 
+    from paper_2504_06716_gb300 import lib
+
     m, view = tr.model, tr.view
-    tot = 0
+    counts = torch.zeros(3, dtype=torch.int64, device=m.P.device)
     sample = views[:: max(1, len(views) // 16)]
     for v in sample:
         m.retarget(view, tr.cams[v])
         m.rasterize(view)
-        tot += int(view.n_last.to(torch.int64).sum().item())
-    return tot / len(sample)
+        lib.gs_raster_pair_counts(m.splats, view.vals, view.ranges, view.cam, view.n_last, m.frozen, counts)
+    return [float(c) / len(sample) for c in counts.cpu().tolist()]
 
 
 def stage_split(tr, n) -> dict:

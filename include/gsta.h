@@ -109,19 +109,26 @@ typedef struct {
 int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, float *splats,
                gs_stream_t stream);
 
-/* Bytes of workspace gs_sort needs for n Gaussians and `capacity` entries. */
+/* Bytes of workspace gs_sort needs for n Gaussians and `capacity` entries
+ * on a width x height image with this tile size (0 for invalid sizes). */
 size_t gs_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t width, int32_t height, int32_t tile);
 
 /* Sec. 3.1 ("blended in a sorted order"). Lists, for every tile, the
- * Gaussians whose tile rectangle holds it, in ascending order of
- * (float32 camera depth, Gaussian index). Equivalent to a stable sort of the
- * 64-bit keys (tile << 32 | depth bits) generated in Gaussian order.
+ * Gaussians that tile lists, in ascending order of (float32 camera depth,
+ * Gaussian index): a tile of a Gaussian's rectangle lists it only if the box
+ * of the tile's pixel centres holds a point where d^T Q d (Q the conic) is
+ * at most tau + 1e-3 (1 + tau), tau = 2 ln(255 opacity) -- elsewhere alpha is
+ * below 1/255 at every pixel of the tile, so images and gradients are those
+ * of the whole rectangle (the tiles count in the splat record is the
+ * rectangle's, an upper bound). Decided in float32 with every operation
+ * rounded; ln by the atanh series (x = m 2^e, ln m = 2 atanh((m-1)/(m+1))).
  * Out: vals [capacity] (Gaussian index per entry), ranges [tiles][2]
- * (start, end) into vals, count_dev [1] int64 = total entries P.
- * If P > capacity, the entries past the capacity are dropped, ranges are
- * clipped to the capacity, count_dev still holds P, and GS_FLAG_CAPACITY is
- * raised. Workspace: ws of ws_bytes >= gs_sort_workspace_bytes(...).
- * Errors: INVALID_ARG (sizes, tile, workspace too small), CUDA. */
+ * (start, end) into vals, (0, 0) for an empty tile, count_dev [1] int64 =
+ * total entries P. If P > capacity, entries are dropped (the lists become
+ * subsets), ranges are clipped to the capacity, count_dev still holds P,
+ * and GS_FLAG_CAPACITY is raised. Workspace: ws of ws_bytes >=
+ * gs_sort_workspace_bytes(...), 256-byte aligned. Errors: INVALID_ARG
+ * (sizes, tile, workspace too small), CUDA. */
 int gs_sort(const float *splats, int64_t n, const gs_camera *cam, void *ws, size_t ws_bytes, int64_t capacity,
             uint32_t *vals, uint32_t *ranges, int64_t *count_dev, gs_stream_t stream);
 
@@ -353,6 +360,18 @@ int gs_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen, in
 int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
                            const int32_t *n_active_dev, const float *lr_dev, float b1, float b2, float eps,
                            int64_t *step_dev, float *scratch_dev, gs_stream_t stream);
+
+/* Measurement support (the paper has no counterpart): classifies the
+ * (pixel, splat) pairs of every pixel's tile list up to its last contributor
+ * (n_last, as left by gs_render_fwd) with the forward's own decisions, and
+ * ADDS the counts to counts_dev [3] (uint64, device): [0] blended by an
+ * unfrozen splat, [1] blended by a frozen splat, [2] skipped (positive
+ * exponent or alpha < 1/255). These are the pairs the rasteriser backward
+ * evaluates; a benchmark weighs them by their arithmetic to state the
+ * backward's algorithmic work. frozen may be NULL. Errors: INVALID_ARG,
+ * CUDA. */
+int gs_raster_pair_counts(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                          const int32_t *n_last, const uint8_t *frozen, uint64_t *counts_dev, gs_stream_t stream);
 
 /* Bytes of workspace gs_psnr needs for S images of H x W. */
 size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W);

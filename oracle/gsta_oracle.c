@@ -261,19 +261,23 @@ static float quad_f32(float a, float b, float c, float dx, float dy) {
     return (a * dx) * dx + ((2.0f * b) * dx) * dy + (c * dy) * dy;
 }
 
+/* On the edge x = X the form is least at y = my - (b / c)(X - mx), on the
+ * edge y = Y at x = mx - (b / a)(Y - my); the two quotients are taken once
+ * per splat. */
 static int tile_hit(float mx, float my, float a, float b, float c, float tau_m, int32_t tile, int32_t x, int32_t y) {
     if (tau_m < 0.0f) return 0;
     float x0 = (float)(x * tile), x1 = (float)(x * tile + tile - 1);
     float y0 = (float)(y * tile), y1 = (float)(y * tile + tile - 1);
     if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 1;
+    float bc = b / c, ba = b / a;
     float ex[2] = {x0, x1}, ey[2] = {y0, y1};
     for (int k = 0; k < 2; ++k) {
         float dx = ex[k] - mx;
-        float yo = my - (b * dx) / c;
+        float yo = my - bc * dx;
         float yy = yo < y0 ? y0 : (yo > y1 ? y1 : yo);
         if (quad_f32(a, b, c, dx, yy - my) <= tau_m) return 1;
         float dy = ey[k] - my;
-        float xo = mx - (b * dy) / a;
+        float xo = mx - ba * dy;
         float xx = xo < x0 ? x0 : (xo > x1 ? x1 : xo);
         if (quad_f32(a, b, c, xx - mx, dy) <= tau_m) return 1;
     }

@@ -307,6 +307,46 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__res
     raster_bwd_tile<TS, PPT, B>(splats, vals, ranges, cam, t_final, n_last, dl_dimage, frozen, grad2d, blockIdx.x);
 }
 
+// ---- measurement support: the (pixel, splat) pairs the backward visits ----
+// One CTA per tile, one thread per pixel, walking the pixel's list up to its
+// last contributor with the forward's own decisions.
+__global__ void k_pair_counts(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
+                              const uint32_t *__restrict__ ranges, DevCam cam, const int32_t *__restrict__ n_last,
+                              const uint8_t *__restrict__ frozen, unsigned long long *__restrict__ counts) {
+    __shared__ unsigned long long s_c[3];
+    if (threadIdx.x < 3) s_c[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int tile = blockIdx.x, TS = cam.tile;
+    const int px = (tile % cam.tiles_x) * TS + (int)(threadIdx.x % TS);
+    const int py = (tile / cam.tiles_x) * TS + (int)(threadIdx.x / TS);
+    uint32_t c[3] = {0u, 0u, 0u};
+    if (px < cam.W && py < cam.H) {
+        const uint32_t start = ranges[2 * tile];
+        const int nl = n_last[(int64_t)py * cam.W + px];
+        const float fpx = (float)px, fpy = (float)py;
+        for (int j = 0; j < nl; ++j) {
+            const uint32_t g = vals[start + j];
+            const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
+            const float4 xa = __ldg(r), co = __ldg(r + 1);
+            const float power = splat_power(__fsub_rn(xa.x, fpx), __fsub_rn(xa.y, fpy), xa.z, xa.w, co.x);
+            const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
+            if (power <= 0.f && alpha >= kAlphaMin)
+                ++c[frozen && frozen[g] ? 1 : 0];
+            else
+                ++c[2];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        unsigned long long v = c[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_c[k], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3 && s_c[threadIdx.x]) atomicAdd(counts + threadIdx.x, s_c[threadIdx.x]);
+}
+
 // ---- many views of many scenes in one persistent launch ----
 // CTAs pull (job, tile) items from a device counter until the batch is done,
 // so jobs of uneven cost (scenes of different sizes) share the GPU without a
@@ -531,3 +571,14 @@ uint32_t take_render_flags() {
     return f;
 }
 }  // namespace gs
+
+extern "C" int gs_raster_pair_counts(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                     const gs_camera *cam, const int32_t *n_last, const uint8_t *frozen,
+                                     uint64_t *counts_dev, gs_stream_t stream) {
+    if (!camera_ok(cam) || !splats || !vals || !ranges || !n_last || !counts_dev) return GS_ERR_INVALID_ARG;
+    const DevCam dc = make_cam(cam);
+    k_pair_counts<<<dc.tiles_x * dc.tiles_y, dc.tile * dc.tile, 0, as_stream(stream)>>>(
+        splats, vals, ranges, dc, n_last, frozen, reinterpret_cast<unsigned long long *>(counts_dev));
+    note_launches(1);
+    return launch_status();
+}

@@ -2,14 +2,21 @@
 // order").
 //
 // The result equals a stable sort of the 64-bit keys (tile << 32 | depth
-// bits) generated in Gaussian order, but it is computed in two cheaper
-// stages instead of one 45-bit sort over every (Gaussian, tile) entry:
+// bits) generated in Gaussian order, but no (Gaussian, tile) entry is ever
+// sorted:
 //   1. compact the visible Gaussians (ascending index) and LSD-radix-sort
 //      them by the bits of their float32 depth (4 passes of 8 bits over the
 //      visible Gaussians only; stable, so equal depths keep index order);
-//   2. emit every Gaussian's tile entries in that depth order and
-//      LSD-radix-sort the entries by tile id only (ceil(log2 tiles) bits, 1-2
-//      passes); stability keeps depth order, then index order, inside a tile.
+//   2. in that depth order, emit one entry per super-tile (8 x 8 tiles) a
+//      Gaussian's tile rectangle meets -- about one per Gaussian -- and
+//      stable-sort those few entries by super-tile id (1-2 radix passes);
+//   3. split each super-tile's depth-ordered list into chunks of 256; per
+//      chunk, every entry's 64-bit mask of the tiles that list it (see the
+//      tile membership rule below) and one warp ballot
+//      per tile give the entry's rank among the chunk's entries of that tile;
+//      a scan over the chunks of a super-tile and one over the tile counts
+//      give every tile's start (the ranges) and every entry's final place,
+//      written once: in depth order, then index order, inside each tile.
 // All counts live on the device; nothing waits on the host.
 #include "common.cuh"
 
@@ -101,28 +108,41 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_visible(const float *__rest
 }
 
 // ---- LSD radix pass: histogram, per-digit row scan, stable scatter ----
+// The number of keys lives on the device; the three kernels derive the same
+// block count nbd from it and loop over those blocks with whatever grid the
+// host launched (sized for the device, not for the worst case). hist is
+// [radix][nbd].
+__device__ __forceinline__ int radix_blocks(const uint32_t *count) {
+    return (int)((*count + kSortBlock - 1) / kSortBlock);
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
                                                             const uint32_t *__restrict__ count, int shift, int bits,
-                                                            uint32_t *__restrict__ hist, int nb) {
+                                                            uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[256];
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
-    h[threadIdx.x] = 0;
-    __syncthreads();
     const uint32_t n = *count;
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
+    const int nbd = radix_blocks(count);
+    for (int b = blockIdx.x; b < nbd; b += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t base = (int64_t)b * kSortBlock;
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = base + r * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+        for (int r = 0; r < kSortItems; ++r) {
+            int64_t i = base + r * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < radix) hist[(int64_t)threadIdx.x * nbd + b] = h[threadIdx.x];
+        __syncthreads();
     }
-    __syncthreads();
-    if ((int)threadIdx.x < radix) hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t *__restrict__ hist, int nb,
+__global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t *__restrict__ hist, const uint32_t *__restrict__ count,
                                                         uint32_t *__restrict__ digit_total) {
     __shared__ uint32_t ws[32];
+    const int nb = radix_blocks(count);
     uint32_t *row = hist + (int64_t)blockIdx.x * nb;
     uint32_t carry = 0;
     for (int base = 0; base < nb; base += 1024) {
@@ -140,57 +160,76 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
                                                                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                                const uint32_t *__restrict__ count, int shift, int bits,
                                                                const uint32_t *__restrict__ hist,
-                                                               const uint32_t *__restrict__ digit_total, int nb) {
+                                                               const uint32_t *__restrict__ digit_total) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t run[256];
     __shared__ uint32_t wc[kWarps][256];
     __shared__ uint32_t ws[32];
     const uint32_t n = *count;
-    const int64_t base = (int64_t)blockIdx.x * kSortBlock;
-    if (base >= n) return;
+    const int nbd = radix_blocks(count);
+    if ((int)blockIdx.x >= nbd) return;
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const int t = threadIdx.x, warp = t >> 5;
     uint32_t tot;
-    uint32_t dt = t < radix ? digit_total[t] : 0u;
-    uint32_t dbase = block_scan_excl<uint32_t>(dt, ws, &tot);
-    if (t < radix) run[t] = dbase + hist[(int64_t)t * nb + blockIdx.x];
+    const uint32_t dt = t < radix ? digit_total[t] : 0u;
+    const uint32_t dbase = block_scan_excl<uint32_t>(dt, ws, &tot);
+    for (int b = blockIdx.x; b < nbd; b += gridDim.x) {
+        const int64_t base = (int64_t)b * kSortBlock;
+        if (t < radix) run[t] = dbase + hist[(int64_t)t * nbd + b];
 #pragma unroll 1
-    for (int r = 0; r < kSortItems; ++r) {
-        int64_t i = base + r * kSortThreads + t;
-        bool valid = i < n;
-        uint32_t key = valid ? kin[i] : 0u;
-        uint32_t d = valid ? ((key >> shift) & mask) : 0xffffu;
-        unsigned peers = __match_any_sync(kFull, d);
-        unsigned lrank = __popc(peers & lanemask_lt());
-        if (t < radix) {
+        for (int r = 0; r < kSortItems; ++r) {
+            int64_t i = base + r * kSortThreads + t;
+            bool valid = i < n;
+            uint32_t key = valid ? kin[i] : 0u;
+            uint32_t d = valid ? ((key >> shift) & mask) : 0xffffu;
+            unsigned peers = __match_any_sync(kFull, d);
+            unsigned lrank = __popc(peers & lanemask_lt());
+            if (t < radix) {
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) wc[w][t] = 0u;
-        }
-        __syncthreads();
-        if (valid && lrank == 0) wc[warp][d] = (uint32_t)__popc(peers);
-        __syncthreads();
-        if (t < radix) {
-            uint32_t c = run[t];
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                uint32_t x = wc[w][t];
-                wc[w][t] = c;
-                c += x;
+                for (int w = 0; w < kWarps; ++w) wc[w][t] = 0u;
             }
-            run[t] = c;
+            __syncthreads();
+            if (valid && lrank == 0) wc[warp][d] = (uint32_t)__popc(peers);
+            __syncthreads();
+            if (t < radix) {
+                uint32_t c = run[t];
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    uint32_t x = wc[w][t];
+                    wc[w][t] = c;
+                    c += x;
+                }
+                run[t] = c;
+            }
+            __syncthreads();
+            if (valid) {
+                uint32_t pos = wc[warp][d] + lrank;
+                kout[pos] = key;
+                vout[pos] = vin[i];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = wc[warp][d] + lrank;
-            kout[pos] = key;
-            vout[pos] = vin[i];
-        }
-        __syncthreads();
     }
 }
 
-// ---- stage 2: tile entries in depth order ----
+// Blocks of 256 threads the device holds at once (grids of the loops above).
+int64_t resident_blocks() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (int64_t)(sms > 0 ? sms : 152) * 8;
+}
+
+__global__ void k_zero_u32(uint32_t *__restrict__ p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0u;
+}
+
+// ---- stage 2: super-tile entries in depth order ----
+constexpr int kSuper = 8;       // a super-tile is kSuper x kSuper tiles (64 = one bit each)
+constexpr int kChunk = 256;     // super-tile list entries per chunk (one per thread)
+
 __device__ __forceinline__ int splat_rect(const float *splats, uint32_t g, const DevCam &cam, int &x0, int &y0,
                                           int &x1, int &y1) {
     const float *r = splats + (int64_t)g * kSplat;
@@ -199,87 +238,473 @@ __device__ __forceinline__ int splat_rect(const float *splats, uint32_t g, const
     return tile_rect(__ldg(r), __ldg(r + 1), rad, cam.tile, cam.tiles_x, cam.tiles_y, x0, y0, x1, y1);
 }
 
+__device__ __forceinline__ int super_rect(int x0, int y0, int x1, int y1, int &sx0, int &sy0, int &sx1, int &sy1) {
+    sx0 = x0 / kSuper; sy0 = y0 / kSuper;
+    sx1 = (x1 - 1) / kSuper + 1; sy1 = (y1 - 1) / kSuper + 1;
+    return (sx1 - sx0) * (sy1 - sy0);
+}
+
+// ---- tile membership ----
+// A tile of a splat's 3-sigma rectangle lists the splat only if the box of its
+// pixel centres [X, X + T - 1] x [Y, Y + T - 1] holds a point where the
+// conic's quadratic form q = a dx^2 + 2 b dx dy + c dy^2 is at most
+// tau + 1e-3 (1 + tau), tau = 2 ln(255 o): elsewhere alpha = o exp(-q/2) is
+// below the 1/255 floor of Eq. 2 at every pixel of the tile, so leaving the
+// splat out changes no image and no gradient. A splat with 255 o < 1 is
+// listed nowhere. Decided in single precision, every operation rounded
+// (explicit intrinsics, no contraction), so that the CPU reference makes the
+// same decisions from the same values.
+
+// ln x for x >= 1: x = m 2^e, m in [1, 2); ln m = 2 atanh(s), s = (m-1)/(m+1),
+// by the series 2 s (1 + s^2/3 + ... + s^14/15).
+__device__ __forceinline__ float ln_f32(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu) - 127;
+    const float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    const float s = __fdiv_rn(__fsub_rn(m, 1.f), __fadd_rn(m, 1.f));
+    const float s2 = __fmul_rn(s, s);
+    float p = 0.0666666667f;
+    p = __fadd_rn(__fmul_rn(p, s2), 0.0769230769f);
+    p = __fadd_rn(__fmul_rn(p, s2), 0.0909090909f);
+    p = __fadd_rn(__fmul_rn(p, s2), 0.111111111f);
+    p = __fadd_rn(__fmul_rn(p, s2), 0.142857143f);
+    p = __fadd_rn(__fmul_rn(p, s2), 0.2f);
+    p = __fadd_rn(__fmul_rn(p, s2), 0.333333333f);
+    p = __fadd_rn(__fmul_rn(p, s2), 1.f);
+    return __fadd_rn(__fmul_rn((float)e, 0.693147181f), __fmul_rn(__fmul_rn(2.f, s), p));
+}
+
+// The bound on q with its margin; negative when the splat is listed nowhere.
+__device__ __forceinline__ float tile_tau(float opacity) {
+    const float x = __fmul_rn(255.f, opacity);
+    if (!(x >= 1.f)) return -1.f;
+    const float tau = __fmul_rn(2.f, ln_f32(x));
+    return __fadd_rn(tau, __fmul_rn(1e-3f, __fadd_rn(1.f, tau)));
+}
+
+__device__ __forceinline__ float quad_f32(float a, float b, float c, float dx, float dy) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(a, dx), dx), __fmul_rn(__fmul_rn(__fmul_rn(2.f, b), dx), dy)),
+                     __fmul_rn(__fmul_rn(c, dy), dy));
+}
+
+struct SplatShape {
+    float mx, my, a, b, c, tau, bc, ba;  // bc = b / c, ba = b / a
+};
+
+__device__ __forceinline__ SplatShape splat_shape(const float *splats, uint32_t g) {
+    const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
+    const float4 p0 = __ldg(r), p1 = __ldg(r + 1);
+    SplatShape sh;
+    sh.mx = p0.x; sh.my = p0.y; sh.a = p0.z; sh.b = p0.w; sh.c = p1.x;
+    sh.tau = tile_tau(p1.y);
+    sh.bc = __fdiv_rn(sh.b, sh.c);
+    sh.ba = __fdiv_rn(sh.b, sh.a);
+    return sh;
+}
+
+// Whether tile (x, y) lists the splat: the box minimum of q is 0 when the mean
+// lies inside, else the least of the four edges' clamped one-dimensional
+// minima (on x = X at y = my - (b/c)(X - mx), on y = Y at x = mx - (b/a)(Y - my)).
+__device__ __forceinline__ bool tile_hit(const SplatShape &sh, int tile, int x, int y) {
+    if (sh.tau < 0.f) return false;
+    const float x0 = (float)(x * tile), x1 = (float)(x * tile + tile - 1);
+    const float y0 = (float)(y * tile), y1 = (float)(y * tile + tile - 1);
+    if (sh.mx >= x0 && sh.mx <= x1 && sh.my >= y0 && sh.my <= y1) return true;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float ex = k ? x1 : x0, ey = k ? y1 : y0;
+        const float dx = __fsub_rn(ex, sh.mx);
+        const float yo = __fsub_rn(sh.my, __fmul_rn(sh.bc, dx));
+        const float yy = yo < y0 ? y0 : (yo > y1 ? y1 : yo);
+        if (quad_f32(sh.a, sh.b, sh.c, dx, __fsub_rn(yy, sh.my)) <= sh.tau) return true;
+        const float dy = __fsub_rn(ey, sh.my);
+        const float xo = __fsub_rn(sh.mx, __fmul_rn(sh.ba, dy));
+        const float xx = xo < x0 ? x0 : (xo > x1 ? x1 : xo);
+        if (quad_f32(sh.a, sh.b, sh.c, __fsub_rn(xx, sh.mx), dy) <= sh.tau) return true;
+    }
+    return false;
+}
+
+// Per block of depth-ordered Gaussians: its super-tile entries (part_s).
+// Only splats some tile can list (255 o >= 1) get entries.
+__device__ __forceinline__ unsigned long long super_entries(const float *splats, uint32_t g, const DevCam &cam,
+                                                            int &sx0, int &sy0, int &sx1, int &sy1) {
+    int x0, y0, x1, y1;
+    if (!(tile_tau(__ldg(splats + (int64_t)g * kSplat + 5)) >= 0.f)) return 0ull;
+    if (!splat_rect(splats, g, cam, x0, y0, x1, y1)) return 0ull;
+    return (unsigned long long)super_rect(x0, y0, x1, y1, sx0, sy0, sx1, sy1);
+}
+
 __global__ void __launch_bounds__(kScanBlock) k_count_entries(const float *__restrict__ splats,
                                                              const uint32_t *__restrict__ order,
                                                              const uint32_t *__restrict__ n_vis, DevCam cam,
-                                                             unsigned long long *__restrict__ part) {
+                                                             unsigned long long *__restrict__ part_s) {
     __shared__ unsigned long long ws[32];
     int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    int x0, y0, x1, y1;
-    unsigned long long c = k < *n_vis ? (unsigned long long)splat_rect(splats, order[k], cam, x0, y0, x1, y1) : 0ull;
+    int sx0, sy0, sx1, sy1;
+    const unsigned long long cs = k < *n_vis ? super_entries(splats, order[k], cam, sx0, sy0, sx1, sy1) : 0ull;
     unsigned long long tot;
-    block_scan_excl<unsigned long long>(c, ws, &tot);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    block_scan_excl<unsigned long long>(cs, ws, &tot);
+    if (threadIdx.x == 0) part_s[blockIdx.x] = tot;
 }
 
-__global__ void k_finish_count(const unsigned long long *__restrict__ total, int64_t capacity,
-                               int64_t *__restrict__ count_dev, uint32_t *__restrict__ pclip) {
-    unsigned long long P = *total;
-    *count_dev = (int64_t)P;
-    if (P > (unsigned long long)capacity) {
-        *pclip = (uint32_t)capacity;
-        atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
-    } else {
-        *pclip = (uint32_t)P;
+// sclip = super-tile entries kept; the flag if they alone exceed the capacity.
+__global__ void k_finish_super(const unsigned long long *__restrict__ total_s, int64_t capacity,
+                               uint32_t *__restrict__ sclip) {
+    const unsigned long long Q = *total_s;
+    *sclip = (uint32_t)(Q > (unsigned long long)capacity ? capacity : Q);
+    if (Q > (unsigned long long)capacity) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
+}
+
+// Only when the super-tile entries alone overflowed the capacity (then the
+// tile counts miss the dropped ones): P counted splat by splat, tile by tile.
+__global__ void __launch_bounds__(256) k_count_exact(const float *__restrict__ splats,
+                                                    const uint32_t *__restrict__ order,
+                                                    const uint32_t *__restrict__ n_vis, DevCam cam,
+                                                    const unsigned long long *__restrict__ total_s, int64_t capacity,
+                                                    unsigned long long *__restrict__ total_exact) {
+    if (*total_s <= (unsigned long long)capacity) return;
+    unsigned long long mine = 0ull;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < *n_vis;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = order[k];
+        int x0, y0, x1, y1;
+        const SplatShape sh = splat_shape(splats, g);
+        if (sh.tau < 0.f || !splat_rect(splats, g, cam, x0, y0, x1, y1)) continue;
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0; x < x1; ++x) mine += tile_hit(sh, cam.tile, x, y) ? 1ull : 0ull;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(kFull, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total_exact, mine);
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_emit_entries(const float *__restrict__ splats,
-                                                            const uint32_t *__restrict__ order,
-                                                            const uint32_t *__restrict__ n_vis, DevCam cam,
-                                                            const unsigned long long *__restrict__ part,
-                                                            int64_t capacity, uint32_t *__restrict__ tkeys,
-                                                            uint32_t *__restrict__ tvals) {
+// count_dev = P, the number of entries: the sum of the tile counts, or the
+// exact count above when the super-tile entries overflowed.
+__global__ void k_finish_count(const unsigned long long *__restrict__ total_t,
+                               const unsigned long long *__restrict__ total_s,
+                               const unsigned long long *__restrict__ total_exact, int64_t capacity,
+                               int64_t *__restrict__ count_dev) {
+    const unsigned long long P = *total_s > (unsigned long long)capacity ? *total_exact : *total_t;
+    *count_dev = (int64_t)P;
+    if (P > (unsigned long long)capacity) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restrict__ splats,
+                                                          const uint32_t *__restrict__ order,
+                                                          const uint32_t *__restrict__ n_vis, DevCam cam,
+                                                          int supers_x, const unsigned long long *__restrict__ part_s,
+                                                          int64_t capacity, uint32_t *__restrict__ skeys,
+                                                          uint32_t *__restrict__ svals) {
     __shared__ unsigned long long ws[32];
     int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    int sx0 = 0, sy0 = 0, sx1 = 0, sy1 = 0;
     uint32_t g = 0;
-    unsigned long long c = 0;
+    unsigned long long c = 0ull;
     if (k < *n_vis) {
         g = order[k];
-        c = (unsigned long long)splat_rect(splats, g, cam, x0, y0, x1, y1);
+        c = super_entries(splats, g, cam, sx0, sy0, sx1, sy1);
     }
     unsigned long long tot;
-    unsigned long long off = part[blockIdx.x] + block_scan_excl<unsigned long long>(c, ws, &tot);
-    if (c == 0 || off >= (unsigned long long)capacity) return;
-    for (int y = y0; y < y1; ++y)
-        for (int x = x0; x < x1; ++x) {
+    unsigned long long off = part_s[blockIdx.x] + block_scan_excl<unsigned long long>(c, ws, &tot);
+    if (c == 0) return;
+    for (int y = sy0; y < sy1; ++y)
+        for (int x = sx0; x < sx1; ++x) {
             if (off >= (unsigned long long)capacity) return;
-            tkeys[off] = (uint32_t)(y * cam.tiles_x + x);
-            tvals[off] = g;
+            skeys[off] = (uint32_t)(y * supers_x + x);
+            svals[off] = g;
             ++off;
         }
 }
 
-__global__ void k_zero_u32(uint32_t *__restrict__ p, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = 0u;
+// Segments of the super-tile-sorted list: seg_lo / seg_hi [ns] (zero for an
+// empty super-tile; both arrays zeroed before).
+__global__ void __launch_bounds__(256) k_seg_mark(const uint32_t *__restrict__ skeys,
+                                                 const uint32_t *__restrict__ count, uint32_t *__restrict__ seg_lo,
+                                                 uint32_t *__restrict__ seg_hi) {
+    const uint32_t n = *count;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = skeys[e];
+        if (e == 0 || skeys[e - 1] != k) seg_lo[k] = (uint32_t)e;
+        if (e == (int64_t)n - 1 || skeys[e + 1] != k) seg_hi[k] = (uint32_t)(e + 1);
+    }
 }
 
-__global__ void __launch_bounds__(256) k_ranges_mark(const uint32_t *__restrict__ tkeys,
-                                                    const uint32_t *__restrict__ pclip,
-                                                    uint32_t *__restrict__ ranges) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t P = *pclip;
-    if (k >= P) return;
-    uint32_t t = tkeys[k];
-    if (k == 0 || tkeys[k - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)k;
-    if (k == (int64_t)P - 1 || tkeys[k + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(k + 1);
+// One block: chunk bases, chunk_base [ns + 1] (exclusive scan of
+// ceil(len / kChunk)), and the super-tile of every chunk, chunk_super [chunks].
+__global__ void __launch_bounds__(1024) k_super_plan(const uint32_t *__restrict__ seg_lo,
+                                                     const uint32_t *__restrict__ seg_hi, int ns,
+                                                     uint32_t *__restrict__ chunk_base,
+                                                     uint32_t *__restrict__ chunk_super) {
+    __shared__ uint32_t ws[32];
+    uint32_t carry = 0;
+    for (int base = 0; base < ns; base += 1024) {
+        const int j = base + threadIdx.x;
+        const uint32_t nc = j < ns ? (seg_hi[j] - seg_lo[j] + kChunk - 1) / kChunk : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_scan_excl<uint32_t>(nc, ws, &tot);
+        if (j < ns) {
+            chunk_base[j] = carry + ex;
+            for (uint32_t c = 0; c < nc; ++c) chunk_super[carry + ex + c] = (uint32_t)j;
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) chunk_base[ns] = carry;
+}
+
+// Bit ly * 8 + lx set for each tile (lx, ly) of super-tile (sx, sy) inside the rectangle.
+__device__ __forceinline__ unsigned long long tile_mask(int x0, int y0, int x1, int y1, int sx, int sy) {
+    const int lx0 = max(x0 - sx * kSuper, 0), lx1 = min(x1 - sx * kSuper, kSuper);
+    const int ly0 = max(y0 - sy * kSuper, 0), ly1 = min(y1 - sy * kSuper, kSuper);
+    if (lx0 >= lx1 || ly0 >= ly1) return 0ull;
+    const unsigned long long row = ((1ull << (lx1 - lx0)) - 1ull) << lx0;
+    unsigned long long m = 0ull;
+    for (int ly = ly0; ly < ly1; ++ly) m |= row << (kSuper * ly);
+    return m;
+}
+
+// Position of the k-th (from 0) set bit of m (k < popcount(m)), by halving.
+__device__ __forceinline__ int select_bit(unsigned long long m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w > 0; w >>= 1) {
+        const unsigned long long low = m & ((1ull << w) - 1ull);
+        const int c = __popcll(low);
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
+// Shared part of the chunk kernels for chunk c: this thread's entry and the
+// mask of the tiles of the super-tile that list it.
+struct ChunkCtx {
+    int s, sx, sy;
+    uint32_t g;
+    unsigned long long mask;
+};
+
+// With masks_in NULL the masks are computed by the tile test (and stored to
+// masks_out when given); else they are read.
+__device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float *__restrict__ splats,
+                                           const uint32_t *__restrict__ svals, const uint32_t *__restrict__ seg_lo,
+                                           const uint32_t *__restrict__ seg_hi,
+                                           const uint32_t *__restrict__ chunk_base,
+                                           const uint32_t *__restrict__ chunk_super, int supers_x,
+                                           const DevCam &cam, uint32_t *hit_mask,
+                                           const unsigned long long *__restrict__ masks_in,
+                                           unsigned long long *__restrict__ masks_out) {
+    __syncthreads();  // the previous chunk's shared data is no longer read
+    cx.s = (int)chunk_super[c];
+    cx.sx = cx.s % supers_x;
+    cx.sy = cx.s / supers_x;
+    const uint32_t e = seg_lo[cx.s] + (c - chunk_base[cx.s]) * kChunk + threadIdx.x;
+    const bool valid = e < seg_hi[cx.s];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    cx.mask = 0ull;
+    cx.g = valid ? svals[e] : 0u;
+    if (masks_in) {
+        if (valid) cx.mask = masks_in[e];
+    } else {
+        // candidate tiles: the entry's rectangle inside this super-tile
+        unsigned long long cand = 0ull;
+        SplatShape sh{};
+        int x0, y0, x1, y1;
+        if (valid && splat_rect(splats, cx.g, cam, x0, y0, x1, y1)) {
+            sh = splat_shape(splats, cx.g);
+            if (sh.tau >= 0.f) cand = tile_mask(x0, y0, x1, y1, cx.sx, cx.sy);
+        }
+        // the warp's (entry, tile) candidates, spread evenly over its lanes
+        const int cnt = __popcll(cand);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - cnt, total = __shfl_sync(kFull, incl, 31);
+        hit_mask[2 * threadIdx.x] = 0u;
+        hit_mask[2 * threadIdx.x + 1] = 0u;
+        __syncwarp();
+        const uint32_t clo = (uint32_t)cand, chi = (uint32_t)(cand >> 32);
+        for (int base = 0; base < total; base += 32) {
+            const int j = base + lane;
+            int i = 0;  // owner: the last lane whose first candidate index is <= j
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int ex = __shfl_sync(kFull, excl, i + step);
+                if (ex <= j) i += step;
+            }
+            const int k = j - __shfl_sync(kFull, excl, i);
+            const uint32_t lo = __shfl_sync(kFull, clo, i), hi = __shfl_sync(kFull, chi, i);
+            SplatShape o;
+            o.mx = __shfl_sync(kFull, sh.mx, i); o.my = __shfl_sync(kFull, sh.my, i);
+            o.a = __shfl_sync(kFull, sh.a, i); o.b = __shfl_sync(kFull, sh.b, i); o.c = __shfl_sync(kFull, sh.c, i);
+            o.tau = __shfl_sync(kFull, sh.tau, i);
+            o.bc = __shfl_sync(kFull, sh.bc, i); o.ba = __shfl_sync(kFull, sh.ba, i);
+            if (j < total) {
+                const int t = select_bit(((unsigned long long)hi << 32) | lo, k);
+                if (tile_hit(o, cam.tile, cx.sx * kSuper + (t & 7), cx.sy * kSuper + (t >> 3)))
+                    atomicOr(&hit_mask[2 * (warp * 32 + i) + (t >> 5)], 1u << (t & 31));  // native 32-bit
+            }
+        }
+        __syncwarp();
+        cx.mask = ((unsigned long long)hit_mask[2 * threadIdx.x + 1] << 32) | hit_mask[2 * threadIdx.x];
+        if (valid && masks_out) masks_out[e] = cx.mask;
+    }
+}
+
+// Global tile id of slot t of super-tile (sx, sy).
+__device__ __forceinline__ int slot_tile(int t, int sx, int sy, int tiles_x) {
+    return (sy * kSuper + (t >> 3)) * tiles_x + sx * kSuper + (t & 7);
+}
+
+__global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict__ splats,
+                                                        const uint32_t *__restrict__ svals,
+                                                        const uint32_t *__restrict__ seg_lo,
+                                                        const uint32_t *__restrict__ seg_hi,
+                                                        const uint32_t *__restrict__ chunk_base,
+                                                        const uint32_t *__restrict__ chunk_super, int ns,
+                                                        int supers_x, DevCam cam, uint32_t *__restrict__ counts,
+                                                        uint32_t *__restrict__ tile_count,
+                                                        unsigned long long *__restrict__ masks) {
+    __shared__ uint32_t hit_mask[2 * kChunk];  // per entry, low and high halves
+    __shared__ uint32_t cnt[64];
+    const uint32_t nc = chunk_base[ns];
+    for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        ChunkCtx cx;
+        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, hit_mask, nullptr,
+                   masks);
+        if (threadIdx.x < 64) cnt[threadIdx.x] = 0u;
+        __syncthreads();
+        for (unsigned long long m = cx.mask; m; m &= m - 1ull) atomicAdd(&cnt[__ffsll((long long)m) - 1], 1u);
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int t = threadIdx.x;
+            const uint32_t n = cnt[t];
+            counts[(int64_t)c * 64 + t] = n;
+            if (n) atomicAdd(tile_count + slot_tile(t, cx.sx, cx.sy, cam.tiles_x), n);
+        }
+    }
+}
+
+// Tile starts (exclusive scan of the tile counts over tile ids) and the
+// ranges, clipped to the capacity: per-block sums, a scan of those, then each
+// block scans its own tiles from its offset.
+__global__ void __launch_bounds__(kScanBlock) k_tile_sums(const uint32_t *__restrict__ tile_count, int64_t tiles,
+                                                         unsigned long long *__restrict__ part) {
+    __shared__ unsigned long long ws[32];
+    const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    unsigned long long tot;
+    block_scan_excl<unsigned long long>(j < tiles ? tile_count[j] : 0ull, ws, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_tile_starts(const uint32_t *__restrict__ tile_count, int64_t tiles,
+                                                           const unsigned long long *__restrict__ part,
+                                                           int64_t capacity, unsigned long long *__restrict__ tile_start,
+                                                           uint32_t *__restrict__ ranges) {
+    __shared__ unsigned long long ws[32];
+    const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const unsigned long long n = j < tiles ? tile_count[j] : 0ull;
+    unsigned long long tot;
+    const unsigned long long st = part[blockIdx.x] + block_scan_excl<unsigned long long>(n, ws, &tot);
+    if (j < tiles) {
+        const unsigned long long cap = (unsigned long long)capacity, en = st + n;
+        tile_start[j] = st;
+        // an empty tile has the range (0, 0)
+        ranges[2 * j] = n ? (uint32_t)(st < cap ? st : cap) : 0u;
+        ranges[2 * j + 1] = n ? (uint32_t)(en < cap ? en : cap) : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ splats, const uint32_t *__restrict__ svals,
+                                                  const uint32_t *__restrict__ seg_lo,
+                                                  const uint32_t *__restrict__ seg_hi,
+                                                  const uint32_t *__restrict__ chunk_base,
+                                                  const uint32_t *__restrict__ chunk_super, int ns, int supers_x,
+                                                  DevCam cam, const uint32_t *__restrict__ counts,
+                                                  const unsigned long long *__restrict__ tile_start, int64_t capacity,
+                                                  const unsigned long long *__restrict__ masks,
+                                                  uint32_t *__restrict__ vals) {
+    constexpr int kW = kChunk / 32;
+    __shared__ uint32_t ballots[kW][64];                 // per (warp, slot): lanes whose entry the tile lists
+    __shared__ uint32_t before[kChunk / 64][64];         // partial sums of earlier chunks' counts
+    __shared__ unsigned long long base[kW][64];         // start of (warp, slot) in the final list
+    const uint32_t nc = chunk_base[ns];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        ChunkCtx cx;
+        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, nullptr, masks,
+                   nullptr);
+#pragma unroll 8
+        for (int t = 0; t < 64; ++t) {
+            const uint32_t b = __ballot_sync(kFull, (cx.mask >> t) & 1ull);
+            if (lane == 0) ballots[warp][t] = b;
+        }
+        {   // entries of each slot in the super-tile's earlier chunks: 4 threads per slot
+            const int t = threadIdx.x & 63, q = threadIdx.x >> 6;
+            uint32_t n = 0;
+            for (uint32_t c2 = chunk_base[cx.s] + q; c2 < c; c2 += kChunk / 64) n += counts[(int64_t)c2 * 64 + t];
+            before[q][t] = n;
+        }
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int t = threadIdx.x;
+            const bool inside = cx.sx * kSuper + (t & 7) < cam.tiles_x && cx.sy * kSuper + (t >> 3) < cam.tiles_y;
+            unsigned long long run = 0ull;
+            if (inside) {
+                run = tile_start[slot_tile(t, cx.sx, cx.sy, cam.tiles_x)];
+#pragma unroll
+                for (int q = 0; q < kChunk / 64; ++q) run += before[q][t];
+            }
+#pragma unroll
+            for (int w = 0; w < kW; ++w) {
+                base[w][t] = run;
+                run += (unsigned long long)__popc(ballots[w][t]);
+            }
+        }
+        __syncthreads();
+        // slot by slot, so that a warp's entries of one tile go to consecutive words
+        for (int t = 0; t < 64; ++t) {
+            const uint32_t b = ballots[warp][t];
+            if (b == 0u) continue;  // warp-uniform
+            if ((cx.mask >> t) & 1ull) {
+                const unsigned long long pos = base[warp][t] + (unsigned long long)__popc(b & lt);
+                if (pos < (unsigned long long)capacity) vals[pos] = cx.g;
+            }
+        }
+    }
 }
 
 // ---- workspace ----
 struct SortWs {
     uint32_t *keys[2], *vals[2];  // visible Gaussians: depth keys and indices
-    uint32_t *tkeys[2], *tvals1;  // tile entries; the other value buffer is the output
+    uint32_t *skeys[2], *svals1;  // super-tile entries; the other value buffer is the output
     uint32_t *hist, *digit_total, *part32;
-    unsigned long long *part64, *total64;
-    uint32_t *n_vis, *pclip;
+    unsigned long long *part_s, *total_s, *total_t, *total_exact;
+    unsigned long long *masks;                 // [capacity] tile mask of each super-tile entry
+    uint32_t *n_vis, *sclip;
+    uint32_t *seg_lo, *seg_hi, *chunk_base;    // [ns], [ns], [ns + 1]
+    uint32_t *tile_count;                      // [tiles]
+    unsigned long long *tile_start;            // [tiles]
+    uint32_t *chunk_counts;                    // [max chunks][64]
+    uint32_t *chunk_super;                     // [max chunks]
+    unsigned long long *tile_part;             // [tile blocks]
     size_t bytes;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-inline SortWs sort_layout(char *base, int64_t n, int64_t cap) {
+inline int64_t max_chunks(int64_t cap, int64_t ns) { return (cap + kChunk - 1) / kChunk + ns + 1; }
+
+inline SortWs sort_layout(char *base, int64_t n, int64_t cap, int64_t tiles, int64_t ns) {
     SortWs w;
     int64_t nbN = (n + kSortBlock - 1) / kSortBlock, nbC = (cap + kSortBlock - 1) / kSortBlock;
     int64_t nbMax = nbN > nbC ? nbN : nbC;
@@ -294,17 +719,44 @@ inline SortWs sort_layout(char *base, int64_t n, int64_t cap) {
     };
     for (int k = 0; k < 2; ++k) w.keys[k] = (uint32_t *)take(4 * (size_t)n);
     for (int k = 0; k < 2; ++k) w.vals[k] = (uint32_t *)take(4 * (size_t)n);
-    for (int k = 0; k < 2; ++k) w.tkeys[k] = (uint32_t *)take(4 * (size_t)cap);
-    w.tvals1 = (uint32_t *)take(4 * (size_t)cap);
+    for (int k = 0; k < 2; ++k) w.skeys[k] = (uint32_t *)take(4 * (size_t)cap);
+    w.svals1 = (uint32_t *)take(4 * (size_t)cap);
     w.hist = (uint32_t *)take(4 * 256 * (size_t)nbMax);
     w.digit_total = (uint32_t *)take(4 * 256);
     w.part32 = (uint32_t *)take(4 * (size_t)nbS);
-    w.part64 = (unsigned long long *)take(8 * (size_t)nbS);
-    w.total64 = (unsigned long long *)take(8);
+    w.part_s = (unsigned long long *)take(8 * (size_t)nbS);
+    w.total_s = (unsigned long long *)take(8);
+    w.total_t = (unsigned long long *)take(8);
+    w.total_exact = (unsigned long long *)take(8);
+    w.masks = (unsigned long long *)take(8 * (size_t)cap);
     w.n_vis = (uint32_t *)take(4);
-    w.pclip = (uint32_t *)take(4);
+    w.sclip = (uint32_t *)take(4);
+    // zeroed together before each sort: segment bounds, then tile counts
+    w.seg_lo = (uint32_t *)take(4 * (size_t)(2 * ns + tiles));
+    w.seg_hi = w.seg_lo ? w.seg_lo + ns : nullptr;
+    w.tile_count = w.seg_lo ? w.seg_lo + 2 * ns : nullptr;
+    w.chunk_base = (uint32_t *)take(4 * (size_t)(ns + 1));
+    w.chunk_super = (uint32_t *)take(4 * (size_t)max_chunks(cap, ns));
+    w.tile_part = (unsigned long long *)take(8 * (size_t)((tiles + kScanBlock - 1) / kScanBlock));
+    w.tile_start = (unsigned long long *)take(8 * (size_t)tiles);
+    w.chunk_counts = (uint32_t *)take(4 * 64 * (size_t)max_chunks(cap, ns));
     w.bytes = off;
     return w;
+}
+
+struct SuperGrid {
+    int supers_x, supers_y;
+    int64_t tiles, ns;
+};
+
+inline SuperGrid super_grid(int32_t width, int32_t height, int32_t tile) {
+    SuperGrid g;
+    const int tx = (width + tile - 1) / tile, ty = (height + tile - 1) / tile;
+    g.supers_x = (tx + kSuper - 1) / kSuper;
+    g.supers_y = (ty + kSuper - 1) / kSuper;
+    g.tiles = (int64_t)tx * ty;
+    g.ns = (int64_t)g.supers_x * g.supers_y;
+    return g;
 }
 
 // One full LSD sort of (keys, vals) over *count (bounded by `bound`) on `bits`
@@ -315,15 +767,15 @@ int radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], int in, const u
     if (total_bits <= 0) return in;
     int npass = (total_bits + 7) / 8;
     int per = (total_bits + npass - 1) / npass;
-    int nb = (int)((bound + kSortBlock - 1) / kSortBlock);
-    if (nb < 1) nb = 1;
+    const int64_t nb = (bound + kSortBlock - 1) / kSortBlock, cap = resident_blocks();
+    const int grid = (int)(nb < 1 ? 1 : (nb < cap ? nb : cap));
     int shift = 0;
     for (int p = 0; p < npass; ++p) {
         int bits = per < total_bits - shift ? per : total_bits - shift;
-        k_radix_hist<<<nb, kSortThreads, 0, s>>>(keys[in], count, shift, bits, w.hist, nb);
-        k_radix_rowscan<<<1 << bits, 1024, 0, s>>>(w.hist, nb, w.digit_total);
-        k_radix_scatter<<<nb, kSortThreads, 0, s>>>(keys[in], vals[in], keys[1 - in], vals[1 - in], count, shift,
-                                                    bits, w.hist, w.digit_total, nb);
+        k_radix_hist<<<grid, kSortThreads, 0, s>>>(keys[in], count, shift, bits, w.hist);
+        k_radix_rowscan<<<1 << bits, 1024, 0, s>>>(w.hist, count, w.digit_total);
+        k_radix_scatter<<<grid, kSortThreads, 0, s>>>(keys[in], vals[in], keys[1 - in], vals[1 - in], count, shift,
+                                                      bits, w.hist, w.digit_total);
         note_launches(3);
         in = 1 - in;
         shift += bits;
@@ -351,51 +803,79 @@ uint32_t take_sort_flags() {
 using namespace gs;
 
 extern "C" size_t gs_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t width, int32_t height, int32_t tile) {
-    (void)width; (void)height; (void)tile;
-    if (n < 0 || capacity < 0) return 0;
-    return sort_layout(nullptr, n, capacity).bytes;
+    if (n < 0 || capacity < 0 || width <= 0 || height <= 0 || !tile_ok(tile)) return 0;
+    const SuperGrid sg = super_grid(width, height, tile);
+    return sort_layout(nullptr, n, capacity, sg.tiles, sg.ns).bytes;
 }
 
 extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, void *ws, size_t ws_bytes,
                        int64_t capacity, uint32_t *vals, uint32_t *ranges, int64_t *count_dev, gs_stream_t stream) {
     if (n < 0 || n > INT32_MAX || capacity < 0 || capacity > INT32_MAX || !camera_ok(cam)) return GS_ERR_INVALID_ARG;
     if (!ranges || !count_dev || (n > 0 && !splats) || (capacity > 0 && !vals)) return GS_ERR_INVALID_ARG;
-    SortWs w = sort_layout(static_cast<char *>(ws), n, capacity);
+    const SuperGrid sg = super_grid(cam->width, cam->height, cam->tile);
+    SortWs w = sort_layout(static_cast<char *>(ws), n, capacity, sg.tiles, sg.ns);
     if (!ws || ws_bytes < w.bytes) return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(ws) & 255) return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     DevCam dc = make_cam(cam);
-    const int64_t tiles = (int64_t)dc.tiles_x * dc.tiles_y;
+    const int64_t tiles = sg.tiles;
+    const int ns = (int)sg.ns;
     const int nbS = (int)((n + kScanBlock - 1) / kScanBlock);
 
-    k_zero_u32<<<grid_for(2 * tiles, 256), 256, 0, s>>>(ranges, 2 * tiles);
-    note_launches(1);
-    if (n == 0) {
-        cudaMemsetAsync(count_dev, 0, sizeof(int64_t), s);
-        return launch_status();
+    if (n == 0 || capacity == 0) {
+        k_zero_u32<<<grid_for(2 * tiles, 256), 256, 0, s>>>(ranges, 2 * tiles);
+        note_launches(1);
+        if (n == 0) {
+            cudaMemsetAsync(count_dev, 0, sizeof(int64_t), s);
+            return launch_status();
+        }
     }
+    k_zero_u32<<<grid_for(2 * sg.ns + tiles, 256), 256, 0, s>>>(w.seg_lo, 2 * sg.ns + tiles);
+    note_launches(1);
     // stage 1: visible Gaussians by depth
     k_count_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32);
     k_scan_parts<uint32_t><<<1, 1024, 0, s>>>(w.part32, nbS, w.n_vis);
     k_emit_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, w.keys[0], w.vals[0]);
     note_launches(3);
     int cur = radix_sort(w.keys, w.vals, 0, w.n_vis, n, 32, w, s);
-    // stage 2: tile entries in depth order, then by tile id
-    k_count_entries<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.part64);
-    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.part64, nbS, w.total64);
-    k_finish_count<<<1, 1, 0, s>>>(w.total64, capacity, count_dev, w.pclip);
-    note_launches(3);
-    const int tbits = ceil_log2(tiles);
-    const int npass = (tbits + 7) / 8;
-    uint32_t *tk[2] = {w.tkeys[0], w.tkeys[1]};
-    uint32_t *tv[2] = {vals, w.tvals1};
-    const int start = (npass % 2 == 0) ? 0 : 1;  // so that the last pass lands in `vals`
-    if (capacity > 0) {
-        k_emit_entries<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.part64, capacity, tk[start],
-                                                  tv[start]);
-        int fin = radix_sort(tk, tv, start, w.pclip, capacity, tbits, w, s);
-        k_ranges_mark<<<grid_for(capacity, 256), 256, 0, s>>>(tk[fin], w.pclip, ranges);
-        note_launches(2);
+    // stage 2: super-tile entries in depth order, stable-sorted by super-tile
+    k_count_entries<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.part_s);
+    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.part_s, nbS, w.total_s);
+    k_finish_super<<<1, 1, 0, s>>>(w.total_s, capacity, w.sclip);
+    cudaMemsetAsync(w.total_exact, 0, sizeof(unsigned long long), s);
+    k_count_exact<<<(unsigned)resident_blocks(), 256, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.total_s, capacity,
+                                                              w.total_exact);
+    note_launches(4);
+    if (capacity == 0) {
+        cudaMemsetAsync(w.total_t, 0, sizeof(unsigned long long), s);
+        k_finish_count<<<1, 1, 0, s>>>(w.total_t, w.total_s, w.total_exact, capacity, count_dev);
+        note_launches(1);
+        return launch_status();
     }
+    const int sbits = ceil_log2(sg.ns);
+    const int npass = (sbits + 7) / 8;
+    uint32_t *sk[2] = {w.skeys[0], w.skeys[1]};
+    uint32_t *sv[2] = {w.svals1, vals};  // the sorted list must end in svals1: vals is written from it
+    const int start = npass % 2;
+    k_emit_super<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s, capacity,
+                                            sk[start], sv[start]);
+    note_launches(1);
+    radix_sort(sk, sv, start, w.sclip, capacity, sbits, w, s);  // ends in skeys[0] / svals1
+    // stage 3: per-tile lists
+    const int64_t chunks = max_chunks(capacity, sg.ns), resident = resident_blocks();
+    const unsigned cgrid = (unsigned)(chunks < resident ? chunks : resident);
+    k_seg_mark<<<(unsigned)resident, 256, 0, s>>>(w.skeys[0], w.sclip, w.seg_lo, w.seg_hi);
+    k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_super);
+    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
+                                            sg.supers_x, dc, w.chunk_counts, w.tile_count, w.masks);
+    const int tb = (int)((tiles + kScanBlock - 1) / kScanBlock);
+    k_tile_sums<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part);
+    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.tile_part, tb, w.total_t);
+    k_finish_count<<<1, 1, 0, s>>>(w.total_t, w.total_s, w.total_exact, capacity, count_dev);
+    k_tile_starts<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part, capacity, w.tile_start, ranges);
+    k_expand<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
+                                      sg.supers_x, dc, w.chunk_counts, w.tile_start, capacity, w.masks, vals);
+    note_launches(3);
+    note_launches(5);
     return launch_status();
 }

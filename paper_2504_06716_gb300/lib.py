@@ -100,6 +100,7 @@ _SIGS = {
     "gs_freeze_apply": ([_I64, _P, _F32, _P, _P, _P, _P, _SZ, _P], _I32),
     "gs_adam_masked_devstep": ([_P, _P, _P, _P, _I64, _P, _P, _P, _F32, _F32, _F32, _P,
                                 _P, _P], _I32),
+    "gs_raster_pair_counts": ([_P, _P, _P, _CAM, _P, _P, _P, _P], _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
     "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
     "gs_get_device_error": ([ctypes.POINTER(ctypes.c_uint32), _P], _I32),
@@ -424,6 +425,16 @@ def gs_get_device_error(stream=None) -> int:
 
 def gs_status_string(status: int) -> str:
     return load().gs_status_string(status).decode()
+
+
+def gs_raster_pair_counts(splats, vals, ranges, cam: GsCamera, n_last, frozen, counts, stream=None):
+    """counts: int64 device tensor [3], added to (blended active, blended frozen, skipped)."""
+    import torch
+
+    _check("gs_raster_pair_counts", load().gs_raster_pair_counts(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), _ptr(n_last, torch.int32, "n_last"), _ptr(frozen, torch.uint8, "frozen"),
+        _ptr(counts, torch.int64, "counts"), _stream(stream)))
 
 
 def gs_launch_count() -> int:
