@@ -36,6 +36,17 @@ class ScheduleConfig:
     lr_decay: float = 0.75
     lr_patience: int = 1
     lr_eps: float = 1.0
+    # densification (Sec. 4.1; 3DGS's mechanics): every den_every iterations
+    # in (den_from, min(window_end, early stop)), opacity reset every
+    # opacity_every in [opacity_every, min(window_end, early stop)]; the plain
+    # 3DGS arm densifies until den_until_plain instead.
+    den_from: int = 500
+    den_every: int = 100
+    opacity_every: int = 3000
+    den_until_plain: int = 15000
+    rgb_every: int = 5  # the diffuse-colour criterion on every fifth densification step (20%)
+    eps0_den_xyz: float = 2e-4
+    eps0_den_rgb: float = 1e-6
 
 
 def threshold(eps0: float, k: int, K: int) -> float:
@@ -88,3 +99,32 @@ class Plateau:
                 self.lr *= self.decay
                 self.bad = 0
         return self.lr
+
+
+def _den_end(cfg: ScheduleConfig, stop_iter: int | None, plain: bool) -> int:
+    if plain:
+        return cfg.den_until_plain
+    return cfg.window_end if stop_iter is None else min(cfg.window_end, stop_iter)
+
+
+def densify_due(k: int, cfg: ScheduleConfig, stop_iter: int | None, plain: bool = False) -> bool:
+    """Densify and prune after iteration k: k a multiple of den_every in the open
+    interval (den_from, end), end = min(window_end, early stop) for GSta."""
+    return k % cfg.den_every == 0 and cfg.den_from < k < _den_end(cfg, stop_iter, plain)
+
+
+def densify_uses_rgb(k: int, cfg: ScheduleConfig) -> bool:
+    """Sec. 4.1: the diffuse-colour criterion on 20% of the densification
+    steps, read as every fifth one."""
+    return (k // cfg.den_every) % cfg.rgb_every == 0
+
+
+def opacity_reset_due(k: int, cfg: ScheduleConfig, stop_iter: int | None, plain: bool = False) -> bool:
+    """Opacity reset after iteration k: k a positive multiple of opacity_every
+    up to the densification end (inclusive)."""
+    return k > 0 and k % cfg.opacity_every == 0 and k <= _den_end(cfg, stop_iter, plain)
+
+
+def size_pruning(k: int, cfg: ScheduleConfig) -> bool:
+    """Screen / world size pruning once past the first opacity reset."""
+    return k > cfg.opacity_every

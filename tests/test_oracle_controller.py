@@ -44,3 +44,17 @@ def test_plateau_schedule():
     p = GOLD["plateau"]
     s = C.Plateau(p["lr0"], 0.75, 1, 1.0)
     assert [s.step(v) for v in p["psnrs"]] == pytest.approx(p["lrs"])
+
+
+def test_densification_cadence_hand_values():
+    cfg = C.ScheduleConfig()
+    due = [k for k in range(0, 12001) if C.densify_due(k, cfg, None)]
+    assert due[0] == 600 and due[-1] == 9900 and len(due) == 94  # (500, 10000), every 100
+    assert [k for k in range(0, 12001) if C.densify_due(k, cfg, 7000)][-1] == 6900  # early stop ends it
+    assert [k for k in range(0, 20001) if C.densify_due(k, cfg, None, plain=True)][-1] == 14900
+    assert [k for k in range(0, 12001) if C.opacity_reset_due(k, cfg, None)] == [3000, 6000, 9000]
+    assert [k for k in range(0, 12001) if C.opacity_reset_due(k, cfg, 6000)] == [3000, 6000]
+    rgb = [k for k in due if C.densify_uses_rgb(k, cfg)]
+    assert rgb[:3] == [1000, 1500, 2000] and abs(len(rgb) / len(due) - 0.2) < 0.02
+    assert not C.size_pruning(3000, cfg) and C.size_pruning(3100, cfg)
+    assert C.threshold(cfg.eps0_den_xyz, 0, 30000) == pytest.approx(1e-4)
