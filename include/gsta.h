@@ -233,6 +233,24 @@ int gs_project_bwd_accum(const float *P, int64_t n, int32_t sh_degree, const gs_
                          const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, float *acc_xyz,
                          float *acc_rgb, int32_t *cnt, gs_stream_t stream);
 
+/* One window of gradient statistics (as gs_project_bwd keeps them): acc_xyz,
+ * acc_rgb float [n], cnt int32 [n]; max_radius int32 [n] or NULL -- the
+ * largest screen radius (px) of the Gaussian in the views counted. */
+typedef struct {
+    float *acc_xyz;
+    float *acc_rgb;
+    int32_t *cnt;
+    int32_t *max_radius;
+} gs_grad_stats;
+
+/* gs_project_bwd (accumulate = 0) or gs_project_bwd_accum (accumulate != 0)
+ * that updates n_sets (0..2) statistics windows at once -- the freeze window
+ * of Sec. 3.2.1 and the densification window of Sec. 4.1 have different
+ * lengths. sets: host array of n_sets. Errors: INVALID_ARG, CUDA. */
+int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
+                         const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, int32_t accumulate,
+                         const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream);
+
 /* gs_raster_bwd followed by gs_project_bwd on the same stream. */
 int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
                   const uint32_t *vals, const uint32_t *ranges, const float *t_final, const int32_t *n_last,
@@ -372,6 +390,71 @@ int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t
  * CUDA. */
 int gs_raster_pair_counts(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                           const int32_t *n_last, const uint8_t *frozen, uint64_t *counts_dev, gs_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Adaptive densification and pruning (Sec. 4.1: thresholds and cadence;
+ * the clone / split / prune rules are those of 3DGS, which the paper builds
+ * on) and opacity reset. Thresholds at the current iteration, compared in
+ * float32; sizes and opacities in the log / logit domain.
+ * --------------------------------------------------------------------- */
+typedef struct {
+    float eps_xyz;           /* average |dL/dmean2d| (NDC) threshold */
+    float eps_rgb;           /* average |dL/dk0| threshold */
+    int32_t use_rgb;         /* the diffuse-colour criterion on this step */
+    float log_clone_max;     /* log(0.01 extent): largest log-scale that clones */
+    float logit_min_opacity; /* logit(0.005): below it, pruned */
+    int32_t prune_big;       /* screen / world size pruning active */
+    int32_t max_screen_radius; /* px (20): larger originals are pruned */
+    float log_max_world;     /* log(0.1 extent): larger Gaussians are pruned */
+    float log_split_div;     /* log(1.6): children's log-scales are this much smaller */
+} gs_densify_params;
+
+/* Bytes of workspace the densification of n Gaussians needs. */
+size_t gs_densify_workspace_bytes(int64_t n);
+
+/* Decides, for each of the n Gaussians (P [n][64], the densification
+ * window's statistics: average = acc / cnt over cnt > 0, max_radius may be
+ * NULL), candidate = average xyz >= eps_xyz (or, with use_rgb, average rgb
+ * >= eps_rgb); clone if its largest log-scale <= log_clone_max, else split;
+ * prune when logit < logit_min_opacity, or (prune_big) largest screen radius
+ * > max_screen_radius (originals only) or largest log-scale > log_max_world
+ * (a child's log-scale is smaller by log_split_div). Writes counts_dev [4]
+ * (int64, device): surviving originals, surviving clones, surviving children
+ * (two per split original whose children survive), split originals (the
+ * number of z draws gs_densify_apply needs). Keeps the decisions in ws for
+ * gs_densify_apply. Errors: INVALID_ARG, CUDA. */
+int gs_densify_plan(int64_t n, const float *P, const gs_grad_stats *stats, const gs_densify_params *prm, void *ws,
+                    size_t ws_bytes, int64_t *counts_dev, gs_stream_t stream);
+
+/* Further per-Gaussian state gs_densify_apply moves with the Gaussians:
+ * rows of row_bytes (a multiple of 4) from src [n] to dst [capacity]; copied
+ * for survivors, zero for new Gaussians (device pointers, 4-byte aligned). */
+typedef struct {
+    const void *src;
+    void *dst;
+    int32_t row_bytes;
+} gs_densify_carry;
+
+/* Writes the densified set planned in ws: rows of P_out / m_out / v_out
+ * [capacity][64], frozen_out [capacity] and of each carried array (carry:
+ * host array of n_carry <= 8, may be NULL with 0): the
+ * surviving originals in index order (all state copied), then the surviving
+ * clones (exact copies of P), then the surviving children, two per split
+ * original in its order: mean + R(q/|q|)(exp(log_s) * z_k) with z [splits][2][3]
+ * (device, N(0, 1) draws of the split originals in index order, child 0
+ * first), log-scales minus log_split_div, the rest of P copied. New rows have
+ * zero m, v and carried state and are not frozen. Writes nothing if the
+ * total exceeds `capacity`. The output buffers must not overlap the inputs.
+ * Errors: INVALID_ARG, CUDA. */
+int gs_densify_apply(int64_t n, const float *P, const float *m, const float *v, const uint8_t *frozen,
+                     const gs_densify_carry *carry, int32_t n_carry, const gs_densify_params *prm, const float *z,
+                     const void *ws, size_t ws_bytes, int64_t capacity, float *P_out, float *m_out, float *v_out,
+                     uint8_t *frozen_out, gs_stream_t stream);
+
+/* 3DGS opacity reset: P[i][10] = min(P[i][10], logit_cap) (logit_cap =
+ * logit(0.01)) and the opacity's Adam moments m, v [i][10] set to 0, for all
+ * n Gaussians. Errors: INVALID_ARG, CUDA. */
+int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, gs_stream_t stream);
 
 /* Bytes of workspace gs_psnr needs for S images of H x W. */
 size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W);

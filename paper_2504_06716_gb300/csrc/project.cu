@@ -216,14 +216,21 @@ __global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P
     o[2] = make_float4(rgb[2], g.tz, __int_as_float(radius), __int_as_float(tiles));
 }
 
+// Up to two statistics windows updated by the backward (e.g. freezing and
+// densification), passed by value.
+struct StatSets {
+    float *ax[2], *ar[2];
+    int32_t *cnt[2], *maxr[2];
+    int n;
+};
+
 // Backward of the projection for act[0 .. *n_active). See gs_project_bwd;
 // with ACC the gradient rows are added to G instead of written.
 template <bool ACC>
 __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, DevCam cam,
                                                      const float *__restrict__ splats, const int32_t *__restrict__ act,
                                                      const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
-                                                     float *__restrict__ G, float *__restrict__ acc_xyz,
-                                                     float *__restrict__ acc_rgb, int32_t *__restrict__ cnt) {
+                                                     float *__restrict__ G, StatSets st) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= *n_active) return;
     const int64_t i = act[k];
@@ -394,11 +401,15 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
         gout[c] = v;
     }
 
-    if (cnt) {
-        float ex = dmx * 0.5f * (float)cam.W, ey = dmy * 0.5f * (float)cam.H;
-        acc_xyz[i] += sqrtf(ex * ex + ey * ey);
-        acc_rgb[i] += sqrtf(gsh[0] * gsh[0] + gsh[1] * gsh[1] + gsh[2] * gsh[2]);
-        cnt[i] += 1;
+    if (st.n) {
+        const float ex = dmx * 0.5f * (float)cam.W, ey = dmy * 0.5f * (float)cam.H;
+        const float nx = sqrtf(ex * ex + ey * ey), nr = sqrtf(gsh[0] * gsh[0] + gsh[1] * gsh[1] + gsh[2] * gsh[2]);
+        for (int k2 = 0; k2 < st.n; ++k2) {
+            st.ax[k2][i] += nx;
+            st.ar[k2][i] += nr;
+            st.cnt[k2][i] += 1;
+            if (st.maxr[k2] && radius > st.maxr[k2][i]) st.maxr[k2][i] = radius;
+        }
     }
 }
 
@@ -418,36 +429,66 @@ extern "C" int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs
     return launch_status();
 }
 
-template <bool ACC>
-static int project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
-                       const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, float *acc_xyz,
-                       float *acc_rgb, int32_t *cnt, gs_stream_t stream) {
-    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam)) return GS_ERR_INVALID_ARG;
+static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
+                       const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G,
+                       const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream) {
+    if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam) || n_sets < 0 || n_sets > 2 ||
+        (n_sets > 0 && !sets))
+        return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !splats || !act || !n_active_dev || !grad2d || !G) return GS_ERR_INVALID_ARG;
-    bool any_stat = acc_xyz || acc_rgb || cnt, all_stat = acc_xyz && acc_rgb && cnt;
-    if (any_stat && !all_stat) return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(splats) | reinterpret_cast<uintptr_t>(grad2d) |
          reinterpret_cast<uintptr_t>(G)) & 15)
         return GS_ERR_INVALID_ARG;
-    k_project_bwd<ACC><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, make_cam(cam), splats, act,
-                                                                         n_active_dev, grad2d, G, acc_xyz, acc_rgb,
-                                                                         cnt);
+    StatSets st{};
+    st.n = n_sets;
+    for (int k = 0; k < n_sets; ++k) {
+        if (!sets[k].acc_xyz || !sets[k].acc_rgb || !sets[k].cnt) return GS_ERR_INVALID_ARG;
+        st.ax[k] = sets[k].acc_xyz;
+        st.ar[k] = sets[k].acc_rgb;
+        st.cnt[k] = sets[k].cnt;
+        st.maxr[k] = sets[k].max_radius;
+    }
+    const DevCam dc = make_cam(cam);
+    if (acc)
+        k_project_bwd<true><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, dc, splats, act,
+                                                                             n_active_dev, grad2d, G, st);
+    else
+        k_project_bwd<false><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, dc, splats, act,
+                                                                              n_active_dev, grad2d, G, st);
     note_launches(1);
     return launch_status();
+}
+
+static int project_bwd_one(bool acc, const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
+                           const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d,
+                           float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt, gs_stream_t stream) {
+    const bool any_stat = acc_xyz || acc_rgb || cnt, all_stat = acc_xyz && acc_rgb && cnt;
+    if (any_stat && !all_stat) return GS_ERR_INVALID_ARG;
+    const gs_grad_stats one{acc_xyz, acc_rgb, cnt, nullptr};
+    return project_bwd(acc, P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, all_stat ? &one : nullptr,
+                       all_stat ? 1 : 0, stream);
 }
 
 extern "C" int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
                               const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d,
                               float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt, gs_stream_t stream) {
-    return project_bwd<false>(P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt,
-                              stream);
+    return project_bwd_one(false, P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt,
+                           stream);
 }
 
 extern "C" int gs_project_bwd_accum(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
                                     const float *splats, const int32_t *act, const int32_t *n_active_dev,
                                     float *grad2d, float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt,
                                     gs_stream_t stream) {
-    return project_bwd<true>(P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt,
-                             stream);
+    return project_bwd_one(true, P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt,
+                           stream);
+}
+
+extern "C" int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
+                                    const float *splats, const int32_t *act, const int32_t *n_active_dev,
+                                    float *grad2d, float *G, int32_t accumulate, const gs_grad_stats *sets,
+                                    int32_t n_sets, gs_stream_t stream) {
+    return project_bwd(accumulate != 0, P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, sets, n_sets,
+                       stream);
 }

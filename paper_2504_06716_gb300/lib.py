@@ -101,6 +101,11 @@ _SIGS = {
     "gs_adam_masked_devstep": ([_P, _P, _P, _P, _I64, _P, _P, _P, _F32, _F32, _F32, _P,
                                 _P, _P], _I32),
     "gs_raster_pair_counts": ([_P, _P, _P, _CAM, _P, _P, _P, _P], _I32),
+    "gs_project_bwd_stats": ([_P, _I64, _I32, _CAM, _P, _P, _P, _P, _P, _I32, _P, _I32, _P], _I32),
+    "gs_densify_workspace_bytes": ([_I64], _SZ),
+    "gs_densify_plan": ([_I64, _P, _P, _P, _P, _SZ, _P, _P], _I32),
+    "gs_densify_apply": ([_I64, _P, _P, _P, _P, _P, _I32, _P, _P, _P, _SZ, _I64, _P, _P, _P, _P, _P], _I32),
+    "gs_opacity_reset": ([_I64, _P, _P, _P, _F32, _P], _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
     "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
     "gs_get_device_error": ([ctypes.POINTER(ctypes.c_uint32), _P], _I32),
@@ -253,6 +258,87 @@ def gs_project_bwd_accum(P, n: int, sh_degree: int, cam: GsCamera, splats, act, 
         _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(grad2d, torch.float32, "grad2d"),
         _ptr(G, torch.float32, "G"), _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
         _ptr(cnt, torch.int32, "cnt"), _stream(stream)))
+
+
+class GsGradStats(ctypes.Structure):
+    _fields_ = [("acc_xyz", ctypes.c_void_p), ("acc_rgb", ctypes.c_void_p), ("cnt", ctypes.c_void_p),
+                ("max_radius", ctypes.c_void_p)]
+
+
+def grad_stats(acc_xyz, acc_rgb, cnt, max_radius=None) -> GsGradStats:
+    """The struct holds raw device pointers: the caller keeps the tensors alive."""
+    import torch
+
+    return GsGradStats(_ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+                       _ptr(cnt, torch.int32, "cnt"), _ptr(max_radius, torch.int32, "max_radius"))
+
+
+def gs_project_bwd_stats(P, n: int, sh_degree: int, cam: GsCamera, splats, act, n_active, grad2d, G, accumulate: bool,
+                         sets, stream=None):
+    """sets: list of up to two GsGradStats."""
+    import torch
+
+    arr = (GsGradStats * max(len(sets), 1))(*sets)
+    _check("gs_project_bwd_stats", load().gs_project_bwd_stats(
+        _ptr(P, torch.float32, "P"), n, sh_degree, ctypes.byref(cam), _ptr(splats, torch.float32, "splats"),
+        _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(grad2d, torch.float32, "grad2d"),
+        _ptr(G, torch.float32, "G"), int(bool(accumulate)), ctypes.cast(arr, ctypes.c_void_p), len(sets),
+        _stream(stream)))
+
+
+class GsDensifyParams(ctypes.Structure):
+    _fields_ = [("eps_xyz", ctypes.c_float), ("eps_rgb", ctypes.c_float), ("use_rgb", ctypes.c_int32),
+                ("log_clone_max", ctypes.c_float), ("logit_min_opacity", ctypes.c_float),
+                ("prune_big", ctypes.c_int32), ("max_screen_radius", ctypes.c_int32),
+                ("log_max_world", ctypes.c_float), ("log_split_div", ctypes.c_float)]
+
+
+def gs_densify_workspace_bytes(n: int) -> int:
+    return int(load().gs_densify_workspace_bytes(n))
+
+
+def gs_densify_plan(n: int, P, stats: GsGradStats, prm: GsDensifyParams, ws, counts, stream=None):
+    """counts: int64 device tensor [4]."""
+    import torch
+
+    _check("gs_densify_plan", load().gs_densify_plan(
+        n, _ptr(P, torch.float32, "P"), ctypes.byref(stats), ctypes.byref(prm), _ptr(ws, torch.uint8, "ws"),
+        ws.numel(), _ptr(counts, torch.int64, "counts"), _stream(stream)))
+
+
+class GsDensifyCarry(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_void_p), ("dst", ctypes.c_void_p), ("row_bytes", ctypes.c_int32)]
+
+
+def densify_carry(src, dst) -> GsDensifyCarry:
+    """A per-Gaussian array (any dtype, rows of the same width) moved by gs_densify_apply. The struct
+    holds raw device pointers: the caller keeps both tensors alive."""
+    if not (src.is_cuda and dst.is_cuda and src.is_contiguous() and dst.is_contiguous() and src.dtype == dst.dtype):
+        raise ValueError("carried arrays must be contiguous CUDA tensors of one dtype")
+    row = src[0].numel() * src.element_size() if src.dim() > 1 else src.element_size()
+    return GsDensifyCarry(src.data_ptr(), dst.data_ptr(), row)
+
+
+def gs_densify_apply(n: int, P, m, v, frozen, carries, prm: GsDensifyParams, z, ws, capacity: int, P_out, m_out, v_out,
+                     frozen_out, stream=None):
+    """carries: list of GsDensifyCarry (at most 8)."""
+    import torch
+
+    arr = (GsDensifyCarry * max(len(carries), 1))(*carries)
+    _check("gs_densify_apply", load().gs_densify_apply(
+        n, _ptr(P, torch.float32, "P"), _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"),
+        _ptr(frozen, torch.uint8, "frozen"), ctypes.cast(arr, ctypes.c_void_p), len(carries), ctypes.byref(prm),
+        _ptr(z, torch.float32, "z"), _ptr(ws, torch.uint8, "ws"), ws.numel(), capacity,
+        _ptr(P_out, torch.float32, "P_out"), _ptr(m_out, torch.float32, "m_out"), _ptr(v_out, torch.float32, "v_out"),
+        _ptr(frozen_out, torch.uint8, "frozen_out"), _stream(stream)))
+
+
+def gs_opacity_reset(n: int, P, m, v, logit_cap: float, stream=None):
+    import torch
+
+    _check("gs_opacity_reset", load().gs_opacity_reset(
+        n, _ptr(P, torch.float32, "P"), _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"), logit_cap,
+        _stream(stream)))
 
 
 class GsRasterJob(ctypes.Structure):
