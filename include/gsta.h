@@ -162,7 +162,8 @@ size_t gs_loss_workspace_bytes(int32_t H, int32_t W);
  * with an 11x11 Gaussian window (sigma 1.5), zero padding, C1 = 0.01^2,
  * C2 = 0.03^2; the windows run as separable 1-D passes (the fused SSIM of
  * Sec. 3.3). Out: loss_dev [1] float, dl_dimage [3][H][W] (d|x-y|/dx at
- * x = y taken as 0). A non-finite loss raises GS_FLAG_NONFINITE.
+ * x = y taken as 0). A non-finite loss or gradient value raises
+ * GS_FLAG_NONFINITE.
  * Errors: INVALID_ARG, CUDA. */
 int gs_loss(const float *image, const float *gt, int32_t H, int32_t W, float lambda, void *ws, size_t ws_bytes,
             float *loss_dev, float *dl_dimage, gs_stream_t stream);
@@ -265,9 +266,11 @@ size_t gs_freeze_workspace_bytes(int64_t n);
  *                                     && acc_rgb[i]/cnt[i] < eps_rgb
  *             (float32 division and strict comparisons; the map only grows);
  *   1 reset : frozen[i] = 0 for all i;
- *   2 clear : the map is kept.
- * Every mode zeroes acc_xyz, acc_rgb, cnt and writes the unfrozen indices in
- * ascending order to act [n] and their number to n_active_dev [1].
+ *   2 clear : the map is kept;
+ *   3 list  : the map and the statistics are kept (for a set the
+ *             densification rearranged; gs_freeze_update_noalloc takes 0-2).
+ * Modes 0-2 zero acc_xyz, acc_rgb, cnt; every mode writes the unfrozen
+ * indices in ascending order to act [n] and their number to n_active_dev [1].
  * Errors: INVALID_ARG (mode, sizes, workspace), CUDA. */
 int gs_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen, float eps_xyz,
                      float eps_rgb, int32_t mode, int32_t *act, int32_t *n_active_dev, void *ws, size_t ws_bytes,

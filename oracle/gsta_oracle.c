@@ -780,9 +780,11 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
                 /* partial derivatives of the map value with respect to the
                    window mean of x, of x^2 and of x*y */
                 int64_t p = (int64_t)i * W + j;
-                A[p] = m * (2 * my / n1 - 2 * my / n2 - 2 * mx / d1 + 2 * mx / d2);
+                /* m / n1 = n2 / (d1 d2) and m / n2 = n1 / (d1 d2): no division
+                   by n1 or n2, which can be zero (d1 >= C1, d2 >= C2) */
+                A[p] = 2 * my * (n2 - n1) / (d1 * d2) - 2 * mx * m / d1 + 2 * mx * m / d2;
                 B[p] = -m / d2;
-                Cm[p] = 2 * m / n2;
+                Cm[p] = 2 * n1 / (d1 * d2);
             }
         if (dl_dimage) {
             for (int32_t i = 0; i < H; ++i)
@@ -1078,10 +1080,12 @@ void or_adam(int64_t n, double *P, const double *G, double *M, double *V, const 
 /*                               && acc_rgb/cnt < eps_rgb   (Eqs. 4, 6)    */
 /*             (a frozen Gaussian stays frozen: the map accumulates);      */
 /*   1 reset : every Gaussian unfrozen;                                    */
-/*   2 clear : the map is kept.                                            */
-/* Every mode then zeroes the statistics and lists the unfrozen Gaussians  */
-/* in ascending order in act. The average and the comparison are taken in  */
-/* single precision. Returns the number of unfrozen Gaussians.             */
+/*   2 clear : the map is kept;                                            */
+/*   3 list  : the map and the statistics are kept (after densification    */
+/*             moved the Gaussians).                                       */
+/* Modes 0-2 then zero the statistics; every mode lists the unfrozen       */
+/* Gaussians in ascending order in act. The average and the comparison are */
+/* taken in single precision. Returns the number of unfrozen Gaussians.    */
 /* ------------------------------------------------------------------ */
 int64_t or_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen, float eps_xyz,
                          float eps_rgb, int32_t mode, int32_t *act) {
@@ -1093,7 +1097,7 @@ int64_t or_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt
             volatile float ax = acc_xyz[i] / c, ar = acc_rgb[i] / c;
             if (ax < eps_xyz && ar < eps_rgb) frozen[i] = 1;
         }
-        acc_xyz[i] = 0; acc_rgb[i] = 0; cnt[i] = 0;
+        if (mode != 3) { acc_xyz[i] = 0; acc_rgb[i] = 0; cnt[i] = 0; }
         if (!frozen[i]) act[k++] = (int32_t)i;
     }
     return k;

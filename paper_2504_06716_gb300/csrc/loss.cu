@@ -81,14 +81,19 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
         float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
         float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
         float d1 = mx * mx + my * my + C1, d2 = vx + vy + C2;
-        float m = (n1 * n2) / (d1 * d2);
+        // d1 >= C1 and d2 >= C2 (up to rounding of the variances): the map and
+        // its partials are formed without dividing by n1 or n2, which may be
+        // zero (m / n2 = n1 / (d1 d2), m / n1 = n2 / (d1 d2))
+        const float q = 1.f / (d1 * d2);
+        const float m_n1 = n2 * q, m_n2 = n1 * q;
+        const float m = n1 * m_n1;
         ss += m;
         l1 += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
         // partials of the map value w.r.t. the window means of x, x^2 and x*y
         int64_t p = ch * HW + (int64_t)gy * W + gx;
-        mapA[p] = m * (2.f * my / n1 - 2.f * my / n2 - 2.f * mx / d1 + 2.f * mx / d2);
+        mapA[p] = 2.f * my * (m_n1 - m_n2) + 2.f * mx * m * (1.f / d2 - 1.f / d1);
         mapB[p] = -m / d2;
-        mapC[p] = 2.f * m / n2;
+        mapC[p] = 2.f * m_n2;
     }
     // block sums
 #pragma unroll
@@ -155,7 +160,9 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
         float d = xv - yv;
         float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
         float dssim = s0 + 2.f * xv * s1 + yv * s2;
-        dl[p] = ((1.f - lambda) * sg - lambda * dssim) * invN;
+        const float g = ((1.f - lambda) * sg - lambda * dssim) * invN;
+        if (!isfinite(g)) atomicOr(&g_loss_flags, GS_FLAG_NONFINITE);
+        dl[p] = g;
     }
 }
 

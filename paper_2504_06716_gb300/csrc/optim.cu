@@ -33,9 +33,11 @@ __global__ void __launch_bounds__(kFB) k_freeze_mark(int64_t n, float *__restric
     if (i < n) {
         bool f = decide(mode, frozen[i], acc_xyz[i], acc_rgb[i], cnt[i], ex, er);
         frozen[i] = f ? 1 : 0;
-        acc_xyz[i] = 0.f;
-        acc_rgb[i] = 0.f;
-        cnt[i] = 0;
+        if (mode != 3) {  // 3: list only, the statistics are kept
+            acc_xyz[i] = 0.f;
+            acc_rgb[i] = 0.f;
+            cnt[i] = 0;
+        }
         active = !f;
     }
     int c = __syncthreads_count(active);
@@ -170,7 +172,7 @@ extern "C" size_t gs_freeze_workspace_bytes(int64_t n) {
 extern "C" int gs_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen,
                                 float eps_xyz, float eps_rgb, int32_t mode, int32_t *act, int32_t *n_active_dev,
                                 void *ws, size_t ws_bytes, gs_stream_t stream) {
-    if (n < 0 || n > INT32_MAX || mode < 0 || mode > 2 || !n_active_dev) return GS_ERR_INVALID_ARG;
+    if (n < 0 || n > INT32_MAX || mode < 0 || mode > 3 || !n_active_dev) return GS_ERR_INVALID_ARG;
     if (n > 0 && (!acc_xyz || !acc_rgb || !cnt || !frozen || !act)) return GS_ERR_INVALID_ARG;
     if (!ws || ws_bytes < gs_freeze_workspace_bytes(n)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);

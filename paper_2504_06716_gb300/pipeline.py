@@ -49,32 +49,107 @@ class View:
 
 
 class Model:
-    """Gaussian parameters, Adam moments, freeze state and per-step scratch on one GPU."""
+    """Gaussian parameters, Adam moments, freeze state and per-step scratch on one GPU.
 
-    def __init__(self, params59: np.ndarray, sh_degree: int = 3, device="cuda", trainable: bool = True):
+    Per-Gaussian buffers hold ``cap`` rows of which the first ``n`` are live;
+    densification (``densify``) writes the new set into a spare copy of the
+    parameters, moments and carried state, swaps, and grows every buffer
+    (``generation`` counts the reallocations) when the set outgrows ``cap``."""
+
+    def __init__(self, params59: np.ndarray, sh_degree: int = 3, device="cuda", trainable: bool = True,
+                 capacity: int | None = None):
         self.device = torch.device(device)
         self.n = int(params59.shape[0])
         self.sh_degree = sh_degree
-        n = self.n
-        f32 = dict(dtype=torch.float32, device=self.device)
-        self.P = pack_params(params59, self.device)
-        self.splats = torch.zeros((n, lib.SPLAT), **f32)
+        self.trainable = trainable
         self.step_count = 0
         self.fwd_cfg = None  # rasteriser launch shapes (None: library defaults); see autotune.py
         self.bwd_cfg = None
-        if not trainable:  # render-only (targets): no gradients, moments or freeze state
+        self.generation = 0
+        self.den = None  # densification window statistics (enable_densify)
+        self.carried: dict[str, torch.Tensor] = {}  # further per-Gaussian state moved by densify
+        self._allocate(max(self.n, capacity or 0, 1))
+        self.P[: self.n, :59] = torch.from_numpy(np.ascontiguousarray(params59, dtype=np.float32)).to(self.device)
+        if trainable:
+            self.act[: self.n] = torch.arange(self.n, dtype=torch.int32, device=self.device)
+            self.n_active.fill_(self.n)
+
+    def _allocate(self, cap: int):
+        """Every per-Gaussian buffer at ``cap`` rows (zero)."""
+        self.cap = cap
+        f32 = dict(dtype=torch.float32, device=self.device)
+        self.P = torch.zeros((cap, lib.ROW), **f32)
+        self.splats = torch.zeros((cap, lib.SPLAT), **f32)
+        if not self.trainable:  # render-only (targets): no gradients, moments or freeze state
             return
-        self.G = torch.zeros((n, lib.ROW), **f32)
-        self.m = torch.zeros((n, lib.ROW), **f32)
-        self.v = torch.zeros((n, lib.ROW), **f32)
-        self.grad2d = torch.zeros((n, lib.GRAD2D), **f32)
-        self.frozen = torch.zeros(n, dtype=torch.uint8, device=self.device)
-        self.act = torch.arange(n, dtype=torch.int32, device=self.device)
-        self.n_active = torch.tensor([n], dtype=torch.int32, device=self.device)
-        self.acc_xyz = torch.zeros(n, **f32)
-        self.acc_rgb = torch.zeros(n, **f32)
-        self.cnt = torch.zeros(n, dtype=torch.int32, device=self.device)
-        self.freeze_ws = torch.zeros(max(lib.gs_freeze_workspace_bytes(n), 256), dtype=torch.uint8, device=self.device)
+        self.G = torch.zeros((cap, lib.ROW), **f32)
+        self.m = torch.zeros((cap, lib.ROW), **f32)
+        self.v = torch.zeros((cap, lib.ROW), **f32)
+        self.grad2d = torch.zeros((cap, lib.GRAD2D), **f32)
+        self.frozen = torch.zeros(cap, dtype=torch.uint8, device=self.device)
+        self.act = torch.zeros(cap, dtype=torch.int32, device=self.device)
+        self.n_active = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.acc_xyz = torch.zeros(cap, **f32)
+        self.acc_rgb = torch.zeros(cap, **f32)
+        self.cnt = torch.zeros(cap, dtype=torch.int32, device=self.device)
+        self.freeze_ws = torch.zeros(max(lib.gs_freeze_workspace_bytes(cap), 256), dtype=torch.uint8,
+                                     device=self.device)
+        if self.den is not None:
+            self.enable_densify()
+
+    # ---- densification (Sec. 4.1) ----
+    def enable_densify(self):
+        cap, f32 = self.cap, dict(dtype=torch.float32, device=self.device)
+        self.den = dict(acc_xyz=torch.zeros(cap, **f32), acc_rgb=torch.zeros(cap, **f32),
+                        cnt=torch.zeros(cap, dtype=torch.int32, device=self.device),
+                        max_radius=torch.zeros(cap, dtype=torch.int32, device=self.device),
+                        ws=torch.zeros(lib.gs_densify_workspace_bytes(cap), dtype=torch.uint8, device=self.device),
+                        counts=torch.zeros(4, dtype=torch.int64, device=self.device))
+
+    def carry(self, name: str, tensor: torch.Tensor):
+        """Register a per-Gaussian tensor ([cap] or [cap][w]) that densification moves along."""
+        self.carried[name] = tensor
+
+    def _den_stats(self):
+        d = self.den
+        return lib.grad_stats(d["acc_xyz"], d["acc_rgb"], d["cnt"], d["max_radius"])
+
+    def densify(self, prm: "lib.GsDensifyParams", rng: np.random.Generator) -> dict:
+        """One densification and pruning step (gs_densify_plan / gs_densify_apply);
+        returns the counts. Restarts the densification window; keeps the freeze
+        window's statistics and the carried state of the surviving Gaussians."""
+        d, n = self.den, self.n
+        lib.gs_densify_plan(n, self.P, self._den_stats(), prm, d["ws"], d["counts"])
+        kept, clones, children, splits = (int(x) for x in d["counts"].cpu().tolist())
+        n_out = kept + clones + children
+        z = torch.from_numpy(rng.standard_normal((max(splits, 1), 2, 3)).astype(np.float32)).to(self.device)
+        cap = self.cap if n_out <= self.cap else int(n_out * 1.5) + 1024
+        f32 = dict(dtype=torch.float32, device=self.device)
+        P2, m2, v2 = (torch.zeros((cap, lib.ROW), **f32) for _ in range(3))
+        fr2 = torch.zeros(cap, dtype=torch.uint8, device=self.device)
+        named = dict(acc_xyz=self.acc_xyz, acc_rgb=self.acc_rgb, cnt=self.cnt, **self.carried)
+        out = {k: torch.zeros((cap,) + tuple(t.shape[1:]), dtype=t.dtype, device=self.device) for k, t in named.items()}
+        carries = [lib.densify_carry(named[k], out[k]) for k in named]
+        lib.gs_densify_apply(n, self.P, self.m, self.v, self.frozen, carries, prm, z, d["ws"], cap, P2, m2, v2, fr2)
+        if cap != self.cap:  # grown: every other buffer anew
+            self.den = dict(self.den)  # keep enable flag
+            self._allocate(cap)
+            self.generation += 1
+        else:
+            for key in ("acc_xyz", "acc_rgb", "cnt", "max_radius"):
+                self.den[key].zero_()
+        self.P, self.m, self.v, self.frozen = P2, m2, v2, fr2
+        self.acc_xyz, self.acc_rgb, self.cnt = out["acc_xyz"], out["acc_rgb"], out["cnt"]
+        for k in self.carried:
+            self.carried[k] = out[k]
+        self.n = n_out
+        # the unfrozen list of the new set; map and freeze statistics kept
+        lib.gs_freeze_update(self.n, self.acc_xyz, self.acc_rgb, self.cnt, self.frozen, 0.0, 0.0, 3, self.act,
+                             self.n_active, self.freeze_ws)
+        return dict(kept=kept, clones=clones, children=children, splits=splits, n=n_out)
+
+    def opacity_reset(self, logit_cap: float):
+        lib.gs_opacity_reset(self.n, self.P, self.m, self.v, logit_cap)
 
     # ---- views ----
     def make_view(self, cam: lib.GsCamera, capacity: int, trainable: bool = True) -> View:
@@ -92,7 +167,7 @@ class Model:
             vals=torch.zeros(max(capacity, 1), dtype=torch.int32, device=dev),
             ranges=torch.zeros((cam.tiles, 2), dtype=torch.int32, device=dev),
             count=torch.zeros(1, dtype=torch.int64, device=dev),
-            sort_ws=torch.zeros(lib.gs_sort_workspace_bytes(self.n, capacity, cam), dtype=torch.uint8, device=dev),
+            sort_ws=torch.zeros(lib.gs_sort_workspace_bytes(self.cap, capacity, cam), dtype=torch.uint8, device=dev),
             capacity=capacity,
         )
 
@@ -114,9 +189,15 @@ class Model:
         lib.gs_loss(view.image, gt, view.cam.height, view.cam.width, lam, view.loss_ws, view.loss, view.dl, stream)
 
     def backward(self, view: View, stats: bool = True, stream=None):
-        """gs_render_bwd, as its two halves so that the tuned launch shape applies."""
+        """gs_render_bwd, as its two halves so that the tuned launch shape applies;
+        the projection backward also feeds the densification window when enabled."""
         lib.gs_raster_bwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.bwd_cfg, view.t_final, view.n_last,
                               view.dl, self.frozen, self.grad2d, stream)
+        if self.den is not None and stats:
+            sets = [lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt), self._den_stats()]
+            lib.gs_project_bwd_stats(self.P, self.n, self.sh_degree, view.cam, self.splats, self.act, self.n_active,
+                                     self.grad2d, self.G, False, sets, stream)
+            return
         lib.gs_project_bwd(self.P, self.n, self.sh_degree, view.cam, self.splats, self.act, self.n_active, self.grad2d,
                            self.G, self.acc_xyz if stats else None, self.acc_rgb if stats else None,
                            self.cnt if stats else None, stream)

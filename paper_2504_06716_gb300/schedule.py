@@ -46,12 +46,30 @@ class GStaConfig:
     # plain 3DGS decays the xyz rate exponentially to 1/100 over the run
     # (Sec. 3.2.3 describes the vanilla decay that GSta's plateau schedule replaces)
     plain_lr_final_ratio: float = 0.01
+    # densification (Sec. 4.1; clone / split / prune are 3DGS's): every den_every
+    # iterations in (den_from, min(window_end, early stop)) -- den_until_plain
+    # for plain 3DGS -- with thresholds eps0_den scaled like Eq. 5; the
+    # diffuse-colour criterion on every rgb_every-th step (the paper's 20%);
+    # opacity reset every opacity_every iterations up to the same end.
+    densify: bool = True
+    den_from: int = 500
+    den_every: int = 100
+    den_until_plain: int = 15000
+    rgb_every: int = 5
+    opacity_every: int = 3000
+    eps0_den_xyz: float = 2e-4
+    eps0_den_rgb: float = 1e-6
+    percent_dense: float = 0.01     # of the scene extent: largest scale that clones
+    min_opacity: float = 0.005
+    max_screen_radius: int = 20
+    max_world_frac: float = 0.1     # of the scene extent
+    split_div: float = 1.6
 
     @staticmethod
     def tiny() -> "GStaConfig":
-        """The schedule scaled to a 200-iteration run."""
+        """The schedule scaled to a 200-iteration run (no densification)."""
         return GStaConfig(total_iter=200, warmup=20, window_end=150, every=10, reset_every=80, wait=20, psnr_every=20,
-                          finetune_iters=20)
+                          finetune_iters=20, densify=False)
 
 
 class GStaController:
@@ -117,6 +135,29 @@ class GStaController:
             self.finetune_left = c.finetune_iters
             return True
         return False
+
+    # ---- densification cadence ----
+    def _den_end(self) -> int:
+        c = self.cfg
+        if not c.freezing:
+            return c.den_until_plain
+        return c.window_end if self.stop_iter is None else min(c.window_end, self.stop_iter)
+
+    def densify_due(self, k: int) -> bool:
+        """Densify and prune after iteration k: a multiple of den_every in (den_from, end)."""
+        c = self.cfg
+        return c.densify and self.finetune_left is None and k % c.den_every == 0 and c.den_from < k < self._den_end()
+
+    def densify_uses_rgb(self, k: int) -> bool:
+        return (k // self.cfg.den_every) % self.cfg.rgb_every == 0
+
+    def opacity_reset_due(self, k: int) -> bool:
+        c = self.cfg
+        return (c.densify and self.finetune_left is None and k > 0 and k % c.opacity_every == 0
+                and k <= self._den_end())
+
+    def size_pruning(self, k: int) -> bool:
+        return k > self.cfg.opacity_every
 
     def finished(self, k: int) -> bool:
         """Training ends after the finetuning stage (entered on early stop or at total_iter)."""

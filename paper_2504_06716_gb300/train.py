@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import time
 
 import numpy as np
@@ -50,9 +51,9 @@ class Trainer:
         if lib.gs_get_device_error():
             raise RuntimeError("device error while rendering targets")
         del gtm, gv
-        self.model = pipeline.Model(scene.init, device=self.device)
-        cap = self.model.measure_capacity([self.cams[v] for v in gt_views])
-        self.view = self.model.make_view(self.cams[scene.train_views[0]], cap)
+        self.extent = extent
+        self.seed = seed
+        self.fresh_model()
         H, W = self.cams[0].height, self.cams[0].width
         self.psnr_ws = torch.zeros(lib.gs_psnr_workspace_bytes(1, H, W), dtype=torch.uint8, device=self.device)
         self.psnr_out = torch.zeros(1, device=self.device)
@@ -76,7 +77,24 @@ class Trainer:
         self.shadow_false = {"rule": 0, "pred": 0}
         self._shadow_sets = {}
 
+    def fresh_model(self, tuning=None):
+        """The trainable model at its initialisation (and its view buffers)."""
+        scene, cfg = self.scene, self.cfg
+        self.model = pipeline.Model(scene.init, device=self.device,
+                                    capacity=int(scene.init.shape[0] * (1.5 if cfg.densify else 1.0)))
+        if cfg.densify:
+            self.model.enable_densify()
+        if tuning is not None:
+            self.model.apply_tuning(tuning)
+        self.den_rng = np.random.default_rng(self.seed + 1000)  # the split draws
+        vis = sorted(set(scene.train_views) | set(scene.test_views))
+        cap = self.model.measure_capacity([self.cams[v] for v in vis])
+        self.view = self.model.make_view(self.cams[scene.train_views[0]], cap)
+        self.generation = self.model.generation
+
     def enable_predictor_state(self):
+        if self.cfg.densify:
+            raise NotImplementedError("the learned predictor is evaluated without densification")
         n, dev = self.model.n, self.device
         self.pred_state = torch.zeros((n, 12), dtype=torch.float32, device=dev)
         self.pred_X = torch.zeros((n, 16), dtype=torch.bfloat16, device=dev)
@@ -259,11 +277,35 @@ class Trainer:
         m.train_step(self.view, self.targets[v], lrs)
         if self.shadow and self._shadow_sets:
             self._shadow_backward()
+        if c.densify_due(k):
+            self._densify(k)
+        if c.opacity_reset_due(k):
+            m.opacity_reset(float(np.float32(math.log(0.01 / 0.99))))
+            self.events.append((k, "opacity_reset", 0.0))
         if c.after_step(k):
             m.freeze_update(0.0, 0.0, FREEZE_RESET)
         self.k += 1
         if self.k % self.capacity_check_every == 0:
             self.check_capacity()
+
+    # ---- densification (Sec. 4.1) ----
+    def densify_params(self, k: int) -> lib.GsDensifyParams:
+        cfg, c = self.cfg, self.ctrl
+        s = min(1.5, max(0.5, 0.5 + 1.5 * k / cfg.total_iter))  # dynamic thresholds, as Eq. 5
+        f = lambda x: float(np.float32(x))  # noqa: E731
+        return lib.GsDensifyParams(f(cfg.eps0_den_xyz * s), f(cfg.eps0_den_rgb * s), int(c.densify_uses_rgb(k)),
+                                   f(math.log(cfg.percent_dense * self.extent)),
+                                   f(math.log(cfg.min_opacity / (1 - cfg.min_opacity))), int(c.size_pruning(k)),
+                                   cfg.max_screen_radius, f(math.log(cfg.max_world_frac * self.extent)),
+                                   f(math.log(cfg.split_div)))
+
+    def _densify(self, k: int):
+        m = self.model
+        res = m.densify(self.densify_params(k), self.den_rng)
+        self.events.append((k, "densify", float(res["n"])))
+        if m.generation != self.generation:  # buffers grew: views anew
+            self.generation = m.generation
+            self.view = m.make_view(self.view.cam, self.view.capacity)
 
     def finished(self) -> bool:
         c = self.ctrl
@@ -275,7 +317,7 @@ class Trainer:
 def run(args) -> dict:
     torch.cuda.set_device(0)
     scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
-    cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters)
+    cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters, densify=not args.no_densify)
     tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
     tuning = None
     if args.autotune:
@@ -284,11 +326,7 @@ def run(args) -> dict:
         tuning = dict(tile=tr.autotune().tile, fwd=tr.tuning.fwd, bwd=tr.tuning.bwd)
         tr2 = Trainer.__new__(Trainer)  # restart training from the initial state with the tuned shapes
         tr2.__dict__.update(tr.__dict__)
-        tr2.model = pipeline.Model(scene.init, device=tr.device)
-        tr2.model.apply_tuning(tr.tuning)
-        vis = sorted(set(scene.train_views) | set(scene.test_views))
-        tr2.view = tr2.model.make_view(tr2.cams[scene.train_views[0]], tr2.model.measure_capacity(
-            [tr2.cams[v] for v in vis]))
+        tr2.fresh_model(tr.tuning)
         tr2.ctrl = GStaController(cfg, tr.lrs[0])
         tr2.k, tr2.calibrated, tr2.eps0, tr2.events, tr2.overflows = 0, False, (cfg.eps0_xyz, cfg.eps0_rgb), [], 0
         tr = tr2
@@ -300,13 +338,14 @@ def run(args) -> dict:
         if tr.k % eval_every == 0:
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            evals.append(dict(k=tr.k, wall_s=el, heldout_psnr=tr.heldout_psnr(),
+            evals.append(dict(k=tr.k, wall_s=el, heldout_psnr=tr.heldout_psnr(), n=tr.model.n,
                               n_active=int(tr.model.n_active.item())))
             t0 = time.perf_counter() - el  # held-out evaluation is not training time
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
     out = dict(arm=args.arm, calibrate=not args.no_calibrate, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(), evals=evals,
-               events=tr.events, eps0=tr.eps0, tuning=tuning, overflows=tr.overflows,
+               events=[e for e in tr.events if e[1] != "densify"], n_final=tr.model.n,
+               densify=[e for e in tr.events if e[1] == "densify"][::10], eps0=tr.eps0, tuning=tuning, overflows=tr.overflows,
                final_capacity=tr.view.capacity, device_flags=lib.gs_get_device_error())
     return out
 
@@ -323,6 +362,7 @@ def main():
     ap.add_argument("--eval-every", type=int, default=1000)
     ap.add_argument("--autotune", action="store_true", help="tune the rasteriser launch shape first")
     ap.add_argument("--no-calibrate", action="store_true", help="use the paper's initial thresholds as they are")
+    ap.add_argument("--no-densify", action="store_true", help="keep the Gaussian set fixed")
     ap.add_argument("--tune-after", type=int, default=300, help="iterations trained before tuning (then restarted)")
     args = ap.parse_args()
     print(json.dumps(run(args)))

@@ -224,6 +224,12 @@ def test_freeze_update_hand_example(orc):
     assert frozen.tolist() == [1, 0, 0, 1, 0, 0, 1] and act.tolist() == [1, 2, 4, 5]
     act = orc.freeze_update(acc_x, acc_r, cnt, frozen, 1.0, 2.0, 1)  # reset
     assert not frozen.any() and act.tolist() == list(range(7))
+    frozen[[0, 6]] = 1
+    acc_x[:] = 0.25
+    cnt[:] = 1
+    act = orc.freeze_update(acc_x, acc_r, cnt, frozen, 1.0, 2.0, 3)  # list only: map and statistics kept
+    assert act.tolist() == [1, 2, 3, 4, 5] and frozen.tolist() == [1, 0, 0, 0, 0, 0, 1]
+    assert acc_x.tolist() == [0.25] * 7 and cnt.tolist() == [1] * 7
 
 
 # ----------------------------------------------------------------------------- PSNR
