@@ -243,11 +243,11 @@ def gpu_arm(args):
                               view.dl, m.frozen, m.grad2d)
         e1.record()
         raster_ev.append((e0, e1, tr.order[tr.k]))
-        lib.gs_project_bwd(m.P, m.n, m.sh_degree, view.cam, m.splats, m.act, m.n_active, m.grad2d, m.G,
-                           m.acc_xyz if stats else None, m.acc_rgb if stats else None, m.cnt if stats else None)
+        m.project_backward(view, stats)
 
     m.backward = backward_split
     active_before = int(m.n_active.item())
+    n_before = m.n
     k_start = tr.k
     if world > 1:
         dist.barrier()
@@ -316,7 +316,8 @@ def gpu_arm(args):
                     data="synthetic",
                     config=dict(workload=WORKLOAD["workload"], gaussians=WORKLOAD["n_init"],
                                 resolution=f"{W_}x{H_}", sh_degree=3, tile=tr.view.cam.tile, raster_tuning=tuning,
-                                views=WORKLOAD["views"],
+                                views=WORKLOAD["views"], densify=tr.cfg.densify,
+                                gaussians_start=n_before, gaussians_end=tr.model.n,
                                 start_iter=k_start, active_gaussians_start=active_before,
                                 active_gaussians_end=active_after, thresholds_eps0=list(tr.eps0),
                                 l2="working set (P, G, m, v = 1 GB) larger than L2; no flush",

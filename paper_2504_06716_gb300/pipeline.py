@@ -189,10 +189,14 @@ class Model:
         lib.gs_loss(view.image, gt, view.cam.height, view.cam.width, lam, view.loss_ws, view.loss, view.dl, stream)
 
     def backward(self, view: View, stats: bool = True, stream=None):
-        """gs_render_bwd, as its two halves so that the tuned launch shape applies;
-        the projection backward also feeds the densification window when enabled."""
+        """gs_render_bwd, as its two halves so that the tuned launch shape applies."""
         lib.gs_raster_bwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.bwd_cfg, view.t_final, view.n_last,
                               view.dl, self.frozen, self.grad2d, stream)
+        self.project_backward(view, stats, stream)
+
+    def project_backward(self, view: View, stats: bool = True, stream=None):
+        """The projection half of the backward; it also feeds the densification
+        window when that is enabled."""
         if self.den is not None and stats:
             sets = [lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt), self._den_stats()]
             lib.gs_project_bwd_stats(self.P, self.n, self.sh_degree, view.cam, self.splats, self.act, self.n_active,

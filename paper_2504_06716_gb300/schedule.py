@@ -61,7 +61,11 @@ class GStaConfig:
     eps0_den_rgb: float = 1e-6
     percent_dense: float = 0.01     # of the scene extent: largest scale that clones
     min_opacity: float = 0.005
-    max_screen_radius: int = 20
+    # 3DGS's screen-size rule (20 px) reads the window's largest screen radii,
+    # which 3DGS clears in its clone / split step before the prune test reads
+    # them, so in 3DGS as run it removes nothing: None keeps it off (an int
+    # turns it on with that many pixels).
+    max_screen_radius: int | None = None
     max_world_frac: float = 0.1     # of the scene extent
     split_div: float = 1.6
 

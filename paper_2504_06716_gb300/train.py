@@ -296,7 +296,8 @@ class Trainer:
         return lib.GsDensifyParams(f(cfg.eps0_den_xyz * s), f(cfg.eps0_den_rgb * s), int(c.densify_uses_rgb(k)),
                                    f(math.log(cfg.percent_dense * self.extent)),
                                    f(math.log(cfg.min_opacity / (1 - cfg.min_opacity))), int(c.size_pruning(k)),
-                                   cfg.max_screen_radius, f(math.log(cfg.max_world_frac * self.extent)),
+                                   2**31 - 1 if cfg.max_screen_radius is None else cfg.max_screen_radius,
+                                   f(math.log(cfg.max_world_frac * self.extent)),
                                    f(math.log(cfg.split_div)))
 
     def _densify(self, k: int):
