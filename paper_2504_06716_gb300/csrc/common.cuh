@@ -86,14 +86,27 @@ __device__ __forceinline__ int tile_rect(float mx, float my, int r, int tile, in
     return (x1 - x0) * (y1 - y0);
 }
 
-// Exponent of the 2-D Gaussian at offset (dx, dy), rounded the same way in
-// every kernel so that the forward and backward passes take identical
-// skip decisions: -0.5 (a dx^2 + c dy^2) - b dx dy.
-__device__ __forceinline__ float splat_power(float dx, float dy, float a, float b, float c) {
-    float t1 = __fmul_rn(__fmul_rn(a, dx), dx);
-    float t2 = __fmul_rn(__fmul_rn(c, dy), dy);
-    float t3 = __fmul_rn(__fmul_rn(b, dx), dy);
-    return __fsub_rn(__fmul_rn(-0.5f, __fadd_rn(t1, t2)), t3);
+// Exponent of the 2-D Gaussian at offset (dx, dy), -0.5 (a dx^2 + c dy^2) -
+// b dx dy, as a quadratic in dy whose coefficients depend on dx only:
+// power = (c2 dy + c1) dy + c0 with c2 = -c/2, c1 = -b dx, c0 = -a dx^2 / 2.
+// A thread's pixels share a column, so per splat it forms the row once and
+// pays two fused multiply-adds per pixel. Every kernel rounds it the same
+// way (explicit intrinsics), so forward and backward take identical skip
+// decisions.
+struct SplatRow {
+    float c0, c1, c2;
+};
+
+__device__ __forceinline__ SplatRow splat_row(float dx, float a, float b, float c) {
+    SplatRow r;
+    r.c0 = __fmul_rn(__fmul_rn(-0.5f, a), __fmul_rn(dx, dx));
+    r.c1 = __fmul_rn(-b, dx);
+    r.c2 = __fmul_rn(-0.5f, c);
+    return r;
+}
+
+__device__ __forceinline__ float splat_power(const SplatRow &r, float dy) {
+    return __fmaf_rn(__fmaf_rn(r.c2, dy, r.c1), dy, r.c0);
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -68,12 +68,12 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
         for (int j = 0; j < cnt; ++j) {
             const float4 xa = s_xyab[j], co = s_cocg[j];
             const float blue = s_blue[j];
-            const float dx = __fsub_rn(xa.x, fpx);
+            const SplatRow row = splat_row(__fsub_rn(xa.x, fpx), xa.z, xa.w, co.x);
             bool alive = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
                 const float dy = __fsub_rn(xa.y, fpy[k]);
-                const float power = splat_power(dx, dy, xa.z, xa.w, co.x);
+                const float power = splat_power(row, dy);
                 const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
                 const float tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                 const bool use = !done[k] && power <= 0.f && alpha >= kAlphaMin;
@@ -158,9 +158,14 @@ struct PixBwd {
     int nl;
 };
 
-__device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, float dx, float dy, const float4 &xa, const float4 &co,
+// One (pixel, splat) step of the backward blend. The exponent's derivatives
+// with respect to the 2-D mean and conic are dx/dy polynomials; the thread's
+// pixels share dx, so only the dy moments of dL/dpower are summed here
+// (g[0] += dpow, g[1] += dy dpow, g[2] += dy^2 dpow) and geo_grads() turns
+// them into the five gradients once per splat.
+__device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row, float dy, const float4 &co,
                                         float blue, bool frz, float (&g)[9]) {
-    const float power = splat_power(dx, dy, xa.z, xa.w, co.x);
+    const float power = splat_power(row, dy);
     const float G = __expf(power);
     const float oG = __fmul_rn(co.y, G);
     const float alpha = fminf(kAlphaMax, oG);
@@ -179,12 +184,11 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, float dx, float dy, 
         g[8] += wT * p.dC2;
         if (!(oG > kAlphaMax)) {
             const float dpow = dA * oG;
+            const float ydp = dy * dpow;
             g[5] += dA * G;
-            g[2] += -0.5f * dx * dx * dpow;
-            g[3] += -dx * dy * dpow;
-            g[4] += -0.5f * dy * dy * dpow;
-            g[0] += -(xa.z * dx + xa.w * dy) * dpow;
-            g[1] += -(xa.w * dx + co.x * dy) * dpow;
+            g[0] += dpow;
+            g[1] += ydp;
+            g[2] += dy * ydp;
         }
     }
     p.la = alpha;
@@ -192,6 +196,18 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, float dx, float dy, 
     p.lc1 = co.w;
     p.lc2 = blue;
     return true;
+}
+
+// dy moments (s0, s1, s2) of dL/dpower -> gradients of the 2-D mean and
+// conic for power = -0.5 (a dx^2 + c dy^2) - b dx dy, dx = mean_x - px.
+__device__ __forceinline__ void geo_grads(float (&g)[9], float dx, float a, float b, float c) {
+    const float s0 = g[0], s1 = g[1], s2 = g[2];
+    const float xs0 = dx * s0;
+    g[0] = -(a * xs0 + b * s1);
+    g[1] = -(b * xs0 + c * s1);
+    g[2] = -0.5f * dx * xs0;
+    g[3] = -dx * s1;
+    g[4] = -0.5f * s2;
 }
 
 __device__ __forceinline__ void pix_load(PixBwd &p, bool inside, int64_t pix, int64_t HW, const float *t_final,
@@ -271,11 +287,13 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
             const float blue = s_blue[j];
             const bool frz = s_frz[j] != 0;
             const float dx = __fsub_rn(xa.x, fpx);
+            const SplatRow row = splat_row(dx, xa.z, xa.w, co.x);
             float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool c = false;
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) c |= pix_bwd(p[k], pos, dx, __fsub_rn(xa.y, fpy[k]), xa, co, blue, frz, g);
+            for (int k = 0; k < PPT; ++k) c |= pix_bwd(p[k], pos, row, __fsub_rn(xa.y, fpy[k]), co, blue, frz, g);
             if (!frz && __any_sync(kFull, c)) {
+                geo_grads(g, dx, xa.z, xa.w, co.x);
                 const float tot = warp_sum9(g, lane);
                 if (writer) atomicAdd(&s_acc[slot][j], tot);
             }
@@ -328,7 +346,7 @@ __global__ void k_pair_counts(const float *__restrict__ splats, const uint32_t *
             const uint32_t g = vals[start + j];
             const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
             const float4 xa = __ldg(r), co = __ldg(r + 1);
-            const float power = splat_power(__fsub_rn(xa.x, fpx), __fsub_rn(xa.y, fpy), xa.z, xa.w, co.x);
+            const float power = splat_power(splat_row(__fsub_rn(xa.x, fpx), xa.z, xa.w, co.x), __fsub_rn(xa.y, fpy));
             const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
             if (power <= 0.f && alpha >= kAlphaMin)
                 ++c[frozen && frozen[g] ? 1 : 0];
