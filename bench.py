@@ -231,21 +231,23 @@ def gpu_arm(args):
         raise RuntimeError("device error flags set during pre-training")
 
     stream = torch.cuda.current_stream()
-    # dominant kernel (rasteriser backward) timed live inside the timed region
+    # dominant kernel (rasteriser backward) timed live inside the timed region:
+    # gs_train_step records a pair of events around it on the step's stream
     raster_ev = []
-    orig_backward = m.backward
+    orig_train_step = m.train_step
 
-    def backward_split(view, stats=True, stream=None):
+    def train_step_timed(view, gt, lrs, stream=None):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        lib.gs_raster_bwd_cfg(m.splats, view.vals, view.ranges, view.cam, m.bwd_cfg, view.t_final, view.n_last,
-                              view.dl, m.frozen, m.grad2d)
+        e0.record()  # creates the events; gs_train_step records them again in place
         e1.record()
+        st = m._step_struct(view)
+        st.bwd_events[0], st.bwd_events[1] = e0.cuda_event, e1.cuda_event
+        orig_train_step(view, gt, lrs, stream)
+        st.bwd_events[0] = st.bwd_events[1] = None
         raster_ev.append((e0, e1, tr.order[tr.k]))
-        m.project_backward(view, stats)
 
-    m.backward = backward_split
+    m.train_step = train_step_timed
     active_before = int(m.n_active.item())
     n_before = m.n
     k_start = tr.k
@@ -270,7 +272,7 @@ def gpu_arm(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    m.backward = orig_backward
+    m.train_step = orig_train_step
     active_after = int(m.n_active.item())
     flags = lib.gs_get_device_error()
     its = args.steps * world / (ms / 1000.0)

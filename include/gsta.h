@@ -109,6 +109,19 @@ typedef struct {
 int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, float *splats,
                gs_stream_t stream);
 
+/* Opacity activations: sigmoid of the parameter (Sec. 3.1), or its absolute
+ * value -- the finetuning stage's activation (Sec. 4.1, a trick taken from
+ * Taming 3DGS): opacities may then exceed 1 (alpha is still capped at 0.99),
+ * which turns capped Gaussians into opaque ones. */
+#define GS_OPACITY_SIGMOID 0
+#define GS_OPACITY_ABS 1
+
+/* gs_project with the opacity activation chosen (GS_OPACITY_*); gs_project
+ * is this with GS_OPACITY_SIGMOID. Errors as gs_project, and INVALID_ARG for
+ * another activation. */
+int gs_project_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act, const gs_camera *cam,
+                  float *splats, gs_stream_t stream);
+
 /* Bytes of workspace gs_sort needs for n Gaussians and `capacity` entries
  * on a width x height image with this tile size (0 for invalid sizes). */
 size_t gs_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t width, int32_t height, int32_t tile);
@@ -252,11 +265,62 @@ int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree, const gs_
                          const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, int32_t accumulate,
                          const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream);
 
+/* gs_project_bwd_stats for the opacity activation `opacity_act`
+ * (GS_OPACITY_*): dL/dx = dL/dopacity * sigmoid'(x), or * sign(x) (0 at
+ * x = 0) under GS_OPACITY_ABS. The other entry points take the sigmoid. */
+int gs_project_bwd_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act, const gs_camera *cam,
+                      const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G,
+                      int32_t accumulate, const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream);
+
 /* gs_raster_bwd followed by gs_project_bwd on the same stream. */
 int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
                   const uint32_t *vals, const uint32_t *ranges, const float *t_final, const int32_t *n_last,
                   const float *dl_dimage, const uint8_t *frozen, const int32_t *act, const int32_t *n_active_dev,
                   float *grad2d, float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt, gs_stream_t stream);
+
+/* One iteration of Algorithm 1's inner body for one view, in one call:
+ * gs_project_ex, gs_sort, gs_render_fwd_cfg, gs_loss, gs_raster_bwd_cfg,
+ * gs_project_bwd_ex (statistics windows `stats`), gs_adam_masked -- the
+ * same kernels, enqueued from native code instead of one binding call
+ * each. Everything the step touches is described by gs_step (device
+ * pointers, sizes, launch shapes); the view's camera, its target image gt
+ * [3][H][W] (device), the six group learning rates lr (host, [6]) and the
+ * Adam step (>= 1) are the per-iteration arguments. Returns the first
+ * non-OK status of the sequence (nothing after it is enqueued). */
+typedef struct {
+    /* Gaussians: P, G, m, v [n][64]; splats, grad2d [n][12] */
+    float *P, *G, *m, *v, *splats, *grad2d;
+    int64_t n;
+    int32_t sh_degree;
+    int32_t opacity_act;              /* GS_OPACITY_* */
+    const uint8_t *frozen;            /* [n] or NULL */
+    const int32_t *act;               /* unfrozen list [n], its length in n_active_dev [1] */
+    const int32_t *n_active_dev;
+    gs_grad_stats stats[2];           /* statistics windows of the projection backward */
+    int32_t n_stats;                  /* 0..2 */
+    /* the view's buffers: sort workspace and lists, image, loss */
+    void *sort_ws;
+    size_t sort_ws_bytes;
+    int64_t capacity;
+    uint32_t *vals, *ranges;
+    int64_t *count_dev;
+    float *image, *t_final;
+    int32_t *n_last;
+    float *dl_dimage;
+    void *loss_ws;
+    size_t loss_ws_bytes;
+    float *loss_dev;
+    float lambda_ssim;                /* 0.2 */
+    /* rasteriser launch shapes; pixels_per_thread 0 takes the default */
+    gs_raster_config fwd, bwd;
+    float b1, b2, eps;                /* Adam */
+    /* optional cudaEvent_t pair (NULL: none) recorded on the stream just
+     * before and just after the rasteriser backward, to time it in place */
+    void *bwd_events[2];
+} gs_step;
+
+int gs_train_step(const gs_step *s, const gs_camera *cam, const float *gt, const float *lr, int64_t step,
+                  gs_stream_t stream);
 
 /* Bytes of workspace gs_freeze_update needs for n Gaussians. */
 size_t gs_freeze_workspace_bytes(int64_t n);
@@ -275,6 +339,35 @@ size_t gs_freeze_workspace_bytes(int64_t n);
 int gs_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen, float eps_xyz,
                      float eps_rgb, int32_t mode, int32_t *act, int32_t *n_active_dev, void *ws, size_t ws_bytes,
                      gs_stream_t stream);
+
+/* Freeze strategies of the ablation (Sec. 5, "Freezing strategies" and
+ * "Gradient information"; Table 3). A Gaussian is eligible when it is not
+ * frozen and cnt[i] > 0; with avg_x = acc_xyz[i]/cnt[i] and avg_r =
+ * acc_rgb[i]/cnt[i] (float32 division), an update freezes the eligible
+ *   GS_FREEZE_RULE    with avg_x < eps_xyz && avg_r < eps_rgb (Eq. 4: the
+ *                     same decision as gs_freeze_update mode 0),
+ *   GS_FREEZE_XYZ     with avg_x < eps_xyz (positional gradients only),
+ *   GS_FREEZE_RANDOM  with u[i] < fraction (u [n]: the caller's uniform
+ *                     draws in [0, 1); each eligible Gaussian is frozen with
+ *                     probability `fraction`),
+ *   GS_FREEZE_MINGRAD the k = floor(fraction * m) of the m eligible with the
+ *                     smallest (score, index), score = max(avg_x / eps_xyz,
+ *                     avg_r / eps_rgb) in float32 (the rule's own measure,
+ *                     with a rank cut instead of the thresholds; NaN orders
+ *                     last), k computed in double.
+ * Then, as mode 0 of gs_freeze_update: the map only grows, acc_xyz,
+ * acc_rgb, cnt are zeroed, act / n_active_dev rebuilt. fraction in [0, 1]
+ * for RANDOM and MINGRAD; eps > 0 for MINGRAD; u may be NULL except for
+ * RANDOM. Workspace: ws of ws_bytes >= gs_freeze_select_workspace_bytes(n),
+ * 256-byte aligned. Errors: INVALID_ARG, CUDA. */
+#define GS_FREEZE_RULE 0
+#define GS_FREEZE_XYZ 1
+#define GS_FREEZE_RANDOM 2
+#define GS_FREEZE_MINGRAD 3
+size_t gs_freeze_select_workspace_bytes(int64_t n);
+int gs_freeze_select(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen, float eps_xyz,
+                     float eps_rgb, int32_t strategy, float fraction, const float *u, int32_t *act,
+                     int32_t *n_active_dev, void *ws, size_t ws_bytes, gs_stream_t stream);
 
 /* gs_freeze_update without a workspace argument. The paper has no
  * counterpart: this exists for callers that cannot allocate device memory
@@ -458,6 +551,22 @@ int gs_densify_apply(int64_t n, const float *P, const float *m, const float *v, 
  * logit(0.01)) and the opacity's Adam moments m, v [i][10] set to 0, for all
  * n Gaussians. Errors: INVALID_ARG, CUDA. */
 int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, gs_stream_t stream);
+
+/* Entry into the absolute-value opacity (Sec. 4.1, finetuning stage): for
+ * all i < n, P[i][10] = o = sigmoid(P[i][10]) -- the same expression, in
+ * float32, that gs_project evaluates, so |new parameter| is bit for bit the
+ * opacity rendered before. The opacity's Adam moments m, v [i][10]:
+ * GS_MOMENTS_ZERO restarts them; GS_MOMENTS_RESCALE carries them over to the
+ * new parameterisation, whose gradient is the old one over s = o (1 - o):
+ * m /= s, v /= s^2 (s floored at 1e-12). slope_sum_dev (device, one float,
+ * or NULL): the sum of s over the n Gaussians is ADDED to it (float atomics,
+ * summation order unspecified) -- s is how far an Adam step of the logit
+ * moved the opacity, for a caller that keeps that step size under |x|.
+ * Errors: INVALID_ARG, CUDA. */
+#define GS_MOMENTS_ZERO 0
+#define GS_MOMENTS_RESCALE 1
+int gs_opacity_to_abs(int64_t n, float *P, float *m, float *v, int32_t moments, float *slope_sum_dev,
+                      gs_stream_t stream);
 
 /* Bytes of workspace gs_psnr needs for S images of H x W. */
 size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W);

@@ -76,7 +76,8 @@ def lib():
             L = ctypes.CDLL(build())
             L.or_sh_basis.argtypes = [_dp, _dp]
             L.or_sh_basis_grad.argtypes = [_dp, _dp]
-            L.or_project.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _dp, _dp, _dp, _dp, _dp, _ip, _ip, _dp]
+            L.or_project_act.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp,
+                                         _ip, _ip, _dp]
             L.or_sort.argtypes = [_i64, _fp, _fp, _fp, _ip, _fp, _i32, _i32, _i32, _i32, _i64, _up, _up]
             L.or_sort.restype = _i64
             L.or_render.argtypes = [_i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp, _ip, _dp]
@@ -93,8 +94,8 @@ def lib():
                                            _ip, _dp]
             L.or_render_pixels_locked.argtypes = [_i64, _ip, _ip, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _up, _up,
                                                   _i32, _i64, _bp, _dp]
-            L.or_project_bwd.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _bp, _dp, _dp, _dp, _dp, _dp,
-                                         _dp, _dp]
+            L.or_project_bwd_act.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _i32, _bp, _dp, _dp, _dp,
+                                             _dp, _dp, _dp, _dp]
             L.or_adam.argtypes = [_i64, _dp, _dp, _dp, _dp, _bp, _dp, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, _i64]
             L.or_freeze_update.argtypes = [_i64, _fp, _fp, _ip, _bp, ctypes.c_float, ctypes.c_float, _i32, _ip]
@@ -139,14 +140,16 @@ def sh_basis_grad(d) -> np.ndarray:
     return out
 
 
-def project(params, cam: Cam, sh_degree: int = 3, smooth: bool = False) -> dict:
-    """Per-Gaussian projection (Eq. 1) and SH colour."""
+def project(params, cam: Cam, sh_degree: int = 3, smooth: bool = False, opacity_act: int = 0) -> dict:
+    """Per-Gaussian projection (Eq. 1) and SH colour; opacity_act 1: opacity = |x|
+    (the finetuning stage's activation, Sec. 4.1) instead of sigmoid(x)."""
     P = _c(params, np.float64)
     n = P.shape[0]
     out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), depth=np.zeros(n), opacity=np.zeros(n),
                rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
                margin=np.zeros(n))
-    lib().or_project(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), _p(out["mean2d"], _dp),
+    lib().or_project_act(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), int(opacity_act),
+                         _p(out["mean2d"], _dp),
                      _p(out["conic"], _dp), _p(out["depth"], _dp), _p(out["opacity"], _dp), _p(out["rgb"], _dp),
                      _p(out["radius"], _ip), _p(out["rect"], _ip), _p(out["margin"], _dp))
     r = out["rect"]
@@ -305,14 +308,15 @@ def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=N
     return out
 
 
-def project_bwd(params, cam: Cam, grads2d: dict, frozen=None, sh_degree: int = 3, smooth: bool = False) -> dict:
+def project_bwd(params, cam: Cam, grads2d: dict, frozen=None, sh_degree: int = 3, smooth: bool = False,
+                opacity_act: int = 0) -> dict:
     P = _c(params, np.float64)
     n = P.shape[0]
     G = np.zeros((n, N_PARAMS))
     xn = np.zeros(n)
     rn = np.zeros(n)
     fr = None if frozen is None else _c(frozen, np.uint8)
-    lib().or_project_bwd(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), _p(fr, _bp),
+    lib().or_project_bwd_act(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), int(opacity_act), _p(fr, _bp),
                          _p(_c(grads2d["d_mean2d"], np.float64), _dp), _p(_c(grads2d["d_conic"], np.float64), _dp),
                          _p(_c(grads2d["d_opacity"], np.float64), _dp), _p(_c(grads2d["d_rgb"], np.float64), _dp),
                          _p(G, _dp), _p(xn, _dp), _p(rn, _dp))
@@ -353,26 +357,27 @@ def psnr(images, gts) -> np.ndarray:
 # Whole-step compositions (each stage above, in the paper's order).
 # ---------------------------------------------------------------------------
 
-def forward(params, cam: Cam, sh_degree: int = 3, smooth: bool = False) -> dict:
+def forward(params, cam: Cam, sh_degree: int = 3, smooth: bool = False, opacity_act: int = 0) -> dict:
     """Projection, per-tile depth order and compositing for one view."""
-    proj = project(params, cam, sh_degree, smooth)
+    proj = project(params, cam, sh_degree, smooth, opacity_act)
     vals, ranges = sort_proj(proj, cam.width, cam.height, cam.tile, smooth)
     ren = render(proj, vals, ranges, cam, smooth)
     return dict(proj=proj, vals=vals, ranges=ranges, **ren)
 
 
 def loss_and_grad(params, cam: Cam, gt, frozen=None, sh_degree: int = 3, smooth: bool = False,
-                  lam: float = 0.2) -> dict:
+                  lam: float = 0.2, opacity_act: int = 0) -> dict:
     """Forward, Eq. 3 loss and the analytic gradient of the loss w.r.t. all 59 parameters."""
-    f = forward(params, cam, sh_degree, smooth)
+    f = forward(params, cam, sh_degree, smooth, opacity_act)
     L, dimg = loss(f["image"], gt, lam)
     g2 = render_bwd(f["proj"], f["vals"], f["ranges"], cam, dimg, frozen, smooth=smooth)
-    pb = project_bwd(params, cam, g2, frozen, sh_degree, smooth)
+    pb = project_bwd(params, cam, g2, frozen, sh_degree, smooth, opacity_act)
     return dict(loss=L, dl_dimage=dimg, grads2d=g2, **pb, fwd=f)
 
 
-def loss_only(params, cam: Cam, gt, sh_degree: int = 3, smooth: bool = False, lam: float = 0.2) -> float:
-    f = forward(params, cam, sh_degree, smooth)
+def loss_only(params, cam: Cam, gt, sh_degree: int = 3, smooth: bool = False, lam: float = 0.2,
+              opacity_act: int = 0) -> float:
+    f = forward(params, cam, sh_degree, smooth, opacity_act)
     return loss(f["image"], gt, lam, grad=False)[0]
 
 

@@ -153,5 +153,23 @@ def opacity_reset(P, M, V, logit_cap):
     V[:, 10] = 0.0
 
 
+def opacity_to_abs(P, M, V, rescale: bool = False):
+    """Start of the finetuning stage's absolute-value opacity (Sec. 4.1): the
+    opacity parameter x becomes o = sigmoid(x), so |new x| is the same
+    opacity. Its Adam moments either restart at zero or (rescale) are carried
+    over: the new parameter's gradient is the old one over s = o (1 - o), so
+    m / s and v / s^2 (s floored at 1e-12). In place."""
+    x = np.asarray(P[:, 10], np.float64)
+    o = 1.0 / (1.0 + np.exp(-x))
+    P[:, 10] = o
+    if rescale:
+        s = np.maximum(o * (1.0 - o), 1e-12)
+        M[:, 10] = M[:, 10] / s
+        V[:, 10] = V[:, 10] / (s * s)
+    else:
+        M[:, 10] = 0.0
+        V[:, 10] = 0.0
+
+
 def logit(p: float) -> float:
     return math.log(p / (1.0 - p))

@@ -308,11 +308,13 @@ typedef struct {
  *  - 2-D covariance J R_c Sigma R_c^T J^T + dilation * I, culled when det <= 0;
  *  - 2-D mean (fx tx/tz + cx, fy ty/tz + cy), pixel (i, j) sits at (i, j);
  *  - radius = ceil(3 sqrt(largest eigenvalue)), tile rectangle as tile_rect;
- *  - opacity = sigmoid(logit);
+ *  - opacity = sigmoid(logit); opacity_act = 1 takes |x| instead (the
+ *    absolute-value activation of the finetuning stage, Sec. 4.1);
  *  - colour = max(0, sum_c k_c Y_c(d) + 1/2), d = (mu - campos)/|mu - campos|.
  * smooth != 0 drops every cut-off except the near plane (for finite
  * differences): no radius, all tiles, no colour clamp. */
-static void project_one(const double *p, const or_camera *cam, int sh_degree, int smooth, gauss_fwd *g) {
+static void project_one(const double *p, const or_camera *cam, int sh_degree, int smooth, int opacity_act,
+                        gauss_fwd *g) {
     memset(g, 0, sizeof(*g));
     g->margin = INFINITY;
     const double *mu = p;
@@ -384,7 +386,7 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
         }
     }
 
-    g->opacity = 1.0 / (1.0 + exp(-p[10]));
+    g->opacity = opacity_act ? fabs(p[10]) : 1.0 / (1.0 + exp(-p[10]));
     double dv[3] = {mu[0] - cam->campos[0], mu[1] - cam->campos[1], mu[2] - cam->campos[2]};
     g->dist = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
     for (int i = 0; i < 3; ++i) g->dir[i] = dv[i] / g->dist;
@@ -402,12 +404,12 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
 /* Per-Gaussian projection. margin[i] is the smallest distance (pixels, or
  * world units for the near plane) of a value that decides an integer
  * (radius, tile rectangle, culling) to its threshold. */
-void or_project(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
-                double *mean2d, double *conic, double *depth, double *opacity, double *rgb,
-                int32_t *radius, int32_t *rect, double *margin) {
+void or_project_act(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
+                    int32_t opacity_act, double *mean2d, double *conic, double *depth, double *opacity, double *rgb,
+                    int32_t *radius, int32_t *rect, double *margin) {
     for (int64_t i = 0; i < n; ++i) {
         gauss_fwd g;
-        project_one(P + NP * i, cam, sh_degree, smooth, &g);
+        project_one(P + NP * i, cam, sh_degree, smooth, opacity_act, &g);
         if (margin) margin[i] = g.margin;
         if (!g.visible) {
             mean2d[2 * i] = mean2d[2 * i + 1] = 0;
@@ -426,6 +428,12 @@ void or_project(int64_t n, const double *P, const or_camera *cam, int32_t sh_deg
         radius[i] = g.radius;
         for (int c = 0; c < 4; ++c) rect[4 * i + c] = g.rect[c];
     }
+}
+
+void or_project(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
+                double *mean2d, double *conic, double *depth, double *opacity, double *rgb,
+                int32_t *radius, int32_t *rect, double *margin) {
+    or_project_act(n, P, cam, sh_degree, smooth, 0, mean2d, conic, depth, opacity, rgb, radius, rect, margin);
 }
 
 /* ------------------------------------------------------------------ */
@@ -948,9 +956,10 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
 /*   rgb_norm = |dL/d k_0| over the 3 channels (the diffuse colour).       */
 /* G is [n][59]; rows of frozen or culled Gaussians are zero.             */
 /* ------------------------------------------------------------------ */
-void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
-                    const uint8_t *frozen, const double *d_mean2d, const double *d_conic, const double *d_opacity,
-                    const double *d_rgb, double *G, double *xyz_norm, double *rgb_norm) {
+void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
+                        int32_t opacity_act, const uint8_t *frozen, const double *d_mean2d, const double *d_conic,
+                        const double *d_opacity, const double *d_rgb, double *G, double *xyz_norm,
+                        double *rgb_norm) {
     memset(G, 0, sizeof(double) * NP * n);
     for (int64_t i = 0; i < n; ++i) {
         if (xyz_norm) xyz_norm[i] = 0;
@@ -959,7 +968,7 @@ void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh
         const double *p = P + NP * i;
         double *gp = G + NP * i;
         gauss_fwd g;
-        project_one(p, cam, sh_degree, smooth, &g);
+        project_one(p, cam, sh_degree, smooth, opacity_act, &g);
         if (!g.visible) continue;
         const double *dm = d_mean2d + 2 * i, *dq = d_conic + 3 * i, *dc = d_rgb + 3 * i;
 
@@ -975,8 +984,11 @@ void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh
         double dmu[3], dd = ddir[0] * g.dir[0] + ddir[1] * g.dir[1] + ddir[2] * g.dir[2];
         for (int a = 0; a < 3; ++a) dmu[a] = (ddir[a] - g.dir[a] * dd) / g.dist;
 
-        /* opacity = sigmoid(logit) */
-        gp[10] = d_opacity[i] * g.opacity * (1 - g.opacity);
+        /* opacity = sigmoid(x): d/dx = o (1 - o); opacity = |x|: d/dx = sign(x) */
+        if (opacity_act)
+            gp[10] = d_opacity[i] * (p[10] > 0 ? 1.0 : (p[10] < 0 ? -1.0 : 0.0));
+        else
+            gp[10] = d_opacity[i] * g.opacity * (1 - g.opacity);
 
         /* conic = inverse of the 2-D covariance: dL/dcov = -Q dL/dQ Q */
         double GQ[4] = {dq[0], 0.5 * dq[1], 0.5 * dq[1], dq[2]}, tmp[4], Gcov[4];
@@ -1038,6 +1050,13 @@ void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh
         }
         if (rgb_norm) rgb_norm[i] = sqrt(gp[11] * gp[11] + gp[12] * gp[12] + gp[13] * gp[13]);
     }
+}
+
+void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
+                    const uint8_t *frozen, const double *d_mean2d, const double *d_conic, const double *d_opacity,
+                    const double *d_rgb, double *G, double *xyz_norm, double *rgb_norm) {
+    or_project_bwd_act(n, P, cam, sh_degree, smooth, 0, frozen, d_mean2d, d_conic, d_opacity, d_rgb, G, xyz_norm,
+                       rgb_norm);
 }
 
 /* ------------------------------------------------------------------ */

@@ -24,6 +24,37 @@ extern "C" int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const
     return gs_project_bwd(P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, acc_xyz, acc_rgb, cnt, stream);
 }
 
+extern "C" int gs_train_step(const gs_step *s, const gs_camera *cam, const float *gt, const float *lr, int64_t step,
+                             gs_stream_t stream) {
+    if (!s || !cam || !gt || !lr || step < 1 || s->n_stats < 0 || s->n_stats > 2) return GS_ERR_INVALID_ARG;
+    const gs_raster_config *fwd = s->fwd.pixels_per_thread ? &s->fwd : nullptr;
+    const gs_raster_config *bwd = s->bwd.pixels_per_thread ? &s->bwd : nullptr;
+    int st = gs_project_ex(s->P, s->n, s->sh_degree, s->opacity_act, cam, s->splats, stream);
+    if (st == GS_OK)
+        st = gs_sort(s->splats, s->n, cam, s->sort_ws, s->sort_ws_bytes, s->capacity, s->vals, s->ranges,
+                     s->count_dev, stream);
+    if (st == GS_OK)
+        st = gs_render_fwd_cfg(s->splats, s->vals, s->ranges, cam, fwd, s->image, s->t_final, s->n_last, stream);
+    if (st == GS_OK)
+        st = gs_loss(s->image, gt, cam->height, cam->width, s->lambda_ssim, s->loss_ws, s->loss_ws_bytes, s->loss_dev,
+                     s->dl_dimage, stream);
+    cudaStream_t cs = as_stream(stream);
+    if (st == GS_OK && s->bwd_events[0] && cudaEventRecord(static_cast<cudaEvent_t>(s->bwd_events[0]), cs) != cudaSuccess)
+        st = GS_ERR_CUDA;
+    if (st == GS_OK)
+        st = gs_raster_bwd_cfg(s->splats, s->vals, s->ranges, cam, bwd, s->t_final, s->n_last, s->dl_dimage,
+                               s->frozen, s->grad2d, stream);
+    if (st == GS_OK && s->bwd_events[1] && cudaEventRecord(static_cast<cudaEvent_t>(s->bwd_events[1]), cs) != cudaSuccess)
+        st = GS_ERR_CUDA;
+    if (st == GS_OK)
+        st = gs_project_bwd_ex(s->P, s->n, s->sh_degree, s->opacity_act, cam, s->splats, s->act, s->n_active_dev,
+                               s->grad2d, s->G, 0, s->stats, s->n_stats, stream);
+    if (st == GS_OK)
+        st = gs_adam_masked(s->P, s->G, s->m, s->v, s->n, s->act, s->n_active_dev, lr, s->b1, s->b2, s->eps, step,
+                            stream);
+    return st;
+}
+
 extern "C" int gs_get_device_error(uint32_t *flags_host, gs_stream_t stream) {
     if (!flags_host) return GS_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return GS_ERR_CUDA;

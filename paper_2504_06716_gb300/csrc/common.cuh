@@ -86,6 +86,11 @@ __device__ __forceinline__ int tile_rect(float mx, float my, int r, int tile, in
     return (x1 - x0) * (y1 - y0);
 }
 
+// Opacity from its parameter under the sigmoid activation; one definition
+// for the projection and for the switch to the absolute-value activation,
+// which must reproduce it bit for bit.
+__device__ __forceinline__ float opacity_sigmoid(float x) { return 1.f / (1.f + expf(-x)); }
+
 // Exponent of the 2-D Gaussian at offset (dx, dy), -0.5 (a dx^2 + c dy^2) -
 // b dx dy, as a quadratic in dy whose coefficients depend on dx only:
 // power = (c2 dy + c1) dy + c0 with c2 = -c/2, c1 = -b dx, c0 = -a dx^2 / 2.

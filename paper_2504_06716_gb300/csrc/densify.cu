@@ -235,6 +235,34 @@ __global__ void k_opacity_reset(int64_t n, float *__restrict__ P, float *__restr
     v[i * kRow + 10] = 0.f;
 }
 
+// rescale: the moments carried into the new parameterisation -- its gradient
+// is the old one divided by s = sigmoid'(x) = o (1 - o), so m / s and v / s^2
+// (s floored at 1e-12); else the moments restart at zero.
+__global__ void __launch_bounds__(256) k_opacity_to_abs(int64_t n, float *__restrict__ P, float *__restrict__ m,
+                                                        float *__restrict__ v, int rescale,
+                                                        float *__restrict__ slope_sum) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float slope = 0.f;
+    if (i < n) {
+        const float o = opacity_sigmoid(P[i * kRow + 10]);
+        slope = o * (1.f - o);
+        P[i * kRow + 10] = o;
+        if (rescale) {
+            const float is = 1.f / fmaxf(slope, 1e-12f);
+            m[i * kRow + 10] *= is;
+            v[i * kRow + 10] *= is * is;
+        } else {
+            m[i * kRow + 10] = 0.f;
+            v[i * kRow + 10] = 0.f;
+        }
+    }
+    if (slope_sum) {  // sum of sigmoid'(x) = o (1 - o) over the Gaussians
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) slope += __shfl_xor_sync(0xffffffffu, slope, off);
+        if ((threadIdx.x & 31) == 0 && slope != 0.f) atomicAdd(slope_sum, slope);
+    }
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct DenWs {
@@ -330,6 +358,17 @@ extern "C" int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float l
     if (n == 0) return GS_OK;
     if (!P || !m || !v) return GS_ERR_INVALID_ARG;
     k_opacity_reset<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(n, P, m, v, logit_cap);
+    note_launches(1);
+    return launch_status();
+}
+
+extern "C" int gs_opacity_to_abs(int64_t n, float *P, float *m, float *v, int32_t moments, float *slope_sum_dev,
+                                 gs_stream_t stream) {
+    if (n < 0 || (moments != GS_MOMENTS_ZERO && moments != GS_MOMENTS_RESCALE)) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    if (!P || !m || !v) return GS_ERR_INVALID_ARG;
+    k_opacity_to_abs<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(n, P, m, v, moments == GS_MOMENTS_RESCALE,
+                                                                       slope_sum_dev);
     note_launches(1);
     return launch_status();
 }

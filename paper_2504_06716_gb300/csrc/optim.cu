@@ -7,6 +7,8 @@
 // only; with the 256-byte parameter rows, every active Gaussian is 15 whole
 // 16-byte vectors of P, G, m and v, so the traffic is proportional to the
 // number of unfrozen Gaussians whatever the freeze pattern.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gs {
@@ -77,6 +79,124 @@ __global__ void __launch_bounds__(kFB) k_freeze_mark_pred(int64_t n, const float
     if (i < n) {
         const bool f = frozen[i] || prob[i] > tau;
         frozen[i] = f ? 1 : 0;
+        active = !f;
+    }
+    int c = __syncthreads_count(active);
+    if (threadIdx.x == 0) part[blockIdx.x] = c;
+}
+
+// ---- Ablation strategies (Sec. 5, "Freezing strategies" and "Gradient
+// information"): which eligible Gaussians (unfrozen, seen in the window) an
+// update freezes. ----
+
+// Radix-select state: the 64-bit key of rank k - 1 among the eligible
+// (score bits << 32 | index), found one 8-bit digit per pass.
+struct SelState {
+    unsigned long long prefix;  // digits chosen so far
+    unsigned long long m;       // eligible count
+    long long k;                // how many to freeze
+    long long r;                // rank still to find inside the current prefix
+};
+
+constexpr unsigned long long kNoKey = ~0ull;
+
+// Average gradient norm over the window, as the Eq. 4 rule reads it.
+__device__ __forceinline__ float window_avg(float acc, int32_t c) { return __fdiv_rn(acc, (float)c); }
+
+// Per Gaussian: the mingrad key (eligible only) and the eligible count.
+__global__ void __launch_bounds__(kFB) k_sel_keys(int64_t n, const float *__restrict__ acc_xyz,
+                                                 const float *__restrict__ acc_rgb, const int32_t *__restrict__ cnt,
+                                                 const uint8_t *__restrict__ frozen, float ex, float er,
+                                                 unsigned long long *__restrict__ keys, SelState *st) {
+    int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    int elig = 0;
+    if (i < n) {
+        unsigned long long key = kNoKey;
+        const int32_t c = cnt[i];
+        if (!frozen[i] && c > 0) {
+            // score: the larger of the two averages in units of their
+            // thresholds (the rule freezes exactly when it is below 1)
+            const float sx = __fdiv_rn(window_avg(acc_xyz[i], c), ex);
+            const float sr = __fdiv_rn(window_avg(acc_rgb[i], c), er);
+            const float sc = sx > sr ? sx : sr;
+            key = ((unsigned long long)__float_as_uint(sc) << 32) | (unsigned long long)i;
+            elig = 1;
+        }
+        keys[i] = key;
+    }
+    const int c = __syncthreads_count(elig);
+    if (threadIdx.x == 0 && c) atomicAdd(&st->m, (unsigned long long)c);
+}
+
+// Histogram of digit `shift` over the keys whose higher digits equal the
+// chosen prefix.
+__global__ void __launch_bounds__(1024) k_sel_hist(int64_t n, const unsigned long long *__restrict__ keys, int shift,
+                                                  const SelState *st, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[256];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const unsigned long long hi = shift == 56 ? 0ull : st->prefix >> (shift + 8);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = keys[i];
+        if (key == kNoKey) continue;
+        if (shift != 56 && (key >> (shift + 8)) != hi) continue;
+        atomicAdd(&h[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// Picks the digit holding rank r, narrows the prefix and clears the
+// histogram for the next pass. At the first pass it also fixes
+// k = floor(fraction * m).
+__global__ void k_sel_pick(int shift, double fraction, SelState *st, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = hist[threadIdx.x];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (shift == 56) {
+            st->k = (long long)floor(fraction * (double)st->m);
+            st->r = st->k - 1;
+        }
+        if (st->k > 0) {
+            long long r = st->r;
+            int b = 0;
+            while (b < 255 && r >= (long long)h[b]) r -= h[b++];
+            st->r = r;
+            st->prefix |= (unsigned long long)b << shift;
+        }
+    }
+}
+
+// New freeze state under `strategy` (GS_FREEZE_*), statistics zeroed,
+// per-block unfrozen counts.
+__global__ void __launch_bounds__(kFB) k_freeze_mark_strat(int64_t n, float *__restrict__ acc_xyz,
+                                                          float *__restrict__ acc_rgb, int32_t *__restrict__ cnt,
+                                                          uint8_t *__restrict__ frozen, float ex, float er,
+                                                          int strategy, float fraction, const float *__restrict__ u,
+                                                          const unsigned long long *__restrict__ keys,
+                                                          const SelState *st, int32_t *__restrict__ part) {
+    int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    int active = 0;
+    if (i < n) {
+        bool f = frozen[i] != 0;
+        const int32_t c = cnt[i];
+        if (!f && c > 0) {
+            switch (strategy) {
+                case GS_FREEZE_RULE:
+                    f = window_avg(acc_xyz[i], c) < ex && window_avg(acc_rgb[i], c) < er;
+                    break;
+                case GS_FREEZE_XYZ: f = window_avg(acc_xyz[i], c) < ex; break;
+                case GS_FREEZE_RANDOM: f = u[i] < fraction; break;
+                default: f = st->k > 0 && keys[i] <= st->prefix; break;
+            }
+        }
+        frozen[i] = f ? 1 : 0;
+        acc_xyz[i] = 0.f;
+        acc_rgb[i] = 0.f;
+        cnt[i] = 0;
         active = !f;
     }
     int c = __syncthreads_count(active);
@@ -198,6 +318,72 @@ extern "C" int gs_freeze_apply(int64_t n, const float *prob, float tau, uint8_t 
     k_freeze_scan<<<1, 1024, 0, s>>>(part, nb, n_active_dev);
     if (nb > 0) k_freeze_emit<<<nb, kFB, 0, s>>>(n, frozen, part, act);
     note_launches(nb > 0 ? 3 : 1);
+    return launch_status();
+}
+
+namespace {
+// Workspace of gs_freeze_select: block counts | selection state | histogram
+// | keys [n].
+struct SelLayout {
+    size_t part, state, hist, keys, total;
+};
+
+SelLayout sel_layout(int64_t n) {
+    SelLayout L;
+    const int64_t nb = (n + kFB - 1) / kFB;
+    L.part = 0;
+    L.state = align256(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+    L.hist = L.state + 256;
+    L.keys = L.hist + align256(256 * sizeof(uint32_t));
+    L.total = L.keys + align256(sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1));
+    return L;
+}
+}  // namespace
+
+extern "C" size_t gs_freeze_select_workspace_bytes(int64_t n) {
+    if (n < 0 || n > INT32_MAX) return 0;
+    return sel_layout(n).total;
+}
+
+extern "C" int gs_freeze_select(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, uint8_t *frozen,
+                                float eps_xyz, float eps_rgb, int32_t strategy, float fraction, const float *u,
+                                int32_t *act, int32_t *n_active_dev, void *ws, size_t ws_bytes, gs_stream_t stream) {
+    if (n < 0 || n > INT32_MAX || !n_active_dev || strategy < GS_FREEZE_RULE || strategy > GS_FREEZE_MINGRAD)
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!acc_xyz || !acc_rgb || !cnt || !frozen || !act)) return GS_ERR_INVALID_ARG;
+    if ((strategy == GS_FREEZE_RANDOM || strategy == GS_FREEZE_MINGRAD) && !(fraction >= 0.f && fraction <= 1.f))
+        return GS_ERR_INVALID_ARG;
+    if (strategy == GS_FREEZE_RANDOM && n > 0 && !u) return GS_ERR_INVALID_ARG;
+    if (strategy == GS_FREEZE_MINGRAD && !(eps_xyz > 0.f && eps_rgb > 0.f)) return GS_ERR_INVALID_ARG;
+    const SelLayout L = sel_layout(n);
+    if (!ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    char *w = static_cast<char *>(ws);
+    int32_t *part = reinterpret_cast<int32_t *>(w + L.part);
+    SelState *st = reinterpret_cast<SelState *>(w + L.state);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(w + L.keys);
+    const int nb = (int)((n + kFB - 1) / kFB);
+    int launches = nb > 0 ? 3 : 1;
+    if (strategy == GS_FREEZE_MINGRAD && nb > 0) {
+        if (cudaMemsetAsync(w + L.state, 0, L.keys - L.state, s) != cudaSuccess) return GS_ERR_CUDA;
+        k_sel_keys<<<nb, kFB, 0, s>>>(n, acc_xyz, acc_rgb, cnt, frozen, eps_xyz, eps_rgb, keys, st);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int hb = (int)std::min<int64_t>(nb, 2 * (int64_t)(sms > 0 ? sms : 152));
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            k_sel_hist<<<hb, 1024, 0, s>>>(n, keys, shift, st, hist);
+            k_sel_pick<<<1, 256, 0, s>>>(shift, (double)fraction, st, hist);
+        }
+        launches += 17;
+    }
+    if (nb > 0)
+        k_freeze_mark_strat<<<nb, kFB, 0, s>>>(n, acc_xyz, acc_rgb, cnt, frozen, eps_xyz, eps_rgb, strategy, fraction,
+                                               u, keys, st, part);
+    k_freeze_scan<<<1, 1024, 0, s>>>(part, nb, n_active_dev);
+    if (nb > 0) k_freeze_emit<<<nb, kFB, 0, s>>>(n, frozen, part, act);
+    note_launches(launches);
     return launch_status();
 }
 

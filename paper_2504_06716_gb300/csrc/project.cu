@@ -163,8 +163,20 @@ __device__ __forceinline__ void write_culled(float *out, int64_t i) {
     o[2] = z;
 }
 
-__global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P, int64_t n, int deg, DevCam cam,
-                                                     float *__restrict__ out) {
+// Opacity from its parameter x: sigmoid(x), or |x| under the absolute-value
+// activation of the finetuning stage (Sec. 4.1); and d opacity / dx.
+__device__ __forceinline__ float opacity_of(float x, int abs_act) {
+    return abs_act ? fabsf(x) : opacity_sigmoid(x);
+}
+
+__device__ __forceinline__ float opacity_slope(float x, int abs_act) {
+    if (abs_act) return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f);
+    const float o = opacity_sigmoid(x);
+    return o * (1.f - o);
+}
+
+__global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P, int64_t n, int deg, int abs_act,
+                                                     DevCam cam, float *__restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 *row = reinterpret_cast<const float4 *>(P + i * kRow);
@@ -182,7 +194,7 @@ __global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P
     if (tiles == 0) { write_culled(out, i); return; }
     float idet = 1.f / g.det;
     float ca = g.C * idet, cb = -g.B * idet, cc = g.A * idet;
-    float opacity = 1.f / (1.f + expf(-r2.z));
+    float opacity = opacity_of(r2.z, abs_act);
 
     // SH colour at the view direction; SH rows are fetched only here.
     float dx = r0.x - cam.campos[0], dy = r0.y - cam.campos[1], dz = r0.z - cam.campos[2];
@@ -227,7 +239,7 @@ struct StatSets {
 // Backward of the projection for act[0 .. *n_active). See gs_project_bwd;
 // with ACC the gradient rows are added to G instead of written.
 template <bool ACC>
-__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, DevCam cam,
+__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, int abs_act, DevCam cam,
                                                      const float *__restrict__ splats, const int32_t *__restrict__ act,
                                                      const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
                                                      float *__restrict__ G, StatSets st) {
@@ -295,9 +307,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
     float dd = gdx * x + gdy * y + gdz * z;
     float dmu0 = (gdx - x * dd) * il, dmu1 = (gdy - y * dd) * il, dmu2 = (gdz - z * dd) * il;
 
-    // ---- opacity = sigmoid(logit) ----
-    float o = 1.f / (1.f + expf(-r2.z));
-    float dlogit = dop * o * (1.f - o);
+    // ---- opacity = sigmoid(x) or |x| ----
+    float dlogit = dop * opacity_slope(r2.z, abs_act);
 
     // ---- conic = inverse of [[A, B], [B, C]] ----
     float id2 = 1.f / (g.det * g.det);
@@ -418,22 +429,29 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
 
 using namespace gs;
 
-extern "C" int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, float *splats,
-                          gs_stream_t stream) {
+extern "C" int gs_project_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act,
+                             const gs_camera *cam, float *splats, gs_stream_t stream) {
     if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam)) return GS_ERR_INVALID_ARG;
+    if (opacity_act != GS_OPACITY_SIGMOID && opacity_act != GS_OPACITY_ABS) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !splats) return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(splats)) & 15) return GS_ERR_INVALID_ARG;
-    k_project_fwd<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(P, n, sh_degree, make_cam(cam), splats);
+    k_project_fwd<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(P, n, sh_degree, opacity_act, make_cam(cam),
+                                                                    splats);
     note_launches(1);
     return launch_status();
 }
 
-static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
-                       const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G,
-                       const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream) {
+extern "C" int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, float *splats,
+                          gs_stream_t stream) {
+    return gs_project_ex(P, n, sh_degree, GS_OPACITY_SIGMOID, cam, splats, stream);
+}
+
+static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act,
+                       const gs_camera *cam, const float *splats, const int32_t *act, const int32_t *n_active_dev,
+                       float *grad2d, float *G, const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream) {
     if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam) || n_sets < 0 || n_sets > 2 ||
-        (n_sets > 0 && !sets))
+        (n_sets > 0 && !sets) || (opacity_act != GS_OPACITY_SIGMOID && opacity_act != GS_OPACITY_ABS))
         return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !splats || !act || !n_active_dev || !grad2d || !G) return GS_ERR_INVALID_ARG;
@@ -451,11 +469,11 @@ static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, c
     }
     const DevCam dc = make_cam(cam);
     if (acc)
-        k_project_bwd<true><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, dc, splats, act,
-                                                                             n_active_dev, grad2d, G, st);
+        k_project_bwd<true><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, dc, splats,
+                                                                             act, n_active_dev, grad2d, G, st);
     else
-        k_project_bwd<false><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, dc, splats, act,
-                                                                              n_active_dev, grad2d, G, st);
+        k_project_bwd<false><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, dc, splats,
+                                                                              act, n_active_dev, grad2d, G, st);
     note_launches(1);
     return launch_status();
 }
@@ -466,8 +484,8 @@ static int project_bwd_one(bool acc, const float *P, int64_t n, int32_t sh_degre
     const bool any_stat = acc_xyz || acc_rgb || cnt, all_stat = acc_xyz && acc_rgb && cnt;
     if (any_stat && !all_stat) return GS_ERR_INVALID_ARG;
     const gs_grad_stats one{acc_xyz, acc_rgb, cnt, nullptr};
-    return project_bwd(acc, P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, all_stat ? &one : nullptr,
-                       all_stat ? 1 : 0, stream);
+    return project_bwd(acc, P, n, sh_degree, GS_OPACITY_SIGMOID, cam, splats, act, n_active_dev, grad2d, G,
+                       all_stat ? &one : nullptr, all_stat ? 1 : 0, stream);
 }
 
 extern "C" int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam,
@@ -489,6 +507,14 @@ extern "C" int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree
                                     const float *splats, const int32_t *act, const int32_t *n_active_dev,
                                     float *grad2d, float *G, int32_t accumulate, const gs_grad_stats *sets,
                                     int32_t n_sets, gs_stream_t stream) {
-    return project_bwd(accumulate != 0, P, n, sh_degree, cam, splats, act, n_active_dev, grad2d, G, sets, n_sets,
-                       stream);
+    return project_bwd(accumulate != 0, P, n, sh_degree, GS_OPACITY_SIGMOID, cam, splats, act, n_active_dev, grad2d,
+                       G, sets, n_sets, stream);
+}
+
+extern "C" int gs_project_bwd_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act,
+                                 const gs_camera *cam, const float *splats, const int32_t *act,
+                                 const int32_t *n_active_dev, float *grad2d, float *G, int32_t accumulate,
+                                 const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream) {
+    return project_bwd(accumulate != 0, P, n, sh_degree, opacity_act, cam, splats, act, n_active_dev, grad2d, G, sets,
+                       n_sets, stream);
 }

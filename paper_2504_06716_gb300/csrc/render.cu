@@ -149,12 +149,13 @@ __device__ __forceinline__ float warp_sum9(const float (&g)[9], int lane) {
     return w + __shfl_xor_sync(kFull, w, 1);
 }
 
-// Backward of one pixel for one splat. Updates the pixel's recovered
-// transmittance T and the colour behind (S, la, lc) and, unless the splat is
-// frozen, adds its nine gradient terms to g.
+// Backward state of one pixel: recovered transmittance T, dL/dC, and the
+// colour blended behind the current splat, S, kept only as D = dL/dC . S
+// (all dL/dalpha needs): with la and ldc = dL/dC . c of the last splat
+// blended behind, S' = la c + (1 - la) S becomes D' = la ldc + (1 - la) D.
 struct PixBwd {
     float T, Tf, dC0, dC1, dC2, bgdot;
-    float S0, S1, S2, la, lc0, lc1, lc2;
+    float D, la, ldc;
     int nl;
 };
 
@@ -172,12 +173,10 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row,
     if (!(pos < p.nl && power <= 0.f && alpha >= kAlphaMin)) return false;
     const float om = 1.f - alpha;
     p.T = __fdividef(p.T, om);  // transmittance in front of this splat
-    p.S0 = p.la * p.lc0 + (1.f - p.la) * p.S0;
-    p.S1 = p.la * p.lc1 + (1.f - p.la) * p.S1;
-    p.S2 = p.la * p.lc2 + (1.f - p.la) * p.S2;
+    p.D = p.la * p.ldc + (1.f - p.la) * p.D;
+    const float dcc = p.dC0 * co.z + p.dC1 * co.w + p.dC2 * blue;
     if (!frz) {
-        const float dA = p.T * (p.dC0 * (co.z - p.S0) + p.dC1 * (co.w - p.S1) + p.dC2 * (blue - p.S2)) -
-                         __fdividef(p.Tf, om) * p.bgdot;
+        const float dA = p.T * (dcc - p.D) - __fdividef(p.Tf, om) * p.bgdot;
         const float wT = alpha * p.T;
         g[6] += wT * p.dC0;
         g[7] += wT * p.dC1;
@@ -192,9 +191,7 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row,
         }
     }
     p.la = alpha;
-    p.lc0 = co.z;
-    p.lc1 = co.w;
-    p.lc2 = blue;
+    p.ldc = dcc;
     return true;
 }
 
@@ -222,8 +219,7 @@ __device__ __forceinline__ void pix_load(PixBwd &p, bool inside, int64_t pix, in
     }
     p.Tf = p.T;
     p.bgdot = cam.bg[0] * p.dC0 + cam.bg[1] * p.dC1 + cam.bg[2] * p.dC2;
-    p.S0 = p.S1 = p.S2 = 0.f;
-    p.la = p.lc0 = p.lc1 = p.lc2 = 0.f;
+    p.D = p.la = p.ldc = 0.f;
 }
 
 template <int TS, int PPT, int B>

@@ -29,6 +29,8 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 4;
 constexpr int kSortBlock = kSortThreads * kSortItems;  // keys per radix block
+constexpr int kMaxRadixBits = 9;                       // digits of up to 9 bits (512 buckets) per pass
+constexpr int kMaxRadix = 1 << kMaxRadixBits;
 constexpr int kScanBlock = 1024;                       // elements per scan block
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -119,13 +121,13 @@ __device__ __forceinline__ int radix_blocks(const uint32_t *count) {
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
                                                             const uint32_t *__restrict__ count, int shift, int bits,
                                                             uint32_t *__restrict__ hist) {
-    __shared__ uint32_t h[256];
+    __shared__ uint32_t h[kMaxRadix];
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const uint32_t n = *count;
     const int nbd = radix_blocks(count);
     for (int b = blockIdx.x; b < nbd; b += gridDim.x) {
-        h[threadIdx.x] = 0;
+        for (int d = threadIdx.x; d < radix; d += kSortThreads) h[d] = 0;
         __syncthreads();
         const int64_t base = (int64_t)b * kSortBlock;
 #pragma unroll
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
             if (i < n) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
         }
         __syncthreads();
-        if ((int)threadIdx.x < radix) hist[(int64_t)threadIdx.x * nbd + b] = h[threadIdx.x];
+        for (int d = threadIdx.x; d < radix; d += kSortThreads) hist[(int64_t)d * nbd + b] = h[d];
         __syncthreads();
     }
 }
@@ -162,8 +164,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
                                                                const uint32_t *__restrict__ hist,
                                                                const uint32_t *__restrict__ digit_total) {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wc[kWarps][256];
+    constexpr int kPer = kMaxRadix / kSortThreads;  // buckets per thread (consecutive)
+    __shared__ uint32_t run[kMaxRadix];
+    __shared__ uint32_t wc[kWarps][kMaxRadix];
     __shared__ uint32_t ws[32];
     const uint32_t n = *count;
     const int nbd = radix_blocks(count);
@@ -171,42 +174,64 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const int t = threadIdx.x, warp = t >> 5;
-    uint32_t tot;
-    const uint32_t dt = t < radix ? digit_total[t] : 0u;
-    const uint32_t dbase = block_scan_excl<uint32_t>(dt, ws, &tot);
+    // exclusive scan of the bucket totals: thread t owns buckets kPer t .. kPer t + kPer - 1
+    uint32_t dtot[kPer], own = 0u, tot;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const int d = kPer * t + q;
+        dtot[q] = d < radix ? digit_total[d] : 0u;
+        own += dtot[q];
+    }
+    uint32_t dbase[kPer];
+    dbase[0] = block_scan_excl<uint32_t>(own, ws, &tot);
+#pragma unroll
+    for (int q = 1; q < kPer; ++q) dbase[q] = dbase[q - 1] + dtot[q - 1];
     for (int b = blockIdx.x; b < nbd; b += gridDim.x) {
         const int64_t base = (int64_t)b * kSortBlock;
-        if (t < radix) run[t] = dbase + hist[(int64_t)t * nbd + b];
-#pragma unroll 1
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int d = kPer * t + q;
+            if (d < radix) run[d] = dbase[q] + hist[(int64_t)d * nbd + b];
+        }
+        // all of the block's keys and values in flight at once; then ranked
+        // and written a sub-block of kSortThreads at a time, in order
+        uint32_t kr[kSortItems], vr[kSortItems];
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const int64_t i = base + r * kSortThreads + t;
+            kr[r] = i < n ? kin[i] : 0u;
+            vr[r] = i < n ? vin[i] : 0u;
+        }
+#pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             int64_t i = base + r * kSortThreads + t;
             bool valid = i < n;
-            uint32_t key = valid ? kin[i] : 0u;
+            uint32_t key = kr[r];
             uint32_t d = valid ? ((key >> shift) & mask) : 0xffffu;
             unsigned peers = __match_any_sync(kFull, d);
             unsigned lrank = __popc(peers & lanemask_lt());
-            if (t < radix) {
+            for (int e = t; e < radix; e += kSortThreads) {
 #pragma unroll
-                for (int w = 0; w < kWarps; ++w) wc[w][t] = 0u;
+                for (int w = 0; w < kWarps; ++w) wc[w][e] = 0u;
             }
             __syncthreads();
             if (valid && lrank == 0) wc[warp][d] = (uint32_t)__popc(peers);
             __syncthreads();
-            if (t < radix) {
-                uint32_t c = run[t];
+            for (int e = t; e < radix; e += kSortThreads) {
+                uint32_t c = run[e];
 #pragma unroll
                 for (int w = 0; w < kWarps; ++w) {
-                    uint32_t x = wc[w][t];
-                    wc[w][t] = c;
+                    uint32_t x = wc[w][e];
+                    wc[w][e] = c;
                     c += x;
                 }
-                run[t] = c;
+                run[e] = c;
             }
             __syncthreads();
             if (valid) {
                 uint32_t pos = wc[warp][d] + lrank;
                 kout[pos] = key;
-                vout[pos] = vin[i];
+                vout[pos] = vr[r];
             }
             __syncthreads();
         }
@@ -452,41 +477,21 @@ __global__ void __launch_bounds__(1024) k_super_plan(const uint32_t *__restrict_
     if (threadIdx.x == 0) chunk_base[ns] = carry;
 }
 
-// Bit ly * 8 + lx set for each tile (lx, ly) of super-tile (sx, sy) inside the rectangle.
-__device__ __forceinline__ unsigned long long tile_mask(int x0, int y0, int x1, int y1, int sx, int sy) {
-    const int lx0 = max(x0 - sx * kSuper, 0), lx1 = min(x1 - sx * kSuper, kSuper);
-    const int ly0 = max(y0 - sy * kSuper, 0), ly1 = min(y1 - sy * kSuper, kSuper);
-    if (lx0 >= lx1 || ly0 >= ly1) return 0ull;
-    const unsigned long long row = ((1ull << (lx1 - lx0)) - 1ull) << lx0;
-    unsigned long long m = 0ull;
-    for (int ly = ly0; ly < ly1; ++ly) m |= row << (kSuper * ly);
-    return m;
-}
-
-// Position of the k-th (from 0) set bit of m (k < popcount(m)), by halving.
-__device__ __forceinline__ int select_bit(unsigned long long m, int k) {
-    int pos = 0;
-#pragma unroll
-    for (int w = 32; w > 0; w >>= 1) {
-        const unsigned long long low = m & ((1ull << w) - 1ull);
-        const int c = __popcll(low);
-        if (k >= c) {
-            k -= c;
-            m >>= w;
-            pos += w;
-        } else {
-            m = low;
-        }
-    }
-    return pos;
-}
-
 // Shared part of the chunk kernels for chunk c: this thread's entry and the
 // mask of the tiles of the super-tile that list it.
 struct ChunkCtx {
     int s, sx, sy;
     uint32_t g;
     unsigned long long mask;
+};
+
+// Scratch of the tile tests (shared memory, one slot per thread): hit
+// masks as two 32-bit halves, the entry's shape and its candidate
+// rectangle packed as lx0 | ly0 << 3 | w << 6 | ceil(512 / w) << 10.
+struct TestScratch {
+    uint32_t *hit;  // [2 * kChunk]
+    float4 *shape;  // [2 * kChunk]
+    uint32_t *rect; // [kChunk]
 };
 
 // With masks_in NULL the masks are computed by the tile test (and stored to
@@ -496,7 +501,7 @@ __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float
                                            const uint32_t *__restrict__ seg_hi,
                                            const uint32_t *__restrict__ chunk_base,
                                            const uint32_t *__restrict__ chunk_super, int supers_x,
-                                           const DevCam &cam, uint32_t *hit_mask,
+                                           const DevCam &cam, const TestScratch &sc,
                                            const unsigned long long *__restrict__ masks_in,
                                            unsigned long long *__restrict__ masks_out) {
     __syncthreads();  // the previous chunk's shared data is no longer read
@@ -510,53 +515,64 @@ __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float
     cx.g = valid ? svals[e] : 0u;
     if (masks_in) {
         if (valid) cx.mask = masks_in[e];
-    } else {
-        // candidate tiles: the entry's rectangle inside this super-tile
-        unsigned long long cand = 0ull;
-        SplatShape sh{};
-        int x0, y0, x1, y1;
-        if (valid && splat_rect(splats, cx.g, cam, x0, y0, x1, y1)) {
-            sh = splat_shape(splats, cx.g);
-            if (sh.tau >= 0.f) cand = tile_mask(x0, y0, x1, y1, cx.sx, cx.sy);
-        }
-        // the warp's (entry, tile) candidates, spread evenly over its lanes
-        const int cnt = __popcll(cand);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int excl = incl - cnt, total = __shfl_sync(kFull, incl, 31);
-        hit_mask[2 * threadIdx.x] = 0u;
-        hit_mask[2 * threadIdx.x + 1] = 0u;
-        __syncwarp();
-        const uint32_t clo = (uint32_t)cand, chi = (uint32_t)(cand >> 32);
-        for (int base = 0; base < total; base += 32) {
-            const int j = base + lane;
-            int i = 0;  // owner: the last lane whose first candidate index is <= j
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int ex = __shfl_sync(kFull, excl, i + step);
-                if (ex <= j) i += step;
-            }
-            const int k = j - __shfl_sync(kFull, excl, i);
-            const uint32_t lo = __shfl_sync(kFull, clo, i), hi = __shfl_sync(kFull, chi, i);
-            SplatShape o;
-            o.mx = __shfl_sync(kFull, sh.mx, i); o.my = __shfl_sync(kFull, sh.my, i);
-            o.a = __shfl_sync(kFull, sh.a, i); o.b = __shfl_sync(kFull, sh.b, i); o.c = __shfl_sync(kFull, sh.c, i);
-            o.tau = __shfl_sync(kFull, sh.tau, i);
-            o.bc = __shfl_sync(kFull, sh.bc, i); o.ba = __shfl_sync(kFull, sh.ba, i);
-            if (j < total) {
-                const int t = select_bit(((unsigned long long)hi << 32) | lo, k);
-                if (tile_hit(o, cam.tile, cx.sx * kSuper + (t & 7), cx.sy * kSuper + (t >> 3)))
-                    atomicOr(&hit_mask[2 * (warp * 32 + i) + (t >> 5)], 1u << (t & 31));  // native 32-bit
-            }
-        }
-        __syncwarp();
-        cx.mask = ((unsigned long long)hit_mask[2 * threadIdx.x + 1] << 32) | hit_mask[2 * threadIdx.x];
-        if (valid && masks_out) masks_out[e] = cx.mask;
+        return;
     }
+    // candidate tiles: the entry's rectangle inside this super-tile, w x h
+    // tiles from (lx0, ly0) in the super-tile's own tile coordinates
+    int lx0 = 0, ly0 = 0, w = 0, h = 0;
+    SplatShape sh{};
+    int x0, y0, x1, y1;
+    if (valid && splat_rect(splats, cx.g, cam, x0, y0, x1, y1)) {
+        sh = splat_shape(splats, cx.g);
+        if (sh.tau >= 0.f) {
+            lx0 = max(x0 - cx.sx * kSuper, 0);
+            ly0 = max(y0 - cx.sy * kSuper, 0);
+            w = max(min(x1 - cx.sx * kSuper, kSuper) - lx0, 0);
+            h = max(min(y1 - cx.sy * kSuper, kSuper) - ly0, 0);
+        }
+    }
+    const int cnt = w * h;
+    sc.shape[2 * threadIdx.x] = make_float4(sh.mx, sh.my, sh.a, sh.b);
+    sc.shape[2 * threadIdx.x + 1] = make_float4(sh.c, sh.tau, sh.bc, sh.ba);
+    // k / w = (k * ceil(512 / w)) >> 9 exactly for k < 64, w <= 8
+    sc.rect[threadIdx.x] = cnt ? (uint32_t)(lx0 | (ly0 << 3) | (w << 6) | (((512 + w - 1) / w) << 10)) : 0u;
+    sc.hit[2 * threadIdx.x] = 0u;
+    sc.hit[2 * threadIdx.x + 1] = 0u;
+    // the warp's (entry, tile) candidates, spread evenly over its lanes
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int excl = incl - cnt, total = __shfl_sync(kFull, incl, 31);
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const int j = base + lane;
+        int i = 0;  // owner: the last lane whose first candidate index is <= j
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int ex = __shfl_sync(kFull, excl, i + step);
+            if (ex <= j) i += step;
+        }
+        const int k = j - __shfl_sync(kFull, excl, i);
+        if (j < total) {
+            const int o = warp * 32 + i;
+            const uint32_t pk = sc.rect[o];
+            const int ow = (int)((pk >> 6) & 15u);
+            const int q = (k * (int)(pk >> 10)) >> 9, r = k - q * ow;
+            const int t = ((int)((pk >> 3) & 7u) + q) * kSuper + (int)(pk & 7u) + r;
+            const float4 s0 = sc.shape[2 * o], s1 = sc.shape[2 * o + 1];
+            SplatShape os;
+            os.mx = s0.x; os.my = s0.y; os.a = s0.z; os.b = s0.w;
+            os.c = s1.x; os.tau = s1.y; os.bc = s1.z; os.ba = s1.w;
+            if (tile_hit(os, cam.tile, cx.sx * kSuper + (t & 7), cx.sy * kSuper + (t >> 3)))
+                atomicOr(&sc.hit[2 * o + (t >> 5)], 1u << (t & 31));  // native 32-bit
+        }
+    }
+    __syncwarp();
+    cx.mask = ((unsigned long long)sc.hit[2 * threadIdx.x + 1] << 32) | sc.hit[2 * threadIdx.x];
+    if (valid && masks_out) masks_out[e] = cx.mask;
 }
 
 // Global tile id of slot t of super-tile (sx, sy).
@@ -574,12 +590,14 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
                                                         uint32_t *__restrict__ tile_count,
                                                         unsigned long long *__restrict__ masks) {
     __shared__ uint32_t hit_mask[2 * kChunk];  // per entry, low and high halves
+    __shared__ float4 shape[2 * kChunk];
+    __shared__ uint32_t rect[kChunk];
     __shared__ uint32_t cnt[64];
+    const TestScratch sc{hit_mask, shape, rect};
     const uint32_t nc = chunk_base[ns];
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
-        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, hit_mask, nullptr,
-                   masks);
+        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, sc, nullptr, masks);
         if (threadIdx.x < 64) cnt[threadIdx.x] = 0u;
         __syncthreads();
         for (unsigned long long m = cx.mask; m; m &= m - 1ull) atomicAdd(&cnt[__ffsll((long long)m) - 1], 1u);
@@ -641,7 +659,7 @@ __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ spl
     const unsigned lt = lanemask_lt();
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
-        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, nullptr, masks,
+        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, TestScratch{}, masks,
                    nullptr);
 #pragma unroll 8
         for (int t = 0; t < 64; ++t) {
@@ -721,8 +739,8 @@ inline SortWs sort_layout(char *base, int64_t n, int64_t cap, int64_t tiles, int
     for (int k = 0; k < 2; ++k) w.vals[k] = (uint32_t *)take(4 * (size_t)n);
     for (int k = 0; k < 2; ++k) w.skeys[k] = (uint32_t *)take(4 * (size_t)cap);
     w.svals1 = (uint32_t *)take(4 * (size_t)cap);
-    w.hist = (uint32_t *)take(4 * 256 * (size_t)nbMax);
-    w.digit_total = (uint32_t *)take(4 * 256);
+    w.hist = (uint32_t *)take(4 * (size_t)kMaxRadix * (size_t)nbMax);
+    w.digit_total = (uint32_t *)take(4 * (size_t)kMaxRadix);
     w.part32 = (uint32_t *)take(4 * (size_t)nbS);
     w.part_s = (unsigned long long *)take(8 * (size_t)nbS);
     w.total_s = (unsigned long long *)take(8);
@@ -765,7 +783,8 @@ inline SuperGrid super_grid(int32_t width, int32_t height, int32_t tile) {
 int radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], int in, const uint32_t *count, int64_t bound,
                int total_bits, const SortWs &w, cudaStream_t s) {
     if (total_bits <= 0) return in;
-    int npass = (total_bits + 7) / 8;
+    // 8-bit digits, or one pass of up to kMaxRadixBits when that suffices
+    int npass = total_bits <= kMaxRadixBits ? 1 : (total_bits + 7) / 8;
     int per = (total_bits + npass - 1) / npass;
     const int64_t nb = (bound + kSortBlock - 1) / kSortBlock, cap = resident_blocks();
     const int grid = (int)(nb < 1 ? 1 : (nb < cap ? nb : cap));
@@ -853,7 +872,7 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
         return launch_status();
     }
     const int sbits = ceil_log2(sg.ns);
-    const int npass = (sbits + 7) / 8;
+    const int npass = sbits <= 0 ? 0 : (sbits <= kMaxRadixBits ? 1 : (sbits + 7) / 8);
     uint32_t *sk[2] = {w.skeys[0], w.skeys[1]};
     uint32_t *sv[2] = {w.svals1, vals};  // the sorted list must end in svals1: vals is written from it
     const int start = npass % 2;

@@ -98,6 +98,8 @@ _SIGS = {
     "gs_mlp_adam": ([_P, _P, _P, _P, _P, _F32, _F32, _F32, _F32, _I64, _P], _I32),
     "gs_mlp_refresh": ([_P, _P, _P], _I32),
     "gs_freeze_apply": ([_I64, _P, _F32, _P, _P, _P, _P, _SZ, _P], _I32),
+    "gs_freeze_select_workspace_bytes": ([_I64], _SZ),
+    "gs_freeze_select": ([_I64, _P, _P, _P, _P, _F32, _F32, _I32, _F32, _P, _P, _P, _P, _SZ, _P], _I32),
     "gs_adam_masked_devstep": ([_P, _P, _P, _P, _I64, _P, _P, _P, _F32, _F32, _F32, _P,
                                 _P, _P], _I32),
     "gs_raster_pair_counts": ([_P, _P, _P, _CAM, _P, _P, _P, _P], _I32),
@@ -106,6 +108,10 @@ _SIGS = {
     "gs_densify_plan": ([_I64, _P, _P, _P, _P, _SZ, _P, _P], _I32),
     "gs_densify_apply": ([_I64, _P, _P, _P, _P, _P, _I32, _P, _P, _P, _SZ, _I64, _P, _P, _P, _P, _P], _I32),
     "gs_opacity_reset": ([_I64, _P, _P, _P, _F32, _P], _I32),
+    "gs_opacity_to_abs": ([_I64, _P, _P, _P, _I32, _P, _P], _I32),
+    "gs_train_step": ([_P, _P, _P, _P, _I64, _P], _I32),
+    "gs_project_ex": ([_P, _I64, _I32, _I32, _P, _P, _P], _I32),
+    "gs_project_bwd_ex": ([_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _I32, _P, _I32, _P], _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
     "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
     "gs_get_device_error": ([ctypes.POINTER(ctypes.c_uint32), _P], _I32),
@@ -171,6 +177,17 @@ def gs_project(P, n: int, sh_degree: int, cam: GsCamera, splats, stream=None):
 
     _check("gs_project", load().gs_project(_ptr(P, torch.float32, "P"), n, sh_degree, ctypes.byref(cam),
                                            _ptr(splats, torch.float32, "splats"), _stream(stream)))
+
+
+GS_OPACITY_SIGMOID, GS_OPACITY_ABS = 0, 1
+
+
+def gs_project_ex(P, n: int, sh_degree: int, opacity_act: int, cam: GsCamera, splats, stream=None):
+    import torch
+
+    _check("gs_project_ex", load().gs_project_ex(_ptr(P, torch.float32, "P"), n, sh_degree, opacity_act,
+                                                 ctypes.byref(cam), _ptr(splats, torch.float32, "splats"),
+                                                 _stream(stream)))
 
 
 def gs_sort_workspace_bytes(n: int, capacity: int, cam: GsCamera) -> int:
@@ -265,6 +282,62 @@ class GsGradStats(ctypes.Structure):
                 ("max_radius", ctypes.c_void_p)]
 
 
+class GsStep(ctypes.Structure):
+    """gs_step: every buffer of one training step (raw device pointers; the
+    caller keeps the tensors alive while the struct is used)."""
+    _fields_ = [
+        ("P", ctypes.c_void_p), ("G", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
+        ("splats", ctypes.c_void_p), ("grad2d", ctypes.c_void_p), ("n", ctypes.c_int64),
+        ("sh_degree", ctypes.c_int32), ("opacity_act", ctypes.c_int32), ("frozen", ctypes.c_void_p),
+        ("act", ctypes.c_void_p), ("n_active_dev", ctypes.c_void_p), ("stats", GsGradStats * 2),
+        ("n_stats", ctypes.c_int32), ("sort_ws", ctypes.c_void_p), ("sort_ws_bytes", ctypes.c_size_t),
+        ("capacity", ctypes.c_int64), ("vals", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
+        ("count_dev", ctypes.c_void_p), ("image", ctypes.c_void_p), ("t_final", ctypes.c_void_p),
+        ("n_last", ctypes.c_void_p), ("dl_dimage", ctypes.c_void_p), ("loss_ws", ctypes.c_void_p),
+        ("loss_ws_bytes", ctypes.c_size_t), ("loss_dev", ctypes.c_void_p), ("lambda_ssim", ctypes.c_float),
+        ("fwd", GsRasterConfig), ("bwd", GsRasterConfig), ("b1", ctypes.c_float), ("b2", ctypes.c_float),
+        ("eps", ctypes.c_float), ("bwd_events", ctypes.c_void_p * 2),
+    ]
+
+
+def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: int, frozen, act, n_active, stats,
+              sort_ws, capacity: int, vals, ranges, count, image, t_final, n_last, dl, loss_ws, loss, lam: float = 0.2,
+              fwd=None, bwd=None, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15) -> GsStep:
+    """A gs_step for gs_train_step (tensors checked here once; the caller keeps them alive)."""
+    import torch
+
+    s = GsStep()
+    f32, i32, u8 = torch.float32, torch.int32, torch.uint8
+    s.P, s.G, s.m, s.v = (_ptr(t, f32, k) for t, k in ((P, "P"), (G, "G"), (m, "m"), (v, "v")))
+    s.splats, s.grad2d = _ptr(splats, f32, "splats"), _ptr(grad2d, f32, "grad2d")
+    s.n, s.sh_degree, s.opacity_act = int(n), int(sh_degree), int(opacity_act)
+    s.frozen, s.act, s.n_active_dev = _ptr(frozen, u8, "frozen"), _ptr(act, i32, "act"), _ptr(n_active, i32, "n_active")
+    if len(stats) > 2:
+        raise ValueError("at most two statistics windows")
+    for k, st in enumerate(stats):
+        s.stats[k] = st
+    s.n_stats = len(stats)
+    s.sort_ws, s.sort_ws_bytes, s.capacity = _ptr(sort_ws, u8, "sort_ws"), sort_ws.numel(), int(capacity)
+    s.vals, s.ranges = _ptr(vals, i32, "vals"), _ptr(ranges, i32, "ranges")
+    s.count_dev = _ptr(count, torch.int64, "count")
+    s.image, s.t_final, s.n_last = _ptr(image, f32, "image"), _ptr(t_final, f32, "t_final"), _ptr(n_last, i32, "n_last")
+    s.dl_dimage = _ptr(dl, f32, "dl")
+    s.loss_ws, s.loss_ws_bytes, s.loss_dev = _ptr(loss_ws, u8, "loss_ws"), loss_ws.numel(), _ptr(loss, f32, "loss")
+    s.lambda_ssim = lam
+    s.fwd = fwd if fwd is not None else GsRasterConfig(0, 0)
+    s.bwd = bwd if bwd is not None else GsRasterConfig(0, 0)
+    s.b1, s.b2, s.eps = b1, b2, eps
+    return s
+
+
+def gs_train_step(step: GsStep, cam: GsCamera, gt, lr, adam_step: int, stream=None):
+    import torch
+
+    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
+    _check("gs_train_step", load().gs_train_step(ctypes.byref(step), ctypes.byref(cam), _ptr(gt, torch.float32, "gt"),
+                                                 lr6, adam_step, _stream(stream)))
+
+
 def grad_stats(acc_xyz, acc_rgb, cnt, max_radius=None) -> GsGradStats:
     """The struct holds raw device pointers: the caller keeps the tensors alive."""
     import torch
@@ -284,6 +357,19 @@ def gs_project_bwd_stats(P, n: int, sh_degree: int, cam: GsCamera, splats, act, 
         _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), _ptr(grad2d, torch.float32, "grad2d"),
         _ptr(G, torch.float32, "G"), int(bool(accumulate)), ctypes.cast(arr, ctypes.c_void_p), len(sets),
         _stream(stream)))
+
+
+def gs_project_bwd_ex(P, n: int, sh_degree: int, opacity_act: int, cam: GsCamera, splats, act, n_active, grad2d, G,
+                      accumulate: bool, sets, stream=None):
+    """gs_project_bwd_stats with the opacity activation chosen (GS_OPACITY_*)."""
+    import torch
+
+    arr = (GsGradStats * max(len(sets), 1))(*sets)
+    _check("gs_project_bwd_ex", load().gs_project_bwd_ex(
+        _ptr(P, torch.float32, "P"), n, sh_degree, opacity_act, ctypes.byref(cam),
+        _ptr(splats, torch.float32, "splats"), _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
+        _ptr(grad2d, torch.float32, "grad2d"), _ptr(G, torch.float32, "G"), int(bool(accumulate)),
+        ctypes.cast(arr, ctypes.c_void_p), len(sets), _stream(stream)))
 
 
 class GsDensifyParams(ctypes.Structure):
@@ -339,6 +425,18 @@ def gs_opacity_reset(n: int, P, m, v, logit_cap: float, stream=None):
     _check("gs_opacity_reset", load().gs_opacity_reset(
         n, _ptr(P, torch.float32, "P"), _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"), logit_cap,
         _stream(stream)))
+
+
+GS_MOMENTS_ZERO, GS_MOMENTS_RESCALE = 0, 1
+
+
+def gs_opacity_to_abs(n: int, P, m, v, moments: int = GS_MOMENTS_ZERO, slope_sum=None, stream=None):
+    import torch
+
+    _check("gs_opacity_to_abs", load().gs_opacity_to_abs(n, _ptr(P, torch.float32, "P"), _ptr(m, torch.float32, "m"),
+                                                         _ptr(v, torch.float32, "v"), moments,
+                                                         _ptr(slope_sum, torch.float32, "slope_sum"),
+                                                         _stream(stream)))
 
 
 class GsRasterJob(ctypes.Structure):
@@ -486,6 +584,25 @@ def gs_freeze_apply(n: int, prob, tau: float, frozen, act, n_active, ws, stream=
     _check("gs_freeze_apply", load().gs_freeze_apply(
         n, _ptr(prob, torch.float32, "prob"), tau, _ptr(frozen, torch.uint8, "frozen"), _ptr(act, torch.int32, "act"),
         _ptr(n_active, torch.int32, "n_active"), _ptr(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
+
+
+GS_FREEZE_RULE, GS_FREEZE_XYZ, GS_FREEZE_RANDOM, GS_FREEZE_MINGRAD = 0, 1, 2, 3
+
+
+def gs_freeze_select_workspace_bytes(n: int) -> int:
+    return int(load().gs_freeze_select_workspace_bytes(n))
+
+
+def gs_freeze_select(n: int, acc_xyz, acc_rgb, cnt, frozen, eps_xyz: float, eps_rgb: float, strategy: int,
+                     fraction: float, u, act, n_active, ws, stream=None):
+    """Freeze update under an ablation strategy (GS_FREEZE_*); u: uniform draws [n] (RANDOM) or None."""
+    import torch
+
+    _check("gs_freeze_select", load().gs_freeze_select(
+        n, _ptr(acc_xyz, torch.float32, "acc_xyz"), _ptr(acc_rgb, torch.float32, "acc_rgb"),
+        _ptr(cnt, torch.int32, "cnt"), _ptr(frozen, torch.uint8, "frozen"), eps_xyz, eps_rgb, strategy, fraction,
+        _ptr(u, torch.float32, "u"), _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
+        _ptr(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
 
 
 def gs_psnr_workspace_bytes(S: int, H: int, W: int) -> int:

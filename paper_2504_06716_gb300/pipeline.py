@@ -67,6 +67,7 @@ class Model:
         self.bwd_cfg = None
         self.generation = 0
         self.den = None  # densification window statistics (enable_densify)
+        self.opacity_act = lib.GS_OPACITY_SIGMOID  # GS_OPACITY_ABS after to_abs_opacity()
         self.carried: dict[str, torch.Tensor] = {}  # further per-Gaussian state moved by densify
         self._allocate(max(self.n, capacity or 0, 1))
         self.P[: self.n, :59] = torch.from_numpy(np.ascontiguousarray(params59, dtype=np.float32)).to(self.device)
@@ -94,6 +95,7 @@ class Model:
         self.cnt = torch.zeros(cap, dtype=torch.int32, device=self.device)
         self.freeze_ws = torch.zeros(max(lib.gs_freeze_workspace_bytes(cap), 256), dtype=torch.uint8,
                                      device=self.device)
+        self.select_ws = None  # gs_freeze_select workspace, made at first use
         if self.den is not None:
             self.enable_densify()
 
@@ -118,6 +120,8 @@ class Model:
         """One densification and pruning step (gs_densify_plan / gs_densify_apply);
         returns the counts. Restarts the densification window; keeps the freeze
         window's statistics and the carried state of the surviving Gaussians."""
+        if self.opacity_act != lib.GS_OPACITY_SIGMOID:
+            raise RuntimeError("densification thresholds are opacity logits: not under the absolute-value opacity")
         d, n = self.den, self.n
         lib.gs_densify_plan(n, self.P, self._den_stats(), prm, d["ws"], d["counts"])
         kept, clones, children, splits = (int(x) for x in d["counts"].cpu().tolist())
@@ -149,6 +153,8 @@ class Model:
         return dict(kept=kept, clones=clones, children=children, splits=splits, n=n_out)
 
     def opacity_reset(self, logit_cap: float):
+        if self.opacity_act != lib.GS_OPACITY_SIGMOID:
+            raise RuntimeError("the opacity reset caps a logit: not under the absolute-value opacity")
         lib.gs_opacity_reset(self.n, self.P, self.m, self.v, logit_cap)
 
     # ---- views ----
@@ -179,7 +185,7 @@ class Model:
 
     # ---- step pieces ----
     def rasterize(self, view: View, stream=None):
-        lib.gs_project(self.P, self.n, self.sh_degree, view.cam, self.splats, stream)
+        lib.gs_project_ex(self.P, self.n, self.sh_degree, self.opacity_act, view.cam, self.splats, stream)
         lib.gs_sort(self.splats, self.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count,
                     stream)
         lib.gs_render_fwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.fwd_cfg, view.image, view.t_final,
@@ -197,14 +203,25 @@ class Model:
     def project_backward(self, view: View, stats: bool = True, stream=None):
         """The projection half of the backward; it also feeds the densification
         window when that is enabled."""
-        if self.den is not None and stats:
-            sets = [lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt), self._den_stats()]
-            lib.gs_project_bwd_stats(self.P, self.n, self.sh_degree, view.cam, self.splats, self.act, self.n_active,
-                                     self.grad2d, self.G, False, sets, stream)
-            return
-        lib.gs_project_bwd(self.P, self.n, self.sh_degree, view.cam, self.splats, self.act, self.n_active, self.grad2d,
-                           self.G, self.acc_xyz if stats else None, self.acc_rgb if stats else None,
-                           self.cnt if stats else None, stream)
+        sets = []
+        if stats:
+            sets.append(lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt))
+            if self.den is not None:
+                sets.append(self._den_stats())
+        lib.gs_project_bwd_ex(self.P, self.n, self.sh_degree, self.opacity_act, view.cam, self.splats, self.act,
+                              self.n_active, self.grad2d, self.G, False, sets, stream)
+
+    def to_abs_opacity(self, moments: int = lib.GS_MOMENTS_ZERO, stream=None) -> float:
+        """Switch to the absolute-value opacity of the finetuning stage (Sec. 4.1):
+        gs_opacity_to_abs keeps every opacity; its Adam moments restart
+        (GS_MOMENTS_ZERO) or are carried over (GS_MOMENTS_RESCALE). Returns
+        the mean of sigmoid'(x) = o (1 - o) over the Gaussians at the switch."""
+        if self.opacity_act == lib.GS_OPACITY_ABS:
+            return 1.0
+        acc = torch.zeros(1, dtype=torch.float32, device=self.device)
+        lib.gs_opacity_to_abs(self.n, self.P, self.m, self.v, moments, acc, stream)
+        self.opacity_act = lib.GS_OPACITY_ABS
+        return float(acc.item()) / max(self.n, 1)
 
     def apply_tuning(self, tuning):
         self.fwd_cfg = lib.raster_config(*tuning.fwd)
@@ -216,11 +233,38 @@ class Model:
                            self.step_count, stream)
 
     def train_step(self, view: View, gt: torch.Tensor, lrs, stream=None):
-        """One iteration of Algorithm 1's inner body on the current freeze map."""
-        self.rasterize(view, stream)
-        self.loss(view, gt, stream=stream)
-        self.backward(view, stream=stream)
-        self.adam(lrs, stream=stream)
+        """One iteration of Algorithm 1's inner body on the current freeze map:
+        gs_train_step, the same kernels as rasterize / loss / backward / adam
+        enqueued from native code in one call."""
+        self.step_count += 1
+        lib.gs_train_step(self._step_struct(view), view.cam, gt, lrs, self.step_count, stream)
+
+    def _step_struct(self, view: View) -> "lib.GsStep":
+        """The gs_step of this model and view, rebuilt when a buffer or size changed."""
+        den = self.den["acc_xyz"].data_ptr() if self.den is not None else 0
+        key = (id(view), view.vals.data_ptr(), view.image.data_ptr(), view.capacity, self.P.data_ptr(),
+               self.G.data_ptr(), self.m.data_ptr(), self.frozen.data_ptr(), self.acc_xyz.data_ptr(), den, self.n,
+               self.opacity_act, id(self.fwd_cfg), id(self.bwd_cfg))
+        if getattr(self, "_step_key", None) != key:
+            stats = [lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt)]
+            if self.den is not None:
+                stats.append(self._den_stats())
+            self._step = lib.step_args(self.P, self.G, self.m, self.v, self.splats, self.grad2d, self.n,
+                                       self.sh_degree, self.opacity_act, self.frozen, self.act, self.n_active, stats,
+                                       view.sort_ws, view.capacity, view.vals, view.ranges, view.count, view.image,
+                                       view.t_final, view.n_last, view.dl, view.loss_ws, view.loss, 0.2, self.fwd_cfg,
+                                       self.bwd_cfg)
+            self._step_key = key
+        return self._step
+
+    def freeze_select(self, eps_xyz: float, eps_rgb: float, strategy: int, fraction: float, u=None, stream=None):
+        """A freeze update under one of the ablation strategies (lib.GS_FREEZE_*):
+        gs_freeze_select; u: uniform draws [n] for the random strategy."""
+        if self.select_ws is None:
+            self.select_ws = torch.zeros(lib.gs_freeze_select_workspace_bytes(self.cap), dtype=torch.uint8,
+                                         device=self.device)
+        lib.gs_freeze_select(self.n, self.acc_xyz, self.acc_rgb, self.cnt, self.frozen, eps_xyz, eps_rgb, strategy,
+                             fraction, u, self.act, self.n_active, self.select_ws, stream)
 
     def freeze_update(self, eps_xyz: float, eps_rgb: float, mode: int, stream=None):
         lib.gs_freeze_update(self.n, self.acc_xyz, self.acc_rgb, self.cnt, self.frozen, eps_xyz, eps_rgb, mode,
@@ -230,7 +274,7 @@ class Model:
         """Largest entry count over ``cams`` (one projection + sort each), times ``slack``."""
         worst = 0
         for cam in cams:
-            lib.gs_project(self.P, self.n, self.sh_degree, cam, self.splats)
+            lib.gs_project_ex(self.P, self.n, self.sh_degree, self.opacity_act, cam, self.splats)
             tt = self.splats[:, 11].contiguous().view(torch.int32)
             worst = max(worst, int(tt.to(torch.int64).sum().item()))
         return int(worst * slack) + 1024

@@ -68,6 +68,23 @@ class GStaConfig:
     max_screen_radius: int | None = None
     max_world_frac: float = 0.1     # of the scene extent
     split_div: float = 1.6
+    # freeze strategy of the ablation (Sec. 5, Table 3): "gsta" the Eq. 4 rule;
+    # "xyz" the rule on positional gradients only (GSta-rgb); "random" /
+    # "mingrad" freeze freeze_fraction of the eligible Gaussians at random / with
+    # the lowest gradients; "none" keeps GSta's schedule, early stop and LR
+    # plateau but never freezes (GSta-freezing).
+    freeze_strategy: str = "gsta"
+    freeze_fraction: float = 0.25
+    # finetune with the absolute-value opacity activation instead of the
+    # sigmoid (Sec. 4.1, the trick taken from Taming 3DGS)
+    abs_opacity_finetune: bool = True
+    # the opacity's Adam moments at that switch: "zero" restarts them,
+    # "rescale" carries them over to the new parameterisation
+    abs_opacity_moments: str = "zero"
+    # opacity learning rate under |x|: None keeps the training rate (0.025);
+    # "slope" scales it by the mean o (1 - o) at the switch, so that an Adam
+    # step moves opacities by as much on average as it did through the sigmoid
+    abs_opacity_lr: float | str | None = None
 
     @staticmethod
     def tiny() -> "GStaConfig":
@@ -107,7 +124,7 @@ class GStaController:
             return FREEZE_RESET
         if self.last_reset is not None and k - self.last_reset < c.wait:
             return FREEZE_CLEAR
-        return FREEZE_UPDATE
+        return FREEZE_CLEAR if c.freeze_strategy == "none" else FREEZE_UPDATE
 
     def lr_xyz_at(self, k: int) -> float:
         """xyz learning rate for iteration k: the plateau schedule under GSta,

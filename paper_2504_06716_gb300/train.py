@@ -64,6 +64,8 @@ class Trainer:
         self.calibrated = False
         self.events: list[tuple[int, str, float]] = []
         self.k = 0
+        self.active_iters = 0  # sum over iterations of the unfrozen count (the work freezing saves)
+        self._act_now = None   # that count, re-read after each change of the freeze map or set
         self.capacity_check_every = 100
         self.overflows = 0
         # learned freeze predictor (predictor.py): state, logging, application
@@ -87,6 +89,7 @@ class Trainer:
         if tuning is not None:
             self.model.apply_tuning(tuning)
         self.den_rng = np.random.default_rng(self.seed + 1000)  # the split draws
+        self.freeze_rng = np.random.default_rng(self.seed + 2000)  # draws of the random freeze strategy
         vis = sorted(set(scene.train_views) | set(scene.test_views))
         cap = self.model.measure_capacity([self.cams[v] for v in vis])
         self.view = self.model.make_view(self.cams[scene.train_views[0]], cap)
@@ -240,6 +243,8 @@ class Trainer:
         k = self.k
         m, c = self.model, self.ctrl
         mode = c.freeze_mode(k)
+        if mode is not None or self._predictor_due(k):
+            self._act_now = None
         if mode is not None:
             if mode == FREEZE_UPDATE:
                 self._maybe_calibrate(k)
@@ -251,7 +256,7 @@ class Trainer:
                     self._close_shadow_window(ex, er)
                 lib.gs_pred_history(m.n, m.acc_xyz, m.acc_rgb, m.cnt, m.frozen, self.pred_state)
             before = m.frozen.clone() if (self.shadow and mode == FREEZE_UPDATE) else None
-            m.freeze_update(ex, er, mode)
+            self._freeze(ex, er, mode)
             if before is not None:
                 self._track("rule", (m.frozen == 1) & (before == 0))
             if self.log is not None:
@@ -267,6 +272,8 @@ class Trainer:
             self.events.append((k, "psnr", p))
             if stop and allow_early_stop:
                 m.freeze_update(0.0, 0.0, FREEZE_RESET)
+                self._act_now = None
+                self._enter_finetune()
                 self.events.append((k, "early_stop", p))
             elif stop:
                 c.stop_iter, c.finetune_left = None, None
@@ -274,19 +281,53 @@ class Trainer:
         m.retarget(self.view, self.cams[v])
         lrs = list(self.lrs)
         lrs[0] = c.lr_xyz_at(k)
+        if self._act_now is None:
+            self._act_now = int(m.n_active.item())
+        self.active_iters += self._act_now
         m.train_step(self.view, self.targets[v], lrs)
         if self.shadow and self._shadow_sets:
             self._shadow_backward()
         if c.densify_due(k):
             self._densify(k)
+            self._act_now = None
         if c.opacity_reset_due(k):
             m.opacity_reset(float(np.float32(math.log(0.01 / 0.99))))
             self.events.append((k, "opacity_reset", 0.0))
         if c.after_step(k):
             m.freeze_update(0.0, 0.0, FREEZE_RESET)
+            self._act_now = None
+            self._enter_finetune()
         self.k += 1
         if self.k % self.capacity_check_every == 0:
             self.check_capacity()
+
+    def _enter_finetune(self):
+        """Start of the finetuning stage: all Gaussians unfrozen (done by the
+        caller) and, as in Sec. 4.1, the absolute-value opacity."""
+        if self.cfg.abs_opacity_finetune:
+            slope = self.model.to_abs_opacity(lib.GS_MOMENTS_RESCALE if self.cfg.abs_opacity_moments == "rescale"
+                                              else lib.GS_MOMENTS_ZERO)
+            self.lrs = list(self.lrs)
+            if self.cfg.abs_opacity_lr == "slope":  # keep the mean opacity step of an Adam update
+                self.lrs[3] *= slope
+            elif self.cfg.abs_opacity_lr is not None:
+                self.lrs[3] = float(self.cfg.abs_opacity_lr)
+            self.events.append((self.k, "abs_opacity", self.lrs[3]))
+
+    STRATEGIES = {"gsta": lib.GS_FREEZE_RULE, "xyz": lib.GS_FREEZE_XYZ, "random": lib.GS_FREEZE_RANDOM,
+                  "mingrad": lib.GS_FREEZE_MINGRAD}
+
+    def _freeze(self, ex: float, er: float, mode: int):
+        """The freeze-map action: Eq. 4 (gs_freeze_update) or, for an update
+        under an ablation strategy, gs_freeze_select."""
+        m, strategy = self.model, self.cfg.freeze_strategy
+        if mode != FREEZE_UPDATE or strategy == "gsta":
+            m.freeze_update(ex, er, mode)
+            return
+        u = None
+        if strategy == "random":
+            u = torch.from_numpy(self.freeze_rng.random(max(m.n, 1), dtype=np.float32)).to(self.device)
+        m.freeze_select(ex, er, self.STRATEGIES[strategy], self.cfg.freeze_fraction, u)
 
     # ---- densification (Sec. 4.1) ----
     def densify_params(self, k: int) -> lib.GsDensifyParams:
@@ -318,7 +359,9 @@ class Trainer:
 def run(args) -> dict:
     torch.cuda.set_device(0)
     scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
-    cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters, densify=not args.no_densify)
+    cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters, densify=not args.no_densify,
+                     freeze_strategy=args.freeze_strategy, abs_opacity_finetune=not args.no_abs_opacity,
+                     abs_opacity_moments=args.abs_moments, abs_opacity_lr=args.abs_lr)
     tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
     tuning = None
     if args.autotune:
@@ -330,6 +373,7 @@ def run(args) -> dict:
         tr2.fresh_model(tr.tuning)
         tr2.ctrl = GStaController(cfg, tr.lrs[0])
         tr2.k, tr2.calibrated, tr2.eps0, tr2.events, tr2.overflows = 0, False, (cfg.eps0_xyz, cfg.eps0_rgb), [], 0
+        tr2.active_iters, tr2._act_now = 0, None
         tr = tr2
     evals = []
     t0 = time.perf_counter()
@@ -344,7 +388,10 @@ def run(args) -> dict:
             t0 = time.perf_counter() - el  # held-out evaluation is not training time
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
-    out = dict(arm=args.arm, calibrate=not args.no_calibrate, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(), evals=evals,
+    out = dict(arm=args.arm, freeze_strategy=cfg.freeze_strategy, abs_opacity_finetune=cfg.abs_opacity_finetune,
+               abs_opacity_moments=cfg.abs_opacity_moments,
+               calibrate=not args.no_calibrate, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(),
+               active_gaussian_iters=tr.active_iters, evals=evals,
                events=[e for e in tr.events if e[1] != "densify"], n_final=tr.model.n,
                densify=[e for e in tr.events if e[1] == "densify"][::10], eps0=tr.eps0, tuning=tuning, overflows=tr.overflows,
                final_capacity=tr.view.capacity, device_flags=lib.gs_get_device_error())
@@ -365,6 +412,15 @@ def main():
     ap.add_argument("--no-calibrate", action="store_true", help="use the paper's initial thresholds as they are")
     ap.add_argument("--no-densify", action="store_true", help="keep the Gaussian set fixed")
     ap.add_argument("--tune-after", type=int, default=300, help="iterations trained before tuning (then restarted)")
+    ap.add_argument("--freeze-strategy", choices=["gsta", "xyz", "random", "mingrad", "none"], default="gsta",
+                    help="freeze rule or an ablation variant (Sec. 5, Table 3)")
+    ap.add_argument("--no-abs-opacity", action="store_true",
+                    help="keep the sigmoid opacity activation in the finetuning stage")
+    ap.add_argument("--abs-moments", choices=["zero", "rescale"], default="zero",
+                    help="the opacity's Adam moments when the finetuning stage switches to |x|")
+    ap.add_argument("--abs-lr", default=None,
+                    help="opacity learning rate under |x|: a number, 'slope' (the rate times the mean o (1 - o) at"
+                         " the switch) or unset (unchanged)")
     args = ap.parse_args()
     print(json.dumps(run(args)))
 
