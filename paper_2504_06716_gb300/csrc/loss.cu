@@ -30,6 +30,15 @@ __device__ __forceinline__ float ld_or_zero(const float *p, int y, int x, int H,
     return (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(p + (int64_t)y * W + x) : 0.f;
 }
 
+// Each pass gives a thread kV = 4 consecutive outputs, so that it reads the
+// kV + 10 inputs of their windows once from shared memory instead of
+// 11 per output. Horizontal items: (row of the haloed tile, 4 columns);
+// vertical items: (column, 4 rows), one per thread, a warp on 32 columns.
+constexpr int kV = 4;
+constexpr int kSeg = kT / kV;              // 8 segments per row / column
+constexpr int kHItems = kE * kSeg;         // 336 horizontal items
+static_assert(kT * kSeg == kLossThreads, "one vertical item per thread");
+
 __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restrict__ img,
                                                           const float *__restrict__ gt, int H, int W, Win win,
                                                           float *__restrict__ mapA, float *__restrict__ mapB,
@@ -47,53 +56,75 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
         sy[r][c] = ld_or_zero(y, oy + r, ox + c, H, W);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kE * kT; k += kLossThreads) {
-        int r = k / kT, c = k % kT;
-        float a = 0.f, b = 0.f, aa = 0.f, bb = 0.f, ab = 0.f;
+    // horizontal: window sums of x, y, x^2, y^2, x y along the rows
+    for (int it = threadIdx.x; it < kHItems; it += kLossThreads) {
+        const int r = it / kSeg, c0 = (it % kSeg) * kV;
+        float a[kV], b[kV], aa[kV], bb[kV], ab[kV];
 #pragma unroll
-        for (int q = 0; q < 11; ++q) {
-            float xv = sx[r][c + q], yv = sy[r][c + q], w = win.w[q];
-            a += w * xv;
-            b += w * yv;
-            aa += w * xv * xv;
-            bb += w * yv * yv;
-            ab += w * xv * yv;
+        for (int v = 0; v < kV; ++v) a[v] = b[v] = aa[v] = bb[v] = ab[v] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kV + 10; ++q) {
+            const float xv = sx[r][c0 + q], yv = sy[r][c0 + q];
+            const float xx = xv * xv, yy = yv * yv, xy = xv * yv;
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int t = q - v;  // tap of input q in output v's window
+                if (t >= 0 && t < 11) {
+                    const float w = win.w[t];
+                    a[v] += w * xv; b[v] += w * yv; aa[v] += w * xx; bb[v] += w * yy; ab[v] += w * xy;
+                }
+            }
         }
-        h[0][r][c] = a; h[1][r][c] = b; h[2][r][c] = aa; h[3][r][c] = bb; h[4][r][c] = ab;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            h[0][r][c0 + v] = a[v]; h[1][r][c0 + v] = b[v]; h[2][r][c0 + v] = aa[v];
+            h[3][r][c0 + v] = bb[v]; h[4][r][c0 + v] = ab[v];
+        }
     }
     __syncthreads();
+    // vertical, then the SSIM map and its partial derivatives
     const float C1 = 0.01f * 0.01f, C2 = 0.03f * 0.03f;
     float l1 = 0.f, ss = 0.f;
-    for (int k = threadIdx.x; k < kT * kT; k += kLossThreads) {
-        int r = k / kT, c = k % kT;
-        int gy = blockIdx.y * kT + r, gx = blockIdx.x * kT + c;
-        if (gy >= H || gx >= W) continue;
-        float mx = 0.f, my = 0.f, xx = 0.f, yy = 0.f, xy = 0.f;
+    {
+        const int c = threadIdx.x % kT, r0 = (threadIdx.x / kT) * kV;
+        float mx[kV], my[kV], xx[kV], yy[kV], xy[kV];
 #pragma unroll
-        for (int q = 0; q < 11; ++q) {
-            float w = win.w[q];
-            mx += w * h[0][r + q][c];
-            my += w * h[1][r + q][c];
-            xx += w * h[2][r + q][c];
-            yy += w * h[3][r + q][c];
-            xy += w * h[4][r + q][c];
+        for (int v = 0; v < kV; ++v) mx[v] = my[v] = xx[v] = yy[v] = xy[v] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kV + 10; ++q) {
+            const float h0 = h[0][r0 + q][c], h1 = h[1][r0 + q][c], h2 = h[2][r0 + q][c];
+            const float h3 = h[3][r0 + q][c], h4 = h[4][r0 + q][c];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int t = q - v;
+                if (t >= 0 && t < 11) {
+                    const float w = win.w[t];
+                    mx[v] += w * h0; my[v] += w * h1; xx[v] += w * h2; yy[v] += w * h3; xy[v] += w * h4;
+                }
+            }
         }
-        float vx = xx - mx * mx, vy = yy - my * my, cxy = xy - mx * my;
-        float n1 = 2.f * mx * my + C1, n2 = 2.f * cxy + C2;
-        float d1 = mx * mx + my * my + C1, d2 = vx + vy + C2;
-        // d1 >= C1 and d2 >= C2 (up to rounding of the variances): the map and
-        // its partials are formed without dividing by n1 or n2, which may be
-        // zero (m / n2 = n1 / (d1 d2), m / n1 = n2 / (d1 d2))
-        const float q = 1.f / (d1 * d2);
-        const float m_n1 = n2 * q, m_n2 = n1 * q;
-        const float m = n1 * m_n1;
-        ss += m;
-        l1 += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
-        // partials of the map value w.r.t. the window means of x, x^2 and x*y
-        int64_t p = ch * HW + (int64_t)gy * W + gx;
-        mapA[p] = 2.f * my * (m_n1 - m_n2) + 2.f * mx * m * (1.f / d2 - 1.f / d1);
-        mapB[p] = -m / d2;
-        mapC[p] = 2.f * m_n2;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int r = r0 + v;
+            const int gy = blockIdx.y * kT + r, gx = blockIdx.x * kT + c;
+            if (gy >= H || gx >= W) continue;
+            const float vx = xx[v] - mx[v] * mx[v], vy = yy[v] - my[v] * my[v], cxy = xy[v] - mx[v] * my[v];
+            const float n1 = 2.f * mx[v] * my[v] + C1, n2 = 2.f * cxy + C2;
+            const float d1 = mx[v] * mx[v] + my[v] * my[v] + C1, d2 = vx + vy + C2;
+            // d1 >= C1 and d2 >= C2 (up to rounding of the variances): the map
+            // and its partials are formed without dividing by n1 or n2, which
+            // may be zero (m / n2 = n1 / (d1 d2), m / n1 = n2 / (d1 d2))
+            const float qd = 1.f / (d1 * d2);
+            const float m_n1 = n2 * qd, m_n2 = n1 * qd;
+            const float m = n1 * m_n1;
+            ss += m;
+            l1 += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
+            // partials of the map value w.r.t. the window means of x, x^2 and x*y
+            const int64_t p = ch * HW + (int64_t)gy * W + gx;
+            mapA[p] = 2.f * my[v] * (m_n1 - m_n2) + 2.f * mx[v] * m * (1.f / d2 - 1.f / d1);
+            mapB[p] = -m / d2;
+            mapC[p] = 2.f * m_n2;
+        }
     }
     // block sums
 #pragma unroll
@@ -129,37 +160,53 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
         sm[2][r][q] = ld_or_zero(c, oy + r, ox + q, H, W);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kE * kT; k += kLossThreads) {
-        int r = k / kT, q = k % kT;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (int it = threadIdx.x; it < kHItems; it += kLossThreads) {
+        const int r = it / kSeg, c0 = (it % kSeg) * kV;
+        float s0[kV], s1[kV], s2[kV];
 #pragma unroll
-        for (int t = 0; t < 11; ++t) {
-            float w = win.w[t];
-            s0 += w * sm[0][r][q + t];
-            s1 += w * sm[1][r][q + t];
-            s2 += w * sm[2][r][q + t];
+        for (int v = 0; v < kV; ++v) s0[v] = s1[v] = s2[v] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kV + 10; ++q) {
+            const float m0 = sm[0][r][c0 + q], m1 = sm[1][r][c0 + q], m2 = sm[2][r][c0 + q];
+#pragma unroll
+            for (int v = 0; v < kV; ++v) {
+                const int t = q - v;
+                if (t >= 0 && t < 11) {
+                    const float w = win.w[t];
+                    s0[v] += w * m0; s1[v] += w * m1; s2[v] += w * m2;
+                }
+            }
         }
-        h[0][r][q] = s0; h[1][r][q] = s1; h[2][r][q] = s2;
+#pragma unroll
+        for (int v = 0; v < kV; ++v) { h[0][r][c0 + v] = s0[v]; h[1][r][c0 + v] = s1[v]; h[2][r][c0 + v] = s2[v]; }
     }
     __syncthreads();
     const float invN = 1.f / (3.f * (float)HW);
-    for (int k = threadIdx.x; k < kT * kT; k += kLossThreads) {
-        int r = k / kT, q = k % kT;
-        int gy = blockIdx.y * kT + r, gx = blockIdx.x * kT + q;
-        if (gy >= H || gx >= W) continue;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    const int cc = threadIdx.x % kT, r0 = (threadIdx.x / kT) * kV;
+    float s0[kV], s1[kV], s2[kV];
 #pragma unroll
-        for (int t = 0; t < 11; ++t) {
-            float w = win.w[t];
-            s0 += w * h[0][r + t][q];
-            s1 += w * h[1][r + t][q];
-            s2 += w * h[2][r + t][q];
+    for (int v = 0; v < kV; ++v) s0[v] = s1[v] = s2[v] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kV + 10; ++q) {
+        const float h0 = h[0][r0 + q][cc], h1 = h[1][r0 + q][cc], h2 = h[2][r0 + q][cc];
+#pragma unroll
+        for (int v = 0; v < kV; ++v) {
+            const int t = q - v;
+            if (t >= 0 && t < 11) {
+                const float w = win.w[t];
+                s0[v] += w * h0; s1[v] += w * h1; s2[v] += w * h2;
+            }
         }
-        int64_t p = ch * HW + (int64_t)gy * W + gx;
-        float xv = __ldg(img + p), yv = __ldg(gt + p);
-        float d = xv - yv;
-        float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-        float dssim = s0 + 2.f * xv * s1 + yv * s2;
+    }
+#pragma unroll
+    for (int v = 0; v < kV; ++v) {
+        const int gy = blockIdx.y * kT + r0 + v, gx = blockIdx.x * kT + cc;
+        if (gy >= H || gx >= W) continue;
+        const int64_t p = ch * HW + (int64_t)gy * W + gx;
+        const float xv = __ldg(img + p), yv = __ldg(gt + p);
+        const float d = xv - yv;
+        const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        const float dssim = s0[v] + 2.f * xv * s1[v] + yv * s2[v];
         const float g = ((1.f - lambda) * sg - lambda * dssim) * invN;
         if (!isfinite(g)) atomicOr(&g_loss_flags, GS_FLAG_NONFINITE);
         dl[p] = g;

@@ -350,13 +350,48 @@ __device__ __forceinline__ bool tile_hit(const SplatShape &sh, int tile, int x, 
     return false;
 }
 
+// The tiles a splat may be listed in: its 3-sigma rectangle, narrowed to the
+// bounding box of the ellipse q <= tau when that box is provably wide
+// enough. tile_hit evaluates q = a dx^2 + 2 b dx dy + c dy^2 (float32) only
+// at points of a tile's pixel-centre box, and min over dy of q is
+// dx^2 det / c (det = a c - b^2), so q > tau wherever |dx| >= sqrt(tau c /
+// det). The rounding error of q is at most 4 u kappa q (u = 2^-24) with
+// kappa = (a + |b| + c)(a + c) / det >= (|a| dx^2 + 2 |b dx dy| + c dy^2) / q,
+// and det carries a relative error of about 2 u kappa; for kappa <= 1e4 both
+// stay below 0.3%, well inside the 4% that the factor 1.02 on the box's half
+// widths leaves (plus a pixel). Ill-conditioned conics keep the rectangle.
+// So every tile dropped here fails tile_hit: the lists are unchanged.
+__device__ __forceinline__ int cand_rect(const float *splats, uint32_t g, const DevCam &cam, float tau, int &x0,
+                                         int &y0, int &x1, int &y1) {
+    if (!splat_rect(splats, g, cam, x0, y0, x1, y1)) return 0;
+    const float *r = splats + (int64_t)g * kSplat;
+    const float mx = __ldg(r), my = __ldg(r + 1), a = __ldg(r + 2), b = __ldg(r + 3), c = __ldg(r + 4);
+    const float det = a * c - b * b;
+    if (!(tau >= 0.f) || !(det > 0.f) || !(a > 0.f) || !(c > 0.f)) return 1;
+    const float kappa = (a + fabsf(b) + c) * (a + c) / det;
+    if (!(kappa <= 1e4f)) return 1;
+    const float hx = sqrtf(tau * c / det) * 1.02f + 1.f;
+    const float hy = sqrtf(tau * a / det) * 1.02f + 1.f;
+    const float inv = 1.f / (float)cam.tile;  // exact: a power of two
+    x0 = max(x0, (int)floorf((mx - hx) * inv));
+    x1 = min(x1, (int)floorf((mx + hx) * inv) + 1);
+    y0 = max(y0, (int)floorf((my - hy) * inv));
+    y1 = min(y1, (int)floorf((my + hy) * inv) + 1);
+    if (x0 >= x1 || y0 >= y1) {
+        x0 = y0 = x1 = y1 = 0;
+        return 0;
+    }
+    return 1;
+}
+
 // Per block of depth-ordered Gaussians: its super-tile entries (part_s).
 // Only splats some tile can list (255 o >= 1) get entries.
 __device__ __forceinline__ unsigned long long super_entries(const float *splats, uint32_t g, const DevCam &cam,
                                                             int &sx0, int &sy0, int &sx1, int &sy1) {
     int x0, y0, x1, y1;
-    if (!(tile_tau(__ldg(splats + (int64_t)g * kSplat + 5)) >= 0.f)) return 0ull;
-    if (!splat_rect(splats, g, cam, x0, y0, x1, y1)) return 0ull;
+    const float tau = tile_tau(__ldg(splats + (int64_t)g * kSplat + 5));
+    if (!(tau >= 0.f)) return 0ull;
+    if (!cand_rect(splats, g, cam, tau, x0, y0, x1, y1)) return 0ull;
     return (unsigned long long)super_rect(x0, y0, x1, y1, sx0, sy0, sx1, sy1);
 }
 
@@ -395,7 +430,7 @@ __global__ void __launch_bounds__(256) k_count_exact(const float *__restrict__ s
         const uint32_t g = order[k];
         int x0, y0, x1, y1;
         const SplatShape sh = splat_shape(splats, g);
-        if (sh.tau < 0.f || !splat_rect(splats, g, cam, x0, y0, x1, y1)) continue;
+        if (sh.tau < 0.f || !cand_rect(splats, g, cam, sh.tau, x0, y0, x1, y1)) continue;
         for (int y = y0; y < y1; ++y)
             for (int x = x0; x < x1; ++x) mine += tile_hit(sh, cam.tile, x, y) ? 1ull : 0ull;
     }
@@ -522,14 +557,12 @@ __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float
     int lx0 = 0, ly0 = 0, w = 0, h = 0;
     SplatShape sh{};
     int x0, y0, x1, y1;
-    if (valid && splat_rect(splats, cx.g, cam, x0, y0, x1, y1)) {
-        sh = splat_shape(splats, cx.g);
-        if (sh.tau >= 0.f) {
-            lx0 = max(x0 - cx.sx * kSuper, 0);
-            ly0 = max(y0 - cx.sy * kSuper, 0);
-            w = max(min(x1 - cx.sx * kSuper, kSuper) - lx0, 0);
-            h = max(min(y1 - cx.sy * kSuper, kSuper) - ly0, 0);
-        }
+    if (valid) sh = splat_shape(splats, cx.g);
+    if (valid && sh.tau >= 0.f && cand_rect(splats, cx.g, cam, sh.tau, x0, y0, x1, y1)) {
+        lx0 = max(x0 - cx.sx * kSuper, 0);
+        ly0 = max(y0 - cx.sy * kSuper, 0);
+        w = max(min(x1 - cx.sx * kSuper, kSuper) - lx0, 0);
+        h = max(min(y1 - cx.sy * kSuper, kSuper) - ly0, 0);
     }
     const int cnt = w * h;
     sc.shape[2 * threadIdx.x] = make_float4(sh.mx, sh.my, sh.a, sh.b);

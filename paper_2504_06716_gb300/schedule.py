@@ -78,13 +78,14 @@ class GStaConfig:
     # finetune with the absolute-value opacity activation instead of the
     # sigmoid (Sec. 4.1, the trick taken from Taming 3DGS)
     abs_opacity_finetune: bool = True
-    # the opacity's Adam moments at that switch: "zero" restarts them,
-    # "rescale" carries them over to the new parameterisation
-    abs_opacity_moments: str = "zero"
-    # opacity learning rate under |x|: None keeps the training rate (0.025);
-    # "slope" scales it by the mean o (1 - o) at the switch, so that an Adam
-    # step moves opacities by as much on average as it did through the sigmoid
-    abs_opacity_lr: float | str | None = None
+    # the opacity's Adam moments at that switch: "rescale" carries them over
+    # to the new parameterisation, "zero" restarts them
+    abs_opacity_moments: str = "rescale"
+    # opacity learning rate under |x|: "slope" scales the training rate by the
+    # mean o (1 - o) at the switch, so that an Adam step moves opacities by
+    # as much on average as it did through the sigmoid; None keeps 0.025; a
+    # number sets it
+    abs_opacity_lr: float | str | None = "slope"
 
     @staticmethod
     def tiny() -> "GStaConfig":

@@ -361,7 +361,9 @@ def run(args) -> dict:
     scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
     cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters, densify=not args.no_densify,
                      freeze_strategy=args.freeze_strategy, abs_opacity_finetune=not args.no_abs_opacity,
-                     abs_opacity_moments=args.abs_moments, abs_opacity_lr=args.abs_lr)
+                     abs_opacity_moments=args.abs_moments,
+                     abs_opacity_lr=None if args.abs_lr == "same" else
+                     ("slope" if args.abs_lr == "slope" else float(args.abs_lr)))
     tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
     tuning = None
     if args.autotune:
@@ -416,11 +418,11 @@ def main():
                     help="freeze rule or an ablation variant (Sec. 5, Table 3)")
     ap.add_argument("--no-abs-opacity", action="store_true",
                     help="keep the sigmoid opacity activation in the finetuning stage")
-    ap.add_argument("--abs-moments", choices=["zero", "rescale"], default="zero",
+    ap.add_argument("--abs-moments", choices=["zero", "rescale"], default="rescale",
                     help="the opacity's Adam moments when the finetuning stage switches to |x|")
-    ap.add_argument("--abs-lr", default=None,
-                    help="opacity learning rate under |x|: a number, 'slope' (the rate times the mean o (1 - o) at"
-                         " the switch) or unset (unchanged)")
+    ap.add_argument("--abs-lr", default="slope",
+                    help="opacity learning rate under |x|: 'slope' (the rate times the mean o (1 - o) at the"
+                         " switch), 'same' (unchanged) or a number")
     args = ap.parse_args()
     print(json.dumps(run(args)))
 

@@ -184,6 +184,53 @@ def test_sort_ties_keep_index_order():
     assert np.array_equal(ranges, want_ranges)
 
 
+@pytest.mark.parametrize("tile", [8, 16])
+def test_sort_extreme_conics(tile):
+    """Splats from needle-thin to round, at every orientation and opacities
+    down to the listing floor: the lists (built from candidate tiles the
+    conic's ellipse bounds) equal the oracle's, which tests every tile of the
+    3-sigma rectangle."""
+    g = np.random.default_rng(11)
+    n = 6000
+    W, H = 400, 260
+    rec = np.zeros((n, 12), np.float32)
+    rec[:, 0] = g.uniform(-30, W + 30, n)
+    rec[:, 1] = g.uniform(-30, H + 30, n)
+    rec[:, 9] = g.uniform(1.0, 9.0, n).astype(np.float32)
+    # 2-D covariance with eigenvalues l1 >= l2 >= 0.3 (the dilation), condition up to 1e5
+    l2 = g.uniform(0.3, 4.0, n)
+    l1 = l2 * np.exp(g.uniform(0, np.log(1e5), n))
+    l1 = np.minimum(l1, 80.0 ** 2)
+    th = g.uniform(0, np.pi, n)
+    cth, sth = np.cos(th), np.sin(th)
+    sxx = l1 * cth * cth + l2 * sth * sth
+    syy = l1 * sth * sth + l2 * cth * cth
+    sxy = (l1 - l2) * cth * sth
+    det = sxx * syy - sxy * sxy
+    rec[:, 2] = syy / det
+    rec[:, 3] = -sxy / det
+    rec[:, 4] = sxx / det
+    rec[:, 5] = np.exp(g.uniform(np.log(1 / 255.0), 0.0, n)).astype(np.float32)
+    rad = np.ceil(3 * np.sqrt(l1)).astype(np.int32)
+    cam = synth.pinhole(W, H, 60.0, (0, -3, 0.5))
+    ocam, gcam = pu.cameras(cam, tile=tile)
+    rec[:, 10] = rad.view(np.float32)
+    tx, ty = (W + tile - 1) // tile, (H + tile - 1) // tile
+    x0 = np.clip(np.floor((rec[:, 0] - rad) / tile), 0, None)
+    x1 = np.clip(np.floor((rec[:, 0] + rad) / tile), None, tx - 1)
+    y0 = np.clip(np.floor((rec[:, 1] - rad) / tile), 0, None)
+    y1 = np.clip(np.floor((rec[:, 1] + rad) / tile), None, ty - 1)
+    tt = np.where((x0 <= x1) & (y0 <= y1), (x1 - x0 + 1) * (y1 - y0 + 1), 0).astype(np.int32)
+    rad[tt == 0] = 0
+    rec[:, 10] = rad.view(np.float32)
+    rec[:, 11] = tt.view(np.float32)
+    want_vals, want_ranges = _oracle_sort(rec, ocam)
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam)
+    assert flags == 0 and Pn == len(want_vals) > 1000
+    assert np.array_equal(vals[:Pn], want_vals)
+    assert np.array_equal(ranges, want_ranges)
+
+
 def test_sort_empty_input():
     P = np.zeros((300, 59))
     P[:, 2] = -50.0  # behind the camera
