@@ -39,21 +39,59 @@ constexpr int kSeg = kT / kV;              // 8 segments per row / column
 constexpr int kHItems = kE * kSeg;         // 336 horizontal items
 static_assert(kT * kSeg == kLossThreads, "one vertical item per thread");
 
+// The loss from the per-block partial sums (L1 sum, SSIM sum), by the last
+// block to finish: every thread sums a fixed stride of them in double, then a
+// fixed-shape tree, so the result does not depend on the block order.
+__device__ void loss_from_parts(const float2 *part, int nparts, int64_t N, float lambda, float *loss,
+                                double *scratch /* shared, 2 * kLossThreads */) {
+    double *r1 = scratch, *r2 = scratch + kLossThreads;
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += kLossThreads) {
+        const float2 v = __ldcg(part + k);
+        a += (double)v.x;
+        b += (double)v.y;
+    }
+    r1[threadIdx.x] = a;
+    r2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = kLossThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            r1[threadIdx.x] += r1[threadIdx.x + w];
+            r2[threadIdx.x] += r2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double L = (1.0 - lambda) * r1[0] / (double)N + lambda * (1.0 - r2[0] / (double)N);
+        const float Lf = (float)L;
+        if (!isfinite(Lf)) atomicOr(&g_loss_flags, GS_FLAG_NONFINITE);
+        *loss = Lf;
+    }
+}
+
 __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restrict__ img,
                                                           const float *__restrict__ gt, int H, int W, Win win,
                                                           float *__restrict__ mapA, float *__restrict__ mapB,
-                                                          float *__restrict__ mapC, float2 *__restrict__ part) {
+                                                          float *__restrict__ mapC, float2 *__restrict__ part,
+                                                          unsigned int *__restrict__ done, float lambda,
+                                                          float *__restrict__ loss) {
     __shared__ float sx[kE][kE + 1], sy[kE][kE + 1];
-    __shared__ float h[5][kE][kT + 1];
+    __shared__ __align__(16) float h[5][kE][kT + 1];  // also the last block's reduction scratch
     __shared__ float red[2][kLossThreads / 32];
+    __shared__ bool last;
+    static_assert(sizeof(h) >= 2 * kLossThreads * sizeof(double), "scratch fits");
     const int ch = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const float *x = img + ch * HW, *y = gt + ch * HW;
     const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
-    for (int k = threadIdx.x; k < kE * kE; k += kLossThreads) {
-        int r = k / kE, c = k % kE;
-        sx[r][c] = ld_or_zero(x, oy + r, ox + c, H, W);
-        sy[r][c] = ld_or_zero(y, oy + r, ox + c, H, W);
+#pragma unroll
+    for (int k0 = 0; k0 < kE * kE; k0 += kLossThreads) {  // all loads of a thread in flight together
+        const int k = k0 + (int)threadIdx.x;
+        if (k < kE * kE) {
+            int r = k / kE, c = k % kE;
+            sx[r][c] = ld_or_zero(x, oy + r, ox + c, H, W);
+            sy[r][c] = ld_or_zero(y, oy + r, ox + c, H, W);
+        }
     }
     __syncthreads();
     // horizontal: window sums of x, y, x^2, y^2, x y along the rows
@@ -134,11 +172,19 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
     }
     if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = l1; red[1][threadIdx.x >> 5] = ss; }
     __syncthreads();
+    const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
     if (threadIdx.x == 0) {
         float a = 0.f, b = 0.f;
         for (int w = 0; w < kLossThreads / 32; ++w) { a += red[0][w]; b += red[1][w]; }
         int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
         part[blk] = make_float2(a, b);
+        __threadfence();  // the partial is visible before this block is counted
+        last = atomicAdd(done, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        loss_from_parts(part, (int)nblk, 3 * HW, lambda, loss, reinterpret_cast<double *>(&h[0][0][0]));
     }
 }
 
@@ -153,11 +199,15 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
     const int64_t HW = (int64_t)H * W;
     const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
     const float *a = mapA + ch * HW, *b = mapB + ch * HW, *c = mapC + ch * HW;
-    for (int k = threadIdx.x; k < kE * kE; k += kLossThreads) {
-        int r = k / kE, q = k % kE;
-        sm[0][r][q] = ld_or_zero(a, oy + r, ox + q, H, W);
-        sm[1][r][q] = ld_or_zero(b, oy + r, ox + q, H, W);
-        sm[2][r][q] = ld_or_zero(c, oy + r, ox + q, H, W);
+#pragma unroll
+    for (int k0 = 0; k0 < kE * kE; k0 += kLossThreads) {
+        const int k = k0 + (int)threadIdx.x;
+        if (k < kE * kE) {
+            int r = k / kE, q = k % kE;
+            sm[0][r][q] = ld_or_zero(a, oy + r, ox + q, H, W);
+            sm[1][r][q] = ld_or_zero(b, oy + r, ox + q, H, W);
+            sm[2][r][q] = ld_or_zero(c, oy + r, ox + q, H, W);
+        }
     }
     __syncthreads();
     for (int it = threadIdx.x; it < kHItems; it += kLossThreads) {
@@ -210,32 +260,6 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
         const float g = ((1.f - lambda) * sg - lambda * dssim) * invN;
         if (!isfinite(g)) atomicOr(&g_loss_flags, GS_FLAG_NONFINITE);
         dl[p] = g;
-    }
-}
-
-__global__ void __launch_bounds__(1024) k_loss_final(const float2 *__restrict__ part, int nparts, int64_t N,
-                                                     float lambda, float *__restrict__ loss) {
-    __shared__ double r1[32], r2[32];
-    double a = 0.0, b = 0.0;
-    for (int k = threadIdx.x; k < nparts; k += 1024) {
-        float2 v = part[k];
-        a += (double)v.x;
-        b += (double)v.y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(kFull, a, o);
-        b += __shfl_xor_sync(kFull, b, o);
-    }
-    if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = a; r2[threadIdx.x >> 5] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double l1 = 0.0, ss = 0.0;
-        for (int w = 0; w < 32; ++w) { l1 += r1[w]; ss += r2[w]; }
-        double L = (1.0 - lambda) * l1 / (double)N + lambda * (1.0 - ss / (double)N);
-        float Lf = (float)L;
-        if (!isfinite(Lf)) atomicOr(&g_loss_flags, GS_FLAG_NONFINITE);
-        *loss = Lf;
     }
 }
 
@@ -316,7 +340,7 @@ using namespace gs;
 extern "C" size_t gs_loss_workspace_bytes(int32_t H, int32_t W) {
     if (H <= 0 || W <= 0) return 0;
     size_t maps = 3 * (size_t)3 * H * W * sizeof(float);
-    return align256(maps) + align256(sizeof(float2) * (size_t)loss_grid(H, W).nparts);
+    return align256(maps) + align256(sizeof(float2) * (size_t)loss_grid(H, W).nparts) + 256;
 }
 
 extern "C" int gs_loss(const float *image, const float *gt, int32_t H, int32_t W, float lambda, void *ws,
@@ -330,11 +354,13 @@ extern "C" int gs_loss(const float *image, const float *gt, int32_t H, int32_t W
     float *mapB = mapA + 3 * HW, *mapC = mapB + 3 * HW;
     float2 *part = reinterpret_cast<float2 *>(static_cast<char *>(ws) + align256(9 * (size_t)HW * sizeof(float)));
     LossGrid g = loss_grid(H, W);
+    unsigned int *done = reinterpret_cast<unsigned int *>(reinterpret_cast<char *>(part) +
+                                                          align256(sizeof(float2) * (size_t)g.nparts));
     Win win = make_window();
-    k_ssim_fwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, mapA, mapB, mapC, part);
+    if (cudaMemsetAsync(done, 0, sizeof(unsigned int), s) != cudaSuccess) return GS_ERR_CUDA;
+    k_ssim_fwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, mapA, mapB, mapC, part, done, lambda, loss_dev);
     k_ssim_bwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, lambda, mapA, mapB, mapC, dl_dimage);
-    k_loss_final<<<1, 1024, 0, s>>>(part, g.nparts, 3 * HW, lambda, loss_dev);
-    note_launches(3);
+    note_launches(2);
     return launch_status();
 }
 

@@ -608,6 +608,26 @@ __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float
     if (valid && masks_out) masks_out[e] = cx.mask;
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane i holds row i (bit j =
+// M[i][j]); on return lane j holds column j (bit i = M[i][j]) -- for every
+// slot j at once what __ballot_sync of bit j would give. Swaps the
+// off-diagonal blocks of 16, 8, 4, 2 and 1 bits.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+    const uint32_t m16 = 0x0000FFFFu, m8 = 0x00FF00FFu, m4 = 0x0F0F0F0Fu, m2 = 0x33333333u, m1 = 0x55555555u;
+#define GS_TSTEP(S, M)                                                                  \
+    {                                                                                   \
+        const uint32_t p = __shfl_xor_sync(kFull, x, S);                                \
+        x = (lane & S) ? ((x & ~(M)) | ((p >> S) & (M))) : ((x & (M)) | ((p & (M)) << S)); \
+    }
+    GS_TSTEP(16, m16)
+    GS_TSTEP(8, m8)
+    GS_TSTEP(4, m4)
+    GS_TSTEP(2, m2)
+    GS_TSTEP(1, m1)
+#undef GS_TSTEP
+    return x;
+}
+
 // Global tile id of slot t of super-tile (sx, sy).
 __device__ __forceinline__ int slot_tile(int t, int sx, int sy, int tiles_x) {
     return (sy * kSuper + (t >> 3)) * tiles_x + sx * kSuper + (t & 7);
@@ -694,11 +714,9 @@ __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ spl
         ChunkCtx cx;
         chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, TestScratch{}, masks,
                    nullptr);
-#pragma unroll 8
-        for (int t = 0; t < 64; ++t) {
-            const uint32_t b = __ballot_sync(kFull, (cx.mask >> t) & 1ull);
-            if (lane == 0) ballots[warp][t] = b;
-        }
+        const uint32_t lo = (uint32_t)cx.mask, hi = (uint32_t)(cx.mask >> 32);
+        ballots[warp][lane] = warp_transpose32(lo, lane);
+        ballots[warp][lane + 32] = warp_transpose32(hi, lane);
         {   // entries of each slot in the super-tile's earlier chunks: 4 threads per slot
             const int t = threadIdx.x & 63, q = threadIdx.x >> 6;
             uint32_t n = 0;
@@ -722,12 +740,18 @@ __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ spl
             }
         }
         __syncthreads();
-        // slot by slot, so that a warp's entries of one tile go to consecutive words
-        for (int t = 0; t < 64; ++t) {
-            const uint32_t b = ballots[warp][t];
-            if (b == 0u) continue;  // warp-uniform
+        // An entry's position in tile t's list: the warp's start there plus the
+        // lanes before it that tile t lists. Written slot by slot over the
+        // slots some lane has (a warp's entries of one tile go to consecutive
+        // words) or, when that takes more rounds, each lane over its own slots.
+        const unsigned long long any = ((unsigned long long)__reduce_or_sync(kFull, hi) << 32) |
+                                       __reduce_or_sync(kFull, lo);
+        const int by_slot = __popcll(any), by_lane = (int)__reduce_max_sync(kFull, (unsigned)__popcll(cx.mask));
+        for (unsigned long long u = by_lane < by_slot ? cx.mask : any; u; u &= u - 1ull) {
+            const int t = __ffsll((long long)u) - 1;
             if ((cx.mask >> t) & 1ull) {
-                const unsigned long long pos = base[warp][t] + (unsigned long long)__popc(b & lt);
+                const unsigned long long pos =
+                    base[warp][t] + (unsigned long long)__popc(ballots[warp][t] & lt);
                 if (pos < (unsigned long long)capacity) vals[pos] = cx.g;
             }
         }
