@@ -223,7 +223,12 @@ def gpu_arm(args):
     tuning = None
     if not args.no_autotune:  # rasteriser tile size and launch shapes for this state (autotune.py)
         tr.autotune()
-        tuning = dict(tile=tr.tuning.tile, fwd_ppt_batch=list(tr.tuning.fwd), bwd_ppt_batch=list(tr.tuning.bwd))
+        tuning = dict(tile=tr.tuning.tile, fwd_ppt_batch=list(tr.tuning.fwd), bwd_ppt_batch=list(tr.tuning.bwd),
+                      per_tile_ms={str(t): dict(project_sort=round(r["project_sort_ms"], 4),
+                                                fwd=[*r["best_fwd"], round(min(r["fwd_ms"].values()), 4)],
+                                                bwd=[*r["best_bwd"], round(min(r["bwd_ms"].values()), 4)],
+                                                total=round(r["total_ms"], 4))
+                                   for t, r in tr.tuning.table.items()})
     for _ in range(args.warmup):
         tr.iteration(allow_early_stop=False)
     torch.cuda.synchronize()
@@ -294,7 +299,7 @@ def gpu_arm(args):
     ops = OPS_BLENDED_ACTIVE * pc[0] + OPS_BLENDED_FROZEN * pc[1] + OPS_SKIPPED * pc[2]
     achieved = ops / (rb_mean / 1e3) / 1e12
     roofline = dict(bound="alu", kernel="k_raster_bwd", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
-                    frac=achieved / alu_peak, traffic=None,
+                    frac=achieved / alu_peak, traffic=raster_bwd_traffic(),
                     work_per_unit=f"FP32 lane-instructions per (pixel, splat) pair over each pixel's list up to its"
                                   f" last contributor: {OPS_BLENDED_ACTIVE} blended by an unfrozen splat,"
                                   f" {OPS_BLENDED_FROZEN} by a frozen one, {OPS_SKIPPED} skipped; per launch"
@@ -332,6 +337,35 @@ def gpu_arm(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# DRAM traffic of the dominant kernel per launch, from one ncu capture of this
+# benchmark's own timed launches (dram__bytes_read.sum + dram__bytes_write.sum,
+# averaged over the captured launches; profiles/k_raster_bwd_traffic_surface-1M-1237x822.md
+# gives the command). Valid only for the kernel sources it was taken on: the
+# digest of those files is compared at run time and traffic is reported as null
+# once they have changed.
+RASTER_BWD_TRAFFIC = dict(bytes_per_launch=72793344,
+                          sources_sha256="73403abe0a8b42a51e02169cd241f0a75df211a10e5ef9ec962075b769ca0fd1")
+RASTER_BWD_SOURCES = ("paper_2504_06716_gb300/csrc/render.cu", "paper_2504_06716_gb300/csrc/common.cuh")
+
+
+def sources_digest(paths) -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    root = os.path.dirname(os.path.abspath(__file__))
+    for p in paths:
+        with open(os.path.join(root, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def raster_bwd_traffic():
+    t = RASTER_BWD_TRAFFIC
+    if t["bytes_per_launch"] is None or t["sources_sha256"] != sources_digest(RASTER_BWD_SOURCES):
+        return None
+    return t["bytes_per_launch"]
 
 
 # Algorithmic FP32 work of the rasteriser backward per (pixel, splat) pair, counted

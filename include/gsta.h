@@ -115,10 +115,16 @@ int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs_camera *ca
  * which turns capped Gaussians into opaque ones. */
 #define GS_OPACITY_SIGMOID 0
 #define GS_OPACITY_ABS 1
+/* Flag of the same argument (or-ed in): float 59 of each parameter row is the
+ * volume-mask logit m of Sec. 3.3 ("Pruning with Volume Masking"). The hard
+ * mask M = 1[sigmoid(m) > 0.01] (m > logit(0.01) = -4.59512 in float32)
+ * multiplies opacity and scales: a Gaussian with M = 0 is culled. */
+#define GS_VOLUME_MASK 2
 
-/* gs_project with the opacity activation chosen (GS_OPACITY_*); gs_project
- * is this with GS_OPACITY_SIGMOID. Errors as gs_project, and INVALID_ARG for
- * another activation. */
+/* gs_project with the parameterisation chosen: opacity_act is
+ * GS_OPACITY_SIGMOID or GS_OPACITY_ABS, optionally or-ed with GS_VOLUME_MASK;
+ * gs_project is this with GS_OPACITY_SIGMOID. Errors as gs_project, and
+ * INVALID_ARG for other flag bits. */
 int gs_project_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act, const gs_camera *cam,
                   float *splats, gs_stream_t stream);
 
@@ -159,7 +165,7 @@ int gs_render_fwd(const float *splats, const uint32_t *vals, const uint32_t *ran
  * results do not depend on it). NULL selects the built-in default for the
  * camera's tile size. */
 typedef struct {
-    int32_t pixels_per_thread; /* pixels each thread composites: 1 or 2 */
+    int32_t pixels_per_thread; /* pixels each thread composites: 1, 2, or 4 (tiles of 16 and 32) */
     int32_t batch;             /* splats staged per shared-memory batch: 32, 64, 128 or 256 */
 } gs_raster_config;
 
@@ -265,12 +271,19 @@ int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree, const gs_
                          const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, int32_t accumulate,
                          const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream);
 
-/* gs_project_bwd_stats for the opacity activation `opacity_act`
- * (GS_OPACITY_*): dL/dx = dL/dopacity * sigmoid'(x), or * sign(x) (0 at
- * x = 0) under GS_OPACITY_ABS. The other entry points take the sigmoid. */
-int gs_project_bwd_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act, const gs_camera *cam,
-                      const float *splats, const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G,
-                      int32_t accumulate, const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream);
+/* gs_project_bwd_stats for the parameterisation `opacity_act` (as in
+ * gs_project_ex): dL/dx = dL/dopacity * sigmoid'(x), or * sign(x) (0 at
+ * x = 0) under GS_OPACITY_ABS. Under GS_VOLUME_MASK the mask logit's
+ * gradient, G[i][59], is the straight-through one, (dL/dM + mask_loss) *
+ * sigmoid'(m) with dL/dM = dL/dopacity * opacity + sum_b dL/dlog s_b for a
+ * visible Gaussian (0 otherwise), where mask_loss >= 0 is the derivative of
+ * the mask term lambda_m mean_i sigmoid(m_i) of the loss with respect to one
+ * sigmoid(m_i) (lambda_m / N); it reaches every Gaussian of the active list.
+ * The other entry points take the sigmoid and no mask. */
+int gs_project_bwd_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act, float mask_loss,
+                      const gs_camera *cam, const float *splats, const int32_t *act, const int32_t *n_active_dev,
+                      float *grad2d, float *G, int32_t accumulate, const gs_grad_stats *sets, int32_t n_sets,
+                      gs_stream_t stream);
 
 /* gs_raster_bwd followed by gs_project_bwd on the same stream. */
 int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
@@ -284,7 +297,7 @@ int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera 
  * same kernels, enqueued from native code instead of one binding call
  * each. Everything the step touches is described by gs_step (device
  * pointers, sizes, launch shapes); the view's camera, its target image gt
- * [3][H][W] (device), the six group learning rates lr (host, [6]) and the
+ * [3][H][W] (device), the group learning rates lr (host, [n_lr]) and the
  * Adam step (>= 1) are the per-iteration arguments. Returns the first
  * non-OK status of the sequence (nothing after it is enqueued). */
 typedef struct {
@@ -292,7 +305,9 @@ typedef struct {
     float *P, *G, *m, *v, *splats, *grad2d;
     int64_t n;
     int32_t sh_degree;
-    int32_t opacity_act;              /* GS_OPACITY_* */
+    int32_t opacity_act;              /* GS_OPACITY_*, optionally | GS_VOLUME_MASK */
+    float mask_loss;                  /* volume mask: lambda_m / N (see gs_project_bwd_ex) */
+    int32_t n_lr;                     /* learning-rate groups in lr: 6, or 7 (the mask logit); 0 reads as 6 */
     const uint8_t *frozen;            /* [n] or NULL */
     const int32_t *act;               /* unfrozen list [n], its length in n_active_dev [1] */
     const int32_t *n_active_dev;
@@ -321,6 +336,22 @@ typedef struct {
 
 int gs_train_step(const gs_step *s, const gs_camera *cam, const float *gt, const float *lr, int64_t step,
                   gs_stream_t stream);
+
+/* Progressive training and blur (Sec. 3.3, "Progressive Training", "Blur";
+ * Sec. 4.1: resolution from scale 0.175 to 1 and a decaying blur until
+ * iteration 6K). gs_resize_area: src [C][H][W] -> dst [C][H2][W2], the area
+ * average over the same extent of the image plane -- with pixel j spanning
+ * [j - 1/2, j + 1/2), target pixel i covers source [i W / W2 - 1/2,
+ * (i + 1) W / W2 - 1/2) (same in y), each source pixel weighted by its
+ * overlap; the matching camera has fx' = fx W2 / W and cx' = (cx + 1/2) W2 /
+ * W - 1/2. gs_blur: dst = src convolved with a 5 x 5 Gaussian of standard
+ * deviation sigma (pixels), its weights renormalised over the taps inside
+ * the image; a plain copy when sigma < GS_BLUR_SIGMA_MIN. Device pointers,
+ * dst distinct from src. Errors: INVALID_ARG, CUDA. */
+#define GS_BLUR_SIGMA_MIN 0.1f
+int gs_resize_area(const float *src, int32_t C, int32_t W, int32_t H, float *dst, int32_t W2, int32_t H2,
+                   gs_stream_t stream);
+int gs_blur(const float *src, int32_t C, int32_t W, int32_t H, float sigma, float *dst, gs_stream_t stream);
 
 /* Bytes of workspace gs_freeze_update needs for n Gaussians. */
 size_t gs_freeze_workspace_bytes(int64_t n);
@@ -401,6 +432,12 @@ int gs_freeze_update_noalloc(int64_t n, float *acc_xyz, float *acc_rgb, int32_t 
 int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
                    const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps, int64_t step,
                    gs_stream_t stream);
+
+/* gs_adam_masked with n_groups (6 or 7) learning rates: a seventh, lr[6],
+ * is the rate of float 59, the volume-mask logit (0 with six). */
+int gs_adam_masked_groups(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
+                          const int32_t *n_active_dev, const float *lr, int32_t n_groups, float b1, float b2,
+                          float eps, int64_t step, gs_stream_t stream);
 
 /* ---------------------------------------------------------------------
  * Learned freeze predictor. The paper has no learned component: these
@@ -503,6 +540,8 @@ typedef struct {
     int32_t max_screen_radius; /* px (20): larger originals are pruned */
     float log_max_world;     /* log(0.1 extent): larger Gaussians are pruned */
     float log_split_div;     /* log(1.6): children's log-scales are this much smaller */
+    int32_t mask_prune;      /* also prune Gaussians whose volume mask is off ... */
+    float mask_logit_min;    /* ... mask logit (float 59) <= this (logit(0.01)) */
 } gs_densify_params;
 
 /* Bytes of workspace the densification of n Gaussians needs. */
@@ -512,7 +551,8 @@ size_t gs_densify_workspace_bytes(int64_t n);
  * window's statistics: average = acc / cnt over cnt > 0, max_radius may be
  * NULL), candidate = average xyz >= eps_xyz (or, with use_rgb, average rgb
  * >= eps_rgb); clone if its largest log-scale <= log_clone_max, else split;
- * prune when logit < logit_min_opacity, or (prune_big) largest screen radius
+ * prune when logit < logit_min_opacity, or (mask_prune) the volume-mask
+ * logit P[i][59] <= mask_logit_min, or (prune_big) largest screen radius
  * > max_screen_radius (originals only) or largest log-scale > log_max_world
  * (a child's log-scale is smaller by log_split_div). Writes counts_dev [4]
  * (int64, device): surviving originals, surviving clones, surviving children
@@ -548,9 +588,12 @@ int gs_densify_apply(int64_t n, const float *P, const float *m, const float *v, 
                      uint8_t *frozen_out, gs_stream_t stream);
 
 /* 3DGS opacity reset: P[i][10] = min(P[i][10], logit_cap) (logit_cap =
- * logit(0.01)) and the opacity's Adam moments m, v [i][10] set to 0, for all
- * n Gaussians. Errors: INVALID_ARG, CUDA. */
-int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, gs_stream_t stream);
+ * logit(0.01)) and the opacity's Adam moments m, v [i][10] set to 0, for
+ * every Gaussian i < n that is not frozen (frozen [n] may be NULL: all of
+ * them, as 3DGS resets; passing the freeze map leaves frozen Gaussians as
+ * they are, like every other parameter update). Errors: INVALID_ARG, CUDA. */
+int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, const uint8_t *frozen,
+                     gs_stream_t stream);
 
 /* Entry into the absolute-value opacity (Sec. 4.1, finetuning stage): for
  * all i < n, P[i][10] = o = sigmoid(P[i][10]) -- the same expression, in

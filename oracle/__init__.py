@@ -77,7 +77,7 @@ def lib():
             L.or_sh_basis.argtypes = [_dp, _dp]
             L.or_sh_basis_grad.argtypes = [_dp, _dp]
             L.or_project_act.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp,
-                                         _ip, _ip, _dp]
+                                         _dp, _ip, _ip, _dp]
             L.or_sort.argtypes = [_i64, _fp, _fp, _fp, _ip, _fp, _i32, _i32, _i32, _i32, _i64, _up, _up]
             L.or_sort.restype = _i64
             L.or_render.argtypes = [_i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp, _ip, _dp]
@@ -94,8 +94,8 @@ def lib():
                                            _ip, _dp]
             L.or_render_pixels_locked.argtypes = [_i64, _ip, _ip, _i32, _i32, _dp, _dp, _dp, _dp, _dp, _up, _up,
                                                   _i32, _i64, _bp, _dp]
-            L.or_project_bwd_act.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _i32, _bp, _dp, _dp, _dp,
-                                             _dp, _dp, _dp, _dp]
+            L.or_project_bwd_act.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _i32, _dp, ctypes.c_double,
+                                             _bp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
             L.or_adam.argtypes = [_i64, _dp, _dp, _dp, _dp, _bp, _dp, ctypes.c_double, ctypes.c_double,
                                   ctypes.c_double, _i64]
             L.or_freeze_update.argtypes = [_i64, _fp, _fp, _ip, _bp, ctypes.c_float, ctypes.c_float, _i32, _ip]
@@ -140,15 +140,17 @@ def sh_basis_grad(d) -> np.ndarray:
     return out
 
 
-def project(params, cam: Cam, sh_degree: int = 3, smooth: bool = False, opacity_act: int = 0) -> dict:
+def project(params, cam: Cam, sh_degree: int = 3, smooth: bool = False, opacity_act: int = 0, mask=None) -> dict:
     """Per-Gaussian projection (Eq. 1) and SH colour; opacity_act 1: opacity = |x|
-    (the finetuning stage's activation, Sec. 4.1) instead of sigmoid(x)."""
+    (the finetuning stage's activation, Sec. 4.1) instead of sigmoid(x); mask:
+    volume-mask logits [n] (Sec. 3.3), a Gaussian whose hard mask is 0 culled."""
     P = _c(params, np.float64)
+    mk = None if mask is None else _c(mask, np.float64)
     n = P.shape[0]
     out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), depth=np.zeros(n), opacity=np.zeros(n),
                rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32), rect=np.zeros((n, 4), np.int32),
                margin=np.zeros(n))
-    lib().or_project_act(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), int(opacity_act),
+    lib().or_project_act(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), int(opacity_act), _p(mk, _dp),
                          _p(out["mean2d"], _dp),
                      _p(out["conic"], _dp), _p(out["depth"], _dp), _p(out["opacity"], _dp), _p(out["rgb"], _dp),
                      _p(out["radius"], _ip), _p(out["rect"], _ip), _p(out["margin"], _dp))
@@ -309,18 +311,23 @@ def render_bwd(proj: dict, vals, ranges, cam: Cam, dl_dimage, frozen=None, amb=N
 
 
 def project_bwd(params, cam: Cam, grads2d: dict, frozen=None, sh_degree: int = 3, smooth: bool = False,
-                opacity_act: int = 0) -> dict:
+                opacity_act: int = 0, mask=None, mask_loss: float = 0.0) -> dict:
+    """Chain rule to the 59 parameters (G), freeze statistics, and with volume
+    masks the straight-through gradient of each mask logit (G_mask)."""
     P = _c(params, np.float64)
     n = P.shape[0]
     G = np.zeros((n, N_PARAMS))
     xn = np.zeros(n)
     rn = np.zeros(n)
     fr = None if frozen is None else _c(frozen, np.uint8)
-    lib().or_project_bwd_act(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), int(opacity_act), _p(fr, _bp),
-                         _p(_c(grads2d["d_mean2d"], np.float64), _dp), _p(_c(grads2d["d_conic"], np.float64), _dp),
-                         _p(_c(grads2d["d_opacity"], np.float64), _dp), _p(_c(grads2d["d_rgb"], np.float64), _dp),
-                         _p(G, _dp), _p(xn, _dp), _p(rn, _dp))
-    return dict(G=G, xyz_norm=xn, rgb_norm=rn)
+    mk = None if mask is None else _c(mask, np.float64)
+    gm = np.zeros(n)
+    lib().or_project_bwd_act(n, _p(P, _dp), ctypes.byref(cam), sh_degree, int(smooth), int(opacity_act), _p(mk, _dp),
+                             float(mask_loss), _p(fr, _bp),
+                             _p(_c(grads2d["d_mean2d"], np.float64), _dp), _p(_c(grads2d["d_conic"], np.float64), _dp),
+                             _p(_c(grads2d["d_opacity"], np.float64), _dp), _p(_c(grads2d["d_rgb"], np.float64), _dp),
+                             _p(G, _dp), _p(gm, _dp), _p(xn, _dp), _p(rn, _dp))
+    return dict(G=G, G_mask=gm, xyz_norm=xn, rgb_norm=rn)
 
 
 def adam(P, G, M, V, frozen, lr, step: int, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15):

@@ -8,7 +8,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   values.
 * Sec. 4.1 freeze cadence: the map is updated every 250 iterations inside
   [3000, min(10000, early-stop iteration)), reset every 2000 iterations, and
-  not updated for 500 iterations after a reset.
+  not updated for 500 iterations after a reset. Freezing is active only in
+  that window, so when it closes at 10000 without an early stop (which
+  resets the map itself) the map is reset.
 * Eq. 7 early stop: PSNR on the training subset every 1000 iterations; stop
   when the last two PSNR changes are both below 0.2 dB.
 * Sec. 3.2.3 plateau schedule on the xyz learning rate: decay 0.75,
@@ -62,6 +64,8 @@ def freeze_action(k: int, cfg: ScheduleConfig, last_reset: int | None, stop_iter
     if k % cfg.every != 0:
         return None
     end = cfg.window_end if stop_iter is None else min(cfg.window_end, stop_iter)
+    if stop_iter is None and k == cfg.window_end:
+        return "reset"  # the window closes without an early stop: nothing stays frozen
     if k >= end:
         return None
     if k < cfg.warmup:

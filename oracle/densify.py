@@ -55,6 +55,8 @@ class DensifyParams:
     max_screen_radius: int    # 20 px
     log_max_world: float      # log(0.1 extent)
     log_split_div: float      # log(1.6)
+    mask_prune: bool = False  # also prune where the volume mask is off (Sec. 3.3) ...
+    mask_logit_min: float = -4.595119850134589  # ... mask logit (column 59) <= logit(0.01)
 
 
 def f32(x):
@@ -87,6 +89,8 @@ def decisions(P, dacc_xyz, dacc_rgb, dcnt, max_radius, prm: DensifyParams) -> di
     split = cand & ~clone
     child_smax = (smax - f32(prm.log_split_div)).astype(np.float32)
     low_op = P32[:, 10] < f32(prm.logit_min_opacity)
+    if prm.mask_prune:  # volume mask off: sigmoid(m) <= 0.01 (P carries the mask logit in column 59)
+        low_op = low_op | ~(P32[:, 59] > f32(prm.mask_logit_min))
     if prm.prune_big:
         big_world = smax > f32(prm.log_max_world)
         big_child = child_smax > f32(prm.log_max_world)
@@ -143,14 +147,17 @@ def carry(values, src, kind, new_value=0):
     return out
 
 
-def opacity_reset(P, M, V, logit_cap):
+def opacity_reset(P, M, V, logit_cap, frozen=None):
     """3DGS opacity reset: opacity <- min(opacity, 0.01) (here in the logit
     domain, logit_cap = logit(0.01) as float32) and the opacity's Adam moments
-    set to zero. In place."""
+    set to zero, In place, for every Gaussian that is not frozen: a frozen
+    Gaussian takes no parameter change until the map releases it (reading of
+    Sec. 3.2.4's "no update for frozen Gaussians" for the reset of Sec. 4.1)."""
     cap = f32(logit_cap)
-    P[:, 10] = np.minimum(np.asarray(P[:, 10], np.float32), cap)
-    M[:, 10] = 0.0
-    V[:, 10] = 0.0
+    sel = np.ones(P.shape[0], bool) if frozen is None else (np.asarray(frozen) == 0)
+    P[sel, 10] = np.minimum(np.asarray(P[sel, 10], np.float32), cap)
+    M[sel, 10] = 0.0
+    V[sel, 10] = 0.0
 
 
 def opacity_to_abs(P, M, V, rescale: bool = False):

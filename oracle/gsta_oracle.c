@@ -313,10 +313,15 @@ typedef struct {
  *  - colour = max(0, sum_c k_c Y_c(d) + 1/2), d = (mu - campos)/|mu - campos|.
  * smooth != 0 drops every cut-off except the near plane (for finite
  * differences): no radius, all tiles, no colour clamp. */
+/* Volume mask (Sec. 3.3): hard mask 1[sigmoid(m) > 0.01], decided on the
+ * float32 logit against logit(0.01) rounded to float32. */
+static int mask_on(double m) { return (float)m > (float)(-4.595119850134589); }
+
 static void project_one(const double *p, const or_camera *cam, int sh_degree, int smooth, int opacity_act,
-                        gauss_fwd *g) {
+                        const double *mask, gauss_fwd *g) {
     memset(g, 0, sizeof(*g));
     g->margin = INFINITY;
+    if (mask && !mask_on(*mask)) return; /* mask 0: opacity and scales 0, culled */
     const double *mu = p;
     for (int i = 0; i < 3; ++i)
         g->tc[i] = cam->R[3 * i] * mu[0] + cam->R[3 * i + 1] * mu[1] + cam->R[3 * i + 2] * mu[2] + cam->t[i];
@@ -405,11 +410,11 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
  * world units for the near plane) of a value that decides an integer
  * (radius, tile rectangle, culling) to its threshold. */
 void or_project_act(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
-                    int32_t opacity_act, double *mean2d, double *conic, double *depth, double *opacity, double *rgb,
-                    int32_t *radius, int32_t *rect, double *margin) {
+                    int32_t opacity_act, const double *mask, double *mean2d, double *conic, double *depth,
+                    double *opacity, double *rgb, int32_t *radius, int32_t *rect, double *margin) {
     for (int64_t i = 0; i < n; ++i) {
         gauss_fwd g;
-        project_one(P + NP * i, cam, sh_degree, smooth, opacity_act, &g);
+        project_one(P + NP * i, cam, sh_degree, smooth, opacity_act, mask ? mask + i : NULL, &g);
         if (margin) margin[i] = g.margin;
         if (!g.visible) {
             mean2d[2 * i] = mean2d[2 * i + 1] = 0;
@@ -433,7 +438,7 @@ void or_project_act(int64_t n, const double *P, const or_camera *cam, int32_t sh
 void or_project(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
                 double *mean2d, double *conic, double *depth, double *opacity, double *rgb,
                 int32_t *radius, int32_t *rect, double *margin) {
-    or_project_act(n, P, cam, sh_degree, smooth, 0, mean2d, conic, depth, opacity, rgb, radius, rect, margin);
+    or_project_act(n, P, cam, sh_degree, smooth, 0, NULL, mean2d, conic, depth, opacity, rgb, radius, rect, margin);
 }
 
 /* ------------------------------------------------------------------ */
@@ -956,19 +961,31 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
 /*   rgb_norm = |dL/d k_0| over the 3 channels (the diffuse colour).       */
 /* G is [n][59]; rows of frozen or culled Gaussians are zero.             */
 /* ------------------------------------------------------------------ */
+/* mask (n or NULL): volume-mask logits; then G_mask [n] receives the
+ * straight-through gradient of each logit, (dL/dM + mask_loss) sigmoid'(m)
+ * with dL/dM = dL/dopacity * opacity + sum_b dL/dlog s_b for a visible
+ * Gaussian and 0 otherwise (mask_loss = lambda_m / N, the mask term's
+ * derivative), 0 for frozen ones. */
 void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
-                        int32_t opacity_act, const uint8_t *frozen, const double *d_mean2d, const double *d_conic,
-                        const double *d_opacity, const double *d_rgb, double *G, double *xyz_norm,
-                        double *rgb_norm) {
+                        int32_t opacity_act, const double *mask, double mask_loss, const uint8_t *frozen,
+                        const double *d_mean2d, const double *d_conic, const double *d_opacity, const double *d_rgb,
+                        double *G, double *G_mask, double *xyz_norm, double *rgb_norm) {
     memset(G, 0, sizeof(double) * NP * n);
     for (int64_t i = 0; i < n; ++i) {
         if (xyz_norm) xyz_norm[i] = 0;
         if (rgb_norm) rgb_norm[i] = 0;
+        if (G_mask) G_mask[i] = 0;
         if (frozen && frozen[i]) continue;
         const double *p = P + NP * i;
         double *gp = G + NP * i;
+        double mslope = 0;
+        if (mask) {
+            double sm = 1.0 / (1.0 + exp(-mask[i]));
+            mslope = sm * (1.0 - sm);
+            if (G_mask) G_mask[i] = mask_loss * mslope;
+        }
         gauss_fwd g;
-        project_one(p, cam, sh_degree, smooth, opacity_act, &g);
+        project_one(p, cam, sh_degree, smooth, opacity_act, mask ? mask + i : NULL, &g);
         if (!g.visible) continue;
         const double *dm = d_mean2d + 2 * i, *dq = d_conic + 3 * i, *dc = d_rgb + 3 * i;
 
@@ -1049,14 +1066,19 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
             xyz_norm[i] = sqrt(ex * ex + ey * ey);
         }
         if (rgb_norm) rgb_norm[i] = sqrt(gp[11] * gp[11] + gp[12] * gp[12] + gp[13] * gp[13]);
+        if (mask && G_mask) {
+            /* o' = M o and s' = M s at M = 1: dL/dM = dL/do' o + sum_b dL/ds'_b s_b */
+            double dM = d_opacity[i] * g.opacity + gp[3] + gp[4] + gp[5];
+            G_mask[i] = (dM + mask_loss) * mslope;
+        }
     }
 }
 
 void or_project_bwd(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
                     const uint8_t *frozen, const double *d_mean2d, const double *d_conic, const double *d_opacity,
                     const double *d_rgb, double *G, double *xyz_norm, double *rgb_norm) {
-    or_project_bwd_act(n, P, cam, sh_degree, smooth, 0, frozen, d_mean2d, d_conic, d_opacity, d_rgb, G, xyz_norm,
-                       rgb_norm);
+    or_project_bwd_act(n, P, cam, sh_degree, smooth, 0, NULL, 0.0, frozen, d_mean2d, d_conic, d_opacity, d_rgb, G,
+                       NULL, xyz_norm, rgb_norm);
 }
 
 /* ------------------------------------------------------------------ */

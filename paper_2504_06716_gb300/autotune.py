@@ -1,7 +1,7 @@
 """Autotuner for the rasteriser launch shape.
 
 Times, on the caller's own model and views, every tile size (8, 16, 32) with
-every pixels-per-thread (1, 2) and batch size (32, 64, 128, 256) of the two
+every pixels-per-thread (1, 2, 4 where a tile fills whole warps) and batch size (32, 64, 128, 256) of the two
 rasteriser kernels, and picks the tile size whose projection + sort + best
 forward + best backward is fastest. Results depend only on timing: every
 shape computes the same image and, up to atomic reordering, the same
@@ -48,12 +48,14 @@ def retile(cam: lib.GsCamera, tile: int) -> lib.GsCamera:
     return c
 
 
-def tune(model, cams, targets, tiles=(8, 16, 32), ppts=(1, 2), batches=(32, 64, 128, 256), reps: int = 3,
+def tune(model, cams, targets, tiles=(8, 16, 32), ppts=(1, 2, 4), batches=(32, 64, 128, 256), reps: int = 3,
          n_views: int = 2) -> RasterTuning:
     """``cams``/``targets``: a few representative views (camera, target image)."""
     table = {}
     best = None
+    all_ppts = ppts
     for tile in tiles:
+        ppts = [p for p in all_ppts if tile * tile // p >= 32]  # whole warps per tile
         views = [retile(c, tile) for c in cams[:n_views]]
         cap = model.measure_capacity(views)
         v = model.make_view(views[0], cap)

@@ -378,14 +378,16 @@ def _time(fn, reps: int) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def tune(bt: BatchTrainer, tiles=(8, 16, 32), ppts=(1, 2), batches=(32, 64, 128, 256), reps: int = 3) -> dict:
+def tune(bt: BatchTrainer, tiles=(8, 16, 32), ppts=(1, 2, 4), batches=(32, 64, 128, 256), reps: int = 3) -> dict:
     """Pick the tile size (8/16/32) and the (pixels per thread, splats per
     shared-memory batch) of the two persistent launches by timing them on the
     trainer's own scenes, for view group 0. Tile size moves work between the
     sort and the rasteriser, so the choice minimises projection + sort + best
     forward + best backward. Runs real training steps (one per tile)."""
     table, best = {}, None
+    all_ppts = ppts
     for tile in tiles:
+        ppts = [p for p in all_ppts if tile * tile // p >= 32]  # whole warps per tile
         bt.set_tile(tile)
         bt.step("batched")  # fills every buffer for group 0 (and advances training one step)
         tbl, n_jobs = bt.job_tables[0]

@@ -47,11 +47,11 @@ extern "C" int gs_train_step(const gs_step *s, const gs_camera *cam, const float
     if (st == GS_OK && s->bwd_events[1] && cudaEventRecord(static_cast<cudaEvent_t>(s->bwd_events[1]), cs) != cudaSuccess)
         st = GS_ERR_CUDA;
     if (st == GS_OK)
-        st = gs_project_bwd_ex(s->P, s->n, s->sh_degree, s->opacity_act, cam, s->splats, s->act, s->n_active_dev,
-                               s->grad2d, s->G, 0, s->stats, s->n_stats, stream);
+        st = gs_project_bwd_ex(s->P, s->n, s->sh_degree, s->opacity_act, s->mask_loss, cam, s->splats, s->act,
+                               s->n_active_dev, s->grad2d, s->G, 0, s->stats, s->n_stats, stream);
     if (st == GS_OK)
-        st = gs_adam_masked(s->P, s->G, s->m, s->v, s->n, s->act, s->n_active_dev, lr, s->b1, s->b2, s->eps, step,
-                            stream);
+        st = gs_adam_masked_groups(s->P, s->G, s->m, s->v, s->n, s->act, s->n_active_dev, lr,
+                                   s->n_lr ? s->n_lr : 6, s->b1, s->b2, s->eps, step, stream);
     return st;
 }
 

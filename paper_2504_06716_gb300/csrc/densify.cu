@@ -41,7 +41,8 @@ __device__ __forceinline__ uint8_t den_flags(const float *__restrict__ P, const 
     const float smax = fmaxf(fmaxf(r[3], r[4]), r[5]);
     const bool clone = cand && smax <= p.log_clone_max;
     const bool split = cand && !clone;
-    const bool low = r[10] < p.logit_min_opacity;
+    // low opacity, or a volume mask that is off (its logit at most logit(0.01))
+    const bool low = r[10] < p.logit_min_opacity || (p.mask_prune && !(r[59] > p.mask_logit_min));
     bool big_world = false, big_child = false, big_screen = false;
     if (p.prune_big) {
         big_world = smax > p.log_max_world;
@@ -227,9 +228,9 @@ __global__ void __launch_bounds__(kDB) k_den_apply(int64_t n, const float *__res
 }
 
 __global__ void k_opacity_reset(int64_t n, float *__restrict__ P, float *__restrict__ m, float *__restrict__ v,
-                                float cap) {
+                                float cap, const uint8_t *__restrict__ frozen) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || (frozen && frozen[i])) return;
     P[i * kRow + 10] = fminf(P[i * kRow + 10], cap);
     m[i * kRow + 10] = 0.f;
     v[i * kRow + 10] = 0.f;
@@ -353,11 +354,12 @@ extern "C" int gs_densify_apply(int64_t n, const float *P, const float *m, const
     return launch_status();
 }
 
-extern "C" int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, gs_stream_t stream) {
+extern "C" int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, const uint8_t *frozen,
+                                gs_stream_t stream) {
     if (n < 0) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !m || !v) return GS_ERR_INVALID_ARG;
-    k_opacity_reset<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(n, P, m, v, logit_cap);
+    k_opacity_reset<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(n, P, m, v, logit_cap, frozen);
     note_launches(1);
     return launch_status();
 }

@@ -387,10 +387,10 @@ extern "C" int gs_freeze_select(int64_t n, float *acc_xyz, float *acc_rgb, int32
     return launch_status();
 }
 
-extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
-                              const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
-                              int64_t step, gs_stream_t stream) {
-    if (n < 0 || step < 1 || !lr || !n_active_dev) return GS_ERR_INVALID_ARG;
+extern "C" int gs_adam_masked_groups(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
+                                     const int32_t *n_active_dev, const float *lr, int32_t n_groups, float b1,
+                                     float b2, float eps, int64_t step, gs_stream_t stream) {
+    if (n < 0 || step < 1 || !lr || !n_active_dev || (n_groups != 6 && n_groups != 7)) return GS_ERR_INVALID_ARG;
     if (!(b1 >= 0.f && b1 < 1.f) || !(b2 >= 0.f && b2 < 1.f) || !(eps >= 0.f)) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !G || !m || !v || !act) return GS_ERR_INVALID_ARG;
@@ -402,6 +402,7 @@ extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int6
                                      5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5,
                                      5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, -1};
     for (int f = 0; f < 64; ++f) a.lr[f] = group_of[f] >= 0 ? lr[group_of[f]] : 0.f;
+    if (n_groups == 7) a.lr[59] = lr[6];  // the volume-mask logit
     double bc1 = 1.0 - pow((double)b1, (double)step), bc2 = 1.0 - pow((double)b2, (double)step);
     a.b1 = b1;
     a.b2 = b2;
@@ -415,6 +416,12 @@ extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int6
     k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a, nullptr, nullptr);
     note_launches(1);
     return launch_status();
+}
+
+extern "C" int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
+                              const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps,
+                              int64_t step, gs_stream_t stream) {
+    return gs_adam_masked_groups(P, G, m, v, n, act, n_active_dev, lr, 6, b1, b2, eps, step, stream);
 }
 
 extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,

@@ -175,14 +175,24 @@ __device__ __forceinline__ float opacity_slope(float x, int abs_act) {
     return o * (1.f - o);
 }
 
-__global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P, int64_t n, int deg, int abs_act,
+// Volume mask (Sec. 3.3, "Pruning with Volume Masking"): float 59 of a row is
+// the mask logit m; the hard mask is 1[sigmoid(m) > 0.01], i.e. m > logit(0.01).
+// A Gaussian whose mask is 0 has zero opacity and zero scale: it is culled.
+constexpr float kMaskLogitMin = -4.59511985f;  // logit(0.01) in float32
+
+__device__ __forceinline__ bool masked_off(const float *__restrict__ P, int64_t i, int flags) {
+    return (flags & GS_VOLUME_MASK) && !(__ldg(P + i * kRow + 59) > kMaskLogitMin);
+}
+
+__global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P, int64_t n, int deg, int flags,
                                                      DevCam cam, float *__restrict__ out) {
+    const int abs_act = flags & GS_OPACITY_ABS;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float4 *row = reinterpret_cast<const float4 *>(P + i * kRow);
     float4 r0 = __ldg(row), r1 = __ldg(row + 1), r2 = __ldg(row + 2);
     Geo g;
-    if (!geometry(r0, r1, r2, cam, g)) { write_culled(out, i); return; }
+    if (masked_off(P, i, flags) || !geometry(r0, r1, r2, cam, g)) { write_culled(out, i); return; }
     float iz = 1.f / g.tz;
     float mean_x = cam.fx * g.tx * iz + cam.cx;
     float mean_y = cam.fy * g.ty * iz + cam.cy;
@@ -238,21 +248,35 @@ struct StatSets {
 
 // Backward of the projection for act[0 .. *n_active). See gs_project_bwd;
 // with ACC the gradient rows are added to G instead of written.
-template <bool ACC>
-__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, int abs_act, DevCam cam,
-                                                     const float *__restrict__ splats, const int32_t *__restrict__ act,
+// One instance for both modes (ACC a run-time flag), so that the row added
+// under ACC is bit for bit the row written without it.
+__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, int flags, float mask_loss,
+                                                     DevCam cam, const float *__restrict__ splats,
+                                                     const int32_t *__restrict__ act,
                                                      const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
-                                                     float *__restrict__ G, StatSets st) {
+                                                     float *__restrict__ G, StatSets st, int ACC) {
+    const int abs_act = flags & GS_OPACITY_ABS;
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= *n_active) return;
     const int64_t i = act[k];
     float4 *gout = reinterpret_cast<float4 *>(G + i * kRow);
     const int radius = __float_as_int(__ldg(splats + i * kSplat + 10));
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // volume mask: sigmoid'(m), the straight-through derivative of the hard mask
+    float mslope = 0.f;
+    if (flags & GS_VOLUME_MASK) {
+        const float sm = opacity_sigmoid(__ldg(P + i * kRow + 59));
+        mslope = sm * (1.f - sm);
+    }
     if (radius <= 0) {
         if (!ACC) {
 #pragma unroll
             for (int c = 0; c < 16; ++c) gout[c] = z4;
+        }
+        if (mslope != 0.f) {  // only the mask term of the loss reaches it
+            float *g59 = G + i * kRow + 59;
+            const float gm = mask_loss * mslope;
+            *g59 = ACC ? __fadd_rn(*g59, gm) : gm;
         }
         return;
     }
@@ -401,6 +425,12 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
     for (int f = 0; f < 48; ++f) grow[11 + f] = gsh[f];
 #pragma unroll
     for (int f = 59; f < 64; ++f) grow[f] = 0.f;
+    if (flags & GS_VOLUME_MASK) {
+        // o' = M o and s' = M s with the hard mask M = 1 here: dL/dM =
+        // dL/do' o + sum_b dL/ds'_b s_b = dop o + sum_b dL/dlog s_b
+        const float dM = dop * opacity_of(r2.z, abs_act) + dls[0] + dls[1] + dls[2];
+        grow[59] = (dM + mask_loss) * mslope;
+    }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
         float4 v = make_float4(grow[4 * c], grow[4 * c + 1], grow[4 * c + 2], grow[4 * c + 3]);
@@ -429,10 +459,12 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
 
 using namespace gs;
 
+static bool flags_ok(int32_t flags) { return (flags & ~(GS_OPACITY_ABS | GS_VOLUME_MASK)) == 0; }
+
 extern "C" int gs_project_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act,
                              const gs_camera *cam, float *splats, gs_stream_t stream) {
     if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam)) return GS_ERR_INVALID_ARG;
-    if (opacity_act != GS_OPACITY_SIGMOID && opacity_act != GS_OPACITY_ABS) return GS_ERR_INVALID_ARG;
+    if (!flags_ok(opacity_act)) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !splats) return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(splats)) & 15) return GS_ERR_INVALID_ARG;
@@ -448,10 +480,11 @@ extern "C" int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs
 }
 
 static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act,
-                       const gs_camera *cam, const float *splats, const int32_t *act, const int32_t *n_active_dev,
-                       float *grad2d, float *G, const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream) {
+                       float mask_loss, const gs_camera *cam, const float *splats, const int32_t *act,
+                       const int32_t *n_active_dev, float *grad2d, float *G, const gs_grad_stats *sets,
+                       int32_t n_sets, gs_stream_t stream) {
     if (n < 0 || sh_degree < 0 || sh_degree > 3 || !camera_ok(cam) || n_sets < 0 || n_sets > 2 ||
-        (n_sets > 0 && !sets) || (opacity_act != GS_OPACITY_SIGMOID && opacity_act != GS_OPACITY_ABS))
+        (n_sets > 0 && !sets) || !flags_ok(opacity_act) || !(mask_loss >= 0.f))
         return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
     if (!P || !splats || !act || !n_active_dev || !grad2d || !G) return GS_ERR_INVALID_ARG;
@@ -468,12 +501,8 @@ static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, i
         st.maxr[k] = sets[k].max_radius;
     }
     const DevCam dc = make_cam(cam);
-    if (acc)
-        k_project_bwd<true><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, dc, splats,
-                                                                             act, n_active_dev, grad2d, G, st);
-    else
-        k_project_bwd<false><<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, dc, splats,
-                                                                              act, n_active_dev, grad2d, G, st);
+    k_project_bwd<<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, mask_loss, dc, splats,
+                                                                    act, n_active_dev, grad2d, G, st, acc ? 1 : 0);
     note_launches(1);
     return launch_status();
 }
@@ -484,7 +513,7 @@ static int project_bwd_one(bool acc, const float *P, int64_t n, int32_t sh_degre
     const bool any_stat = acc_xyz || acc_rgb || cnt, all_stat = acc_xyz && acc_rgb && cnt;
     if (any_stat && !all_stat) return GS_ERR_INVALID_ARG;
     const gs_grad_stats one{acc_xyz, acc_rgb, cnt, nullptr};
-    return project_bwd(acc, P, n, sh_degree, GS_OPACITY_SIGMOID, cam, splats, act, n_active_dev, grad2d, G,
+    return project_bwd(acc, P, n, sh_degree, GS_OPACITY_SIGMOID, 0.f, cam, splats, act, n_active_dev, grad2d, G,
                        all_stat ? &one : nullptr, all_stat ? 1 : 0, stream);
 }
 
@@ -507,14 +536,14 @@ extern "C" int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree
                                     const float *splats, const int32_t *act, const int32_t *n_active_dev,
                                     float *grad2d, float *G, int32_t accumulate, const gs_grad_stats *sets,
                                     int32_t n_sets, gs_stream_t stream) {
-    return project_bwd(accumulate != 0, P, n, sh_degree, GS_OPACITY_SIGMOID, cam, splats, act, n_active_dev, grad2d,
-                       G, sets, n_sets, stream);
+    return project_bwd(accumulate != 0, P, n, sh_degree, GS_OPACITY_SIGMOID, 0.f, cam, splats, act, n_active_dev,
+                       grad2d, G, sets, n_sets, stream);
 }
 
 extern "C" int gs_project_bwd_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act,
-                                 const gs_camera *cam, const float *splats, const int32_t *act,
+                                 float mask_loss, const gs_camera *cam, const float *splats, const int32_t *act,
                                  const int32_t *n_active_dev, float *grad2d, float *G, int32_t accumulate,
                                  const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream) {
-    return project_bwd(accumulate != 0, P, n, sh_degree, opacity_act, cam, splats, act, n_active_dev, grad2d, G, sets,
-                       n_sets, stream);
+    return project_bwd(accumulate != 0, P, n, sh_degree, opacity_act, mask_loss, cam, splats, act, n_active_dev,
+                       grad2d, G, sets, n_sets, stream);
 }

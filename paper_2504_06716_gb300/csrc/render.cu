@@ -497,15 +497,19 @@ int dispatch(int tile, int ppt, int batch, const A &a, cudaStream_t s) {
         case 82: by_batch<8, 2>(batch, a, s); break;
         case 161: by_batch<16, 1>(batch, a, s); break;
         case 162: by_batch<16, 2>(batch, a, s); break;
+        case 164: by_batch<16, 4>(batch, a, s); break;
         case 321: by_batch<32, 1>(batch, a, s); break;
+        case 324: by_batch<32, 4>(batch, a, s); break;
         default: by_batch<32, 2>(batch, a, s); break;
     }
     note_launches(1);
     return launch_status();
 }
 
-inline bool config_ok(const gs_raster_config *c) {
-    return !c || ((c->pixels_per_thread == 1 || c->pixels_per_thread == 2) &&
+// Four pixels per thread only where a tile still fills whole warps (16, 32).
+inline bool config_ok(const gs_raster_config *c, int tile) {
+    return !c || ((c->pixels_per_thread == 1 || c->pixels_per_thread == 2 ||
+                   (c->pixels_per_thread == 4 && tile >= 16)) &&
                   (c->batch == 32 || c->batch == 64 || c->batch == 128 || c->batch == 256));
 }
 
@@ -517,7 +521,8 @@ using namespace gs;
 extern "C" int gs_render_fwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
                                  const gs_camera *cam, const gs_raster_config *cfg, float *image, float *t_final,
                                  int32_t *n_last, gs_stream_t stream) {
-    if (!camera_ok(cam) || !config_ok(cfg) || !ranges || !image || !t_final || !n_last) return GS_ERR_INVALID_ARG;
+    if (!camera_ok(cam) || !config_ok(cfg, cam->tile) || !ranges || !image || !t_final || !n_last)
+        return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
     FwdArgs a{splats, vals, ranges, make_cam(cam), image, t_final, n_last};
     int ppt, batch;
@@ -535,7 +540,7 @@ extern "C" int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, cons
                                  const gs_camera *cam, const gs_raster_config *cfg, const float *t_final,
                                  const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen, float *grad2d,
                                  gs_stream_t stream) {
-    if (!camera_ok(cam) || !config_ok(cfg) || !ranges || !t_final || !n_last || !dl_dimage || !grad2d)
+    if (!camera_ok(cam) || !config_ok(cfg, cam->tile) || !ranges || !t_final || !n_last || !dl_dimage || !grad2d)
         return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
     BwdArgs a{splats, vals, ranges, make_cam(cam), t_final, n_last, dl_dimage, frozen, grad2d};
@@ -553,7 +558,8 @@ extern "C" int gs_raster_bwd(const float *splats, const uint32_t *vals, const ui
 
 static int batch_common(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
                         const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream, bool bwd) {
-    if (!jobs_dev || !queue_dev || n_jobs < 0 || width <= 0 || height <= 0 || !tile_ok(tile) || !config_ok(cfg))
+    if (!jobs_dev || !queue_dev || n_jobs < 0 || width <= 0 || height <= 0 || !tile_ok(tile) ||
+        !config_ok(cfg, tile))
         return GS_ERR_INVALID_ARG;
     if (n_jobs == 0) return GS_OK;
     const int64_t tiles = (int64_t)((width + tile - 1) / tile) * ((height + tile - 1) / tile);

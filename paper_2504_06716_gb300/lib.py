@@ -110,8 +110,11 @@ _SIGS = {
     "gs_opacity_reset": ([_I64, _P, _P, _P, _F32, _P], _I32),
     "gs_opacity_to_abs": ([_I64, _P, _P, _P, _I32, _P, _P], _I32),
     "gs_train_step": ([_P, _P, _P, _P, _I64, _P], _I32),
+    "gs_resize_area": ([_P, _I32, _I32, _I32, _P, _I32, _I32, _P], _I32),
+    "gs_blur": ([_P, _I32, _I32, _I32, _F32, _P, _P], _I32),
     "gs_project_ex": ([_P, _I64, _I32, _I32, _P, _P, _P], _I32),
-    "gs_project_bwd_ex": ([_P, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, _I32, _P, _I32, _P], _I32),
+    "gs_project_bwd_ex": ([_P, _I64, _I32, _I32, _F32, _P, _P, _P, _P, _P, _P, _I32, _P, _I32, _P], _I32),
+    "gs_adam_masked_groups": ([_P, _P, _P, _P, _I64, _P, _P, _P, _I32, _F32, _F32, _F32, _I64, _P], _I32),
     "gs_psnr_workspace_bytes": ([_I32, _I32, _I32], _SZ),
     "gs_psnr": ([_P, _P, _I32, _I32, _I32, _P, _SZ, _P, _P], _I32),
     "gs_get_device_error": ([ctypes.POINTER(ctypes.c_uint32), _P], _I32),
@@ -179,7 +182,7 @@ def gs_project(P, n: int, sh_degree: int, cam: GsCamera, splats, stream=None):
                                            _ptr(splats, torch.float32, "splats"), _stream(stream)))
 
 
-GS_OPACITY_SIGMOID, GS_OPACITY_ABS = 0, 1
+GS_OPACITY_SIGMOID, GS_OPACITY_ABS, GS_VOLUME_MASK = 0, 1, 2
 
 
 def gs_project_ex(P, n: int, sh_degree: int, opacity_act: int, cam: GsCamera, splats, stream=None):
@@ -288,7 +291,8 @@ class GsStep(ctypes.Structure):
     _fields_ = [
         ("P", ctypes.c_void_p), ("G", ctypes.c_void_p), ("m", ctypes.c_void_p), ("v", ctypes.c_void_p),
         ("splats", ctypes.c_void_p), ("grad2d", ctypes.c_void_p), ("n", ctypes.c_int64),
-        ("sh_degree", ctypes.c_int32), ("opacity_act", ctypes.c_int32), ("frozen", ctypes.c_void_p),
+        ("sh_degree", ctypes.c_int32), ("opacity_act", ctypes.c_int32), ("mask_loss", ctypes.c_float),
+        ("n_lr", ctypes.c_int32), ("frozen", ctypes.c_void_p),
         ("act", ctypes.c_void_p), ("n_active_dev", ctypes.c_void_p), ("stats", GsGradStats * 2),
         ("n_stats", ctypes.c_int32), ("sort_ws", ctypes.c_void_p), ("sort_ws_bytes", ctypes.c_size_t),
         ("capacity", ctypes.c_int64), ("vals", ctypes.c_void_p), ("ranges", ctypes.c_void_p),
@@ -302,7 +306,8 @@ class GsStep(ctypes.Structure):
 
 def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: int, frozen, act, n_active, stats,
               sort_ws, capacity: int, vals, ranges, count, image, t_final, n_last, dl, loss_ws, loss, lam: float = 0.2,
-              fwd=None, bwd=None, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15) -> GsStep:
+              fwd=None, bwd=None, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15, mask_loss: float = 0.0,
+              n_lr: int = 6) -> GsStep:
     """A gs_step for gs_train_step (tensors checked here once; the caller keeps them alive)."""
     import torch
 
@@ -311,6 +316,7 @@ def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: i
     s.P, s.G, s.m, s.v = (_ptr(t, f32, k) for t, k in ((P, "P"), (G, "G"), (m, "m"), (v, "v")))
     s.splats, s.grad2d = _ptr(splats, f32, "splats"), _ptr(grad2d, f32, "grad2d")
     s.n, s.sh_degree, s.opacity_act = int(n), int(sh_degree), int(opacity_act)
+    s.mask_loss, s.n_lr = float(mask_loss), int(n_lr)
     s.frozen, s.act, s.n_active_dev = _ptr(frozen, u8, "frozen"), _ptr(act, i32, "act"), _ptr(n_active, i32, "n_active")
     if len(stats) > 2:
         raise ValueError("at most two statistics windows")
@@ -333,9 +339,28 @@ def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: i
 def gs_train_step(step: GsStep, cam: GsCamera, gt, lr, adam_step: int, stream=None):
     import torch
 
-    lr6 = (ctypes.c_float * 6)(*[float(x) for x in lr])
+    if len(lr) != (step.n_lr or 6):
+        raise ValueError(f"gs_train_step wants {step.n_lr or 6} learning rates, got {len(lr)}")
+    lr6 = (ctypes.c_float * len(lr))(*[float(x) for x in lr])
     _check("gs_train_step", load().gs_train_step(ctypes.byref(step), ctypes.byref(cam), _ptr(gt, torch.float32, "gt"),
                                                  lr6, adam_step, _stream(stream)))
+
+
+GS_BLUR_SIGMA_MIN = float(np.float32(0.1))  # gs_blur copies below this (float32 comparison)
+
+
+def gs_resize_area(src, C: int, W: int, H: int, dst, W2: int, H2: int, stream=None):
+    import torch
+
+    _check("gs_resize_area", load().gs_resize_area(_ptr(src, torch.float32, "src"), C, W, H,
+                                                   _ptr(dst, torch.float32, "dst"), W2, H2, _stream(stream)))
+
+
+def gs_blur(src, C: int, W: int, H: int, sigma: float, dst, stream=None):
+    import torch
+
+    _check("gs_blur", load().gs_blur(_ptr(src, torch.float32, "src"), C, W, H, sigma,
+                                     _ptr(dst, torch.float32, "dst"), _stream(stream)))
 
 
 def grad_stats(acc_xyz, acc_rgb, cnt, max_radius=None) -> GsGradStats:
@@ -360,13 +385,13 @@ def gs_project_bwd_stats(P, n: int, sh_degree: int, cam: GsCamera, splats, act, 
 
 
 def gs_project_bwd_ex(P, n: int, sh_degree: int, opacity_act: int, cam: GsCamera, splats, act, n_active, grad2d, G,
-                      accumulate: bool, sets, stream=None):
-    """gs_project_bwd_stats with the opacity activation chosen (GS_OPACITY_*)."""
+                      accumulate: bool, sets, mask_loss: float = 0.0, stream=None):
+    """gs_project_bwd_stats with the parameterisation chosen (GS_OPACITY_* | GS_VOLUME_MASK)."""
     import torch
 
     arr = (GsGradStats * max(len(sets), 1))(*sets)
     _check("gs_project_bwd_ex", load().gs_project_bwd_ex(
-        _ptr(P, torch.float32, "P"), n, sh_degree, opacity_act, ctypes.byref(cam),
+        _ptr(P, torch.float32, "P"), n, sh_degree, opacity_act, mask_loss, ctypes.byref(cam),
         _ptr(splats, torch.float32, "splats"), _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
         _ptr(grad2d, torch.float32, "grad2d"), _ptr(G, torch.float32, "G"), int(bool(accumulate)),
         ctypes.cast(arr, ctypes.c_void_p), len(sets), _stream(stream)))
@@ -376,7 +401,8 @@ class GsDensifyParams(ctypes.Structure):
     _fields_ = [("eps_xyz", ctypes.c_float), ("eps_rgb", ctypes.c_float), ("use_rgb", ctypes.c_int32),
                 ("log_clone_max", ctypes.c_float), ("logit_min_opacity", ctypes.c_float),
                 ("prune_big", ctypes.c_int32), ("max_screen_radius", ctypes.c_int32),
-                ("log_max_world", ctypes.c_float), ("log_split_div", ctypes.c_float)]
+                ("log_max_world", ctypes.c_float), ("log_split_div", ctypes.c_float),
+                ("mask_prune", ctypes.c_int32), ("mask_logit_min", ctypes.c_float)]
 
 
 def gs_densify_workspace_bytes(n: int) -> int:
@@ -419,12 +445,12 @@ def gs_densify_apply(n: int, P, m, v, frozen, carries, prm: GsDensifyParams, z, 
         _ptr(frozen_out, torch.uint8, "frozen_out"), _stream(stream)))
 
 
-def gs_opacity_reset(n: int, P, m, v, logit_cap: float, stream=None):
+def gs_opacity_reset(n: int, P, m, v, logit_cap: float, frozen=None, stream=None):
     import torch
 
     _check("gs_opacity_reset", load().gs_opacity_reset(
         n, _ptr(P, torch.float32, "P"), _ptr(m, torch.float32, "m"), _ptr(v, torch.float32, "v"), logit_cap,
-        _stream(stream)))
+        _ptr(frozen, torch.uint8, "frozen"), _stream(stream)))
 
 
 GS_MOMENTS_ZERO, GS_MOMENTS_RESCALE = 0, 1
@@ -474,6 +500,18 @@ def gs_render_bwd(P, n: int, sh_degree: int, cam: GsCamera, splats, vals, ranges
         _ptr(frozen, torch.uint8, "frozen"), _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"),
         _ptr(grad2d, torch.float32, "grad2d"), _ptr(G, torch.float32, "G"), _ptr(acc_xyz, torch.float32, "acc_xyz"),
         _ptr(acc_rgb, torch.float32, "acc_rgb"), _ptr(cnt, torch.int32, "cnt"), _stream(stream)))
+
+
+def gs_adam_masked_groups(P, G, m, v, n: int, act, n_active, lr, b1: float, b2: float, eps: float, step: int,
+                          stream=None):
+    """gs_adam_masked with len(lr) (6 or 7) group rates; the seventh is the volume-mask logit's."""
+    import torch
+
+    lra = (ctypes.c_float * len(lr))(*[float(x) for x in lr])
+    _check("gs_adam_masked_groups", load().gs_adam_masked_groups(
+        _ptr(P, torch.float32, "P"), _ptr(G, torch.float32, "G"), _ptr(m, torch.float32, "m"),
+        _ptr(v, torch.float32, "v"), n, _ptr(act, torch.int32, "act"), _ptr(n_active, torch.int32, "n_active"), lra,
+        len(lr), b1, b2, eps, step, _stream(stream)))
 
 
 def gs_freeze_workspace_bytes(n: int) -> int:

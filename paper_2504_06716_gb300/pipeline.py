@@ -23,6 +23,17 @@ def default_lrs(scene_extent: float) -> list[float]:
     return [1.6e-4 * scene_extent, 5e-3, 1e-3, 0.025, 2.5e-3, 2.5e-3 / 20.0]
 
 
+def scaled_camera(cam: lib.GsCamera, W2: int, H2: int) -> lib.GsCamera:
+    """The camera of a W2 x H2 image covering the same extent of the image
+    plane (pixel j spans [j - 1/2, j + 1/2)): f' = f r, c' = (c + 1/2) r - 1/2."""
+    c = lib.GsCamera.from_buffer_copy(cam)
+    rx, ry = W2 / cam.width, H2 / cam.height
+    c.width, c.height = int(W2), int(H2)
+    c.fx, c.fy = cam.fx * rx, cam.fy * ry
+    c.cx, c.cy = (cam.cx + 0.5) * rx - 0.5, (cam.cy + 0.5) * ry - 0.5
+    return c
+
+
 def pack_params(p59: np.ndarray, device="cuda") -> torch.Tensor:
     """(N, 59) array -> (N, 64) float32 device tensor with zero padding."""
     n = p59.shape[0]
@@ -67,7 +78,9 @@ class Model:
         self.bwd_cfg = None
         self.generation = 0
         self.den = None  # densification window statistics (enable_densify)
-        self.opacity_act = lib.GS_OPACITY_SIGMOID  # GS_OPACITY_ABS after to_abs_opacity()
+        self.opacity_act = lib.GS_OPACITY_SIGMOID  # GS_OPACITY_ABS after to_abs_opacity(), | GS_VOLUME_MASK
+        self.mask_loss = 0.0  # lambda_m / N while the volume masks learn (set_volume_mask)
+        self.mask_lr = None   # their learning rate (a seventh group), None: no mask
         self.carried: dict[str, torch.Tensor] = {}  # further per-Gaussian state moved by densify
         self._allocate(max(self.n, capacity or 0, 1))
         self.P[: self.n, :59] = torch.from_numpy(np.ascontiguousarray(params59, dtype=np.float32)).to(self.device)
@@ -120,10 +133,20 @@ class Model:
         """One densification and pruning step (gs_densify_plan / gs_densify_apply);
         returns the counts. Restarts the densification window; keeps the freeze
         window's statistics and the carried state of the surviving Gaussians."""
-        if self.opacity_act != lib.GS_OPACITY_SIGMOID:
+        if self.opacity_act & lib.GS_OPACITY_ABS:
             raise RuntimeError("densification thresholds are opacity logits: not under the absolute-value opacity")
-        d, n = self.den, self.n
-        lib.gs_densify_plan(n, self.P, self._den_stats(), prm, d["ws"], d["counts"])
+        prune_only = self.den is None  # no candidates then: the freeze window stands in for the statistics
+        if prune_only:
+            if getattr(self, "_prune", None) is None or self._prune["ws"].numel() < lib.gs_densify_workspace_bytes(
+                    self.cap):
+                self._prune = dict(ws=torch.zeros(lib.gs_densify_workspace_bytes(self.cap), dtype=torch.uint8,
+                                                  device=self.device),
+                                   counts=torch.zeros(4, dtype=torch.int64, device=self.device))
+            d, stats = self._prune, lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt)
+        else:
+            d, stats = self.den, self._den_stats()
+        n = self.n
+        lib.gs_densify_plan(n, self.P, stats, prm, d["ws"], d["counts"])
         kept, clones, children, splits = (int(x) for x in d["counts"].cpu().tolist())
         n_out = kept + clones + children
         z = torch.from_numpy(rng.standard_normal((max(splits, 1), 2, 3)).astype(np.float32)).to(self.device)
@@ -136,10 +159,11 @@ class Model:
         carries = [lib.densify_carry(named[k], out[k]) for k in named]
         lib.gs_densify_apply(n, self.P, self.m, self.v, self.frozen, carries, prm, z, d["ws"], cap, P2, m2, v2, fr2)
         if cap != self.cap:  # grown: every other buffer anew
-            self.den = dict(self.den)  # keep enable flag
+            if self.den is not None:
+                self.den = dict(self.den)  # keep enable flag
             self._allocate(cap)
             self.generation += 1
-        else:
+        elif not prune_only:
             for key in ("acc_xyz", "acc_rgb", "cnt", "max_radius"):
                 self.den[key].zero_()
         self.P, self.m, self.v, self.frozen = P2, m2, v2, fr2
@@ -152,10 +176,27 @@ class Model:
                              self.n_active, self.freeze_ws)
         return dict(kept=kept, clones=clones, children=children, splits=splits, n=n_out)
 
+    def prune_masked(self, logit_min: float, rng: np.random.Generator) -> dict:
+        """Remove the Gaussians whose volume mask is off (Sec. 3.3): a
+        densification pass with no candidates and only the mask rule."""
+        inf = float("inf")
+        prm = lib.GsDensifyParams(inf, inf, 0, 0.0, -inf, 0, 2**31 - 1, inf, 0.0, 1, logit_min)
+        return self.densify(prm, rng)
+
+    def set_volume_mask(self, on: bool, learn_lr: float | None = None, loss_weight: float = 0.0):
+        """Volume masks (Sec. 3.3) applied (on) and, with learn_lr, learned with
+        that rate and the mask term loss_weight * mean sigmoid(m)."""
+        self.opacity_act = (self.opacity_act | lib.GS_VOLUME_MASK) if on else (
+            self.opacity_act & ~lib.GS_VOLUME_MASK)
+        self.mask_lr = learn_lr if on else None
+        self.mask_loss = (loss_weight / max(self.n, 1)) if (on and learn_lr) else 0.0
+
     def opacity_reset(self, logit_cap: float):
-        if self.opacity_act != lib.GS_OPACITY_SIGMOID:
+        if self.opacity_act & lib.GS_OPACITY_ABS:
             raise RuntimeError("the opacity reset caps a logit: not under the absolute-value opacity")
-        lib.gs_opacity_reset(self.n, self.P, self.m, self.v, logit_cap)
+        # every Gaussian, frozen or not, as 3DGS resets them (frozen ones
+        # recover once the map releases them: at the next reset of the map)
+        lib.gs_opacity_reset(self.n, self.P, self.m, self.v, logit_cap, None)
 
     # ---- views ----
     def make_view(self, cam: lib.GsCamera, capacity: int, trainable: bool = True) -> View:
@@ -178,8 +219,11 @@ class Model:
         )
 
     def retarget(self, view: View, cam: lib.GsCamera) -> View:
-        """Same buffers, another camera of the same resolution and tile size."""
-        assert (cam.width, cam.height, cam.tile) == (view.cam.width, view.cam.height, view.cam.tile)
+        """Same buffers, another camera with the same tile size and at most the
+        resolution the buffers were made for (a smaller image uses a prefix)."""
+        H0, W0 = view.image.shape[1], view.image.shape[2]
+        assert cam.tile == view.cam.tile and cam.width * cam.height <= W0 * H0
+        assert cam.width <= W0 and cam.height <= H0
         view.cam = cam
         return view
 
@@ -209,18 +253,18 @@ class Model:
             if self.den is not None:
                 sets.append(self._den_stats())
         lib.gs_project_bwd_ex(self.P, self.n, self.sh_degree, self.opacity_act, view.cam, self.splats, self.act,
-                              self.n_active, self.grad2d, self.G, False, sets, stream)
+                              self.n_active, self.grad2d, self.G, False, sets, self.mask_loss, stream)
 
     def to_abs_opacity(self, moments: int = lib.GS_MOMENTS_ZERO, stream=None) -> float:
         """Switch to the absolute-value opacity of the finetuning stage (Sec. 4.1):
         gs_opacity_to_abs keeps every opacity; its Adam moments restart
         (GS_MOMENTS_ZERO) or are carried over (GS_MOMENTS_RESCALE). Returns
         the mean of sigmoid'(x) = o (1 - o) over the Gaussians at the switch."""
-        if self.opacity_act == lib.GS_OPACITY_ABS:
+        if self.opacity_act & lib.GS_OPACITY_ABS:
             return 1.0
         acc = torch.zeros(1, dtype=torch.float32, device=self.device)
         lib.gs_opacity_to_abs(self.n, self.P, self.m, self.v, moments, acc, stream)
-        self.opacity_act = lib.GS_OPACITY_ABS
+        self.opacity_act |= lib.GS_OPACITY_ABS
         return float(acc.item()) / max(self.n, 1)
 
     def apply_tuning(self, tuning):
@@ -229,22 +273,26 @@ class Model:
 
     def adam(self, lrs, b1=0.9, b2=0.999, eps=1e-15, stream=None):
         self.step_count += 1
-        lib.gs_adam_masked(self.P, self.G, self.m, self.v, self.n, self.act, self.n_active, lrs, b1, b2, eps,
-                           self.step_count, stream)
+        lib.gs_adam_masked_groups(self.P, self.G, self.m, self.v, self.n, self.act, self.n_active,
+                                  self._rates(lrs), b1, b2, eps, self.step_count, stream)
+
+    def _rates(self, lrs) -> list:
+        """The six group rates, and the volume masks' as a seventh while they learn."""
+        return list(lrs) + ([self.mask_lr] if self.mask_lr else [])
 
     def train_step(self, view: View, gt: torch.Tensor, lrs, stream=None):
         """One iteration of Algorithm 1's inner body on the current freeze map:
         gs_train_step, the same kernels as rasterize / loss / backward / adam
         enqueued from native code in one call."""
         self.step_count += 1
-        lib.gs_train_step(self._step_struct(view), view.cam, gt, lrs, self.step_count, stream)
+        lib.gs_train_step(self._step_struct(view), view.cam, gt, self._rates(lrs), self.step_count, stream)
 
     def _step_struct(self, view: View) -> "lib.GsStep":
         """The gs_step of this model and view, rebuilt when a buffer or size changed."""
         den = self.den["acc_xyz"].data_ptr() if self.den is not None else 0
         key = (id(view), view.vals.data_ptr(), view.image.data_ptr(), view.capacity, self.P.data_ptr(),
                self.G.data_ptr(), self.m.data_ptr(), self.frozen.data_ptr(), self.acc_xyz.data_ptr(), den, self.n,
-               self.opacity_act, id(self.fwd_cfg), id(self.bwd_cfg))
+               self.opacity_act, self.mask_loss, bool(self.mask_lr), id(self.fwd_cfg), id(self.bwd_cfg))
         if getattr(self, "_step_key", None) != key:
             stats = [lib.grad_stats(self.acc_xyz, self.acc_rgb, self.cnt)]
             if self.den is not None:
@@ -253,7 +301,7 @@ class Model:
                                        self.sh_degree, self.opacity_act, self.frozen, self.act, self.n_active, stats,
                                        view.sort_ws, view.capacity, view.vals, view.ranges, view.count, view.image,
                                        view.t_final, view.n_last, view.dl, view.loss_ws, view.loss, 0.2, self.fwd_cfg,
-                                       self.bwd_cfg)
+                                       self.bwd_cfg, mask_loss=self.mask_loss, n_lr=7 if self.mask_lr else 6)
             self._step_key = key
         return self._step
 

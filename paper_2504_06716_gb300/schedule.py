@@ -9,7 +9,8 @@ Readings of the paper taken here:
   [3000, min(10000, early-stop iteration)); reset every 2000 iterations and
   left alone for 500 iterations after a reset; the gradient statistics are
   restarted at every 250-iteration boundary, so each update averages the
-  iterations since the previous boundary.
+  iterations since the previous boundary. Freezing is active only in that
+  window: if it closes at 10000 without an early stop, the map is reset.
 * Eq. 7 -- PSNR of a fixed training subset every 1000 iterations while the
   freezing phase lasts; stop when the last two changes are both < 0.2 dB;
   then all Gaussians are unfrozen for a finetuning stage of K_f iterations,
@@ -20,6 +21,7 @@ Readings of the paper taken here:
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import numpy as np
 
@@ -81,6 +83,29 @@ class GStaConfig:
     # the opacity's Adam moments at that switch: "rescale" carries them over
     # to the new parameterisation, "zero" restarts them
     abs_opacity_moments: str = "rescale"
+    # Trick-GS image-space schedules (Sec. 3.3, Sec. 4.1; off in plain GSta):
+    # train on the area-averaged target at scale prog_start rising by a cosine
+    # to full resolution at prog_until; blur the target with a 5x5 Gaussian
+    # whose sigma (pixels) falls by a cosine from blur_sigma0 to 0 at blur_until
+    progressive: bool = False
+    prog_start: float = 0.175
+    prog_until: int = 6000
+    blur: bool = False
+    blur_sigma0: float = 1.0
+    blur_until: int = 6000
+    # Trick-GS volume masks (Sec. 3.3 "Pruning with Volume Masking"; Sec. 4.1:
+    # learned from 1K to 10K, masked Gaussians pruned every 1K): a mask logit
+    # per Gaussian (float 59 of its row), hard mask 1[sigmoid(m) > 0.01] on
+    # opacity and scales, straight-through gradient, loss term
+    # mask_lambda * mean sigmoid(m); rate, weight and start value are the
+    # compact-3DGS method's defaults (readings)
+    volume_mask: bool = False
+    mask_init: float = 2.0
+    mask_lr: float = 0.01
+    mask_lambda: float = 5e-4
+    mask_from: int = 1000
+    mask_until: int = 10000
+    mask_prune_every: int = 1000
     # opacity learning rate under |x|: "slope" scales the training rate by the
     # mean o (1 - o) at the switch, so that an Adam step moves opacities by
     # as much on average as it did through the sigmoid; None keeps 0.025; a
@@ -116,6 +141,8 @@ class GStaController:
         if not c.freezing or self.finetune_left is not None or k % c.every:
             return None
         end = c.window_end if self.stop_iter is None else min(c.window_end, self.stop_iter)
+        if self.stop_iter is None and k == c.window_end:
+            return FREEZE_RESET  # freezing ends with the window: nothing stays frozen
         if k >= end:
             return None
         if k < c.warmup:
@@ -198,6 +225,38 @@ class GStaController:
             self.finetune_left = c.finetune_iters
             return True
         return False
+
+
+def train_resolution(k: int, cfg: GStaConfig, W: int, H: int) -> tuple[int, int]:
+    """Image size at iteration k under the progressive schedule: scale
+    s = s0 + (1 - s0)(1 - cos(pi t)) / 2, t = min(k, K) / K, rounded per axis."""
+    if not cfg.progressive:
+        return W, H
+    t = min(k, cfg.prog_until) / cfg.prog_until
+    sc = cfg.prog_start + (1.0 - cfg.prog_start) * (1.0 - math.cos(math.pi * t)) / 2.0
+    return max(1, int(round(sc * W))), max(1, int(round(sc * H)))
+
+
+def blur_sigma(k: int, cfg: GStaConfig) -> float:
+    """Blur standard deviation (pixels) at iteration k: sigma0 (1 + cos(pi t)) / 2."""
+    if not cfg.blur:
+        return 0.0
+    t = min(k, cfg.blur_until) / cfg.blur_until
+    return cfg.blur_sigma0 * (1.0 + math.cos(math.pi * t)) / 2.0
+
+
+def mask_phase(k: int, cfg: GStaConfig) -> tuple[bool, bool]:
+    """(masks applied, masks learned) at iteration k: applied from mask_from
+    on, learned until mask_until."""
+    if not cfg.volume_mask or k < cfg.mask_from:
+        return False, False
+    return True, k < cfg.mask_until
+
+
+def mask_prune_due(k: int, cfg: GStaConfig) -> bool:
+    """Prune masked-off Gaussians after iteration k: every mask_prune_every in [mask_from, mask_until]."""
+    return (cfg.volume_mask and cfg.mask_from <= k <= cfg.mask_until and k > 0
+            and k % cfg.mask_prune_every == 0)
 
 
 def calibrate_eps0(cfg: GStaConfig, ctrl: GStaController, k: int, acc_xyz: np.ndarray, acc_rgb: np.ndarray,

@@ -27,7 +27,8 @@ import numpy as np
 import torch
 
 from . import autotune, lib, pipeline, synth
-from .schedule import FREEZE_RESET, FREEZE_UPDATE, GStaConfig, GStaController, calibrate_eps0
+from .schedule import (FREEZE_RESET, FREEZE_UPDATE, GStaConfig, GStaController, blur_sigma, calibrate_eps0,
+                       mask_phase, mask_prune_due, train_resolution)
 
 
 class Trainer:
@@ -56,6 +57,8 @@ class Trainer:
         self.fresh_model()
         H, W = self.cams[0].height, self.cams[0].width
         self.psnr_ws = torch.zeros(lib.gs_psnr_workspace_bytes(1, H, W), dtype=torch.uint8, device=self.device)
+        # targets of the progressive / blur schedules (prefixes used at the reduced size)
+        self.sched_buf = [torch.zeros(3 * H * W, dtype=torch.float32, device=self.device) for _ in range(2)]
         self.psnr_out = torch.zeros(1, device=self.device)
         self.lrs = pipeline.default_lrs(extent)
         self.ctrl = GStaController(cfg, self.lrs[0])
@@ -86,6 +89,8 @@ class Trainer:
                                     capacity=int(scene.init.shape[0] * (1.5 if cfg.densify else 1.0)))
         if cfg.densify:
             self.model.enable_densify()
+        if cfg.volume_mask:  # every Gaussian starts with its mask on
+            self.model.P[: self.model.n, 59] = cfg.mask_init
         if tuning is not None:
             self.model.apply_tuning(tuning)
         self.den_rng = np.random.default_rng(self.seed + 1000)  # the split draws
@@ -278,18 +283,29 @@ class Trainer:
             elif stop:
                 c.stop_iter, c.finetune_left = None, None
         v = self.order[k]
-        m.retarget(self.view, self.cams[v])
+        cam, gt = self._scheduled_view(k, v)
+        m.retarget(self.view, cam)
         lrs = list(self.lrs)
         lrs[0] = c.lr_xyz_at(k)
         if self._act_now is None:
             self._act_now = int(m.n_active.item())
         self.active_iters += self._act_now
-        m.train_step(self.view, self.targets[v], lrs)
+        if self.cfg.volume_mask:
+            applied, learned = mask_phase(k, self.cfg)
+            m.set_volume_mask(applied, self.cfg.mask_lr if learned else None, self.cfg.mask_lambda)
+        m.train_step(self.view, gt, lrs)
         if self.shadow and self._shadow_sets:
             self._shadow_backward()
         if c.densify_due(k):
             self._densify(k)
             self._act_now = None
+        if mask_prune_due(k, self.cfg) and c.finetune_left is None:
+            res = m.prune_masked(float(np.float32(math.log(0.01 / 0.99))), self.den_rng)
+            self.events.append((k, "mask_prune", float(res["n"])))
+            self._act_now = None
+            if m.generation != self.generation:
+                self.generation = m.generation
+                self.view = m.make_view(self.view.cam, self.view.capacity)
         if c.opacity_reset_due(k):
             m.opacity_reset(float(np.float32(math.log(0.01 / 0.99))))
             self.events.append((k, "opacity_reset", 0.0))
@@ -300,6 +316,25 @@ class Trainer:
         self.k += 1
         if self.k % self.capacity_check_every == 0:
             self.check_capacity()
+
+    def _scheduled_view(self, k: int, v: int):
+        """Camera and target of view v at iteration k: the full-resolution ones,
+        or under the progressive / blur schedules (Sec. 3.3) the area-averaged
+        target at the scheduled size (gs_resize_area), blurred (gs_blur)."""
+        cam, gt = self.cams[v], self.targets[v]
+        W, H = cam.width, cam.height
+        W2, H2 = train_resolution(k, self.cfg, W, H)
+        sigma = float(np.float32(blur_sigma(k, self.cfg)))
+        if (W2, H2) == (W, H) and sigma < lib.GS_BLUR_SIGMA_MIN:
+            return cam, gt
+        a, b = (t[: 3 * H2 * W2].view(3, H2, W2) for t in self.sched_buf)
+        if (W2, H2) != (W, H):
+            lib.gs_resize_area(gt, 3, W, H, a, W2, H2)
+            cam, gt = pipeline.scaled_camera(cam, W2, H2), a
+        if sigma >= lib.GS_BLUR_SIGMA_MIN:
+            lib.gs_blur(gt, 3, W2, H2, sigma, b)
+            gt = b
+        return cam, gt
 
     def _enter_finetune(self):
         """Start of the finetuning stage: all Gaussians unfrozen (done by the
@@ -363,7 +398,8 @@ def run(args) -> dict:
                      freeze_strategy=args.freeze_strategy, abs_opacity_finetune=not args.no_abs_opacity,
                      abs_opacity_moments=args.abs_moments,
                      abs_opacity_lr=None if args.abs_lr == "same" else
-                     ("slope" if args.abs_lr == "slope" else float(args.abs_lr)))
+                     ("slope" if args.abs_lr == "slope" else float(args.abs_lr)),
+                     progressive=args.trick_gs, blur=args.trick_gs, volume_mask=args.trick_gs or args.volume_mask)
     tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
     tuning = None
     if args.autotune:
@@ -391,6 +427,7 @@ def run(args) -> dict:
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
     out = dict(arm=args.arm, freeze_strategy=cfg.freeze_strategy, abs_opacity_finetune=cfg.abs_opacity_finetune,
+               trick_gs=args.trick_gs,
                abs_opacity_moments=cfg.abs_opacity_moments,
                calibrate=not args.no_calibrate, iters=tr.k, train_s=total, final_heldout_psnr=tr.heldout_psnr(),
                active_gaussian_iters=tr.active_iters, evals=evals,
@@ -420,6 +457,9 @@ def main():
                     help="keep the sigmoid opacity activation in the finetuning stage")
     ap.add_argument("--abs-moments", choices=["zero", "rescale"], default="rescale",
                     help="the opacity's Adam moments when the finetuning stage switches to |x|")
+    ap.add_argument("--trick-gs", action="store_true",
+                    help="progressive resolution and blur of the targets until 6K, volume masks (Sec. 3.3)")
+    ap.add_argument("--volume-mask", action="store_true", help="volume masks only (Sec. 3.3)")
     ap.add_argument("--abs-lr", default="slope",
                     help="opacity learning rate under |x|: 'slope' (the rate times the mean o (1 - o) at the"
                          " switch), 'same' (unchanged) or a number")

@@ -134,7 +134,7 @@ def test_invalid_activation_is_rejected():
     Pt = torch.from_numpy(pu.pack64(P)).to(DEV)
     spl = torch.zeros((100, 12), device=DEV)
     with pytest.raises(lib.GsError):
-        lib.gs_project_ex(Pt, 100, 3, 2, gcam, spl)
+        lib.gs_project_ex(Pt, 100, 3, 4, gcam, spl)  # no such flag
 
 
 def test_training_enters_finetune_with_abs_opacity():

@@ -143,11 +143,16 @@ def test_opacity_reset_matches_oracle():
     P = g.normal(0, 3, (n, 64)).astype(np.float32)
     M, V = g.normal(0, 1, (n, 64)).astype(np.float32), g.uniform(0, 1, (n, 64)).astype(np.float32)
     cap = float(np.float32(D.logit(0.01)))
-    t = [torch.from_numpy(a.copy()).to(DEV) for a in (P, M, V)]
-    lib.gs_opacity_reset(n, t[0], t[1], t[2], cap)
-    D.opacity_reset(P, M, V, cap)
-    assert np.array_equal(t[0].cpu().numpy(), P) and np.array_equal(t[1].cpu().numpy(), M)
-    assert np.array_equal(t[2].cpu().numpy(), V)
+    frozen = (g.uniform(size=n) < 0.3).astype(np.uint8)
+    for fr in (None, frozen):
+        P2, M2, V2 = P.copy(), M.copy(), V.copy()
+        t = [torch.from_numpy(a.copy()).to(DEV) for a in (P2, M2, V2)]
+        lib.gs_opacity_reset(n, t[0], t[1], t[2], cap, None if fr is None else torch.from_numpy(fr).to(DEV))
+        D.opacity_reset(P2, M2, V2, cap, fr)
+        assert np.array_equal(t[0].cpu().numpy(), P2) and np.array_equal(t[1].cpu().numpy(), M2)
+        assert np.array_equal(t[2].cpu().numpy(), V2)
+        if fr is not None:  # frozen rows untouched
+            assert np.array_equal(P2[fr == 1], P[fr == 1]) and np.array_equal(M2[fr == 1], M[fr == 1])
 
 
 def test_projection_backward_updates_two_statistics_windows():

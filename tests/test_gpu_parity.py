@@ -585,7 +585,7 @@ def test_every_launch_shape_gives_the_same_result(tile):
     dlt = torch.from_numpy(st["dl"].astype(np.float32)).to(DEV)
     fr = torch.from_numpy(st["frozen"]).to(DEV)
     ref = None
-    for ppt in (1, 2):
+    for ppt in (1, 2, 4) if tile >= 16 else (1, 2):
         for batch in (32, 64, 128, 256):
             cfg = lib.raster_config(ppt, batch)
             img = torch.zeros((3, H, W), device=DEV)
@@ -603,3 +603,15 @@ def test_every_launch_shape_gives_the_same_result(tile):
             assert np.array_equal(out[2], ref[2])
             good, worst = pu.close(out[3], ref[3], 1e-4, 1e-3 * np.abs(ref[3]).max())
             assert good, (ppt, batch, worst)
+
+
+def test_four_pixels_per_thread_needs_a_16_pixel_tile():
+    st = _stage_inputs("ragged", 8)
+    gcam = st["gcam"]
+    vals = torch.from_numpy(st["vals"].view(np.int32).copy()).to(DEV)
+    ranges = torch.from_numpy(st["ranges"].view(np.int32).copy()).to(DEV)
+    H, W = gcam.height, gcam.width
+    img, tf = torch.zeros((3, H, W), device=DEV), torch.zeros((H, W), device=DEV)
+    nl = torch.zeros((H, W), dtype=torch.int32, device=DEV)
+    with pytest.raises(lib.GsError):
+        lib.gs_render_fwd_cfg(st["spl"], vals, ranges, gcam, lib.raster_config(4, 64), img, tf, nl)

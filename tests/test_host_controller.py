@@ -62,3 +62,15 @@ def test_early_stop_and_plateau_match_oracle():
             break
     else:
         pytest.fail("no early stop")
+
+
+def test_image_schedules_match_oracle():
+    from oracle import image_schedules as IS
+    from paper_2504_06716_gb300.schedule import blur_sigma, train_resolution
+
+    cfg = GStaConfig(progressive=True, blur=True)
+    for k in list(range(0, 6001, 50)) + [6500, 30000]:
+        assert train_resolution(k, cfg, 1237, 822) == IS.size_at(k, 1237, 822)
+        assert blur_sigma(k, cfg) == pytest.approx(IS.sigma_at(k), abs=1e-12)
+    off = GStaConfig()
+    assert train_resolution(0, off, 1237, 822) == (1237, 822) and blur_sigma(0, off) == 0.0

@@ -102,6 +102,12 @@ def test_opacity_reset_caps_and_clears_moments():
     assert P[:, 10].tolist() == [-6.0, np.float32(cap), np.float32(cap)]
     assert not M[:, 10].any() and not V[:, 10].any()
     assert M[:, 9].all() and V[:, 11].all()
+    # frozen Gaussians keep opacity and moments
+    P2 = np.zeros((3, 59), np.float32)
+    P2[:, 10] = [-6.0, -4.0, 3.0]
+    M2, V2 = np.ones((3, 59), np.float32), np.ones((3, 59), np.float32)
+    D.opacity_reset(P2, M2, V2, cap, frozen=np.array([0, 1, 1], np.uint8))
+    assert P2[:, 10].tolist() == [-6.0, -4.0, 3.0] and M2[1:, 10].all() and V2[1:, 10].all()
 
 
 def test_carry_keeps_survivors_and_zeroes_new():
