@@ -353,6 +353,23 @@ int gs_resize_area(const float *src, int32_t C, int32_t W, int32_t H, float *dst
                    gs_stream_t stream);
 int gs_blur(const float *src, int32_t C, int32_t W, int32_t H, float sigma, float *dst, gs_stream_t stream);
 
+/* Significance pruning (Sec. 3.3, "Pruning with Significance of Gaussians",
+ * after LightGaussian; Sec. 4.1: at 4K and 7K). gs_hit_counts ADDS to hits_dev
+ * [n] (uint32), for every pixel of this view, 1 to each Gaussian the pixel
+ * blends (the forward's own decisions up to n_last). gs_significance_mark
+ * scores score_i = hits_i * o_i * (V_i / V_q)^beta with V_i = exp(s_0 + s_1 +
+ * s_2) (float32) and V_q the volume of rank floor(quantile n) - 1 in
+ * ascending (volume, index) order, o the opacity under opacity_act, and sets
+ * mark [n] to 1 for the floor(fraction n) Gaussians of lowest (score, index),
+ * 0 elsewhere (gs_densify_plan's prune_mark). Workspace:
+ * gs_significance_workspace_bytes(n), 256-byte aligned. Errors: INVALID_ARG,
+ * CUDA. */
+int gs_hit_counts(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                  const int32_t *n_last, uint32_t *hits_dev, gs_stream_t stream);
+size_t gs_significance_workspace_bytes(int64_t n);
+int gs_significance_mark(int64_t n, const float *P, const uint32_t *hits, int32_t opacity_act, float beta,
+                         float quantile, float fraction, uint8_t *mark, void *ws, size_t ws_bytes, gs_stream_t stream);
+
 /* Bytes of workspace gs_freeze_update needs for n Gaussians. */
 size_t gs_freeze_workspace_bytes(int64_t n);
 
@@ -542,6 +559,7 @@ typedef struct {
     float log_split_div;     /* log(1.6): children's log-scales are this much smaller */
     int32_t mask_prune;      /* also prune Gaussians whose volume mask is off ... */
     float mask_logit_min;    /* ... mask logit (float 59) <= this (logit(0.01)) */
+    const uint8_t *prune_mark; /* device [n] or NULL: also prune where nonzero (significance) */
 } gs_densify_params;
 
 /* Bytes of workspace the densification of n Gaussians needs. */
@@ -552,7 +570,8 @@ size_t gs_densify_workspace_bytes(int64_t n);
  * NULL), candidate = average xyz >= eps_xyz (or, with use_rgb, average rgb
  * >= eps_rgb); clone if its largest log-scale <= log_clone_max, else split;
  * prune when logit < logit_min_opacity, or (mask_prune) the volume-mask
- * logit P[i][59] <= mask_logit_min, or (prune_big) largest screen radius
+ * logit P[i][59] <= mask_logit_min, or prune_mark[i] != 0, or (prune_big)
+ * largest screen radius
  * > max_screen_radius (originals only) or largest log-scale > log_max_world
  * (a child's log-scale is smaller by log_split_div). Writes counts_dev [4]
  * (int64, device): surviving originals, surviving clones, surviving children

@@ -42,7 +42,8 @@ __device__ __forceinline__ uint8_t den_flags(const float *__restrict__ P, const 
     const bool clone = cand && smax <= p.log_clone_max;
     const bool split = cand && !clone;
     // low opacity, or a volume mask that is off (its logit at most logit(0.01))
-    const bool low = r[10] < p.logit_min_opacity || (p.mask_prune && !(r[59] > p.mask_logit_min));
+    const bool low = r[10] < p.logit_min_opacity || (p.mask_prune && !(r[59] > p.mask_logit_min)) ||
+                     (p.prune_mark && p.prune_mark[i]);
     bool big_world = false, big_child = false, big_screen = false;
     if (p.prune_big) {
         big_world = smax > p.log_max_world;

@@ -203,6 +203,47 @@ __global__ void __launch_bounds__(kFB) k_freeze_mark_strat(int64_t n, float *__r
     if (threadIdx.x == 0) part[blockIdx.x] = c;
 }
 
+// ---- Significance pruning (Sec. 3.3, "Pruning with Significance of
+// Gaussians", after LightGaussian): score_i = hits_i o_i (V_i / V_q)^beta,
+// V_i = exp(s_0 + s_1 + s_2) the product of the scales, V_q the volume of
+// rank floor(q n); the floor(fraction n) lowest (score, index) are marked. ----
+
+// Keys of the volumes (all Gaussians count).
+__global__ void __launch_bounds__(kFB) k_sig_vol_keys(int64_t n, const float *__restrict__ P,
+                                                     unsigned long long *__restrict__ keys, SelState *st) {
+    const int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    if (i < n) {
+        const float *r = P + i * kRow;
+        const float vol = expf(r[3] + r[4] + r[5]);
+        keys[i] = ((unsigned long long)__float_as_uint(vol) << 32) | (unsigned long long)i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->m = (unsigned long long)n;
+}
+
+// Keys of the scores, the volume normaliser read from the first selection.
+__global__ void __launch_bounds__(kFB) k_sig_score_keys(int64_t n, const float *__restrict__ P,
+                                                       const uint32_t *__restrict__ hits, float beta, int abs_act,
+                                                       const SelState *vq, unsigned long long *__restrict__ keys,
+                                                       SelState *st) {
+    const int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    if (i < n) {
+        const float *r = P + i * kRow;
+        const float vol = expf(r[3] + r[4] + r[5]);
+        const float v_q = __uint_as_float((uint32_t)(vq->prefix >> 32));
+        const float o = abs_act ? fabsf(r[10]) : opacity_sigmoid(r[10]);
+        const float v = v_q > 0.f ? powf(vol / v_q, beta) : 1.f;
+        const float score = (float)hits[i] * o * v;
+        keys[i] = ((unsigned long long)__float_as_uint(score) << 32) | (unsigned long long)i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->m = (unsigned long long)n;
+}
+
+__global__ void __launch_bounds__(kFB) k_sig_mark(int64_t n, const unsigned long long *__restrict__ keys,
+                                                 const SelState *st, uint8_t *__restrict__ mark) {
+    const int64_t i = (int64_t)blockIdx.x * kFB + threadIdx.x;
+    if (i < n) mark[i] = (st->k > 0 && keys[i] <= st->prefix) ? 1 : 0;
+}
+
 struct AdamArgs {
     float lr[64];  // per float of a row (group rate; 0 for padding)
     float b1, b2, eps, step_size_scale, inv_sqrt_bc2;
@@ -384,6 +425,68 @@ extern "C" int gs_freeze_select(int64_t n, float *acc_xyz, float *acc_rgb, int32
     k_freeze_scan<<<1, 1024, 0, s>>>(part, nb, n_active_dev);
     if (nb > 0) k_freeze_emit<<<nb, kFB, 0, s>>>(n, frozen, part, act);
     note_launches(launches);
+    return launch_status();
+}
+
+namespace {
+// Radix selection of the key of rank floor(fraction * m) - 1 into st.
+void select_rank(int64_t n, const unsigned long long *keys, double fraction, SelState *st, uint32_t *hist,
+                 cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t nb = (n + kFB - 1) / kFB;
+    const int hb = (int)std::min<int64_t>(nb, 2 * (int64_t)(sms > 0 ? sms : 152));
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        k_sel_hist<<<hb, 1024, 0, s>>>(n, keys, shift, st, hist);
+        k_sel_pick<<<1, 256, 0, s>>>(shift, fraction, st, hist);
+    }
+    note_launches(16);
+}
+
+struct SigLayout {
+    size_t st1, st2, hist, keys, total;
+};
+
+SigLayout sig_layout(int64_t n) {
+    SigLayout L;
+    L.st1 = 0;
+    L.st2 = 256;
+    L.hist = 512;
+    L.keys = L.hist + align256(256 * sizeof(uint32_t));
+    L.total = L.keys + align256(sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1));
+    return L;
+}
+}  // namespace
+
+extern "C" size_t gs_significance_workspace_bytes(int64_t n) {
+    if (n < 0 || n > INT32_MAX) return 0;
+    return sig_layout(n).total;
+}
+
+extern "C" int gs_significance_mark(int64_t n, const float *P, const uint32_t *hits, int32_t opacity_act,
+                                    float beta, float quantile, float fraction, uint8_t *mark, void *ws,
+                                    size_t ws_bytes, gs_stream_t stream) {
+    if (n < 0 || n > INT32_MAX || !(beta >= 0.f) || !(quantile > 0.f && quantile <= 1.f) ||
+        !(fraction >= 0.f && fraction <= 1.f) || (opacity_act & ~(GS_OPACITY_ABS | GS_VOLUME_MASK)))
+        return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    if (!P || !hits || !mark) return GS_ERR_INVALID_ARG;
+    const SigLayout L = sig_layout(n);
+    if (!ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    char *w = static_cast<char *>(ws);
+    SelState *st1 = reinterpret_cast<SelState *>(w + L.st1), *st2 = reinterpret_cast<SelState *>(w + L.st2);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + L.hist);
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(w + L.keys);
+    if (cudaMemsetAsync(w, 0, L.keys, s) != cudaSuccess) return GS_ERR_CUDA;
+    const int nb = (int)((n + kFB - 1) / kFB);
+    k_sig_vol_keys<<<nb, kFB, 0, s>>>(n, P, keys, st1);
+    select_rank(n, keys, (double)quantile, st1, hist, s);
+    k_sig_score_keys<<<nb, kFB, 0, s>>>(n, P, hits, beta, opacity_act & GS_OPACITY_ABS, st1, keys, st2);
+    select_rank(n, keys, (double)fraction, st2, hist, s);
+    k_sig_mark<<<nb, kFB, 0, s>>>(n, keys, st2, mark);
+    note_launches(3);
     return launch_status();
 }
 

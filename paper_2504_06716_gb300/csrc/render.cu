@@ -322,6 +322,42 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__res
 }
 
 // ---- measurement support: the (pixel, splat) pairs the backward visits ----
+// Per Gaussian, the pixels of this view it is blended into (the "hits" of
+// significance pruning, Sec. 3.3): one CTA per tile, one thread per pixel,
+// all threads at the same list position at once, one atomic per warp and
+// position with the number of its pixels that blend the splat there.
+__global__ void k_hit_counts(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
+                             const uint32_t *__restrict__ ranges, DevCam cam, const int32_t *__restrict__ n_last,
+                             uint32_t *__restrict__ hits) {
+    __shared__ int s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    const int tile = blockIdx.x, TS = cam.tile;
+    const int px = (tile % cam.tiles_x) * TS + (int)(threadIdx.x % TS);
+    const int py = (tile / cam.tiles_x) * TS + (int)(threadIdx.x / TS);
+    const bool inside = px < cam.W && py < cam.H;
+    const int nl = inside ? n_last[(int64_t)py * cam.W + px] : 0;
+    if (nl > 0) atomicMax(&s_max, nl);
+    __syncthreads();
+    const int jmax = s_max;
+    const uint32_t start = ranges[2 * tile];
+    const float fpx = (float)px, fpy = (float)py;
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < jmax; ++j) {
+        const uint32_t g = vals[start + j];
+        bool hit = false;
+        if (j < nl) {
+            const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
+            const float4 xa = __ldg(r), co = __ldg(r + 1);
+            const float power = splat_power(splat_row(__fsub_rn(xa.x, fpx), xa.z, xa.w, co.x), __fsub_rn(xa.y, fpy));
+            const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
+            hit = power <= 0.f && alpha >= kAlphaMin;
+        }
+        const unsigned b = __ballot_sync(kFull, hit);
+        if (lane == 0 && b) atomicAdd(hits + g, (uint32_t)__popc(b));
+    }
+}
+
 // One CTA per tile, one thread per pixel, walking the pixel's list up to its
 // last contributor with the forward's own decisions.
 __global__ void k_pair_counts(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
@@ -599,6 +635,16 @@ extern "C" int gs_raster_pair_counts(const float *splats, const uint32_t *vals, 
     const DevCam dc = make_cam(cam);
     k_pair_counts<<<dc.tiles_x * dc.tiles_y, dc.tile * dc.tile, 0, as_stream(stream)>>>(
         splats, vals, ranges, dc, n_last, frozen, reinterpret_cast<unsigned long long *>(counts_dev));
+    note_launches(1);
+    return launch_status();
+}
+
+extern "C" int gs_hit_counts(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                             const int32_t *n_last, uint32_t *hits_dev, gs_stream_t stream) {
+    if (!camera_ok(cam) || !splats || !vals || !ranges || !n_last || !hits_dev) return GS_ERR_INVALID_ARG;
+    const DevCam dc = make_cam(cam);
+    k_hit_counts<<<dc.tiles_x * dc.tiles_y, dc.tile * dc.tile, 0, as_stream(stream)>>>(splats, vals, ranges, dc,
+                                                                                      n_last, hits_dev);
     note_launches(1);
     return launch_status();
 }

@@ -110,6 +110,9 @@ _SIGS = {
     "gs_opacity_reset": ([_I64, _P, _P, _P, _F32, _P], _I32),
     "gs_opacity_to_abs": ([_I64, _P, _P, _P, _I32, _P, _P], _I32),
     "gs_train_step": ([_P, _P, _P, _P, _I64, _P], _I32),
+    "gs_hit_counts": ([_P, _P, _P, _CAM, _P, _P, _P], _I32),
+    "gs_significance_workspace_bytes": ([_I64], _SZ),
+    "gs_significance_mark": ([_I64, _P, _P, _I32, _F32, _F32, _F32, _P, _P, _SZ, _P], _I32),
     "gs_resize_area": ([_P, _I32, _I32, _I32, _P, _I32, _I32, _P], _I32),
     "gs_blur": ([_P, _I32, _I32, _I32, _F32, _P, _P], _I32),
     "gs_project_ex": ([_P, _I64, _I32, _I32, _P, _P, _P], _I32),
@@ -349,6 +352,27 @@ def gs_train_step(step: GsStep, cam: GsCamera, gt, lr, adam_step: int, stream=No
 GS_BLUR_SIGMA_MIN = float(np.float32(0.1))  # gs_blur copies below this (float32 comparison)
 
 
+def gs_hit_counts(splats, vals, ranges, cam: GsCamera, n_last, hits, stream=None):
+    import torch
+
+    _check("gs_hit_counts", load().gs_hit_counts(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), _ptr(n_last, torch.int32, "n_last"), _ptr(hits, torch.int32, "hits"), _stream(stream)))
+
+
+def gs_significance_workspace_bytes(n: int) -> int:
+    return int(load().gs_significance_workspace_bytes(n))
+
+
+def gs_significance_mark(n: int, P, hits, opacity_act: int, beta: float, quantile: float, fraction: float, mark, ws,
+                         stream=None):
+    import torch
+
+    _check("gs_significance_mark", load().gs_significance_mark(
+        n, _ptr(P, torch.float32, "P"), _ptr(hits, torch.int32, "hits"), opacity_act, beta, quantile, fraction,
+        _ptr(mark, torch.uint8, "mark"), _ptr(ws, torch.uint8, "ws"), ws.numel(), _stream(stream)))
+
+
 def gs_resize_area(src, C: int, W: int, H: int, dst, W2: int, H2: int, stream=None):
     import torch
 
@@ -402,7 +426,8 @@ class GsDensifyParams(ctypes.Structure):
                 ("log_clone_max", ctypes.c_float), ("logit_min_opacity", ctypes.c_float),
                 ("prune_big", ctypes.c_int32), ("max_screen_radius", ctypes.c_int32),
                 ("log_max_world", ctypes.c_float), ("log_split_div", ctypes.c_float),
-                ("mask_prune", ctypes.c_int32), ("mask_logit_min", ctypes.c_float)]
+                ("mask_prune", ctypes.c_int32), ("mask_logit_min", ctypes.c_float),
+                ("prune_mark", ctypes.c_void_p)]
 
 
 def gs_densify_workspace_bytes(n: int) -> int:

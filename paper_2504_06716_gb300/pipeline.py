@@ -183,6 +183,23 @@ class Model:
         prm = lib.GsDensifyParams(inf, inf, 0, 0.0, -inf, 0, 2**31 - 1, inf, 0.0, 1, logit_min)
         return self.densify(prm, rng)
 
+    def prune_marked(self, mark: torch.Tensor, rng: np.random.Generator) -> dict:
+        """Remove the Gaussians with mark[i] != 0 (uint8 [n], device): a
+        densification pass with no candidates and only that rule."""
+        inf = float("inf")
+        prm = lib.GsDensifyParams(inf, inf, 0, 0.0, -inf, 0, 2**31 - 1, inf, 0.0, 0, 0.0,
+                                  lib._ptr(mark, torch.uint8, "mark"))
+        return self.densify(prm, rng)
+
+    def significance_mark(self, hits: torch.Tensor, fraction: float, beta: float = 0.1,
+                          quantile: float = 0.9) -> torch.Tensor:
+        """Marks (uint8 [n]) of the floor(fraction n) least significant Gaussians
+        given their hit counts over the training views (gs_significance_mark)."""
+        mark = torch.zeros(max(self.n, 1), dtype=torch.uint8, device=self.device)
+        ws = torch.zeros(lib.gs_significance_workspace_bytes(self.n), dtype=torch.uint8, device=self.device)
+        lib.gs_significance_mark(self.n, self.P, hits, self.opacity_act, beta, quantile, fraction, mark, ws)
+        return mark
+
     def set_volume_mask(self, on: bool, learn_lr: float | None = None, loss_weight: float = 0.0):
         """Volume masks (Sec. 3.3) applied (on) and, with learn_lr, learned with
         that rate and the mask term loss_weight * mean sigmoid(m)."""

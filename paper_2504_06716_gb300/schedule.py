@@ -106,6 +106,16 @@ class GStaConfig:
     mask_from: int = 1000
     mask_until: int = 10000
     mask_prune_every: int = 1000
+    # Trick-GS significance pruning (Sec. 3.3, after LightGaussian; Sec. 4.1):
+    # at sig_iters, remove the least significant sig_fraction of the Gaussians
+    # (times sig_decay per earlier pruning); score = hits * opacity *
+    # (volume / 90th-percentile volume)^sig_beta over the training views
+    significance: bool = False
+    sig_iters: tuple = (4000, 7000)
+    sig_fraction: float = 0.75
+    sig_decay: float = 0.8
+    sig_beta: float = 0.1
+    sig_quantile: float = 0.9
     # opacity learning rate under |x|: "slope" scales the training rate by the
     # mean o (1 - o) at the switch, so that an Adam step moves opacities by
     # as much on average as it did through the sigmoid; None keeps 0.025; a

@@ -299,6 +299,8 @@ class Trainer:
         if c.densify_due(k):
             self._densify(k)
             self._act_now = None
+        if self.cfg.significance and k in self.cfg.sig_iters and c.finetune_left is None:
+            self._significance_prune(k)
         if mask_prune_due(k, self.cfg) and c.finetune_left is None:
             res = m.prune_masked(float(np.float32(math.log(0.01 / 0.99))), self.den_rng)
             self.events.append((k, "mask_prune", float(res["n"])))
@@ -316,6 +318,25 @@ class Trainer:
         self.k += 1
         if self.k % self.capacity_check_every == 0:
             self.check_capacity()
+
+    def _significance_prune(self, k: int):
+        """Significance pruning (Sec. 3.3): hit counts over every training view
+        (gs_hit_counts after each view's forward), scores, marks, removal."""
+        m = self.model
+        hits = torch.zeros(max(m.n, 1), dtype=torch.int32, device=self.device)
+        for v in self.scene.train_views:
+            m.retarget(self.view, self.cams[v])
+            m.rasterize(self.view)
+            lib.gs_hit_counts(m.splats, self.view.vals, self.view.ranges, self.view.cam, self.view.n_last, hits)
+        i = list(self.cfg.sig_iters).index(k)
+        frac = self.cfg.sig_fraction * self.cfg.sig_decay ** i
+        mark = m.significance_mark(hits, frac, self.cfg.sig_beta, self.cfg.sig_quantile)
+        res = m.prune_marked(mark, self.den_rng)
+        self.events.append((k, "significance_prune", float(res["n"])))
+        self._act_now = None
+        if m.generation != self.generation:
+            self.generation = m.generation
+            self.view = m.make_view(self.view.cam, self.view.capacity)
 
     def _scheduled_view(self, k: int, v: int):
         """Camera and target of view v at iteration k: the full-resolution ones,
@@ -399,7 +420,8 @@ def run(args) -> dict:
                      abs_opacity_moments=args.abs_moments,
                      abs_opacity_lr=None if args.abs_lr == "same" else
                      ("slope" if args.abs_lr == "slope" else float(args.abs_lr)),
-                     progressive=args.trick_gs, blur=args.trick_gs, volume_mask=args.trick_gs or args.volume_mask)
+                     progressive=args.trick_gs, blur=args.trick_gs, volume_mask=args.trick_gs or args.volume_mask,
+                     significance=args.trick_gs or args.significance)
     tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
     tuning = None
     if args.autotune:
@@ -458,8 +480,10 @@ def main():
     ap.add_argument("--abs-moments", choices=["zero", "rescale"], default="rescale",
                     help="the opacity's Adam moments when the finetuning stage switches to |x|")
     ap.add_argument("--trick-gs", action="store_true",
-                    help="progressive resolution and blur of the targets until 6K, volume masks (Sec. 3.3)")
+                    help="progressive resolution and blur of the targets until 6K, volume masks, significance"
+                         " pruning (Sec. 3.3)")
     ap.add_argument("--volume-mask", action="store_true", help="volume masks only (Sec. 3.3)")
+    ap.add_argument("--significance", action="store_true", help="significance pruning only (Sec. 3.3)")
     ap.add_argument("--abs-lr", default="slope",
                     help="opacity learning rate under |x|: 'slope' (the rate times the mean o (1 - o) at the"
                          " switch), 'same' (unchanged) or a number")
