@@ -475,22 +475,31 @@ def e2e_rate(tr, n) -> dict:
     its target image from pinned host memory and reads the loss back."""
     import torch
 
+    from paper_2504_06716_gb300.pipeline import TargetFeeder
+
     m, view = tr.model, tr.view
     views = [tr.order[i] for i in range(n)]
     host = {v: tr.targets[v].cpu().pin_memory() for v in set(views)}
-    dev = torch.empty_like(tr.targets[views[0]])
+    feeder = TargetFeeder(tuple(tr.targets[views[0]].shape))
     loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
+    done = torch.cuda.Event()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for v in views:
-        dev.copy_(host[v], non_blocking=True)
+    feeder.prefetch(host[views[0]])
+    for i, v in enumerate(views):
+        gt = feeder.take()
         m.retarget(view, tr.cams[v])
-        m.train_step(view, dev, tr.lrs)
+        m.train_step(view, gt, tr.lrs)
+        feeder.release()
+        if i + 1 < n:
+            feeder.prefetch(host[views[i + 1]])  # the next upload overlaps this step
         loss_host.copy_(view.loss, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        done.record()
+        done.synchronize()  # the step's loss is on the host
     dt = time.perf_counter() - t0
-    return dict(value=n / dt, unit="it/s", h2d_bytes_per_step=int(dev.numel() * 4), d2h_bytes_per_step=4,
-                note="host-pinned target upload and loss read-back every step; freeze map as in the timed region")
+    return dict(value=n / dt, unit="it/s", h2d_bytes_per_step=int(feeder.bufs[0].numel() * 4), d2h_bytes_per_step=4,
+                note="host-pinned target upload (the next step's overlapping the current one, two device buffers) "
+                     "and loss read-back every step; freeze map as in the timed region")
 
 
 def main():

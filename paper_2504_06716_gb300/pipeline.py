@@ -343,3 +343,37 @@ class Model:
             tt = self.splats[:, 11].contiguous().view(torch.int32)
             worst = max(worst, int(tt.to(torch.int64).sum().item()))
         return int(worst * slack) + 1024
+
+
+class TargetFeeder:
+    """Targets from host memory for training from host buffers: each step's
+    image is copied from pinned host memory into one of two device buffers
+    on a copy stream, the copy of the next step's image overlapping the
+    current step (the step waits for its own copy; a buffer is refilled only
+    after the step that read it)."""
+
+    def __init__(self, shape, device="cuda"):
+        self.bufs = [torch.empty(shape, dtype=torch.float32, device=device) for _ in range(2)]
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.used = [torch.cuda.Event() for _ in range(2)]
+        self.stream = torch.cuda.Stream(device=device)
+        self.k = 0
+
+    def prefetch(self, host: torch.Tensor):
+        """Start copying the next step's target (pinned host tensor)."""
+        b = self.k % 2
+        with torch.cuda.stream(self.stream):
+            self.stream.wait_event(self.used[b])  # the step that last read this buffer is done with it
+            self.bufs[b].copy_(host, non_blocking=True)
+            self.copied[b].record(self.stream)
+
+    def take(self) -> torch.Tensor:
+        """The buffer of the prefetched target, after the current stream waits for its copy."""
+        b = self.k % 2
+        torch.cuda.current_stream().wait_event(self.copied[b])
+        return self.bufs[b]
+
+    def release(self):
+        """Mark the current buffer as read by the work enqueued so far; move on."""
+        self.used[self.k % 2].record(torch.cuda.current_stream())
+        self.k += 1

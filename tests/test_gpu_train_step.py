@@ -86,3 +86,23 @@ def test_native_step_rejects_bad_arguments():
     st.n_stats = 3
     with pytest.raises(lib.GsError):
         lib.gs_train_step(st, cam, gt, pipeline.default_lrs(4.4), 1)
+
+
+def test_target_feeder_delivers_each_step_its_image():
+    """Double-buffered uploads: every take() returns the image prefetched for
+    that step, with the next upload in flight during the step."""
+    g = np.random.default_rng(4)
+    imgs = [torch.from_numpy(g.uniform(0, 1, (3, 96, 128)).astype(np.float32)) for _ in range(6)]
+    host = [x.pin_memory() for x in imgs]
+    feeder = pipeline.TargetFeeder((3, 96, 128))
+    sink = torch.zeros((3, 96, 128), device=DEV)
+    feeder.prefetch(host[0])
+    for i in range(6):
+        t = feeder.take()
+        sink.copy_(t)  # the step's use of its target
+        sink.mul_(1.0)
+        feeder.release()
+        if i + 1 < 6:
+            feeder.prefetch(host[i + 1])
+        torch.cuda.current_stream().synchronize()
+        assert torch.equal(sink.cpu(), imgs[i])
