@@ -345,8 +345,8 @@ def gpu_arm(args):
 # gives the command). Valid only for the kernel sources it was taken on: the
 # digest of those files is compared at run time and traffic is reported as null
 # once they have changed.
-RASTER_BWD_TRAFFIC = dict(bytes_per_launch=72793344,
-                          sources_sha256="73403abe0a8b42a51e02169cd241f0a75df211a10e5ef9ec962075b769ca0fd1")
+RASTER_BWD_TRAFFIC = dict(bytes_per_launch=72891853,
+                          sources_sha256="1b09d07e683ea1a70bff1ebf02d655e1f8267a556bc0025ae4a502d9b5810589")
 RASTER_BWD_SOURCES = ("paper_2504_06716_gb300/csrc/render.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 
 

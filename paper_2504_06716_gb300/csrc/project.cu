@@ -6,6 +6,8 @@
 // read (mean, scales, rotation, opacity) and its 192 bytes of SH are never
 // fetched. The backward runs over the compacted active list, so a frozen
 // Gaussian is never read or written.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gs {
@@ -250,14 +252,11 @@ struct StatSets {
 // with ACC the gradient rows are added to G instead of written.
 // One instance for both modes (ACC a run-time flag), so that the row added
 // under ACC is bit for bit the row written without it.
-__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, int flags, float mask_loss,
-                                                     DevCam cam, const float *__restrict__ splats,
-                                                     const int32_t *__restrict__ act,
-                                                     const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
-                                                     float *__restrict__ G, StatSets st, int ACC) {
+__device__ __forceinline__ void project_bwd_one(int64_t k, const float *__restrict__ P, int deg, int flags,
+                                                float mask_loss, const DevCam &cam, const float *__restrict__ splats,
+                                                const int32_t *__restrict__ act, float *__restrict__ grad2d,
+                                                float *__restrict__ G, const StatSets &st, int ACC) {
     const int abs_act = flags & GS_OPACITY_ABS;
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= *n_active) return;
     const int64_t i = act[k];
     float4 *gout = reinterpret_cast<float4 *>(G + i * kRow);
     const int radius = __float_as_int(__ldg(splats + i * kSplat + 10));
@@ -454,6 +453,18 @@ __global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P
     }
 }
 
+// A grid sized for the device, each thread walking the active list with a
+// stride: the list's length is known only on the device.
+__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, int flags, float mask_loss,
+                                                     DevCam cam, const float *__restrict__ splats,
+                                                     const int32_t *__restrict__ act,
+                                                     const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
+                                                     float *__restrict__ G, StatSets st, int ACC) {
+    const int64_t na = *n_active;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < na; k += (int64_t)gridDim.x * blockDim.x)
+        project_bwd_one(k, P, deg, flags, mask_loss, cam, splats, act, grad2d, G, st, ACC);
+}
+
 }  // namespace
 }  // namespace gs
 
@@ -501,8 +512,12 @@ static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, i
         st.maxr[k] = sets[k].max_radius;
     }
     const DevCam dc = make_cam(cam);
-    k_project_bwd<<<grid_for(n, 128), 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, mask_loss, dc, splats,
-                                                                    act, n_active_dev, grad2d, G, st, acc ? 1 : 0);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = std::min<unsigned>(grid_for(n, 128), (unsigned)(sms > 0 ? sms : 152) * 8u);
+    k_project_bwd<<<grid, 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, mask_loss, dc, splats, act,
+                                                        n_active_dev, grad2d, G, st, acc ? 1 : 0);
     note_launches(1);
     return launch_status();
 }

@@ -183,6 +183,39 @@ class Model:
         prm = lib.GsDensifyParams(inf, inf, 0, 0.0, -inf, 0, 2**31 - 1, inf, 0.0, 1, logit_min)
         return self.densify(prm, rng)
 
+    # ---- checkpoint ----
+    _STATE = ("P", "G", "m", "v", "frozen", "act", "n_active", "acc_xyz", "acc_rgb", "cnt")
+
+    def state_dict(self) -> dict:
+        """Everything training needs to continue: parameters, gradients,
+        moments, freeze map and list, both statistics windows, counters and
+        the parameterisation (host copies)."""
+        st = {k: getattr(self, k).detach().cpu().clone() for k in self._STATE}
+        st.update(n=self.n, cap=self.cap, step_count=self.step_count, sh_degree=self.sh_degree,
+                  opacity_act=self.opacity_act, mask_loss=self.mask_loss, mask_lr=self.mask_lr,
+                  generation=self.generation)
+        if self.den is not None:
+            st["den"] = {k: t.detach().cpu().clone() for k, t in self.den.items()
+                         if k in ("acc_xyz", "acc_rgb", "cnt", "max_radius")}
+        return st
+
+    def load_state_dict(self, st: dict):
+        """Restore a state_dict (buffers reallocated at its capacity)."""
+        self.sh_degree = st["sh_degree"]
+        had_den = self.den is not None or "den" in st
+        self.den = None
+        self._allocate(st["cap"])
+        for k in self._STATE:
+            getattr(self, k).copy_(st[k].to(self.device))
+        self.n, self.step_count = st["n"], st["step_count"]
+        self.opacity_act, self.mask_loss, self.mask_lr = st["opacity_act"], st["mask_loss"], st["mask_lr"]
+        self.generation = st["generation"] + 1  # buffers are new: views must be remade
+        if had_den:
+            self.enable_densify()
+            for k, t in st.get("den", {}).items():
+                self.den[k].copy_(t.to(self.device))
+        self._step_key = None
+
     def prune_marked(self, mark: torch.Tensor, rng: np.random.Generator) -> dict:
         """Remove the Gaussians with mark[i] != 0 (uint8 [n], device): a
         densification pass with no candidates and only that rule."""

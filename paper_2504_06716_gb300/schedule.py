@@ -140,6 +140,15 @@ class GStaController:
         self.stop_iter: int | None = None
         self.finetune_left: int | None = None
 
+    def state_dict(self) -> dict:
+        return dict(lr_xyz=self.lr_xyz, best=self._best, bad=self._bad, psnrs=list(self.psnrs),
+                    last_reset=self.last_reset, stop_iter=self.stop_iter, finetune_left=self.finetune_left)
+
+    def load_state_dict(self, st: dict):
+        self.lr_xyz, self._best, self._bad = st["lr_xyz"], st["best"], st["bad"]
+        self.psnrs = list(st["psnrs"])
+        self.last_reset, self.stop_iter, self.finetune_left = st["last_reset"], st["stop_iter"], st["finetune_left"]
+
     def thresholds(self, k: int) -> tuple[float, float]:
         c = self.cfg
         s = min(1.5, max(0.5, 0.5 + 1.5 * k / c.total_iter))

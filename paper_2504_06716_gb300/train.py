@@ -338,6 +338,31 @@ class Trainer:
             self.generation = m.generation
             self.view = m.make_view(self.view.cam, self.view.capacity)
 
+    # ---- checkpoint / resume ----
+    def save_checkpoint(self, path: str):
+        """Model, controller and trainer state (iteration, thresholds, lrs,
+        random generators, events) in one file: resuming continues the run."""
+        torch.save(dict(model=self.model.state_dict(), ctrl=self.ctrl.state_dict(), k=self.k, eps0=self.eps0,
+                        calibrated=self.calibrated, lrs=list(self.lrs), events=list(self.events),
+                        active_iters=self.active_iters, overflows=self.overflows,
+                        den_rng=self.den_rng.bit_generator.state, freeze_rng=self.freeze_rng.bit_generator.state,
+                        capacity=self.view.capacity), path)
+
+    def load_checkpoint(self, path: str):
+        st = torch.load(path, weights_only=False)
+        self.model.load_state_dict(st["model"])
+        self.ctrl.load_state_dict(st["ctrl"])
+        self.k, self.eps0, self.calibrated = st["k"], tuple(st["eps0"]), st["calibrated"]
+        self.lrs, self.events, self.active_iters = list(st["lrs"]), list(st["events"]), st["active_iters"]
+        self.overflows = st["overflows"]
+        self.den_rng.bit_generator.state = st["den_rng"]
+        self.freeze_rng.bit_generator.state = st["freeze_rng"]
+        self._act_now = None
+        self.generation = self.model.generation
+        self.view = self.model.make_view(self.view.cam, st["capacity"])
+        if getattr(self, "tuning", None) is not None:
+            self.model.apply_tuning(self.tuning)
+
     def _scheduled_view(self, k: int, v: int):
         """Camera and target of view v at iteration k: the full-resolution ones,
         or under the progressive / blur schedules (Sec. 3.3) the area-averaged

@@ -74,3 +74,17 @@ def test_image_schedules_match_oracle():
         assert blur_sigma(k, cfg) == pytest.approx(IS.sigma_at(k), abs=1e-12)
     off = GStaConfig()
     assert train_resolution(0, off, 1237, 822) == (1237, 822) and blur_sigma(0, off) == 0.0
+
+
+def test_controller_state_round_trip():
+    cfg = GStaConfig()
+    a = GStaController(cfg, lr_xyz=1.0)
+    for i, p in enumerate([20.0, 24.0, 25.5, 26.1]):
+        a.report_psnr(1000 * (i + 1), p)
+    a.freeze_mode(4000)
+    b = GStaController(cfg, lr_xyz=7.0)
+    b.load_state_dict(a.state_dict())
+    assert b.state_dict() == a.state_dict()
+    for k in range(4000, 12001, 250):
+        assert a.freeze_mode(k) == b.freeze_mode(k)
+    assert a.report_psnr(5000, 26.2) == b.report_psnr(5000, 26.2) and a.lr_xyz == b.lr_xyz
