@@ -189,23 +189,73 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- replicas
+
+
+class Replicas:
+    """N independent replicas of the step, one process per GPU (torchrun sets
+    WORLD_SIZE / RANK / LOCAL_RANK). The training step has no exchange step,
+    so nothing on the data path is collective: only the timing is combined --
+    a barrier on both sides of the timed region, the slowest rank's time, and
+    the units every rank processed. ``backend`` is "nccl" for the GPU arm and
+    "gloo" on the CPU; with WORLD_SIZE 1 no process group is made."""
+
+    def __init__(self, backend: str = "nccl", device=None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            kw = {} if device is None else dict(device_id=device)
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    @property
+    def printer(self) -> bool:
+        """Rank 0 alone prints the result line."""
+        return self.rank == 0
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def slowest_ms(self, ms: float) -> float:
+        """The largest of the ranks' timed-region durations."""
+        if self.dist is None:
+            return ms
+        import torch
+
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda" if self.backend == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def rate(self, units_per_rank: int, ms: float) -> float:
+        """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+        return units_per_rank * self.world / (ms / 1000.0)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 
 def gpu_arm(args):
     import torch
-    import torch.distributed as dist
 
     from paper_2504_06716_gb300 import lib, pipeline, synth
     from paper_2504_06716_gb300.schedule import GStaConfig
     from paper_2504_06716_gb300.train import Trainer
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    reps = Replicas("nccl", torch.device("cuda", local))
+    world, rank = reps.world, reps.rank
     lib.load()
 
     W_, H_ = WORKLOAD["width"], WORKLOAD["height"]
@@ -256,8 +306,7 @@ def gpu_arm(args):
     active_before = int(m.n_active.item())
     n_before = m.n
     k_start = tr.k
-    if world > 1:
-        dist.barrier()
+    reps.barrier()
     torch.cuda.synchronize()
     launches0 = lib.gs_launch_count()
     with ClockSampler(local) as clk:
@@ -271,16 +320,12 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     launches = lib.gs_launch_count() - launches0
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = reps.slowest_ms(t0.elapsed_time(t1))
+    reps.barrier()
     m.train_step = orig_train_step
     active_after = int(m.n_active.item())
     flags = lib.gs_get_device_error()
-    its = args.steps * world / (ms / 1000.0)
+    its = reps.rate(args.steps, ms)
 
     # ---- per-stage split (fwd / bwd ms) on the same state, untimed above ----
     stages = stage_split(tr, 20)
@@ -317,7 +362,7 @@ def gpu_arm(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene)
 
-    if rank == 0:
+    if reps.printer:
         line = dict(metric=METRIC, value=its, unit="it/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic",
@@ -335,8 +380,7 @@ def gpu_arm(args):
                     roofline=roofline, roofline_adam=adam, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
                     clocks=clk_summary, device_flags=flags)
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
 
 
 # DRAM traffic of the dominant kernel per launch, from one ncu capture of this
