@@ -69,7 +69,7 @@ typedef enum {
 /* Device error word bits. */
 #define GS_FLAG_CAPACITY 1u
 #define GS_FLAG_NONFINITE 2u
-#define GS_FLAG_TIMEOUT 4u
+#define GS_FLAG_TIMEOUT 4u /* reserved: no kernel of this library waits on another block or a flag */
 #define GS_FLAG_BADJOB 8u /* a batch job whose camera differs from the batch's size or tile */
 
 typedef void *gs_stream_t; /* a cudaStream_t */

@@ -31,6 +31,48 @@ from .schedule import (FREEZE_RESET, FREEZE_UPDATE, GStaConfig, GStaController, 
                        mask_phase, mask_prune_due, train_resolution)
 
 
+class JsonlLog:
+    """Training record as JSON lines, one object per line.
+
+    Every ``every`` iterations: ``{"k", "loss", "n", "n_active",
+    "frozen_frac", "entries", "lr_xyz"}`` for the step just taken (k is that
+    step's iteration; loss is its training loss; entries the (Gaussian, tile)
+    pairs its sort produced). Schedule events (subset PSNR checks, early stop,
+    densification, prunes, resets) are written as ``{"k", "event", "value"}``
+    when they have happened, and held-out evaluations as ``{"k", "eval", ...}``.
+    Reading the loss and the counts waits for the step, so the cadence sets
+    what the log costs."""
+
+    def __init__(self, path: str, every: int = 100):
+        if every < 1:
+            raise ValueError("every must be >= 1")
+        self.f = open(path, "w")
+        self.every = every
+        self._events_seen = 0
+
+    def _write(self, rec: dict):
+        self.f.write(json.dumps(rec) + "\n")
+
+    def after_iteration(self, tr):
+        for k, kind, value in tr.events[self._events_seen:]:
+            self._write(dict(k=int(k), event=kind, value=float(value)))
+        self._events_seen = len(tr.events)
+        k = tr.k - 1
+        if k < 0 or k % self.every:
+            return
+        m = tr.model
+        n, n_active = int(m.n), int(m.n_active.item())
+        self._write(dict(k=k, loss=float(tr.view.loss.item()), n=n, n_active=n_active,
+                         frozen_frac=(n - n_active) / n if n else 0.0, entries=int(tr.view.count.item()),
+                         lr_xyz=float(tr.ctrl.lr_xyz_at(k))))
+
+    def evaluation(self, rec: dict):
+        self._write(dict(k=int(rec["k"]), eval=True, **{a: b for a, b in rec.items() if a != "k"}))
+
+    def close(self):
+        self.f.close()
+
+
 class Trainer:
     def __init__(self, scene: synth.Scene, cfg: GStaConfig, tile: int = 16, calibrate: bool = True,
                  extent: float = 4.4, seed: int = 3, device="cuda"):
@@ -461,18 +503,25 @@ def run(args) -> dict:
         tr2.active_iters, tr2._act_now = 0, None
         tr = tr2
     evals = []
+    log = JsonlLog(args.log_jsonl, args.log_every) if getattr(args, "log_jsonl", None) else None
     t0 = time.perf_counter()
     eval_every = args.eval_every
     while not tr.finished():
         tr.iteration()
+        if log is not None:  # counted as training time (a short wait every log.every iterations)
+            log.after_iteration(tr)
         if tr.k % eval_every == 0:
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
             evals.append(dict(k=tr.k, wall_s=el, heldout_psnr=tr.heldout_psnr(), n=tr.model.n,
                               n_active=int(tr.model.n_active.item())))
+            if log is not None:
+                log.evaluation(evals[-1])
             t0 = time.perf_counter() - el  # held-out evaluation is not training time
     torch.cuda.synchronize()
     total = time.perf_counter() - t0
+    if log is not None:
+        log.close()
     out = dict(arm=args.arm, freeze_strategy=cfg.freeze_strategy, abs_opacity_finetune=cfg.abs_opacity_finetune,
                trick_gs=args.trick_gs,
                abs_opacity_moments=cfg.abs_opacity_moments,
@@ -512,6 +561,8 @@ def main():
     ap.add_argument("--abs-lr", default="slope",
                     help="opacity learning rate under |x|: 'slope' (the rate times the mean o (1 - o) at the"
                          " switch), 'same' (unchanged) or a number")
+    ap.add_argument("--log-jsonl", default=None, help="write a per-iteration training record (JSON lines) here")
+    ap.add_argument("--log-every", type=int, default=100, help="iterations between records of --log-jsonl")
     args = ap.parse_args()
     print(json.dumps(run(args)))
 
