@@ -27,15 +27,29 @@ _lib = None
 N_PARAMS = 59
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (IEEE arithmetic: no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+def _plant() -> int:
+    """Planted-mistake number of this process (environment GSTA_ORACLE_PLANT),
+    0 -- the oracle itself -- unless the pins' own test set it."""
+    return int(os.environ.get("GSTA_ORACLE_PLANT", "0") or 0)
+
+
+def build(force: bool = False, plant: int | None = None) -> str:
+    """Compile the oracle with gcc (IEEE arithmetic: no fast-math, no FMA contraction).
+    plant k >= 1 compiles the copy with planted mistake k, into the temporary
+    directory (see PLANTED in gsta_oracle.c)."""
+    plant = _plant() if plant is None else int(plant)
+    out = _LIB
+    if plant:
+        import tempfile
+
+        out = os.path.join(tempfile.gettempdir(), f"gsta_liboracle_plant{plant}_{os.getuid()}.so")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(
             ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-             "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+             f"-DORACLE_PLANT={plant}", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Cam(ctypes.Structure):

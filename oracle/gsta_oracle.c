@@ -45,6 +45,15 @@
 
 #define NP 59
 
+/* Planted mistakes, for the test that shows the pins catch them
+ * (tests/test_oracle_mutants.py): a build with -DORACLE_PLANT=k, k >= 1,
+ * changes the one step marked PLANTED(k) below. Every normal build has
+ * ORACLE_PLANT 0, where each PLANTED(k) is the constant 0. */
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+#define PLANTED(k) (ORACLE_PLANT == (k))
+
 typedef struct {
     int32_t width, height, tile, pad0;
     double fx, fy, cx, cy;
@@ -115,7 +124,7 @@ static void sh_eval(const double dir[3], double *Y, double *dY) {
         for (int m = 0; m <= l; ++m) {
             /* Q = d^m P_l / dz^m, dQ = its derivative */
             poly_deriv(Q, dQ);
-            double K = sqrt((2 * l + 1) / (4.0 * PI) * factorial(l - m) / factorial(l + m));
+            double K = sqrt((2 * l + 1) / (4.0 * PI) * (PLANTED(4) ? 1.0 : factorial(l - m) / factorial(l + m)));
             double q = poly_eval(Q, 3, z), dq = poly_eval(dQ, 3, z);
             if (m == 0) {
                 int c = l * l + l;
@@ -324,7 +333,8 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
     if (mask && !mask_on(*mask)) return; /* mask 0: opacity and scales 0, culled */
     const double *mu = p;
     for (int i = 0; i < 3; ++i)
-        g->tc[i] = cam->R[3 * i] * mu[0] + cam->R[3 * i + 1] * mu[1] + cam->R[3 * i + 2] * mu[2] + cam->t[i];
+        g->tc[i] = PLANTED(3) ? cam->R[i] * mu[0] + cam->R[3 + i] * mu[1] + cam->R[6 + i] * mu[2] + cam->t[i]
+                              : cam->R[3 * i] * mu[0] + cam->R[3 * i + 1] * mu[1] + cam->R[3 * i + 2] * mu[2] + cam->t[i];
     if (!smooth) g->margin = fabs(g->tc[2] - cam->znear);
     if (g->tc[2] <= cam->znear) return;
     double tz = g->tc[2];
@@ -350,15 +360,17 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
     if (v > limy) { g->cuy = limy; g->clampy = 1; }
     if (v < -limy) { g->cuy = -limy; g->clampy = 1; }
     double *J = g->J;
-    J[0] = cam->fx / tz; J[1] = 0; J[2] = -cam->fx * g->cux / tz;
+    J[0] = cam->fx / tz; J[1] = 0; J[2] = PLANTED(2) ? 0.0 : -cam->fx * g->cux / tz;
     J[3] = 0; J[4] = cam->fy / tz; J[5] = -cam->fy * g->cuy / tz;
     matmul(J, cam->R, g->Tm, 2, 3, 3);
     double TS[6], Tt[6];
     matmul(g->Tm, g->Sigma, TS, 2, 3, 3);
     transpose(g->Tm, Tt, 2, 3);
     matmul(TS, Tt, g->cov, 2, 3, 2);
-    g->cov[0] += cam->dilation;
-    g->cov[3] += cam->dilation;
+    if (!PLANTED(1)) {
+        g->cov[0] += cam->dilation;
+        g->cov[3] += cam->dilation;
+    }
     g->det = g->cov[0] * g->cov[3] - g->cov[1] * g->cov[2];
     if (g->det <= 0) return;
     g->Q[0] = g->cov[3] / g->det; g->Q[1] = -g->cov[1] / g->det;
@@ -457,6 +469,7 @@ typedef struct {
 static int cmp_entry(const void *a, const void *b) {
     const sort_entry *x = (const sort_entry *)a, *y = (const sort_entry *)b;
     if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (PLANTED(13)) return x->order > y->order ? -1 : (x->order < y->order);
     return x->order < y->order ? -1 : (x->order > y->order);
 }
 
@@ -552,14 +565,14 @@ static void eval_entry(const double *mean2d, const double *conic, const double *
     if (!smooth) {
         double m = fabs(oG - ALPHA_MAX) / ALPHA_MAX;
         if (m < e->rel_margin) e->rel_margin = m;
-        if (oG > ALPHA_MAX) { e->alpha = ALPHA_MAX; e->capped = 1; }
+        if (oG > ALPHA_MAX && !PLANTED(14)) { e->alpha = ALPHA_MAX; e->capped = 1; }
         m = fabs(e->alpha - ALPHA_MIN) / ALPHA_MIN;
         if (m < e->rel_margin) e->rel_margin = m;
         if (e->alpha < ALPHA_MIN) { e->skip = 1; return; }
         double tn = T * (1.0 - e->alpha);
         m = fabs(tn - T_MIN) / T_MIN;
         if (m < e->rel_margin) e->rel_margin = m;
-        if (tn < T_MIN) e->stop = 1;
+        if (tn < (PLANTED(11) ? 1e-3 : T_MIN)) e->stop = 1;
     }
 }
 
@@ -583,8 +596,9 @@ void or_render(int32_t W, int32_t H, int32_t tile, const double *bg, int32_t smo
                 if (ev.rel_margin < mg) mg = ev.rel_margin;
                 if (ev.skip) continue;
                 if (ev.stop) break;
+                if (PLANTED(5)) T *= 1.0 - ev.alpha;
                 for (int c = 0; c < 3; ++c) C[c] += rgb[3 * g + c] * ev.alpha * T;
-                T *= 1.0 - ev.alpha;
+                if (!PLANTED(5)) T *= 1.0 - ev.alpha;
                 last = (int32_t)(k - s + 1);
             }
             int64_t pix = (int64_t)py * W + px;
@@ -758,7 +772,7 @@ typedef struct { double m, mx, my, n1, n2, d1, d2; } ssim_px;
 
 static ssim_px ssim_at(const double *x, const double *y, int32_t H, int32_t W, int32_t i, int32_t j,
                        double w[11][11]) {
-    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    const double C1 = 0.01 * 0.01, C2 = PLANTED(8) ? 0.02 * 0.02 : 0.03 * 0.03;
     double mx = 0, my = 0, xx = 0, yy = 0, xy = 0;
     for (int di = -5; di <= 5; ++di)
         for (int dj = -5; dj <= 5; ++dj) {
@@ -922,7 +936,7 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                 double a = ev[k].alpha, dA = 0;
                 double *ab = (ambiguous && amb_abs) ? amb_abs + 9 * (int64_t)g : NULL;
                 for (int c = 0; c < 3; ++c) {
-                    double dCda = rgb[3 * g + c] * Tk[k] - (S[3 * k + c] + Tf * bg[c]) / (1.0 - a);
+                    double dCda = rgb[3 * g + c] * Tk[k] - (S[3 * k + c] + (PLANTED(7) ? 0.0 : Tf * bg[c])) / (1.0 - a);
                     dA += dC[c] * dCda;
                     d_rgb[3 * g + c] += a * Tk[k] * dC[c];
                     if (ab) ab[6 + c] += fabs(a * Tk[k] * dC[c]);
@@ -936,7 +950,7 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                 d_conic[3 * g] += -0.5 * dx * dx * dpow;
                 d_conic[3 * g + 1] += -dx * dy * dpow;
                 d_conic[3 * g + 2] += -0.5 * dy * dy * dpow;
-                d_mean2d[2 * g] += -(qa * dx + qb * dy) * dpow;
+                d_mean2d[2 * g] += (PLANTED(6) ? 1.0 : -1.0) * (qa * dx + qb * dy) * dpow;
                 d_mean2d[2 * g + 1] += -(qb * dx + qc * dy) * dpow;
                 if (ab) {
                     ab[0] += fabs((qa * dx + qb * dy) * dpow);
@@ -999,7 +1013,7 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
                 for (int a = 0; a < 3; ++a) ddir[a] += p[11 + 3 * k + ch] * gc[ch] * g.dY[3 * k + a];
             }
         double dmu[3], dd = ddir[0] * g.dir[0] + ddir[1] * g.dir[1] + ddir[2] * g.dir[2];
-        for (int a = 0; a < 3; ++a) dmu[a] = (ddir[a] - g.dir[a] * dd) / g.dist;
+        for (int a = 0; a < 3; ++a) dmu[a] = PLANTED(15) ? 0.0 : (ddir[a] - g.dir[a] * dd) / g.dist;
 
         /* opacity = sigmoid(x): d/dx = o (1 - o); opacity = |x|: d/dx = sign(x) */
         if (opacity_act)
@@ -1020,7 +1034,7 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
         matmul(t1, g.Tm, GSig, 3, 2, 3);
         matmul(Gcov, g.Tm, t2, 2, 2, 3);
         matmul(t2, g.Sigma, GTm, 2, 3, 3);
-        for (int a = 0; a < 6; ++a) GTm[a] *= 2;
+        for (int a = 0; a < 6; ++a) GTm[a] *= PLANTED(17) ? 1 : 2;
 
         /* Tm = J R_c */
         double Rct[9], GJ[6];
@@ -1030,7 +1044,7 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
         double dtz = GJ[0] * (-cam->fx / (tz * tz)) + GJ[4] * (-cam->fy / (tz * tz)) +
                      GJ[2] * (cam->fx * g.cux / (tz * tz)) + GJ[5] * (cam->fy * g.cuy / (tz * tz));
         double dcu = GJ[2] * (-cam->fx / tz), dcv = GJ[5] * (-cam->fy / tz);
-        double du = (g.clampx ? 0.0 : dcu) + cam->fx * dm[0];
+        double du = ((g.clampx && !PLANTED(18)) ? 0.0 : dcu) + cam->fx * dm[0];
         double dv = (g.clampy ? 0.0 : dcv) + cam->fy * dm[1];
         double dtc[3] = {du / tz, dv / tz, dtz - du * tx / (tz * tz) - dv * ty / (tz * tz)};
         for (int a = 0; a < 3; ++a)
@@ -1059,10 +1073,10 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
             for (int a = 0; a < 9; ++a) dqn[k] += GR[a] * dR[k][a];
             qd += dqn[k] * g.qn[k];
         }
-        for (int k = 0; k < 4; ++k) gp[6 + k] = (dqn[k] - g.qn[k] * qd) / g.qlen;
+        for (int k = 0; k < 4; ++k) gp[6 + k] = (dqn[k] - (PLANTED(16) ? 0.0 : g.qn[k] * qd)) / g.qlen;
 
         if (xyz_norm) {
-            double ex = dm[0] * 0.5 * cam->width, ey = dm[1] * 0.5 * cam->height;
+            double ex = dm[0] * (PLANTED(19) ? 1.0 : 0.5 * cam->width), ey = dm[1] * (PLANTED(19) ? 1.0 : 0.5 * cam->height);
             xyz_norm[i] = sqrt(ex * ex + ey * ey);
         }
         if (rgb_norm) rgb_norm[i] = sqrt(gp[11] * gp[11] + gp[12] * gp[12] + gp[13] * gp[13]);
@@ -1101,13 +1115,13 @@ void or_adam(int64_t n, double *P, const double *G, double *M, double *V, const 
              double b1, double b2, double eps, int64_t step) {
     double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
     for (int64_t i = 0; i < n; ++i) {
-        if (frozen && frozen[i]) continue;
+        if (frozen && frozen[i] && !PLANTED(12)) continue;
         for (int r = 0; r < NP; ++r) {
             int64_t k = NP * i + r;
             double g = G[k];
             M[k] = b1 * M[k] + (1 - b1) * g;
             V[k] = b2 * V[k] + (1 - b2) * g * g;
-            double mh = M[k] / bc1, vh = V[k] / bc2;
+            double mh = M[k] / bc1, vh = PLANTED(9) ? V[k] : V[k] / bc2;
             P[k] -= lr[param_group(r)] * mh / (sqrt(vh) + eps);
         }
     }
@@ -1136,7 +1150,7 @@ int64_t or_freeze_update(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt
         if (mode == 0 && cnt[i] > 0) {
             volatile float c = (float)cnt[i];
             volatile float ax = acc_xyz[i] / c, ar = acc_rgb[i] / c;
-            if (ax < eps_xyz && ar < eps_rgb) frozen[i] = 1;
+            if (PLANTED(10) ? (ax < eps_xyz || ar < eps_rgb) : (ax < eps_xyz && ar < eps_rgb)) frozen[i] = 1;
         }
         if (mode != 3) { acc_xyz[i] = 0; acc_rgb[i] = 0; cnt[i] = 0; }
         if (!frozen[i]) act[k++] = (int32_t)i;

@@ -70,6 +70,45 @@ def test_gradients_match_central_differences_with_cutoffs(orc):
     assert checked > 100
 
 
+def test_gradients_at_the_clamped_screen_coordinate(orc):
+    """The projection Jacobian takes x/z and y/z clamped to 1.3 times the
+    half field of view, so beyond that limit the mean reaches the 2-D
+    covariance only through 1/z: central differences of the loss see no
+    dependence through the clamped coordinate. Two large anisotropic
+    Gaussians whose centres lie past the limit (one in x, one in y) still
+    cover pixels; the analytic gradient of every parameter must match."""
+    W, H, f = 40, 32, 50.0
+    cam = orc.make_cam(synth.Camera(W, H, f, f, W / 2.0, H / 2.0, np.eye(3), np.zeros(3), np.zeros(3)),
+                       tile=8, dilation=0.3, bg=(0.05, 0.1, 0.15))
+    g = np.random.default_rng(5)
+    limx, limy = 1.3 * 0.5 * W / f, 1.3 * 0.5 * H / f
+    P = np.zeros((2, 59))
+    P[0, 0:3] = [(limx + 0.1234) * 3.0, 0.1, 3.0]
+    P[1, 0:3] = [-0.2, -(limy + 0.1) * 3.4, 3.4]
+    P[:, 3:6] = [[-0.3, -0.9, -0.6], [-1.0, -0.4, -0.7]]
+    P[:, 6:10] = g.normal(size=(2, 4))
+    P[:, 10] = [0.8, 0.5]
+    P[:, 11:] = g.normal(0, 0.3, (2, 48))
+    u, v = P[:, 0] / P[:, 2], P[:, 1] / P[:, 2]
+    assert u[0] > limx and abs(v[0]) < limy and v[1] < -limy and abs(u[1]) < limx
+    gt = g.uniform(0, 1, (3, H, W))
+    res = orc.loss_and_grad(P, cam, gt, smooth=True)
+    assert np.all(res["fwd"]["proj"]["radius"] > 0)
+    G = res["G"]
+    h = 1e-5
+    fd = np.zeros_like(P)
+    for i in range(2):
+        for k in range(59):
+            Pp, Pm = P.copy(), P.copy()
+            Pp[i, k] += h
+            Pm[i, k] -= h
+            fd[i, k] = (orc.loss_only(Pp, cam, gt, smooth=True) - orc.loss_only(Pm, cam, gt, smooth=True)) / (2 * h)
+    scale = np.abs(fd).max()
+    err = np.abs(G - fd)
+    assert np.all(err <= 1e-5 * np.abs(fd) + 1e-7 * scale), (err / (np.abs(fd) + 1e-7 * scale)).max()
+    assert np.abs(G[:, 0:3]).min() > 1e-4 * scale
+
+
 def test_frozen_rows_get_no_gradient_and_active_rows_are_unchanged(orc):
     """Sec. 3.2.4: frozen Gaussians skip the gradient; unfrozen rows are exactly
     what the unmasked backward gives."""

@@ -116,6 +116,28 @@ def test_two_gaussians_blend_front_to_back(orc):
         assert np.allclose(f_["image"][:, v, u], want, atol=1e-12)
 
 
+def test_equal_depths_blend_in_index_order(orc):
+    """Splats at the same depth have equal sort keys; the stable sort keeps
+    them in ascending Gaussian index, so with two copies of one Gaussian
+    (different colours) the lower index is in front: C = c_lo a + c_hi a (1 - a),
+    and every tile lists the lower index first."""
+    W, H, f = 32, 32, 60.0
+    cam = _cam_on_axis(W, H, f, 16, 0.0, (0, 0, 0), orc)
+    red = _gauss([0, 0, 4.0], [math.log(0.4)] * 3, logit=0.3, dc=(1.0, 0.0, 0.0))
+    blue = _gauss([0, 0, 4.0], [math.log(0.4)] * 3, logit=0.3, dc=(0.0, 0.0, 1.0))
+    a = min(0.99, 1 / (1 + math.exp(-0.3)))
+    cr = np.array([1.0, 0, 0]) / (2 * math.sqrt(math.pi)) + 0.5
+    cb = np.array([0, 0, 1.0]) / (2 * math.sqrt(math.pi)) + 0.5
+    for lo, hi, c_lo, c_hi in ((red, blue, cr, cb), (blue, red, cb, cr)):
+        f_ = orc.forward(np.stack([lo, hi]), cam, sh_degree=0)
+        assert f_["proj"]["depth"][0] == f_["proj"]["depth"][1]
+        u, v = W // 2, H // 2
+        assert np.allclose(f_["image"][:, v, u], c_lo * a + c_hi * a * (1 - a), atol=1e-12)
+        rg = f_["ranges"]
+        lists = [f_["vals"][s:e].tolist() for s, e in rg if e > s]
+        assert lists and all(x == [0, 1] for x in lists)
+
+
 def test_anisotropic_projection_closed_form(orc):
     """An axis-aligned Gaussian straight ahead of the camera projects to
     J S^2 J^T (+ dilation): variances (f s_x / z)^2 + d and (f s_y / z)^2 + d,
