@@ -354,6 +354,8 @@ def gpu_arm(args):
                                 f"{peak_kind} peaks file)",
                     mean_launch_ms=rb_mean)
     adam = stages.get("adam_roofline")
+    project = stages.get("project_roofline")
+    adam_all = plain.get("adam_roofline")
 
     # ---- end to end through the public API with host buffers ----
     e2e = e2e_rate(tr, max(30, min(args.steps, 200)))
@@ -377,7 +379,8 @@ def gpu_arm(args):
                     fwd_ms=stages["fwd_ms"], bwd_ms=stages["bwd_ms"], stage_ms=stages["stage_ms"],
                     plain_its=plain["its"], plain_stage_ms=plain["stage_ms"], gsta_speedup_vs_plain=its / world /
                     plain["its"],
-                    roofline=roofline, roofline_adam=adam, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
+                    roofline=roofline, roofline_adam=adam, roofline_adam_all_active=adam_all,
+                    roofline_project=project, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
                     clocks=clk_summary, device_flags=flags)
         print(json.dumps(line), flush=True)
     reps.close()
@@ -440,6 +443,14 @@ def pair_counts(tr, views) -> list[float]:
     return [float(c) / len(sample) for c in counts.cpu().tolist()]
 
 
+# Algorithmic bytes of the projection per Gaussian: a culled one reads its
+# mean, scale, rotation and opacity (three 16-byte vectors) and writes a zero
+# splat record (48 B); a visible one also reads its 48 SH coefficients
+# (240 B in all) and writes its 48-byte record.
+PROJECT_BYTES_CULLED = 48 + 48
+PROJECT_BYTES_VISIBLE = 240 + 48
+
+
 def stage_split(tr, n) -> dict:
     import torch
 
@@ -449,6 +460,7 @@ def stage_split(tr, n) -> dict:
     names = ["project", "sort", "render", "loss", "raster_bwd", "project_bwd", "adam"]
     acc = {k: 0.0 for k in names}
     lrs = list(tr.lrs)
+    proj_bytes = 0
     for i in range(n):
         v = tr.order[tr.k + i]
         m.retarget(view, tr.cams[v])
@@ -474,8 +486,11 @@ def stage_split(tr, n) -> dict:
         torch.cuda.synchronize()
         for j, k in enumerate(names):
             acc[k] += ev[j].elapsed_time(ev[j + 1])
+        n_vis = int((m.splats[:m.n, 10].contiguous().view(torch.int32) > 0).sum().item())
+        proj_bytes += n_vis * PROJECT_BYTES_VISIBLE + (m.n - n_vis) * PROJECT_BYTES_CULLED
     st = {k: v / n for k, v in acc.items()}
     peaks, kind = _peaks()
+    proj_gbs = proj_bytes / n / (st["project"] / 1e3) / 1e9
     n_act = int(m.n_active.item())
     adam_bytes = n_act * 15 * 16 * 7  # read P, G, m, v and write P, m, v: 15 16-byte vectors each
     adam_gbs = adam_bytes / (st["adam"] / 1e3) / 1e9
@@ -483,7 +498,12 @@ def stage_split(tr, n) -> dict:
                 bwd_ms=st["loss"] + st["raster_bwd"] + st["project_bwd"],
                 adam_roofline=dict(bound="hbm", kernel="k_adam", achieved=adam_gbs, peak=peaks["hbm_gbs"],
                                    unit="GB/s", frac=adam_gbs / peaks["hbm_gbs"], traffic=None,
-                                   bytes_per_active_gaussian=15 * 16 * 7, active=n_act, peak_source=kind))
+                                   bytes_per_active_gaussian=15 * 16 * 7, active=n_act, peak_source=kind),
+                project_roofline=dict(bound="hbm", kernel="k_project_fwd", achieved=proj_gbs, peak=peaks["hbm_gbs"],
+                                      unit="GB/s", frac=proj_gbs / peaks["hbm_gbs"], traffic=None,
+                                      bytes_per_gaussian=dict(visible=PROJECT_BYTES_VISIBLE,
+                                                              culled=PROJECT_BYTES_CULLED),
+                                      gaussians=m.n, bytes_per_launch=round(proj_bytes / n), peak_source=kind))
 
 
 def plain_rate(tr, n) -> dict:
@@ -507,11 +527,11 @@ def plain_rate(tr, n) -> dict:
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    st = stage_split(tr, 10)["stage_ms"]
+    sp = stage_split(tr, 10)
     m.frozen.copy_(saved[0])
     m.act.copy_(saved[1])
     m.n_active.copy_(saved[2])
-    return dict(its=n / (ms / 1e3), stage_ms=st)
+    return dict(its=n / (ms / 1e3), stage_ms=sp["stage_ms"], adam_roofline=sp["adam_roofline"])
 
 
 def e2e_rate(tr, n) -> dict:
