@@ -244,8 +244,12 @@ __global__ void __launch_bounds__(kFB) k_sig_mark(int64_t n, const unsigned long
     if (i < n) mark[i] = (st->k > 0 && keys[i] <= st->prefix) ? 1 : 0;
 }
 
+// Group rates: lr[0..5] for xyz, scale, rotation, opacity, SH DC, SH rest;
+// lr[6] for float 59 (the volume-mask logit, 0 when it is not trained). The
+// kernel reads them at constant indices only: indexing a parameter array by
+// a run-time value makes every thread copy the whole struct to local memory.
 struct AdamArgs {
-    float lr[64];  // per float of a row (group rate; 0 for padding)
+    float lr[7];
     float b1, b2, eps, step_size_scale, inv_sqrt_bc2;
 };
 
@@ -260,10 +264,10 @@ __global__ void k_adam_step(int64_t *__restrict__ step, float b1, float b2, floa
     scales[1] = (float)(1.0 / sqrt(1.0 - pow((double)b2, (double)t)));
 }
 
-// Parameter group of float f of a row: xyz, scale, rotation, opacity, SH DC,
-// SH rest; -1 for the padding floats 59-63.
-__device__ __forceinline__ int lr_group(int f) {
-    return f < 3 ? 0 : f < 6 ? 1 : f < 10 ? 2 : f < 11 ? 3 : f < 14 ? 4 : f < 59 ? 5 : -1;
+// Rate of float f (0..59) of a row from the group rates l0..l6 (see AdamArgs).
+__device__ __forceinline__ float lr_of(int f, float l0, float l1, float l2, float l3, float l4, float l5,
+                                       float l6) {
+    return f < 3 ? l0 : f < 6 ? l1 : f < 10 ? l2 : f < 11 ? l3 : f < 14 ? l4 : f < 59 ? l5 : l6;
 }
 
 __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float *__restrict__ G,
@@ -271,14 +275,19 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float
                                               const int32_t *__restrict__ act, const int32_t *__restrict__ n_active,
                                               AdamArgs a, const float *__restrict__ scales,
                                               const float *__restrict__ lr_dev) {
-    if (scales) {
-        a.step_size_scale = scales[0];
-        a.inv_sqrt_bc2 = scales[1];
-    }
+    const float step_size_scale = scales ? scales[0] : a.step_size_scale;
+    const float inv_sqrt_bc2 = scales ? scales[1] : a.inv_sqrt_bc2;
+    float l0 = a.lr[0], l1 = a.lr[1], l2 = a.lr[2], l3 = a.lr[3], l4 = a.lr[4], l5 = a.lr[5], l6 = a.lr[6];
     if (lr_dev) {  // group rates from device memory (changed between graph replays)
-#pragma unroll
-        for (int f = 0; f < 64; ++f) a.lr[f] = lr_group(f) >= 0 ? lr_dev[lr_group(f)] : 0.f;
+        l0 = lr_dev[0];
+        l1 = lr_dev[1];
+        l2 = lr_dev[2];
+        l3 = lr_dev[3];
+        l4 = lr_dev[4];
+        l5 = lr_dev[5];
+        l6 = 0.f;
     }
+    const float b1 = a.b1, b2 = a.b2, eps = a.eps;
     const int64_t total = (int64_t)(*n_active) * kChunks;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -294,10 +303,10 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float g = gg[e];
-            mm[e] = a.b1 * mm[e] + (1.f - a.b1) * g;
-            vv[e] = a.b2 * vv[e] + (1.f - a.b2) * g * g;
-            const float lr = a.lr[4 * c + e];
-            pp[e] -= lr * a.step_size_scale * mm[e] / (sqrtf(vv[e]) * a.inv_sqrt_bc2 + a.eps);
+            mm[e] = b1 * mm[e] + (1.f - b1) * g;
+            vv[e] = b2 * vv[e] + (1.f - b2) * g * g;
+            const float lr = lr_of(4 * c + e, l0, l1, l2, l3, l4, l5, l6);
+            pp[e] -= lr * step_size_scale * mm[e] / (sqrtf(vv[e]) * inv_sqrt_bc2 + eps);
         }
         *reinterpret_cast<float4 *>(P + off) = make_float4(pp[0], pp[1], pp[2], pp[3]);
         *reinterpret_cast<float4 *>(m + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
@@ -317,6 +326,21 @@ int num_sms() {
         g_num_sms = v > 0 ? v : 152;
     }
     return g_num_sms;
+}
+
+int g_adam_per_sm = 0;
+
+// Blocks of k_adam that fit on the GPU at once: its grid-stride loop then runs
+// in a single wave, each block's share of the rows the same.
+int64_t adam_grid(int64_t n) {
+    if (g_adam_per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_adam, 256, 0) != cudaSuccess || v < 1) v = 4;
+        g_adam_per_sm = v;
+    }
+    int64_t blocks = (n * kChunks + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * g_adam_per_sm;
+    return blocks < cap ? blocks : cap;
 }
 
 }  // namespace
@@ -501,21 +525,15 @@ extern "C" int gs_adam_masked_groups(float *P, const float *G, float *m, float *
          reinterpret_cast<uintptr_t>(v)) & 15)
         return GS_ERR_INVALID_ARG;
     AdamArgs a;
-    static const int group_of[64] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 2, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5,
-                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5,
-                                     5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, -1};
-    for (int f = 0; f < 64; ++f) a.lr[f] = group_of[f] >= 0 ? lr[group_of[f]] : 0.f;
-    if (n_groups == 7) a.lr[59] = lr[6];  // the volume-mask logit
+    for (int k = 0; k < 6; ++k) a.lr[k] = lr[k];
+    a.lr[6] = n_groups == 7 ? lr[6] : 0.f;  // the volume-mask logit
     double bc1 = 1.0 - pow((double)b1, (double)step), bc2 = 1.0 - pow((double)b2, (double)step);
     a.b1 = b1;
     a.b2 = b2;
     a.eps = eps;
     a.step_size_scale = (float)(1.0 / bc1);
     a.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
-    const int64_t max_items = n * kChunks;
-    int64_t blocks = (max_items + 255) / 256;
-    int64_t cap = (int64_t)num_sms() * 8;
-    if (blocks > cap) blocks = cap;
+    const int64_t blocks = adam_grid(n);
     k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a, nullptr, nullptr);
     note_launches(1);
     return launch_status();
@@ -538,7 +556,7 @@ extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float 
          reinterpret_cast<uintptr_t>(v)) & 15)
         return GS_ERR_INVALID_ARG;
     AdamArgs a;
-    for (int f = 0; f < 64; ++f) a.lr[f] = 0.f;  // taken from lr_dev on the device
+    for (int k = 0; k < 7; ++k) a.lr[k] = 0.f;  // taken from lr_dev on the device
     a.b1 = b1;
     a.b2 = b2;
     a.eps = eps;
@@ -546,10 +564,7 @@ extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float 
     a.inv_sqrt_bc2 = 1.f;
     cudaStream_t s = as_stream(stream);
     k_adam_step<<<1, 1, 0, s>>>(step_dev, b1, b2, scratch_dev);
-    const int64_t max_items = n * kChunks;
-    int64_t blocks = (max_items + 255) / 256;
-    int64_t cap = (int64_t)num_sms() * 8;
-    if (blocks > cap) blocks = cap;
+    const int64_t blocks = adam_grid(n);
     k_adam<<<(unsigned)blocks, 256, 0, s>>>(P, G, m, v, act, n_active_dev, a, scratch_dev, lr_dev);
     note_launches(2);
     return launch_status();

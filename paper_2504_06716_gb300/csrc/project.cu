@@ -444,7 +444,9 @@ __device__ __forceinline__ void project_bwd_one(int64_t k, const float *__restri
     if (st.n) {
         const float ex = dmx * 0.5f * (float)cam.W, ey = dmy * 0.5f * (float)cam.H;
         const float nx = sqrtf(ex * ex + ey * ey), nr = sqrtf(gsh[0] * gsh[0] + gsh[1] * gsh[1] + gsh[2] * gsh[2]);
-        for (int k2 = 0; k2 < st.n; ++k2) {
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) {  // constant indices: st stays in parameter space
+            if (k2 >= st.n) break;
             st.ax[k2][i] += nx;
             st.ar[k2][i] += nr;
             st.cnt[k2][i] += 1;
