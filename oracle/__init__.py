@@ -33,6 +33,13 @@ def _plant() -> int:
     return int(os.environ.get("GSTA_ORACLE_PLANT", "0") or 0)
 
 
+def planted(k: int) -> bool:
+    """Whether this process runs the copy of the oracle with planted mistake k
+    (the Python modules' steps marked ``planted(k)``); False unless the pins'
+    own test set GSTA_ORACLE_PLANT."""
+    return _plant() == k
+
+
 def build(force: bool = False, plant: int | None = None) -> str:
     """Compile the oracle with gcc (IEEE arithmetic: no fast-math, no FMA contraction).
     plant k >= 1 compiles the copy with planted mistake k, into the temporary

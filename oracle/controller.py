@@ -21,6 +21,8 @@ from __future__ import annotations
 import dataclasses
 import math
 
+from oracle import planted
+
 
 @dataclasses.dataclass
 class ScheduleConfig:
@@ -54,7 +56,7 @@ class ScheduleConfig:
 def threshold(eps0: float, k: int, K: int) -> float:
     """Eq. 5 under the clamped-linear reading."""
     f = 0.5 + 1.5 * k / K
-    return eps0 * min(1.5, max(0.5, f))
+    return eps0 * (f if planted(31) else min(1.5, max(0.5, f)))
 
 
 def freeze_action(k: int, cfg: ScheduleConfig, last_reset: int | None, stop_iter: int | None) -> str | None:
@@ -72,7 +74,7 @@ def freeze_action(k: int, cfg: ScheduleConfig, last_reset: int | None, stop_iter
         return "clear"
     if k % cfg.reset_every == 0:
         return "reset"
-    if last_reset is not None and k < last_reset + cfg.wait:
+    if last_reset is not None and k < last_reset + cfg.wait and not planted(33):
         return "clear"
     return "update"
 
@@ -81,7 +83,7 @@ def early_stop(psnrs: list[float], eps: float) -> bool:
     """Eq. 7: both of the two most recent PSNR changes are below eps (signed changes)."""
     if len(psnrs) < 3:
         return False
-    return (psnrs[-1] - psnrs[-2]) < eps and (psnrs[-2] - psnrs[-3]) < eps
+    return (psnrs[-1] - psnrs[-2]) < eps and (planted(32) or (psnrs[-2] - psnrs[-3]) < eps)
 
 
 class Plateau:
@@ -99,7 +101,7 @@ class Plateau:
             self.bad = 0
         else:
             self.bad += 1
-            if self.bad > self.patience:
+            if self.bad > (0 if planted(36) else self.patience):
                 self.lr *= self.decay
                 self.bad = 0
         return self.lr

@@ -43,6 +43,8 @@ import math
 
 import numpy as np
 
+from oracle import planted
+
 
 @dataclasses.dataclass
 class DensifyParams:
@@ -85,7 +87,7 @@ def decisions(P, dacc_xyz, dacc_rgb, dcnt, max_radius, prm: DensifyParams) -> di
     if prm.use_rgb:
         cand |= seen & (avg_r >= f32(prm.eps_rgb))
     smax = P32[:, 3:6].max(axis=1) if n else np.zeros(0, np.float32)
-    clone = cand & (smax <= f32(prm.log_clone_max))
+    clone = cand & ((smax > f32(prm.log_clone_max)) if planted(27) else (smax <= f32(prm.log_clone_max)))
     split = cand & ~clone
     child_smax = (smax - f32(prm.log_split_div)).astype(np.float32)
     low_op = P32[:, 10] < f32(prm.logit_min_opacity)
@@ -112,7 +114,7 @@ def densify(P, dacc_xyz, dacc_rgb, dcnt, max_radius, prm: DensifyParams, z):
     n = P.shape[0]
     P32 = P.astype(np.float32)
     d = decisions(P, dacc_xyz, dacc_rgb, dcnt, max_radius, prm)
-    keep_orig = ~d["split"] & ~d["low_op"] & ~d["big_world"] & ~d["big_screen"]
+    keep_orig = (True if planted(29) else ~d["split"]) & ~d["low_op"] & ~d["big_world"] & ~d["big_screen"]
     keep_clone = d["clone"] & ~d["low_op"] & ~d["big_world"]   # a clone is an exact copy, with no screen record
     keep_child = d["split"] & ~d["low_op"] & ~d["big_child"]
     split_idx = np.nonzero(d["split"])[0]
@@ -129,7 +131,7 @@ def densify(P, dacc_xyz, dacc_rgb, dcnt, max_radius, prm: DensifyParams, z):
         s = np.exp(P[i, 3:6])
         for k in range(2):
             c = P[i].copy()
-            c[0:3] = P[i, 0:3] + R @ (s * z[r, k])
+            c[0:3] = P[i, 0:3] + (s * z[r, k] if planted(28) else R @ (s * z[r, k]))
             c[3:6] = [float(f32(P32[i, 3 + a] - f32(prm.log_split_div))) for a in range(3)]
             rows.append(c); src.append(i); kind.append(2 + k)
     out = np.array(rows).reshape(-1, P.shape[1]) if rows else np.zeros((0, P.shape[1]))
@@ -156,8 +158,9 @@ def opacity_reset(P, M, V, logit_cap, frozen=None):
     cap = f32(logit_cap)
     sel = np.ones(P.shape[0], bool) if frozen is None else (np.asarray(frozen) == 0)
     P[sel, 10] = np.minimum(np.asarray(P[sel, 10], np.float32), cap)
-    M[sel, 10] = 0.0
-    V[sel, 10] = 0.0
+    if not planted(30):
+        M[sel, 10] = 0.0
+        V[sel, 10] = 0.0
 
 
 def opacity_to_abs(P, M, V, rescale: bool = False):

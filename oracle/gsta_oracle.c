@@ -1202,7 +1202,7 @@ double or_bf16(double x) {
     float f = (float)x;
     uint32_t b;
     memcpy(&b, &f, 4);
-    b += 0x7fffu + ((b >> 16) & 1u);
+    if (!PLANTED(22)) b += 0x7fffu + ((b >> 16) & 1u);
     b &= 0xffff0000u;
     memcpy(&f, &b, 4);
     return (double)f;
@@ -1222,7 +1222,7 @@ void or_pred_history(int64_t n, const float *acc_xyz, const float *acc_rgb, cons
         if (cnt[i] > 0) {
             s[8] = 0.5 * s[8] + 0.5 * ((double)acc_xyz[i] / cnt[i]);
             s[9] = 0.5 * s[9] + 0.5 * ((double)acc_rgb[i] / cnt[i]);
-            s[10] += cnt[i];
+            s[10] += PLANTED(23) ? 1 : cnt[i];
         }
         if (frozen && frozen[i]) s[11] += 1;
         for (int j = 3; j > 0; --j) { s[j] = s[j - 1]; s[4 + j] = s[4 + j - 1]; }
@@ -1252,7 +1252,7 @@ void or_pred_features(int64_t n, const double *P, const float *acc_xyz, const fl
             x[j] = log_ratio(s[j], eps_xyz);
             x[4 + j] = log_ratio(s[4 + j], eps_rgb);
         }
-        x[8] = 1.0 / (1.0 + exp(-p[10]));
+        x[8] = PLANTED(24) ? p[10] : 1.0 / (1.0 + exp(-p[10]));
         double mx = p[3], mn = p[3];
         for (int j = 4; j < 6; ++j) { if (p[j] > mx) mx = p[j]; if (p[j] < mn) mn = p[j]; }
         x[9] = mx;
@@ -1280,7 +1280,7 @@ static double mlp_row(const double *xin, const double *prm, int round, double *x
             s += xr[c] * (round ? or_bf16(w) : w);
         }
         a1[j] = s;
-        double h = s > 0 ? s : 0;
+        double h = (s > 0 || PLANTED(20)) ? s : 0;
         h1r[j] = round ? or_bf16(h) : h;
     }
     double z = prm[OFF_B3];
@@ -1329,7 +1329,7 @@ double or_mlp_loss_grad(int64_t n, const double *X, const double *y, const doubl
         for (int j = 0; j < MLP_H; ++j) {
             double w3 = prm[OFF_W3 + j];
             ADDG(OFF_W3 + j, dz * h2[j]);
-            dh2[j] = a2[j] > 0 ? dz * (round ? or_bf16(w3) : w3) : 0.0;
+            dh2[j] = (a2[j] > 0 || PLANTED(21)) ? dz * (round ? or_bf16(w3) : w3) : 0.0;
             ADDG(OFF_B2 + j, dh2[j]);
         }
         for (int c = 0; c < MLP_H; ++c) {
@@ -1356,7 +1356,7 @@ void or_mlp_adam(double *prm, const double *grad, double *m, double *v, double l
     for (int k = 0; k < MLP_NPARAM; ++k) {
         m[k] = b1 * m[k] + (1 - b1) * grad[k];
         v[k] = b2 * v[k] + (1 - b2) * grad[k] * grad[k];
-        prm[k] -= lr * (m[k] / bc1) / (sqrt(v[k] / bc2) + eps);
+        prm[k] -= lr * (m[k] / (PLANTED(26) ? 1.0 : bc1)) / (sqrt(v[k] / bc2) + eps);
     }
 }
 
@@ -1366,6 +1366,7 @@ int64_t or_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen
     int64_t k = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (prob[i] > tau) frozen[i] = 1;
+        else if (PLANTED(25)) frozen[i] = 0;
         if (!frozen[i]) act[k++] = (int32_t)i;
     }
     return k;

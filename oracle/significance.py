@@ -47,6 +47,8 @@ def scores(P, hits, beta: float = BETA, quantile: float = QUANTILE, opacity_abs:
     k = int(math.floor(quantile * n))
     v_q = vol[order[k - 1]] if k >= 1 else 0.0
     o = np.abs(P[:, 10]) if opacity_abs else 1.0 / (1.0 + np.exp(-P[:, 10]))
+    if oracle.planted(34):
+        o = 1.0
     v = (vol / v_q) ** beta if v_q > 0 else np.ones(n)
     return np.asarray(hits, np.float64) * o * v
 
@@ -58,5 +60,6 @@ def mark(score, fraction: float) -> np.ndarray:
     k = int(math.floor(fraction * n))
     out = np.zeros(n, np.uint8)
     if k > 0:
-        out[np.lexsort((np.arange(n), score))[:k]] = 1
+        order = np.lexsort((np.arange(n), score))
+        out[(order[::-1] if oracle.planted(35) else order)[:k]] = 1
     return out

@@ -1,9 +1,11 @@
 """The oracle's pins catch planted mistakes.
 
-Each mutant is the oracle compiled with one deliberate mistake (the step
-marked PLANTED(k) in ``oracle/gsta_oracle.c``): a dropped term, a sign flip,
-a transposed operand, a missing Jacobian entry, a wrong constant or cut-off,
-a wrong tie order, a skipped freeze test. The oracle's CPU pins
+Each mutant is the oracle with one deliberate mistake: the step marked
+PLANTED(k) in ``oracle/gsta_oracle.c`` (compiled in with -DORACLE_PLANT=k)
+or ``planted(k)`` in the oracle's Python modules (switched on by the
+environment variable GSTA_ORACLE_PLANT=k) -- a dropped term, a sign flip, a
+transposed operand, a missing Jacobian entry, a wrong constant or cut-off,
+a wrong tie order, a skipped freeze test, a wrong schedule or selection. The oracle's CPU pins
 (``tests/test_oracle_*.py`` and the finite-difference checks in
 ``tests/test_fd_local.py``) run against each mutant in a child process and
 must fail; against the oracle itself they pass (the rest of this suite).
@@ -38,6 +40,23 @@ MUTANTS = {
     17: "factor 2 of the projected-covariance gradient dropped",
     18: "clamped screen coordinates still pass gradient",
     19: "positional gradient norm in pixels instead of (W/2, H/2) units",
+    20: "predictor: first hidden layer without its ReLU",
+    21: "predictor: second ReLU's derivative dropped in the gradient",
+    22: "predictor: bfloat16 by truncation instead of round-to-nearest-even",
+    23: "predictor history: one view per visible window instead of the visible count",
+    24: "predictor feature 8: opacity logit instead of the opacity",
+    25: "predicted freezing clears an existing freeze",
+    26: "predictor Adam: first-moment bias correction dropped",
+    27: "densification clones the large candidates and splits the small",
+    28: "split children offset without the Gaussian's rotation",
+    29: "a split original is kept beside its children",
+    30: "opacity reset leaves the opacity's Adam moments",
+    31: "Eq. 5 thresholds without the [0.5, 1.5] clamp",
+    32: "Eq. 7 early stop on the most recent PSNR change alone",
+    33: "no waiting period after a freeze-map reset",
+    34: "significance score without the opacity factor",
+    35: "significance pruning removes the highest scores",
+    36: "plateau schedule decays without patience",
 }
 
 
@@ -54,8 +73,7 @@ def _pins(k: int) -> subprocess.CompletedProcess:
 def outcomes():
     import oracle
 
-    for k in MUTANTS:
-        oracle.build(plant=k)
+    oracle.build()  # the unplanted library; each child compiles its own planted copy
     with ThreadPoolExecutor(4) as ex:
         return dict(zip(MUTANTS, ex.map(_pins, MUTANTS)))
 
