@@ -35,6 +35,8 @@ import math
 
 import numpy as np
 
+from oracle import planted
+
 RULE, XYZ, RANDOM, MINGRAD = 0, 1, 2, 3
 
 
@@ -57,6 +59,8 @@ def mingrad_scores(acc_xyz, acc_rgb, cnt, eps_xyz: float, eps_rgb: float):
     ax, ar = window_averages(acc_xyz, acc_rgb, cnt)
     sx = ax / np.float32(eps_xyz)
     sr = ar / np.float32(eps_rgb)
+    if planted(37):
+        return np.where(sx > sr, sr, sx).astype(np.float32)
     return np.where(sx > sr, sx, sr).astype(np.float32)
 
 
@@ -68,7 +72,7 @@ def select(acc_xyz, acc_rgb, cnt, frozen, eps_xyz: float, eps_rgb: float, strate
     frozen = np.asarray(frozen, np.uint8)
     n = frozen.shape[0]
     cnt = np.asarray(cnt, np.int64)
-    eligible = (frozen == 0) & (cnt > 0)
+    eligible = (frozen == 0) & ((cnt >= 0) if planted(38) else (cnt > 0))
     ax, ar = window_averages(acc_xyz, acc_rgb, cnt)
     new = np.zeros(n, bool)
     if strategy == RULE:

@@ -31,6 +31,8 @@ import math
 
 import numpy as np
 
+from oracle import planted
+
 S0, K_PROG, SIGMA0, K_BLUR, SIGMA_MIN, BLUR_RADIUS = 0.175, 6000, 1.0, 6000, 0.1, 2
 
 
@@ -54,7 +56,7 @@ def area_weights(n_src: int, n_dst: int) -> np.ndarray:
     r = n_dst / n_src
     Wm = np.zeros((n_dst, n_src))
     for i in range(n_dst):
-        a, b = i / r - 0.5, (i + 1) / r - 0.5
+        a, b = (i / r, (i + 1) / r) if planted(40) else (i / r - 0.5, (i + 1) / r - 0.5)
         for j in range(n_src):
             ov = min(b, j + 0.5) - max(a, j - 0.5)
             if ov > 0:
@@ -74,6 +76,8 @@ def resize_area(img, W2: int, H2: int) -> np.ndarray:
 def camera_at(fx: float, fy: float, cx: float, cy: float, W: int, H: int, W2: int, H2: int):
     """Intrinsics of the W2 x H2 image covering the same extent of the image plane."""
     rx, ry = W2 / W, H2 / H
+    if planted(39):
+        return fx * rx, fy * ry, cx * rx, cy * ry
     return fx * rx, fy * ry, (cx + 0.5) * rx - 0.5, (cy + 0.5) * ry - 0.5
 
 
@@ -93,7 +97,7 @@ def blur(img, sigma: float, radius: int = BLUR_RADIUS) -> np.ndarray:
                 for dx in range(-radius, radius + 1):
                     yy, xx = y + dy, x + dx
                     if 0 <= yy < H and 0 <= xx < W:
-                        w = math.exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma))
+                        w = math.exp(-(dx * dx + dy * dy) / ((1.0 if planted(41) else 2.0) * sigma * sigma))
                         acc += w * img[:, yy, xx]
                         wsum += w
             out[:, y, x] = acc / wsum

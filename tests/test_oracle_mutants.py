@@ -57,6 +57,11 @@ MUTANTS = {
     34: "significance score without the opacity factor",
     35: "significance pruning removes the highest scores",
     36: "plateau schedule decays without patience",
+    37: "mingrad score takes the smaller of the two ratios",
+    38: "Gaussians not seen in the window are eligible for freezing",
+    39: "downscaled camera's principal point without the half-pixel shift",
+    40: "area average footprint shifted by half a source pixel",
+    41: "blur kernel exp(-r^2 / sigma^2)",
 }
 
 
