@@ -457,7 +457,7 @@ __device__ __forceinline__ void project_bwd_one(int64_t k, const float *__restri
 
 // A grid sized for the device, each thread walking the active list with a
 // stride: the list's length is known only on the device.
-__global__ void __launch_bounds__(128) k_project_bwd(const float *__restrict__ P, int deg, int flags, float mask_loss,
+__global__ void __launch_bounds__(128, 4) k_project_bwd(const float *__restrict__ P, int deg, int flags, float mask_loss,
                                                      DevCam cam, const float *__restrict__ splats,
                                                      const int32_t *__restrict__ act,
                                                      const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
@@ -517,7 +517,15 @@ static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, i
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const unsigned grid = std::min<unsigned>(grid_for(n, 128), (unsigned)(sms > 0 ? sms : 152) * 8u);
+    // as many blocks as are resident at once: the grid-stride loop then runs in
+    // one wave, every block with the same share of the active list
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_project_bwd, 128, 0) != cudaSuccess || v < 1) v = 2;
+        per_sm = v;
+    }
+    const unsigned grid = std::min<unsigned>(grid_for(n, 128), (unsigned)(sms > 0 ? sms : 152) * (unsigned)per_sm);
     k_project_bwd<<<grid, 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, mask_loss, dc, splats, act,
                                                         n_active_dev, grad2d, G, st, acc ? 1 : 0);
     note_launches(1);
