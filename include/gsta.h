@@ -128,7 +128,8 @@ int gs_project(const float *P, int64_t n, int32_t sh_degree, const gs_camera *ca
 int gs_project_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opacity_act, const gs_camera *cam,
                   float *splats, gs_stream_t stream);
 
-/* Bytes of workspace gs_sort needs for n Gaussians and `capacity` entries
+/* Workspace of the per-tile depth order (Sec. 3.1, the sort below).
+ * Bytes of workspace gs_sort needs for n Gaussians and `capacity` entries
  * on a width x height image with this tile size (0 for invalid sizes). */
 size_t gs_sort_workspace_bytes(int64_t n, int64_t capacity, int32_t width, int32_t height, int32_t tile);
 
@@ -169,11 +170,12 @@ typedef struct {
     int32_t batch;             /* splats staged per shared-memory batch: 32, 64, 128 or 256 */
 } gs_raster_config;
 
-/* gs_render_fwd with an explicit launch shape (cfg may be NULL). */
+/* Sec. 3.1, Eq. 2: gs_render_fwd with an explicit launch shape (cfg may be
+ * NULL). */
 int gs_render_fwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                       const gs_raster_config *cfg, float *image, float *t_final, int32_t *n_last, gs_stream_t stream);
 
-/* Bytes of workspace gs_loss needs for an H x W image. */
+/* Workspace of the Eq. 3 loss: bytes gs_loss needs for an H x W image. */
 size_t gs_loss_workspace_bytes(int32_t H, int32_t W);
 
 /* Sec. 3.1, Eq. 3, L = (1 - lambda) L1 + lambda (1 - SSIM), lambda = 0.2 in
@@ -198,12 +200,16 @@ int gs_raster_bwd(const float *splats, const uint32_t *vals, const uint32_t *ran
                   const float *t_final, const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen,
                   float *grad2d, gs_stream_t stream);
 
-/* gs_raster_bwd with an explicit launch shape (cfg may be NULL). */
+/* Sec. 3.2.4: gs_raster_bwd with an explicit launch shape (cfg may be
+ * NULL). */
 int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                       const gs_raster_config *cfg, const float *t_final, const int32_t *n_last,
                       const float *dl_dimage, const uint8_t *frozen, float *grad2d, gs_stream_t stream);
 
-/* One rendering job of a batch: a view of one scene (all pointers device,
+/* Several scenes in one launch. The paper trains one scene at a time and
+ * has no counterpart; each job computes what gs_render_fwd (Sec. 3.1,
+ * Eq. 2) or gs_raster_bwd (Sec. 3.2.4) computes for one view.
+ * One rendering job of a batch: a view of one scene (all pointers device,
  * the camera by value). Used by the batch calls below. */
 typedef struct {
     const float *splats;     /* [n][12] of the job's scene, projected for this view */
@@ -246,7 +252,7 @@ int gs_project_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera
                    const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, float *acc_xyz,
                    float *acc_rgb, int32_t *cnt, gs_stream_t stream);
 
-/* gs_project_bwd that ADDS its gradient rows into G instead of writing them
+/* Sec. 3.2.4: gs_project_bwd that ADDS its gradient rows into G instead of writing them
  * (several views of one scene in one optimiser step: call gs_project_bwd for
  * the first view, this for the others). */
 int gs_project_bwd_accum(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
@@ -271,7 +277,8 @@ int gs_project_bwd_stats(const float *P, int64_t n, int32_t sh_degree, const gs_
                          const int32_t *act, const int32_t *n_active_dev, float *grad2d, float *G, int32_t accumulate,
                          const gs_grad_stats *sets, int32_t n_sets, gs_stream_t stream);
 
-/* gs_project_bwd_stats for the parameterisation `opacity_act` (as in
+/* Sec. 3.2.4 under the activations of Sec. 4.1 (absolute-value opacity) and
+ * Sec. 3.3 (volume mask): gs_project_bwd_stats for the parameterisation `opacity_act` (as in
  * gs_project_ex): dL/dx = dL/dopacity * sigmoid'(x), or * sign(x) (0 at
  * x = 0) under GS_OPACITY_ABS. Under GS_VOLUME_MASK the mask logit's
  * gradient, G[i][59], is the straight-through one, (dL/dM + mask_loss) *
@@ -285,7 +292,8 @@ int gs_project_bwd_ex(const float *P, int64_t n, int32_t sh_degree, int32_t opac
                       float *grad2d, float *G, int32_t accumulate, const gs_grad_stats *sets, int32_t n_sets,
                       gs_stream_t stream);
 
-/* gs_raster_bwd followed by gs_project_bwd on the same stream. */
+/* Sec. 3.2.4, the backward of Algorithm 1's rasterisation step:
+ * gs_raster_bwd followed by gs_project_bwd on the same stream. */
 int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera *cam, const float *splats,
                   const uint32_t *vals, const uint32_t *ranges, const float *t_final, const int32_t *n_last,
                   const float *dl_dimage, const uint8_t *frozen, const int32_t *act, const int32_t *n_active_dev,
@@ -370,7 +378,8 @@ size_t gs_significance_workspace_bytes(int64_t n);
 int gs_significance_mark(int64_t n, const float *P, const uint32_t *hits, int32_t opacity_act, float beta,
                          float quantile, float fraction, uint8_t *mark, void *ws, size_t ws_bytes, gs_stream_t stream);
 
-/* Bytes of workspace gs_freeze_update needs for n Gaussians. */
+/* Workspace of the Sec. 3.2.1 freeze update: bytes gs_freeze_update needs
+ * for n Gaussians. */
 size_t gs_freeze_workspace_bytes(int64_t n);
 
 /* Sec. 3.2.1, Eqs. 4-6, with the cadence of Sec. 4.1. mode:
@@ -450,8 +459,9 @@ int gs_adam_masked(float *P, const float *G, float *m, float *v, int64_t n, cons
                    const int32_t *n_active_dev, const float *lr, float b1, float b2, float eps, int64_t step,
                    gs_stream_t stream);
 
-/* gs_adam_masked with n_groups (6 or 7) learning rates: a seventh, lr[6],
- * is the rate of float 59, the volume-mask logit (0 with six). */
+/* Sec. 3.2.4 with the volume masks of Sec. 3.3: gs_adam_masked with
+ * n_groups (6 or 7) learning rates: a seventh, lr[6], is the rate of
+ * float 59, the volume-mask logit (0 with six). */
 int gs_adam_masked_groups(float *P, const float *G, float *m, float *v, int64_t n, const int32_t *act,
                           const int32_t *n_active_dev, const float *lr, int32_t n_groups, float b1, float b2,
                           float eps, int64_t step, gs_stream_t stream);
@@ -518,7 +528,8 @@ int gs_mlp_refresh(const float *params, uint16_t *wb, gs_stream_t stream);
 int gs_freeze_apply(int64_t n, const float *prob, float tau, uint8_t *frozen, int32_t *act, int32_t *n_active_dev,
                     void *ws, size_t ws_bytes, gs_stream_t stream);
 
-/* gs_adam_masked with the step counter and the six group learning rates in
+/* Sec. 3.2.4 for graph replay (the paper has no counterpart of the device-side
+ * step): gs_adam_masked with the step counter and the six group learning rates in
  * device memory: *step_dev is advanced by one and the bias correction taken
  * at the new value, and the rates are read from lr_dev [6] (same order as
  * gs_adam_masked's lr) when the kernel runs, so a captured CUDA graph can
@@ -630,7 +641,7 @@ int gs_opacity_reset(int64_t n, float *P, float *m, float *v, float logit_cap, c
 int gs_opacity_to_abs(int64_t n, float *P, float *m, float *v, int32_t moments, float *slope_sum_dev,
                       gs_stream_t stream);
 
-/* Bytes of workspace gs_psnr needs for S images of H x W. */
+/* Workspace of the Eq. 7 PSNR: bytes gs_psnr needs for S images of H x W. */
 size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W);
 
 /* Sec. 3.2.2, Eq. 7 input: psnr[s] = 10 log10(1 / MSE) of clamp(image, 0, 1)
@@ -639,7 +650,9 @@ size_t gs_psnr_workspace_bytes(int32_t S, int32_t H, int32_t W);
 int gs_psnr(const float *images, const float *gts, int32_t S, int32_t H, int32_t W, void *ws, size_t ws_bytes,
             float *psnr_dev, gs_stream_t stream);
 
-/* Synchronises `stream`, then reads and clears the current device's error
+/* Library plumbing below (errors, accounting, version): the paper has no
+ * counterpart.
+ * Synchronises `stream`, then reads and clears the current device's error
  * word into *flags_host (GS_FLAG_* bits). Returns GS_OK when no bit was set,
  * GS_ERR_DEVICE_FLAG otherwise, GS_ERR_CUDA on a CUDA failure. */
 int gs_get_device_error(uint32_t *flags_host, gs_stream_t stream);
