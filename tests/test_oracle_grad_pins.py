@@ -159,6 +159,38 @@ def test_loss_single_pixel_closed_form(orc):
     assert orc.loss(x, y, grad=False)[0] == pytest.approx(want, rel=1e-14)
 
 
+def test_loss_equals_ssim_from_library_convolutions(orc):
+    """Eq. 3 against an independent statement: the 11x11 Gaussian window
+    (sigma 1.5, normalised) applied with scipy's 2-D convolution (zero fill
+    outside the image), SSIM = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 +
+    C1)(sx + sy + C2)) with C1 = 0.01^2, C2 = 0.03^2, averaged over the three
+    channels; L = 0.8 mean|x - y| + 0.2 (1 - SSIM)."""
+    from scipy.signal import convolve2d
+
+    g = np.random.default_rng(4)
+    H, W = 23, 31
+    x = g.uniform(0, 1, (3, H, W))
+    y = np.clip(x + g.normal(0, 0.2, (3, H, W)), 0, 1)
+    t = np.exp(-((np.arange(11) - 5.0) ** 2) / (2 * 1.5 ** 2))
+    t /= t.sum()
+    w = np.outer(t, t)
+
+    def filt(a):
+        return convolve2d(a, w, mode="same", boundary="fill", fillvalue=0.0)
+
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    ssim = []
+    for c in range(3):
+        mx, my = filt(x[c]), filt(y[c])
+        sx, sy, sxy = filt(x[c] ** 2) - mx ** 2, filt(y[c] ** 2) - my ** 2, filt(x[c] * y[c]) - mx * my
+        ssim.append((2 * mx * my + C1) * (2 * sxy + C2) / ((mx ** 2 + my ** 2 + C1) * (sx + sy + C2)))
+    want = 0.8 * np.abs(x - y).mean() + 0.2 * (1.0 - np.mean(ssim))
+    got = orc.loss(x, y, grad=False)[0]
+    assert got == pytest.approx(want, rel=1e-12, abs=1e-14)
+    assert orc.loss(x, y, lam=0.5, grad=False)[0] == pytest.approx(
+        0.5 * np.abs(x - y).mean() + 0.5 * (1.0 - np.mean(ssim)), rel=1e-12)
+
+
 def test_loss_is_symmetric(orc):
     g = np.random.default_rng(1)
     x, y = g.uniform(0, 1, (3, 19, 14)), g.uniform(0, 1, (3, 19, 14))

@@ -42,6 +42,27 @@ def test_sh_orthonormal_by_quadrature(orc):
     assert np.abs(G - np.eye(16)).max() < 1e-12
 
 
+def test_sh_basis_equals_library_spherical_harmonics(orc):
+    """The real basis against scipy's complex spherical harmonics (which
+    carry the Condon-Shortley phase): coefficient l^2 + l + m is
+    sqrt(2) Re Y_l^m for m > 0, sqrt(2) Im Y_l^|m| for m < 0 and Y_l^0 for
+    m = 0, at the polar angle of z and the azimuth of (x, y)."""
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    g = np.random.default_rng(8)
+    for _ in range(50):
+        d = g.normal(size=3)
+        d /= np.linalg.norm(d)
+        theta, phi = math.acos(d[2]), math.atan2(d[1], d[0])
+        want = []
+        for l in range(4):
+            for m in range(-l, l + 1):
+                y = complex(sp.sph_harm_y(l, abs(m), theta, phi))
+                want.append(math.sqrt(2) * y.real if m > 0 else math.sqrt(2) * y.imag if m < 0 else y.real)
+        assert np.allclose(orc.sh_basis(d), want, rtol=1e-12, atol=1e-13)
+
+
 def test_sh_band0_constant_and_band1_directions(orc):
     d = np.array([0.36, -0.48, 0.8])
     Y = orc.sh_basis(d)
