@@ -174,6 +174,47 @@ def test_anisotropic_projection_closed_form(orc):
     assert pr["radius"][0] == math.ceil(3 * math.sqrt(max(vx, vy)))
 
 
+def test_projected_covariance_from_library_rotation_and_numeric_jacobian(orc):
+    """Eq. 1 against independent pieces: the rotation of the quaternion
+    (w, x, y, z) from scipy's Rotation (scalar-last input), Sigma = R S^2 R^T,
+    and the Jacobian of the pixel mapping mu -> (fx x_c / z_c + cx, fy y_c /
+    z_c + cy) taken by central differences in world space; the 2-D
+    covariance is J Sigma J^T + dilation I, its inverse the conic, the mean
+    the mapping itself. Gaussians well inside the view (no clamping)."""
+    Rot = pytest.importorskip("scipy.spatial.transform").Rotation
+    cam = synth.pinhole(96, 72, 60.0, (0.7, -3.5, 1.2))
+    ocam = orc.make_cam(cam, tile=16, dilation=0.3)
+    g = np.random.default_rng(12)
+    n = 40
+    P = np.zeros((n, 59))
+    P[:, 0:3] = g.uniform(-0.4, 0.4, (n, 3))
+    P[:, 3:6] = g.normal(-2.0, 0.4, (n, 3))
+    P[:, 6:10] = g.normal(size=(n, 4))
+    P[:, 10] = 1.0
+    pr = orc.project(P, ocam, 0)
+    R_c, t_c = np.asarray(cam.R), np.asarray(cam.t)
+
+    def pix(mu):
+        c = R_c @ mu + t_c
+        return np.array([cam.fx * c[0] / c[2] + cam.cx, cam.fy * c[1] / c[2] + cam.cy])
+
+    checked = 0
+    for i in range(n):
+        if pr["radius"][i] <= 0:
+            continue
+        q = P[i, 6:10]
+        R = Rot.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        Sigma = R @ np.diag(np.exp(2 * P[i, 3:6])) @ R.T
+        h = 1e-6
+        J = np.stack([(pix(P[i, 0:3] + h * e) - pix(P[i, 0:3] - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        cov = J @ Sigma @ J.T + 0.3 * np.eye(2)
+        conic = np.linalg.inv(cov)
+        assert np.allclose(pr["conic"][i], [conic[0, 0], conic[0, 1], conic[1, 1]], rtol=1e-7, atol=1e-12)
+        assert np.allclose(pr["mean2d"][i], pix(P[i, 0:3]), rtol=1e-12, atol=1e-9)
+        checked += 1
+    assert checked > 30
+
+
 def test_near_plane_and_offscreen_culling(orc):
     cam = _cam_on_axis(64, 64, 100.0, 16, 0.3, (0, 0, 0), orc)
     P = np.stack([
