@@ -263,6 +263,31 @@ def test_adam_first_steps_closed_form(orc):
     assert np.allclose(P, P1 - lr[group] * m / (np.sqrt(v) + 1e-15), rtol=1e-13, atol=1e-16)
 
 
+def test_adam_matches_torch_adam_over_several_steps(orc):
+    """The oracle's Adam (Sec. 3.2.4's optimiser, vanilla 3DGS settings)
+    against torch.optim.Adam in float64 with the six parameter groups as
+    separate groups: five steps of random gradients, nothing frozen."""
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(17)
+    n = 7
+    P0 = g.normal(size=(n, 59))
+    groups = [(0, 3), (3, 6), (6, 10), (10, 11), (11, 14), (14, 59)]
+    lr = np.array([1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4])
+    b1, b2, eps = 0.9, 0.999, 1e-15
+    tp = [torch.tensor(P0[:, a:b], dtype=torch.float64, requires_grad=True) for a, b in groups]
+    opt = torch.optim.Adam([dict(params=[t], lr=float(r)) for t, r in zip(tp, lr)], betas=(b1, b2), eps=eps,
+                           foreach=False)
+    P, M, V = P0.copy(), np.zeros_like(P0), np.zeros_like(P0)
+    for step in range(1, 6):
+        G = g.normal(size=(n, 59)) * 10.0 ** g.uniform(-6, 0, (n, 59))
+        for t, (a, b) in zip(tp, groups):
+            t.grad = torch.tensor(G[:, a:b], dtype=torch.float64)
+        opt.step()
+        orc.adam(P, G, M, V, None, lr, step=step, b1=b1, b2=b2, eps=eps)
+        want = np.concatenate([t.detach().numpy() for t in tp], axis=1)
+        assert np.allclose(P, want, rtol=1e-12, atol=1e-15)
+
+
 def test_adam_leaves_frozen_rows_bit_unchanged(orc):
     rng = np.random.default_rng(1)
     P, M, V = rng.normal(size=(6, 59)), rng.normal(size=(6, 59)), rng.uniform(0, 1, (6, 59))

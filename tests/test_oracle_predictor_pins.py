@@ -64,6 +64,38 @@ def test_mlp_gradient_by_central_differences(weighted):
         assert grad[k] == pytest.approx(fd, rel=1e-5, abs=1e-10), k
 
 
+def test_mlp_loss_and_gradient_match_torch_autograd():
+    """Without bfloat16 rounding, the forward p = sigmoid(relu(relu(X W1 +
+    b1) W2 + b2) . W3 + b3) and the weighted binary cross-entropy's gradient
+    over all 5313 parameters against torch autograd in float64."""
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(23)
+    n = 57
+    X = g.normal(0, 1.5, (n, 16))
+    y = (g.uniform(size=n) < 0.4).astype(np.float64)
+    w = g.uniform(0.2, 3.0, n)
+    prm = _params(5, 0.4)
+    t = torch.tensor(prm, dtype=torch.float64, requires_grad=True)
+    W1 = t[0:1024].view(16, 64)
+    b1 = t[1024:1088]
+    W2 = t[1088:5184].view(64, 64)
+    b2 = t[5184:5248]
+    W3 = t[5248:5312]
+    b3 = t[5312]
+    Xt = torch.tensor(X)
+    z = torch.relu(torch.relu(Xt @ W1 + b1) @ W2 + b2) @ W3 + b3
+    wt = torch.tensor(w)
+    L = (wt * (torch.nn.functional.softplus(z) - torch.tensor(y) * z)).sum() / wt.sum()
+    L.backward()
+    p = O.mlp_forward(X, prm, round_bf16=False)
+    assert np.allclose(p, torch.sigmoid(z).detach().numpy(), rtol=1e-12, atol=1e-15)
+    Lo, go = O.mlp_loss_grad(X, y, prm, w=w, round_bf16=False)
+    assert Lo == pytest.approx(float(L.detach()), rel=1e-12)
+    gt = t.grad.numpy()
+    assert np.allclose(go, gt, rtol=1e-10, atol=1e-14 * np.abs(gt).max())
+    assert np.abs(gt[0:1024]).max() > 0 and np.abs(gt[1088:5184]).max() > 0
+
+
 def test_mlp_rounding_applies_to_inputs_weights_and_first_hidden_layer():
     """Rounding mode equals the unrounded network evaluated on pre-rounded
     inputs and weights, except for the first hidden layer's rounding."""
