@@ -87,3 +87,43 @@ def test_host_validation_rejects_bad_arguments_without_launching(cdll):
     assert L.gs_loss(None, None, 8, 8, 1.5, None, 0, None, None, None) == 1
     assert L.gs_sort_workspace_bytes(1000, 4000, 64, 64, 16) > 0
     assert L.gs_loss_workspace_bytes(8, 8) > 0
+
+
+def test_host_validation_of_the_update_loss_and_metric_calls(cdll):
+    """More argument checks that return GS_ERR_INVALID_ARG (1) on the host
+    before any CUDA call: bad modes, sizes, optimiser constants, workspace
+    size and alignment, and the fixed-scratch freeze update's size limit.
+    Placeholder addresses are never dereferenced on these paths (the checks
+    come first); the test runs only where no GPU is visible."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("host-only checks; placeholder pointers are not for a machine with a GPU")
+    from paper_2504_06716_gb300 import lib
+
+    lib.load()
+    L = lib._lib
+    fake = ctypes.c_void_p(0x1000)
+    lr = (ctypes.c_float * 7)(*([1e-3] * 7))
+    # freeze update: unknown mode, missing workspace
+    assert L.gs_freeze_update(10, fake, fake, fake, fake, 1e-4, 1e-4, 4, fake, fake, fake, 1 << 20, None) == 1
+    assert L.gs_freeze_update(10, fake, fake, fake, fake, 1e-4, 1e-4, 0, fake, fake, None, 0, None) == 1
+    # fixed-scratch variant: more Gaussians than its array covers, and mode 3 (not offered)
+    assert L.gs_freeze_update_noalloc(65536 * 1024 + 1, fake, fake, fake, fake, 1e-4, 1e-4, 0, fake, fake,
+                                      None) == 1
+    assert L.gs_freeze_update_noalloc(10, fake, fake, fake, fake, 1e-4, 1e-4, 3, fake, fake, None) == 1
+    assert L.gs_freeze_update_noalloc(-1, fake, fake, fake, fake, 1e-4, 1e-4, 0, fake, fake, None) == 1
+    # Adam: step 0, beta1 = 1, negative eps, seven-plus-one groups
+    lrp = ctypes.cast(lr, ctypes.POINTER(ctypes.c_float))
+    assert L.gs_adam_masked(fake, fake, fake, fake, 10, fake, fake, lrp, 0.9, 0.999, 1e-15, 0, None) == 1
+    assert L.gs_adam_masked(fake, fake, fake, fake, 10, fake, fake, lrp, 1.0, 0.999, 1e-15, 1, None) == 1
+    assert L.gs_adam_masked(fake, fake, fake, fake, 10, fake, fake, lrp, 0.9, 0.999, -1.0, 1, None) == 1
+    assert L.gs_adam_masked_groups(fake, fake, fake, fake, 10, fake, fake, lr, 8, 0.9, 0.999, 1e-15, 1, None) == 1
+    # loss: empty image, lambda outside [0, 1], misaligned workspace
+    big = 1 << 30
+    assert L.gs_loss(fake, fake, 0, 16, 0.2, fake, big, fake, fake, None) == 1
+    assert L.gs_loss(fake, fake, 16, 16, 1.5, fake, big, fake, fake, None) == 1
+    assert L.gs_loss(fake, fake, 16, 16, 0.2, ctypes.c_void_p(0x1010), big, fake, fake, None) == 1
+    # PSNR: a negative image count is rejected; zero images is a valid empty call
+    assert L.gs_psnr(fake, fake, -1, 16, 16, fake, big, fake, None) == 1
+    assert L.gs_psnr(None, None, 0, 16, 16, None, 0, None, None) == 0
