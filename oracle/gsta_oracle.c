@@ -260,7 +260,7 @@ static float ln_f32(float x) {
  * one-dimensional minima. Decided in single precision, every operation
  * rounded, on both the oracle and the CUDA path. */
 static float tile_tau(float opacity) {
-    float x = 255.0f * opacity;
+    float x = (PLANTED(44) ? 128.0f : 255.0f) * opacity;
     if (!(x >= 1.0f)) return -1.0f;
     float tau = 2.0f * ln_f32(x);
     return tau + 1e-3f * (1.0f + tau);
@@ -324,7 +324,7 @@ typedef struct {
  * differences): no radius, all tiles, no colour clamp. */
 /* Volume mask (Sec. 3.3): hard mask 1[sigmoid(m) > 0.01], decided on the
  * float32 logit against logit(0.01) rounded to float32. */
-static int mask_on(double m) { return (float)m > (float)(-4.595119850134589); }
+static int mask_on(double m) { return (float)m > (float)(PLANTED(45) ? -2.1972245773362196 : -4.595119850134589); }
 
 static void project_one(const double *p, const or_camera *cam, int sh_degree, int smooth, int opacity_act,
                         const double *mask, gauss_fwd *g) {
@@ -948,7 +948,7 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                 double dx = ev[k].dx, dy = ev[k].dy;
                 double qa = conic[3 * g], qb = conic[3 * g + 1], qc = conic[3 * g + 2];
                 d_conic[3 * g] += -0.5 * dx * dx * dpow;
-                d_conic[3 * g + 1] += -dx * dy * dpow;
+                d_conic[3 * g + 1] += (PLANTED(43) ? -0.5 : -1.0) * dx * dy * dpow;
                 d_conic[3 * g + 2] += -0.5 * dy * dy * dpow;
                 d_mean2d[2 * g] += (PLANTED(6) ? 1.0 : -1.0) * (qa * dx + qb * dy) * dpow;
                 d_mean2d[2 * g + 1] += -(qb * dx + qc * dy) * dpow;
@@ -1017,7 +1017,7 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
 
         /* opacity = sigmoid(x): d/dx = o (1 - o); opacity = |x|: d/dx = sign(x) */
         if (opacity_act)
-            gp[10] = d_opacity[i] * (p[10] > 0 ? 1.0 : (p[10] < 0 ? -1.0 : 0.0));
+            gp[10] = d_opacity[i] * (PLANTED(42) ? 1.0 : (p[10] > 0 ? 1.0 : (p[10] < 0 ? -1.0 : 0.0)));
         else
             gp[10] = d_opacity[i] * g.opacity * (1 - g.opacity);
 

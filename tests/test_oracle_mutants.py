@@ -62,6 +62,10 @@ MUTANTS = {
     39: "downscaled camera's principal point without the half-pixel shift",
     40: "area average footprint shifted by half a source pixel",
     41: "blur kernel exp(-r^2 / sigma^2)",
+    42: "absolute-value opacity: gradient without the sign of the parameter",
+    43: "dL/dconic off-diagonal term halved",
+    44: "tile membership cut-off at alpha 1/128 instead of 1/255",
+    45: "volume mask threshold sigmoid(m) > 0.1 instead of 0.01",
 }
 
 
@@ -79,7 +83,7 @@ def outcomes():
     import oracle
 
     oracle.build()  # the unplanted library; each child compiles its own planted copy
-    with ThreadPoolExecutor(4) as ex:
+    with ThreadPoolExecutor(max(2, min(8, os.cpu_count() or 2))) as ex:
         return dict(zip(MUTANTS, ex.map(_pins, MUTANTS)))
 
 
