@@ -235,7 +235,7 @@ typedef struct {
 int gs_render_fwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
                         const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream);
 
-/* gs_raster_bwd for n_jobs jobs in one persistent launch, as above. Jobs of
+/* Sec. 3.2.4 per job: gs_raster_bwd for n_jobs jobs in one persistent launch, as above. Jobs of
  * one scene may share grad2d (their terms add up). */
 int gs_raster_bwd_batch(const gs_raster_job *jobs_dev, int32_t n_jobs, int32_t width, int32_t height, int32_t tile,
                         const gs_raster_config *cfg, uint32_t *queue_dev, gs_stream_t stream);

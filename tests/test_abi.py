@@ -127,3 +127,28 @@ def test_host_validation_of_the_update_loss_and_metric_calls(cdll):
     # PSNR: a negative image count is rejected; zero images is a valid empty call
     assert L.gs_psnr(fake, fake, -1, 16, 16, fake, big, fake, None) == 1
     assert L.gs_psnr(None, None, 0, 16, 16, None, 0, None, None) == 0
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration in the header is documented with the passage of the
+    paper it computes (Sec./Eq./Algorithm/Table), or says the paper has no
+    counterpart -- in its own comment or in the comment opening its section."""
+    import re
+
+    src = open(os.path.join(ROOT, "include", "gsta.h")).read()
+    cite = re.compile(r"Sec\.|Eq\.|Algorithm|Table|counterpart|no learned component|3DGS")
+    section_starts = [m.start() for m in re.finditer(r"/\* -{10,}", src)]
+    decls = list(re.finditer(r"\n(?:int|size_t|int64_t|uint64_t|const char \*)\s*\*?\s*(gs_\w+)\(", src))
+    assert len(decls) > 40
+    prev = 0
+    missing = []
+    own = ""
+    for m in decls:
+        # declarations with no comment of their own share the one above them
+        own = " ".join(re.findall(r"/\*.*?\*/", src[prev:m.start()], re.S)) or own
+        sec = max([s for s in section_starts if s < m.start()], default=None)
+        head = re.match(r"/\*.*?\*/", src[sec:], re.S).group(0) if sec is not None else ""
+        if not (cite.search(own) or cite.search(head)):
+            missing.append(m.group(1))
+        prev = m.end()
+    assert not missing, missing
