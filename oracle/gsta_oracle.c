@@ -222,74 +222,27 @@ static int32_t tile_rect(float mx, float my, int32_t r, int32_t tile, int32_t tx
     return (rect[2] - rect[0]) * (rect[3] - rect[1]);
 }
 
-/* Natural logarithm in single precision, step by step (test infrastructure's
- * own definition, not a library's): x = m 2^e with m in [1, 2), ln x = e ln 2
- * + ln m, ln m = 2 atanh(s) with s = (m - 1)/(m + 1) in [0, 1/3), summed as
- * 2 s (1 + s^2/3 + s^4/5 + ... + s^14/15) (truncation < 1e-9). Every
- * operation rounds to float. For x >= 1 only. */
-static float ln_f32(float x) {
-    uint32_t b;
-    memcpy(&b, &x, 4);
-    int e = (int)((b >> 23) & 0xffu) - 127;
-    b = (b & 0x007fffffu) | 0x3f800000u;
-    float m;
-    memcpy(&m, &b, 4);
-    float s = (m - 1.0f) / (m + 1.0f);
-    float s2 = s * s;
-    float p = 0.0666666667f;       /* 1/15 */
-    p = p * s2 + 0.0769230769f;    /* 1/13 */
-    p = p * s2 + 0.0909090909f;    /* 1/11 */
-    p = p * s2 + 0.111111111f;     /* 1/9 */
-    p = p * s2 + 0.142857143f;     /* 1/7 */
-    p = p * s2 + 0.2f;
-    p = p * s2 + 0.333333333f;
-    p = p * s2 + 1.0f;
-    float lm = (2.0f * s) * p;
-    return (float)e * 0.693147181f + lm;
-}
-
-/* Reading of the tile lists (3DGS, which the paper builds on, lists a splat
- * in every tile of its 3-sigma rectangle): a tile of the rectangle lists the
- * splat only if the box of its pixel centres [X, X + T - 1] x [Y, Y + T - 1]
- * holds a point where q = a dx^2 + 2 b dx dy + c dy^2 (d = point - mean, the
- * conic's quadratic form) is at most tau + 1e-3 (1 + tau), tau = 2 ln(255 o):
- * elsewhere alpha = o exp(-q/2) < 1/255 and every pixel of the tile skips the
- * splat, so the image and every gradient are those of the full rectangle. A
- * splat with 255 o < 1 is listed nowhere. The box minimum of q is the clamped
- * mean when the mean lies inside, else the least of the four edges' clamped
- * one-dimensional minima. Decided in single precision, every operation
- * rounded, on both the oracle and the CUDA path. */
-static float tile_tau(float opacity) {
-    float x = (PLANTED(44) ? 128.0f : 255.0f) * opacity;
-    if (!(x >= 1.0f)) return -1.0f;
-    float tau = 2.0f * ln_f32(x);
-    return tau + 1e-3f * (1.0f + tau);
-}
-
-static float quad_f32(float a, float b, float c, float dx, float dy) {
-    return (a * dx) * dx + ((2.0f * b) * dx) * dy + (c * dy) * dy;
-}
-
-/* On the edge x = X the form is least at y = my - (b / c)(X - mx), on the
- * edge y = Y at x = mx - (b / a)(Y - my); the two quotients are taken once
- * per splat. */
-static int tile_hit(float mx, float my, float a, float b, float c, float tau_m, int32_t tile, int32_t x, int32_t y) {
-    if (tau_m < 0.0f) return 0;
-    float x0 = (float)(x * tile), x1 = (float)(x * tile + tile - 1);
-    float y0 = (float)(y * tile), y1 = (float)(y * tile + tile - 1);
-    if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 1;
-    float bc = b / c, ba = b / a;
-    float ex[2] = {x0, x1}, ey[2] = {y0, y1};
-    for (int k = 0; k < 2; ++k) {
-        float dx = ex[k] - mx;
-        float yo = my - bc * dx;
-        float yy = yo < y0 ? y0 : (yo > y1 ? y1 : yo);
-        if (quad_f32(a, b, c, dx, yy - my) <= tau_m) return 1;
-        float dy = ey[k] - my;
-        float xo = mx - ba * dy;
-        float xx = xo < x0 ? x0 : (xo > x1 ? x1 : xo);
-        if (quad_f32(a, b, c, xx - mx, dy) <= tau_m) return 1;
-    }
+/* Reading of the tile lists (Sec. 3.1, Eq. 2; 3DGS, which the paper builds
+ * on, lists a splat in every tile of its 3-sigma rectangle): a tile of the
+ * rectangle lists the splat only if one of its pixel centres inside the image
+ * has alpha = o exp(-q/2) >= 1/255, q = d^T Q d with d = pixel - mean and Q
+ * the conic. At every other pixel of the rectangle the compositing floor of
+ * Eq. 2 skips the splat, so the image and every gradient are those of the
+ * full rectangle. Brute force over the tile's pixels in double precision;
+ * o exp(-q/2) >= 1/255 is tested in the equivalent form q <= 2 ln(255 o)
+ * (no pixel qualifies when 255 o < 1). */
+static int tile_lists(double mx, double my, double a, double b, double c, double o, int32_t tile, int32_t x,
+                      int32_t y, int32_t W, int32_t H) {
+    double floor_alpha = PLANTED(44) ? 1.0 / 128.0 : 1.0 / 255.0;
+    if (!(o >= floor_alpha)) return 0;
+    double tau = 2.0 * log(o / floor_alpha);
+    int32_t px1 = x * tile + tile < W ? x * tile + tile : W;
+    int32_t py1 = y * tile + tile < H ? y * tile + tile : H;
+    for (int32_t py = y * tile; py < py1; ++py)
+        for (int32_t px = x * tile; px < px1; ++px) {
+            double dx = px - mx, dy = py - my;
+            if (a * dx * dx + 2.0 * b * dx * dy + c * dy * dy <= tau) return 1;
+        }
     return 0;
 }
 
@@ -474,14 +427,14 @@ static int cmp_entry(const void *a, const void *b) {
 }
 
 /* Whether tile (x, y) lists splat i (rectangle already known to hold it). */
-static int lists(const float *mean2d, const float *conic, float tau_m, int64_t i, int32_t tile, int32_t x,
-                 int32_t y) {
-    return tile_hit(mean2d[2 * i], mean2d[2 * i + 1], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], tau_m, tile,
-                    x, y);
+static int lists(const float *mean2d, const float *conic, const float *opacity, int64_t i, int32_t tile, int32_t x,
+                 int32_t y, int32_t W, int32_t H) {
+    return tile_lists(mean2d[2 * i], mean2d[2 * i + 1], conic[3 * i], conic[3 * i + 1], conic[3 * i + 2], opacity[i],
+                      tile, x, y, W, H);
 }
 
 /* Returns P, the number of entries (tiles of each splat's rectangle that
- * list it, see tile_hit). Writes vals[P] and ranges[tiles][2] (start, end;
+ * list it, see tile_lists). Writes vals[P] and ranges[tiles][2] (start, end;
  * (0, 0) for an empty tile) when P <= capacity; otherwise writes nothing and
  * returns -P. mean2d, conic, opacity, depth are the splats' single-precision
  * values. smooth != 0: every Gaussian with radius > 0 covers every tile. */
@@ -495,9 +448,8 @@ int64_t or_sort(int64_t n, const float *mean2d, const float *conic, const float 
         if (radius[i] <= 0) continue;
         if (smooth) { P += (int64_t)tx * ty; continue; }
         if (tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect) == 0) continue;
-        float tau_m = tile_tau(opacity[i]);
         for (int32_t y = rect[1]; y < rect[3]; ++y)
-            for (int32_t x = rect[0]; x < rect[2]; ++x) P += lists(mean2d, conic, tau_m, i, tile, x, y);
+            for (int32_t x = rect[0]; x < rect[2]; ++x) P += lists(mean2d, conic, opacity, i, tile, x, y, W, H);
     }
     if (P > capacity) return -P;
     sort_entry *e = (sort_entry *)malloc(sizeof(sort_entry) * (P > 0 ? P : 1));
@@ -506,12 +458,11 @@ int64_t or_sort(int64_t n, const float *mean2d, const float *conic, const float 
         if (radius[i] <= 0) continue;
         if (smooth) { rect[0] = 0; rect[1] = 0; rect[2] = tx; rect[3] = ty; }
         else if (tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect) == 0) continue;
-        float tau_m = tile_tau(opacity[i]);
         uint32_t dbits;
         memcpy(&dbits, &depth[i], 4);
         for (int32_t y = rect[1]; y < rect[3]; ++y)
             for (int32_t x = rect[0]; x < rect[2]; ++x) {
-                if (!smooth && !lists(mean2d, conic, tau_m, i, tile, x, y)) continue;
+                if (!smooth && !lists(mean2d, conic, opacity, i, tile, x, y, W, H)) continue;
                 e[k].key = ((uint64_t)(uint32_t)(y * tx + x) << 32) | dbits;
                 e[k].order = k;
                 e[k].val = (uint32_t)i;

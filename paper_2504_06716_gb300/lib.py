@@ -50,8 +50,12 @@ class GsCamera(ctypes.Structure):
     ]
 
     @property
+    def tiles_x(self) -> int:
+        return (self.width + self.tile - 1) // self.tile
+
+    @property
     def tiles(self) -> int:
-        return ((self.width + self.tile - 1) // self.tile) * ((self.height + self.tile - 1) // self.tile)
+        return self.tiles_x * ((self.height + self.tile - 1) // self.tile)
 
 
 def camera(cam, tile: int = 16, znear: float = 0.2, dilation: float = 0.3, bg=(0.0, 0.0, 0.0)) -> GsCamera:

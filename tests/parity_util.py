@@ -128,3 +128,70 @@ def close_bound(got, want, rtol, floor, extra, mask=None):
         return True, 0.0
     ratio = float((err / np.maximum(lim, 1e-300)).max())
     return ratio <= 1.0, ratio
+
+
+# The CUDA sort lists a splat in a tile when the box of the tile's pixel
+# centres holds a point with q = d^T Q d <= tau + 1e-3 (1 + tau), tau =
+# 2 ln(255 o), tested in float32; the oracle lists it when a pixel centre of
+# the tile inside the image has alpha >= 1/255, in double precision. So the
+# CUDA lists hold the oracle's, and every further entry lies within this
+# band of the floor (box minimum of q in double precision).
+LIST_BAND = 2e-3
+
+
+def box_min_q(mx, my, a, b, c, X0, Y0, X1, Y1):
+    """Least value of q = a dx^2 + 2 b dx dy + c dy^2 (d = point - mean) over
+    the boxes [X0, X1] x [Y0, Y1], in double precision: 0 when the mean lies
+    inside, else the least of the four edges' clamped one-dimensional minima
+    (q is convex, so its minimum over a box without the mean is on the edge)."""
+    inside = (mx >= X0) & (mx <= X1) & (my >= Y0) & (my <= Y1)
+    best = np.full(np.shape(mx), np.inf)
+    for ex in (X0, X1):
+        dx = ex - mx
+        dy = np.clip(-(b / c) * dx, Y0 - my, Y1 - my)
+        best = np.minimum(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    for ey in (Y0, Y1):
+        dy = ey - my
+        dx = np.clip(-(b / a) * dy, X0 - mx, X1 - mx)
+        best = np.minimum(best, a * dx * dx + 2 * b * dx * dy + c * dy * dy)
+    return np.where(inside, 0.0, best)
+
+
+def _entries(vals, ranges):
+    """(tile, splat) of every entry, checking that the ranges tile the list in order."""
+    ranges = np.asarray(ranges, np.int64).reshape(-1, 2)
+    cnt = ranges[:, 1] - ranges[:, 0]
+    assert np.all(cnt >= 0)
+    ne = np.nonzero(cnt)[0]
+    if ne.size:
+        assert ranges[ne[0], 0] == 0 and np.all(ranges[ne[1:], 0] == ranges[ne[:-1], 1])
+    tiles = np.repeat(np.arange(ranges.shape[0], dtype=np.int64), cnt)
+    return tiles, np.asarray(vals, np.int64)[: tiles.size] & 0xFFFFFFFF
+
+
+def check_lists(vals, ranges, want_vals, want_ranges, rec, tile: int, tiles_x: int) -> int:
+    """The CUDA tile lists against the oracle's: every oracle entry present, in
+    the same order; every CUDA-only entry within LIST_BAND of the alpha floor;
+    each tile's list in ascending (float32 depth, index). Returns the number of
+    CUDA-only entries."""
+    gt, gs = _entries(vals, ranges)
+    wt, ws = _entries(want_vals, want_ranges)
+    gkey, wkey = (gt << 32) | gs, (wt << 32) | ws
+    member = np.isin(gkey, wkey)
+    assert np.array_equal(gkey[member], wkey), "oracle entries missing or out of order"
+    dbits = np.ascontiguousarray(rec[:, 9], np.float32).view(np.uint32).astype(np.int64)
+    order = np.stack([gt, dbits[gs], gs], 1)
+    same = gt[1:] == gt[:-1]
+    step = order[1:] - order[:-1]
+    first = np.where(step[:, 1] != 0, step[:, 1], step[:, 2])
+    assert np.all(first[same] > 0), "a tile's list is not in (depth, index) order"
+    xt, xs = gt[~member], gs[~member]
+    if xt.size:
+        r = rec[xs].astype(np.float64)
+        X0, Y0 = (xt % tiles_x) * tile, (xt // tiles_x) * tile
+        q = box_min_q(r[:, 0], r[:, 1], r[:, 2], r[:, 3], r[:, 4], X0, Y0, X0 + tile - 1, Y0 + tile - 1)
+        tau = 2 * np.log(np.maximum(255.0 * r[:, 5], 1e-300))
+        assert np.all(255.0 * r[:, 5] >= 1.0 - 1e-6)
+        worst = float(np.max(q - tau - LIST_BAND * (1 + np.abs(tau))))
+        assert worst <= 0.0, f"a CUDA-only entry lies outside the band (excess {worst:.3e})"
+    return int(xt.size)

