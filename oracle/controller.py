@@ -15,6 +15,11 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   when the last two PSNR changes are both below 0.2 dB.
 * Sec. 3.2.3 plateau schedule on the xyz learning rate: decay 0.75,
   patience 1, threshold read as 1 dB on the PSNR (absolute, mode max).
+  Sec. 4.1 says GSta keeps vanilla 3DGS's learning rates except the opacity
+  rate, so its xyz rate is vanilla's exponential decay (to 1/100 of the
+  start over the iteration budget) times the plateau decays.
+* The opacity reset of Sec. 4.1 leaves frozen Gaussians alone: a frozen
+  Gaussian takes no parameter change (Sec. 3.2.4); see densify.opacity_reset.
 """
 from __future__ import annotations
 
@@ -105,6 +110,15 @@ class Plateau:
                 self.lr *= self.decay
                 self.bad = 0
         return self.lr
+
+
+def xyz_rate(k: int, K: int, lr0: float, plateau_factor: float = 1.0, final_ratio: float = 0.01) -> float:
+    """xyz learning rate at iteration k: lr0 final_ratio^(min(k, K) / K), vanilla
+    3DGS's exponential decay, times the product of the plateau decays so far
+    (1 for plain 3DGS)."""
+    t = min(max(k, 0), K) / K
+    decay = final_ratio ** (1.0 if planted(48) else t)
+    return lr0 * decay * plateau_factor
 
 
 def _den_end(cfg: ScheduleConfig, stop_iter: int | None, plain: bool) -> int:

@@ -88,3 +88,21 @@ def test_controller_state_round_trip():
     for k in range(4000, 12001, 250):
         assert a.freeze_mode(k) == b.freeze_mode(k)
     assert a.report_psnr(5000, 26.2) == b.report_psnr(5000, 26.2) and a.lr_xyz == b.lr_xyz
+
+
+def test_xyz_rate_matches_oracle():
+    """GSta: vanilla exponential decay times the plateau decays (Sec. 4.1 keeps
+    the vanilla rates); plain 3DGS: the vanilla decay alone."""
+    lr0 = 1.6e-4 * 4.4
+    g = GStaController(GStaConfig(), lr_xyz=lr0)
+    p = GStaController(GStaConfig(freezing=False), lr_xyz=lr0)
+    seq = [20.0, 24.0, 24.5, 24.6, 26.0, 26.1, 26.15]
+    plateau = C.Plateau(lr0, 0.75, 1, 1.0)
+    for i, psnr in enumerate(seq):
+        k = 1000 * (i + 1)
+        g.report_psnr(k, psnr)
+        f = plateau.step(psnr) / lr0
+        for kk in (k, k + 500, 30000, 31000):
+            assert g.lr_xyz_at(kk) == pytest.approx(C.xyz_rate(kk, 30000, lr0, f), rel=1e-12)
+            assert p.lr_xyz_at(kk) == pytest.approx(C.xyz_rate(kk, 30000, lr0), rel=1e-12)
+    assert g.lr_xyz < lr0  # a plateau decay happened

@@ -58,3 +58,9 @@ def test_densification_cadence_hand_values():
     assert rgb[:3] == [1000, 1500, 2000] and abs(len(rgb) / len(due) - 0.2) < 0.02
     assert not C.size_pruning(3000, cfg) and C.size_pruning(3100, cfg)
     assert C.threshold(cfg.eps0_den_xyz, 0, 30000) == pytest.approx(1e-4)
+
+
+def test_xyz_rate_hand_values():
+    x = GOLD["xyz_rate"]
+    for k, factor, want in x["cases"]:
+        assert C.xyz_rate(k, x["K"], x["lr0"], factor) == pytest.approx(want, rel=1e-12), k

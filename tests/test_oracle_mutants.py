@@ -66,6 +66,9 @@ MUTANTS = {
     43: "dL/dconic off-diagonal term halved",
     44: "tile membership cut-off at alpha 1/128 instead of 1/255",
     45: "volume mask threshold sigmoid(m) > 0.1 instead of 0.01",
+    46: "batched step: the scene's gradient is its last view's, not the sum",
+    47: "batched step: Adam's bias correction one step ahead of the scene's counter",
+    48: "xyz rate without the vanilla exponential decay",
 }
 
 
