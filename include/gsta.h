@@ -435,7 +435,9 @@ int gs_freeze_select(int64_t n, float *acc_xyz, float *acc_rgb, int32_t *cnt, ui
  * inside the library that every GPU which loads the library keeps until the
  * process exits; it allows n <= 67,108,864 and returns GS_ERR_INVALID_ARG for
  * more. The first call on a device, made with that device current, looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
+ * the array's device address (cudaGetSymbolAddress) and keeps it for that
+ * device's context; after a device reset (a new context) the next call looks
+ * it up again. Make the first call on a device, and the first after a reset,
  * before any stream capture. All calls share the one array: each call writes
  * every entry it reads before reading it, so nothing has to be cleared
  * between calls, but calls whose executions overlap on the GPU (other

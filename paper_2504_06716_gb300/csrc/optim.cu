@@ -575,6 +575,8 @@ extern "C" int gs_adam_masked_devstep(float *P, const float *G, float *m, float 
 // per block of 1024 Gaussians) in a fixed array inside the library, for
 // callers that cannot allocate device memory where they call it.
 // ---------------------------------------------------------------------------
+#include <cuda.h>  // CUcontext / CUresult types; the two driver calls are fetched through the runtime
+
 #include <mutex>
 
 namespace gs {
@@ -586,17 +588,49 @@ static __device__ __align__(256) int32_t g_freeze_scratch[kNoAllocBlocks];
 constexpr int kMaxDevices = 256;
 std::mutex g_scratch_mu;
 int32_t *g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of g_freeze_scratch on the current device, looked up once per
-// device. Returns nullptr if the lookup fails.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the context current on this thread, 0 if it cannot be read. A device
+// reset replaces the primary context by one with a new id, so an address
+// cached under the old id is looked up again instead of being reused.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_freeze_scratch in the current device's current context,
+// looked up on the first call there (and again after a device reset; on every
+// call if the context id cannot be read). Returns nullptr if the lookup fails.
 int32_t *scratch_on_current_device() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_scratch_ptr[dev] || id == 0 || id != g_scratch_ctx[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_freeze_scratch) != cudaSuccess) return nullptr;
         g_scratch_ptr[dev] = static_cast<int32_t *>(p);
+        g_scratch_ctx[dev] = current_context_id();  // the lookup made the context current if it was not
     }
     return g_scratch_ptr[dev];
 }

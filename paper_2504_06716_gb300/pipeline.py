@@ -241,12 +241,12 @@ class Model:
         self.mask_lr = learn_lr if on else None
         self.mask_loss = (loss_weight / max(self.n, 1)) if (on and learn_lr) else 0.0
 
-    def opacity_reset(self, logit_cap: float):
+    def opacity_reset(self, logit_cap: float, skip_frozen: bool = False):
+        """Cap every opacity logit at logit_cap (moments zeroed), as 3DGS does;
+        with skip_frozen the frozen Gaussians keep theirs."""
         if self.opacity_act & lib.GS_OPACITY_ABS:
             raise RuntimeError("the opacity reset caps a logit: not under the absolute-value opacity")
-        # every Gaussian, frozen or not, as 3DGS resets them (frozen ones
-        # recover once the map releases them: at the next reset of the map)
-        lib.gs_opacity_reset(self.n, self.P, self.m, self.v, logit_cap, None)
+        lib.gs_opacity_reset(self.n, self.P, self.m, self.v, logit_cap, self.frozen if skip_frozen else None)
 
     # ---- views ----
     def make_view(self, cam: lib.GsCamera, capacity: int, trainable: bool = True) -> View:

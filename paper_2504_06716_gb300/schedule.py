@@ -16,7 +16,9 @@ Readings of the paper taken here:
   then all Gaussians are unfrozen for a finetuning stage of K_f iterations,
   after which training ends.
 * Sec. 3.2.3 -- the xyz learning rate decays by 0.75 when the PSNR has not
-  risen by more than 1 dB for more than one evaluation.
+  risen by more than 1 dB for more than one evaluation; Sec. 4.1 keeps the
+  vanilla rates, so these decays multiply vanilla 3DGS's exponential decay
+  of the xyz rate (to 1/100 over the iteration budget).
 """
 from __future__ import annotations
 
@@ -121,6 +123,24 @@ class GStaConfig:
     # as much on average as it did through the sigmoid; None keeps 0.025; a
     # number sets it
     abs_opacity_lr: float | str | None = "slope"
+    # Eq. 7 on (False: PSNR is still checked, for the plateau rate, but the
+    # run never stops early and trains to total_iter)
+    early_stop: bool = True
+    # reset the map when the freezing window closes at window_end without an
+    # early stop (False: the Gaussians frozen last stay frozen to total_iter)
+    window_end_reset: bool = True
+    # what the opacity reset does to a frozen Gaussian: "skip" leaves it
+    # untouched (a frozen Gaussian takes no parameter change, Sec. 3.2.4);
+    # "reset" caps its opacity like every other's (3DGS); "unfreeze" caps
+    # every opacity and resets the map
+    opacity_reset_frozen: str = "skip"
+    # Sec. 4.1: GSta keeps vanilla 3DGS's learning rates (opacity aside), so
+    # the plateau decays of Sec. 3.2.3 multiply the vanilla exponential decay
+    # of the xyz rate; False: they replace it (a constant rate between decays)
+    plateau_on_vanilla: bool = True
+    # vanilla 3DGS's opacity rate for the plain arm (Sec. 4.1 sets GSta's to
+    # 0.025 "except" the vanilla one)
+    plain_opacity_lr: float = 0.05
 
     @staticmethod
     def tiny() -> "GStaConfig":
@@ -161,7 +181,8 @@ class GStaController:
             return None
         end = c.window_end if self.stop_iter is None else min(c.window_end, self.stop_iter)
         if self.stop_iter is None and k == c.window_end:
-            return FREEZE_RESET  # freezing ends with the window: nothing stays frozen
+            # freezing ends with the window: nothing stays frozen
+            return FREEZE_RESET if c.window_end_reset else None
         if k >= end:
             return None
         if k < c.warmup:
@@ -177,9 +198,9 @@ class GStaController:
         """xyz learning rate for iteration k: the plateau schedule under GSta,
         vanilla exponential decay for plain training."""
         c = self.cfg
-        if c.freezing:
-            return self.lr_xyz
         t = min(1.0, max(0.0, k / c.total_iter))
+        if c.freezing:
+            return self.lr_xyz * (c.plain_lr_final_ratio ** t if c.plateau_on_vanilla else 1.0)
         return self.lr_xyz * c.plain_lr_final_ratio ** t
 
     def wants_psnr(self, k: int) -> bool:

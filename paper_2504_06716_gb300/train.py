@@ -75,7 +75,7 @@ class JsonlLog:
 
 class Trainer:
     def __init__(self, scene: synth.Scene, cfg: GStaConfig, tile: int = 16, calibrate: bool = True,
-                 extent: float = 4.4, seed: int = 3, device="cuda"):
+                 extent: float = 4.4, seed: int = 3, device="cuda", target_noise: float = 0.0):
         self.scene = scene
         self.cfg = cfg
         self.calibrate = calibrate
@@ -91,6 +91,10 @@ class Trainer:
             gtm.retarget(gv, self.cams[v])
             gtm.rasterize(gv)
             self.targets[v] = gv.image.clone()
+            if target_noise > 0:  # sensor noise of a captured image, drawn per view on the host
+                g = torch.Generator().manual_seed(7919 * (v + 1))
+                noise = torch.randn(gv.image.shape, generator=g) * target_noise
+                self.targets[v] = (self.targets[v] + noise.to(self.device)).clamp_(0.0, 1.0)
         if lib.gs_get_device_error():
             raise RuntimeError("device error while rendering targets")
         del gtm, gv
@@ -103,6 +107,8 @@ class Trainer:
         self.sched_buf = [torch.zeros(3 * H * W, dtype=torch.float32, device=self.device) for _ in range(2)]
         self.psnr_out = torch.zeros(1, device=self.device)
         self.lrs = pipeline.default_lrs(extent)
+        if not cfg.freezing:  # plain 3DGS: vanilla opacity rate
+            self.lrs[3] = cfg.plain_opacity_lr
         self.ctrl = GStaController(cfg, self.lrs[0])
         self.order = synth.view_order(cfg.total_iter + cfg.finetune_iters + 1, scene.train_views, seed)
         self.eps0 = (cfg.eps0_xyz, cfg.eps0_rgb)
@@ -351,7 +357,11 @@ class Trainer:
                 self.generation = m.generation
                 self.view = m.make_view(self.view.cam, self.view.capacity)
         if c.opacity_reset_due(k):
-            m.opacity_reset(float(np.float32(math.log(0.01 / 0.99))))
+            how = self.cfg.opacity_reset_frozen
+            m.opacity_reset(float(np.float32(math.log(0.01 / 0.99))), skip_frozen=(how == "skip"))
+            if how == "unfreeze" and self.cfg.freezing:
+                m.freeze_update(0.0, 0.0, FREEZE_RESET)
+                self._act_now = None
             self.events.append((k, "opacity_reset", 0.0))
         if c.after_step(k):
             m.freeze_update(0.0, 0.0, FREEZE_RESET)
@@ -479,17 +489,22 @@ class Trainer:
         return self.k >= self.cfg.total_iter and not self.cfg.freezing
 
 
-def run(args) -> dict:
-    torch.cuda.set_device(0)
-    scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
+def run(args, scene: synth.Scene | None = None) -> dict:
+    """One training run as the arguments of parser() say, on the current CUDA
+    device; the surface scene is generated unless one is given."""
+    if scene is None:
+        scene = synth.surface_scene(args.n_init, args.n_gt, args.views, args.width, args.height)
     cfg = GStaConfig(freezing=(args.arm == "gsta"), total_iter=args.iters, densify=not args.no_densify,
                      freeze_strategy=args.freeze_strategy, abs_opacity_finetune=not args.no_abs_opacity,
                      abs_opacity_moments=args.abs_moments,
                      abs_opacity_lr=None if args.abs_lr == "same" else
                      ("slope" if args.abs_lr == "slope" else float(args.abs_lr)),
                      progressive=args.trick_gs, blur=args.trick_gs, volume_mask=args.trick_gs or args.volume_mask,
-                     significance=args.trick_gs or args.significance)
-    tr = Trainer(scene, cfg, calibrate=not args.no_calibrate)
+                     significance=args.trick_gs or args.significance, early_stop=not args.no_early_stop,
+                     window_end_reset=not args.no_window_end_reset, opacity_reset_frozen=args.opacity_reset_frozen,
+                     eps0_xyz=3e-5 * args.eps_scale, eps0_rgb=1e-4 * args.eps_scale,
+                     plateau_on_vanilla=not args.plateau_alone)
+    tr = Trainer(scene, cfg, calibrate=not args.no_calibrate, target_noise=args.target_noise)
     tuning = None
     if args.autotune:
         for _ in range(args.tune_after):
@@ -507,7 +522,7 @@ def run(args) -> dict:
     t0 = time.perf_counter()
     eval_every = args.eval_every
     while not tr.finished():
-        tr.iteration()
+        tr.iteration(allow_early_stop=cfg.early_stop)
         if log is not None:  # counted as training time (a short wait every log.every iterations)
             log.after_iteration(tr)
         if tr.k % eval_every == 0:
@@ -533,7 +548,7 @@ def run(args) -> dict:
     return out
 
 
-def main():
+def parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--arm", choices=["gsta", "plain"], default="gsta")
     ap.add_argument("--n-init", type=int, default=1_000_000)
@@ -561,10 +576,25 @@ def main():
     ap.add_argument("--abs-lr", default="slope",
                     help="opacity learning rate under |x|: 'slope' (the rate times the mean o (1 - o) at the"
                          " switch), 'same' (unchanged) or a number")
+    ap.add_argument("--no-early-stop", action="store_true", help="Eq. 7 never ends the run (PSNR still checked)")
+    ap.add_argument("--no-window-end-reset", action="store_true",
+                    help="keep the map when the freezing window closes without an early stop")
+    ap.add_argument("--opacity-reset-frozen", choices=["reset", "skip", "unfreeze"], default="skip",
+                    help="the opacity reset on frozen Gaussians: leave them, cap them too, or cap all and reset the map")
+    ap.add_argument("--plateau-alone", action="store_true",
+                    help="the plateau decays replace the vanilla exponential xyz schedule (a constant rate between "
+                         "decays) instead of multiplying it")
+    ap.add_argument("--target-noise", type=float, default=0.0,
+                    help="standard deviation of seeded per-pixel noise added to every target image")
+    ap.add_argument("--eps-scale", type=float, default=1.0, help="factor on the paper's initial freeze thresholds")
     ap.add_argument("--log-jsonl", default=None, help="write a per-iteration training record (JSON lines) here")
     ap.add_argument("--log-every", type=int, default=100, help="iterations between records of --log-jsonl")
-    args = ap.parse_args()
-    print(json.dumps(run(args)))
+    return ap
+
+
+def main():
+    torch.cuda.set_device(0)
+    print(json.dumps(run(parser().parse_args())))
 
 
 if __name__ == "__main__":

@@ -176,14 +176,19 @@ def test_sort_ties_keep_index_order():
     rec[:, 5] = 0.9
     cam = synth.pinhole(200, 120, 60.0, (0, -3, 0.5))
     ocam, gcam = pu.cameras(cam, tile=16)
-    tiles = np.zeros(n, np.int32)
+    listed = np.zeros(n, np.int32)
     for i in range(n):  # tiles listing the splat by the oracle's rule
         if rad[i] > 0:
             v, _ = oracle.sort_records(rec[i:i + 1], 200, 120, 16)
-            tiles[i] = len(v)
-    rad[tiles == 0] = 0
+            listed[i] = len(v)
+    rad[listed == 0] = 0
     rec[:, 10] = rad.view(np.float32)
-    rec[:, 11] = tiles.view(np.float32)
+    x0 = np.clip(np.floor((rec[:, 0] - rad) / 16), 0, None)
+    x1 = np.clip(np.floor((rec[:, 0] + rad) / 16), None, (200 + 15) // 16 - 1)
+    y0 = np.clip(np.floor((rec[:, 1] - rad) / 16), 0, None)
+    y1 = np.clip(np.floor((rec[:, 1] + rad) / 16), None, (120 + 15) // 16 - 1)
+    rect = np.where((rad > 0) & (x0 <= x1) & (y0 <= y1), (x1 - x0 + 1) * (y1 - y0 + 1), 0).astype(np.int32)
+    rec[:, 11] = rect.view(np.float32)  # the projection's count: tiles of the rectangle
     want_vals, want_ranges = _oracle_sort(rec, ocam)
     vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam)
     assert flags == 0

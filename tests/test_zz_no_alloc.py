@@ -46,14 +46,17 @@ def _state(n, frozen):
                 na=torch.zeros(1, dtype=torch.int32, device="cuda"))
 
 
-@pytest.mark.parametrize("n", [5000, 1_300_001])
-def test_noalloc_matches_workspace_version_on_two_calls(n):
+@pytest.mark.parametrize("n,modes", [(5000, (0, 0)), (1_300_001, (0, 0)), (70_001, (1, 0)), (70_001, (2, 0)),
+                                     (70_001, (0, 1)), (0, (0, 2))])
+def test_noalloc_matches_workspace_version_on_two_calls(n, modes):
+    """Two calls in a row (update, reset or clear; an empty set too), each
+    against gs_freeze_update on the same inputs."""
     frozen0 = (np.random.default_rng(n).uniform(0, 1, n) < 0.1).astype(np.uint8)
     ref, new = _state(n, frozen0), _state(n, frozen0)
-    ws = torch.zeros(lib.gs_freeze_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(max(lib.gs_freeze_workspace_bytes(n), 256), dtype=torch.uint8, device="cuda")
     L = lib.load()
-    for call, (mode, seed) in enumerate([(0, 1), (0, 2)]):
-        acc_x, acc_r, cnt = _inputs(n, seed)
+    for call, mode in enumerate(modes):
+        acc_x, acc_r, cnt = _inputs(n, call + 1)
         a = [torch.from_numpy(x.copy()).cuda() for x in (acc_x, acc_r, cnt)]
         b = [torch.from_numpy(x.copy()).cuda() for x in (acc_x, acc_r, cnt)]
         lib.gs_freeze_update(n, *a, ref["frozen"], 4e-5, 1.1e-4, mode, ref["act"], ref["na"], ws)
@@ -68,7 +71,10 @@ def test_noalloc_matches_workspace_version_on_two_calls(n):
         assert torch.equal(new["act"][:k], ref["act"][:k]), f"call {call}"
         for x in b:
             assert not x.any()
-        assert k < n  # the rule froze something, so the comparison is not vacuous
+        if mode == 0 and n:
+            assert k < n  # the rule froze something, so the comparison is not vacuous
+        if mode == 1:
+            assert k == n  # a reset unfreezes everything
     assert lib.gs_get_device_error() == 0
 
 
