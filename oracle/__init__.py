@@ -53,7 +53,7 @@ def build(force: bool = False, plant: int | None = None) -> str:
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
         tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
              f"-DORACLE_PLANT={plant}", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, out)
     return out
@@ -99,6 +99,8 @@ def lib():
             L.or_sh_basis_grad.argtypes = [_dp, _dp]
             L.or_project_act.argtypes = [_i64, _dp, ctypes.POINTER(Cam), _i32, _i32, _i32, _dp, _dp, _dp, _dp, _dp,
                                          _dp, _ip, _ip, _dp]
+            L.or_set_threads.argtypes = [_i32]
+            L.or_max_threads.restype = _i32
             L.or_sort.argtypes = [_i64, _fp, _fp, _fp, _ip, _fp, _i32, _i32, _i32, _i32, _i64, _up, _up]
             L.or_sort.restype = _i64
             L.or_render.argtypes = [_i32, _i32, _i32, _dp, _i32, _dp, _dp, _dp, _dp, _up, _up, _dp, _dp, _ip, _dp]
@@ -145,6 +147,15 @@ def _p(a, t):
 
 def _c(a, dt):
     return np.ascontiguousarray(a, dtype=dt)
+
+
+def set_threads(n: int):
+    """Host threads of the oracle's parallel loops (results do not depend on it)."""
+    lib().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
 
 
 def sh_basis(d) -> np.ndarray:

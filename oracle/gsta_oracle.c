@@ -26,6 +26,10 @@
  * clamp, SSIM window) are stated at each function and are shared with the
  * CUDA path only through their written statement.
  *
+ * Loops over independent Gaussians, pixels or tiles run on all host cores
+ * (OpenMP); every sum is taken in an order that does not depend on the
+ * number of threads, so results are the same with one core or many.
+ *
  * Every computation is a direct loop in double precision. Where a floating
  * point value decides an integer that the CUDA path must reproduce bit for
  * bit (the tile rectangle of a Gaussian, the sort key, the freeze test) the
@@ -39,6 +43,7 @@
  *   image   [3][H][W]
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -66,6 +71,10 @@ typedef struct {
 } or_camera;
 
 static const double PI = 3.14159265358979323846;
+
+/* Host threads the parallel loops use (the baseline timing reports them). */
+void or_set_threads(int32_t n) { omp_set_num_threads(n > 0 ? n : 1); }
+int32_t or_max_threads(void) { return (int32_t)omp_get_max_threads(); }
 
 /* ------------------------------------------------------------------ */
 /* Real spherical harmonics, degree <= 3 (Sec. 3.1: "a set of spherical
@@ -377,6 +386,7 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
 void or_project_act(int64_t n, const double *P, const or_camera *cam, int32_t sh_degree, int32_t smooth,
                     int32_t opacity_act, const double *mask, double *mean2d, double *conic, double *depth,
                     double *opacity, double *rgb, int32_t *radius, int32_t *rect, double *margin) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         gauss_fwd g;
         project_one(P + NP * i, cam, sh_degree, smooth, opacity_act, mask ? mask + i : NULL, &g);
@@ -442,24 +452,33 @@ int64_t or_sort(int64_t n, const float *mean2d, const float *conic, const float 
                 const float *depth, int32_t W, int32_t H, int32_t tile, int32_t smooth, int64_t capacity,
                 uint32_t *vals, uint32_t *ranges) {
     int32_t tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    int64_t P = 0;
-    int32_t rect[4];
+    int64_t *first = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1)); /* entries of Gaussians before i */
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
-        if (radius[i] <= 0) continue;
-        if (smooth) { P += (int64_t)tx * ty; continue; }
-        if (tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect) == 0) continue;
-        for (int32_t y = rect[1]; y < rect[3]; ++y)
-            for (int32_t x = rect[0]; x < rect[2]; ++x) P += lists(mean2d, conic, opacity, i, tile, x, y, W, H);
+        int64_t c = 0;
+        int32_t rect[4];
+        if (radius[i] > 0) {
+            if (smooth) c = (int64_t)tx * ty;
+            else if (tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect) > 0)
+                for (int32_t y = rect[1]; y < rect[3]; ++y)
+                    for (int32_t x = rect[0]; x < rect[2]; ++x) c += lists(mean2d, conic, opacity, i, tile, x, y, W, H);
+        }
+        first[i + 1] = c;
     }
-    if (P > capacity) return -P;
+    first[0] = 0;
+    for (int64_t i = 0; i < n; ++i) first[i + 1] += first[i];
+    int64_t P = first[n];
+    if (P > capacity) { free(first); return -P; }
     sort_entry *e = (sort_entry *)malloc(sizeof(sort_entry) * (P > 0 ? P : 1));
-    int64_t k = 0;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
-        if (radius[i] <= 0) continue;
+        if (first[i + 1] == first[i]) continue;
+        int32_t rect[4];
         if (smooth) { rect[0] = 0; rect[1] = 0; rect[2] = tx; rect[3] = ty; }
-        else if (tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect) == 0) continue;
+        else tile_rect(mean2d[2 * i], mean2d[2 * i + 1], radius[i], tile, tx, ty, rect);
         uint32_t dbits;
         memcpy(&dbits, &depth[i], 4);
+        int64_t k = first[i]; /* entries in (Gaussian index, tile row-major) order */
         for (int32_t y = rect[1]; y < rect[3]; ++y)
             for (int32_t x = rect[0]; x < rect[2]; ++x) {
                 if (!smooth && !lists(mean2d, conic, opacity, i, tile, x, y, W, H)) continue;
@@ -469,6 +488,7 @@ int64_t or_sort(int64_t n, const float *mean2d, const float *conic, const float 
                 ++k;
             }
     }
+    free(first);
     qsort(e, (size_t)P, sizeof(sort_entry), cmp_entry);
     for (int64_t t = 0; t < (int64_t)tx * ty; ++t) ranges[2 * t] = ranges[2 * t + 1] = 0;
     for (int64_t j = 0; j < P; ++j) {
@@ -534,6 +554,7 @@ void or_render(int32_t W, int32_t H, int32_t tile, const double *bg, int32_t smo
                const double *conic, const double *opacity, const double *rgb, const uint32_t *vals,
                const uint32_t *ranges, double *image, double *t_final, int32_t *n_last, double *margin) {
     int32_t tx = (W + tile - 1) / tile;
+#pragma omp parallel for schedule(dynamic, 4)
     for (int32_t py = 0; py < H; ++py)
         for (int32_t px = 0; px < W; ++px) {
             int32_t t = (py / tile) * tx + (px / tile);
@@ -748,13 +769,16 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
     double l1 = 0, ssim = 0;
     double *A = (double *)malloc(sizeof(double) * HW), *B = (double *)malloc(sizeof(double) * HW),
            *Cm = (double *)malloc(sizeof(double) * HW);
+    double *row_ssim = (double *)malloc(sizeof(double) * (size_t)H), *row_l1 = (double *)malloc(sizeof(double) * H);
     for (int ch = 0; ch < 3; ++ch) {
         const double *x = image + ch * HW, *y = gt + ch * HW;
-        for (int32_t i = 0; i < H; ++i)
+#pragma omp parallel for schedule(static)
+        for (int32_t i = 0; i < H; ++i) {
+            row_ssim[i] = 0;
             for (int32_t j = 0; j < W; ++j) {
                 ssim_px r = ssim_at(x, y, H, W, i, j, w);
                 double m = r.m, mx = r.mx, my = r.my, n1 = r.n1, n2 = r.n2, d1 = r.d1, d2 = r.d2;
-                ssim += m;
+                row_ssim[i] += m;
                 /* partial derivatives of the map value with respect to the
                    window mean of x, of x^2 and of x*y */
                 int64_t p = (int64_t)i * W + j;
@@ -764,7 +788,10 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
                 B[p] = -m / d2;
                 Cm[p] = 2 * n1 / (d1 * d2);
             }
+        }
+        for (int32_t i = 0; i < H; ++i) ssim += row_ssim[i];
         if (dl_dimage) {
+#pragma omp parallel for schedule(static)
             for (int32_t i = 0; i < H; ++i)
                 for (int32_t j = 0; j < W; ++j) {
                     double ga = 0, gb = 0, gc = 0;
@@ -783,9 +810,14 @@ double or_loss(int32_t H, int32_t W, const double *image, const double *gt, doub
                     dl_dimage[ch * HW + p] = (1 - lambda) * sg / N - lambda * dssim;
                 }
         }
-        for (int64_t p = 0; p < HW; ++p) l1 += fabs(x[p] - y[p]);
+#pragma omp parallel for schedule(static)
+        for (int32_t i = 0; i < H; ++i) {
+            row_l1[i] = 0;
+            for (int32_t j = 0; j < W; ++j) row_l1[i] += fabs(x[(int64_t)i * W + j] - y[(int64_t)i * W + j]);
+        }
+        for (int32_t i = 0; i < H; ++i) l1 += row_l1[i];
     }
-    free(A); free(B); free(Cm);
+    free(A); free(B); free(Cm); free(row_ssim); free(row_l1);
     return (1 - lambda) * l1 / N + lambda * (1 - ssim / N);
 }
 
@@ -837,8 +869,8 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
                    const uint32_t *vals, const uint32_t *ranges, const double *dl_dimage, const uint8_t *frozen,
                    const uint8_t *amb, const uint8_t *tile_mask, double *d_mean2d, double *d_conic,
                    double *d_opacity, double *d_rgb, uint8_t *tainted, double *amb_abs) {
-    int32_t tx = (W + tile - 1) / tile;
-    int64_t HW = (int64_t)H * W;
+    int32_t tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
+    int64_t ntiles = (int64_t)tx * ty, HW = (int64_t)H * W;
     memset(d_mean2d, 0, sizeof(double) * 2 * n);
     memset(d_conic, 0, sizeof(double) * 3 * n);
     memset(d_opacity, 0, sizeof(double) * n);
@@ -846,74 +878,107 @@ void or_render_bwd(int64_t n, int32_t W, int32_t H, int32_t tile, const double *
     if (tainted) memset(tainted, 0, (size_t)n);
     if (amb_abs) memset(amb_abs, 0, sizeof(double) * 9 * n);
     int32_t cap = 0;
-    for (int64_t t = 0; t < (int64_t)tx * ((H + tile - 1) / tile); ++t) {
+    int64_t P = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
         int32_t len = (int32_t)(ranges[2 * t + 1] - ranges[2 * t]);
         if (len > cap) cap = len;
+        if ((int64_t)ranges[2 * t + 1] > P) P = ranges[2 * t + 1];
     }
-    blend_eval *ev = (blend_eval *)malloc(sizeof(blend_eval) * (cap > 0 ? cap : 1));
-    uint32_t *gid = (uint32_t *)malloc(sizeof(uint32_t) * (cap > 0 ? cap : 1));
-    double *Tk = (double *)malloc(sizeof(double) * (cap > 0 ? cap : 1));
-    double *S = (double *)malloc(sizeof(double) * 3 * (cap > 0 ? cap : 1));
-    for (int32_t py = 0; py < H; ++py)
-        for (int32_t px = 0; px < W; ++px) {
-            int32_t t = (py / tile) * tx + (px / tile);
+    /* Each tile's pixels add into per-entry partial sums (an entry belongs to
+     * one tile); the partials are then added into the per-Gaussian gradients
+     * in entry order, so the summation order is the same on any number of
+     * threads. Per entry: d_mean2d (2), d_conic (3), d_opacity, d_rgb (3). */
+    double *part = (double *)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double));
+    double *part_amb = amb_abs ? (double *)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double)) : NULL;
+    uint8_t *part_taint = tainted ? (uint8_t *)calloc((size_t)(P > 0 ? P : 1), 1) : NULL;
+#pragma omp parallel
+    {
+        blend_eval *ev = (blend_eval *)malloc(sizeof(blend_eval) * (cap > 0 ? cap : 1));
+        uint32_t *pos = (uint32_t *)malloc(sizeof(uint32_t) * (cap > 0 ? cap : 1));
+        double *Tk = (double *)malloc(sizeof(double) * (cap > 0 ? cap : 1));
+        double *S = (double *)malloc(sizeof(double) * 3 * (cap > 0 ? cap : 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t t = 0; t < ntiles; ++t) {
             if (tile_mask && !tile_mask[t]) continue;
             uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
-            int64_t pix = (int64_t)py * W + px;
-            int ambiguous = amb ? amb[pix] : 0;
-            double T = 1.0;
-            int nc = 0;
-            for (uint32_t k = s; k < e; ++k) {
-                uint32_t g = vals[k];
-                blend_eval b;
-                eval_entry(mean2d, conic, opacity, g, px, py, T, smooth, &b);
-                if (ambiguous && tainted) tainted[g] = 1;
-                if (b.skip) continue;
-                if (b.stop) break;
-                ev[nc] = b; gid[nc] = g; Tk[nc] = T; ++nc;
-                T *= 1.0 - b.alpha;
-            }
-            double Tf = T;
-            double acc[3] = {0, 0, 0};
-            for (int k = nc - 1; k >= 0; --k) {
-                for (int c = 0; c < 3; ++c) S[3 * k + c] = acc[c];
-                for (int c = 0; c < 3; ++c) acc[c] += rgb[3 * gid[k] + c] * ev[k].alpha * Tk[k];
-            }
-            double dC[3];
-            for (int c = 0; c < 3; ++c) dC[c] = dl_dimage[c * HW + pix];
-            for (int k = 0; k < nc; ++k) {
-                uint32_t g = gid[k];
-                if (frozen && frozen[g]) continue;
-                double a = ev[k].alpha, dA = 0;
-                double *ab = (ambiguous && amb_abs) ? amb_abs + 9 * (int64_t)g : NULL;
-                for (int c = 0; c < 3; ++c) {
-                    double dCda = rgb[3 * g + c] * Tk[k] - (S[3 * k + c] + (PLANTED(7) ? 0.0 : Tf * bg[c])) / (1.0 - a);
-                    dA += dC[c] * dCda;
-                    d_rgb[3 * g + c] += a * Tk[k] * dC[c];
-                    if (ab) ab[6 + c] += fabs(a * Tk[k] * dC[c]);
+            int32_t x0 = (int32_t)(t % tx) * tile, y0 = (int32_t)(t / tx) * tile;
+            for (int32_t py = y0; py < y0 + tile && py < H; ++py)
+                for (int32_t px = x0; px < x0 + tile && px < W; ++px) {
+                    int64_t pix = (int64_t)py * W + px;
+                    int ambiguous = amb ? amb[pix] : 0;
+                    double T = 1.0;
+                    int nc = 0;
+                    for (uint32_t k = s; k < e; ++k) {
+                        blend_eval b;
+                        eval_entry(mean2d, conic, opacity, vals[k], px, py, T, smooth, &b);
+                        if (ambiguous && part_taint) part_taint[k] = 1;
+                        if (b.skip) continue;
+                        if (b.stop) break;
+                        ev[nc] = b; pos[nc] = k; Tk[nc] = T; ++nc;
+                        T *= 1.0 - b.alpha;
+                    }
+                    double Tf = T;
+                    double acc[3] = {0, 0, 0};
+                    for (int k = nc - 1; k >= 0; --k) {
+                        uint32_t g = vals[pos[k]];
+                        for (int c = 0; c < 3; ++c) S[3 * k + c] = acc[c];
+                        for (int c = 0; c < 3; ++c) acc[c] += rgb[3 * g + c] * ev[k].alpha * Tk[k];
+                    }
+                    double dC[3];
+                    for (int c = 0; c < 3; ++c) dC[c] = dl_dimage[c * HW + pix];
+                    for (int k = 0; k < nc; ++k) {
+                        uint32_t g = vals[pos[k]];
+                        if (frozen && frozen[g]) continue;
+                        double *pt = part + 9 * (int64_t)pos[k];
+                        double a = ev[k].alpha, dA = 0;
+                        double *ab = (ambiguous && part_amb) ? part_amb + 9 * (int64_t)pos[k] : NULL;
+                        for (int c = 0; c < 3; ++c) {
+                            double dCda = rgb[3 * g + c] * Tk[k] - (S[3 * k + c] + (PLANTED(7) ? 0.0 : Tf * bg[c])) / (1.0 - a);
+                            dA += dC[c] * dCda;
+                            pt[6 + c] += a * Tk[k] * dC[c];
+                            if (ab) ab[6 + c] += fabs(a * Tk[k] * dC[c]);
+                        }
+                        if (ev[k].capped) continue; /* alpha = 0.99 does not depend on o or G */
+                        double o = opacity[g], G = ev[k].G;
+                        pt[5] += dA * G;
+                        double dpow = dA * o * G;
+                        double dx = ev[k].dx, dy = ev[k].dy;
+                        double qa = conic[3 * g], qb = conic[3 * g + 1], qc = conic[3 * g + 2];
+                        pt[2] += -0.5 * dx * dx * dpow;
+                        pt[3] += (PLANTED(43) ? -0.5 : -1.0) * dx * dy * dpow;
+                        pt[4] += -0.5 * dy * dy * dpow;
+                        pt[0] += (PLANTED(6) ? 1.0 : -1.0) * (qa * dx + qb * dy) * dpow;
+                        pt[1] += -(qb * dx + qc * dy) * dpow;
+                        if (ab) {
+                            ab[0] += fabs((qa * dx + qb * dy) * dpow);
+                            ab[1] += fabs((qb * dx + qc * dy) * dpow);
+                            ab[2] += fabs(0.5 * dx * dx * dpow);
+                            ab[3] += fabs(dx * dy * dpow);
+                            ab[4] += fabs(0.5 * dy * dy * dpow);
+                            ab[5] += fabs(dA * G);
+                        }
+                    }
                 }
-                if (ev[k].capped) continue; /* alpha = 0.99 does not depend on o or G */
-                double o = opacity[g], G = ev[k].G;
-                d_opacity[g] += dA * G;
-                double dpow = dA * o * G;
-                double dx = ev[k].dx, dy = ev[k].dy;
-                double qa = conic[3 * g], qb = conic[3 * g + 1], qc = conic[3 * g + 2];
-                d_conic[3 * g] += -0.5 * dx * dx * dpow;
-                d_conic[3 * g + 1] += (PLANTED(43) ? -0.5 : -1.0) * dx * dy * dpow;
-                d_conic[3 * g + 2] += -0.5 * dy * dy * dpow;
-                d_mean2d[2 * g] += (PLANTED(6) ? 1.0 : -1.0) * (qa * dx + qb * dy) * dpow;
-                d_mean2d[2 * g + 1] += -(qb * dx + qc * dy) * dpow;
-                if (ab) {
-                    ab[0] += fabs((qa * dx + qb * dy) * dpow);
-                    ab[1] += fabs((qb * dx + qc * dy) * dpow);
-                    ab[2] += fabs(0.5 * dx * dx * dpow);
-                    ab[3] += fabs(dx * dy * dpow);
-                    ab[4] += fabs(0.5 * dy * dy * dpow);
-                    ab[5] += fabs(dA * G);
-                }
-            }
         }
-    free(ev); free(gid); free(Tk); free(S);
+        free(ev); free(pos); free(Tk); free(S);
+    }
+    for (int64_t k = 0; k < P; ++k) {
+        uint32_t g = vals[k];
+        const double *pt = part + 9 * k;
+        d_mean2d[2 * g] += pt[0]; d_mean2d[2 * g + 1] += pt[1];
+        d_conic[3 * g] += pt[2]; d_conic[3 * g + 1] += pt[3]; d_conic[3 * g + 2] += pt[4];
+        d_opacity[g] += pt[5];
+        d_rgb[3 * g] += pt[6]; d_rgb[3 * g + 1] += pt[7]; d_rgb[3 * g + 2] += pt[8];
+        if (part_amb) {
+            const double *pa = part_amb + 9 * k;
+            double *ab = amb_abs + 9 * (int64_t)g;
+            for (int c = 0; c < 9; ++c) ab[c] += pa[c];
+        }
+        if (part_taint && part_taint[k]) tainted[g] = 1;
+    }
+    free(part);
+    free(part_amb);
+    free(part_taint);
 }
 
 /* ------------------------------------------------------------------ */
@@ -936,6 +1001,7 @@ void or_project_bwd_act(int64_t n, const double *P, const or_camera *cam, int32_
                         const double *d_mean2d, const double *d_conic, const double *d_opacity, const double *d_rgb,
                         double *G, double *G_mask, double *xyz_norm, double *rgb_norm) {
     memset(G, 0, sizeof(double) * NP * n);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (xyz_norm) xyz_norm[i] = 0;
         if (rgb_norm) rgb_norm[i] = 0;
@@ -1065,6 +1131,7 @@ static int param_group(int r) {
 void or_adam(int64_t n, double *P, const double *G, double *M, double *V, const uint8_t *frozen, const double *lr,
              double b1, double b2, double eps, int64_t step) {
     double bc1 = 1.0 - pow(b1, (double)step), bc2 = 1.0 - pow(b2, (double)step);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         if (frozen && frozen[i] && !PLANTED(12)) continue;
         for (int r = 0; r < NP; ++r) {

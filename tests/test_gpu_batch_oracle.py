@@ -108,7 +108,9 @@ def test_graph_replayed_batch_step_matches_oracle(tile):
         assert er == pytest.approx(C.threshold(s.eps0[1], k_cmp, ocfg.total_iter), rel=1e-12)
         oracle_scenes.append(dict(P=P.copy(), M=st["M"].astype(np.float64), V=st["V"].astype(np.float64),
                                   frozen=st["frozen"].copy(), acc_x=st["acc_x"].copy(), acc_r=st["acc_r"].copy(),
-                                  cnt=st["cnt"].copy(), step=st["step"], lr=st["lr"].astype(np.float64),
+                                  cnt=st["cnt"].copy(), step=st["step"],
+                                  lr=np.concatenate([[np.float32(s.ctrl.lr_xyz_at(k_cmp))], st["lr"][1:]]).astype(
+                                      np.float64),
                                   cams=ocams, gts=[pu.f32(s.targets[v].cpu().numpy()) for v in views], action=0,
                                   eps_xyz=np.float32(ex), eps_rgb=np.float32(er)))
     assert sum(int((st["frozen"] == 1).sum()) for st in snaps) > 0  # the first update froze something
@@ -154,11 +156,14 @@ def test_graph_replayed_batch_step_matches_oracle(tile):
         for key in ("acc_x", "acc_r"):
             good, worst = pu.close(got[key][clean], o[key][clean], 1e-3, 1e-2 * np.abs(o[key][clean]).max())
             assert good, (s.n, key, worst)
-        # one Adam step at the scene's counter, from the step's own gradient
+        # one Adam step at the scene's counter, from the step's own gradient, at
+        # the rates the host set for this iteration (the xyz rate decays each one)
         assert got["step"] == st0["step"] + 1 == o["step"]
+        lr = got["lr"].astype(np.float64)
+        assert lr[0] == pytest.approx(s.ctrl.lr_xyz_at(k_cmp), rel=1e-6) and np.array_equal(lr[1:], st0["lr"][1:])
         Po, Mo, Vo = (st0[k].astype(np.float64) for k in ("P", "M", "V"))
         Gd = got["G"].astype(np.float64)
-        oracle.adam(Po, Gd, Mo, Vo, o["frozen"], st0["lr"].astype(np.float64), got["step"], b1=b1, b2=b2, eps=eps)
+        oracle.adam(Po, Gd, Mo, Vo, o["frozen"], lr, got["step"], b1=b1, b2=b2, eps=eps)
         assert np.array_equal(got["P"][fr], st0["P"][fr]) and np.array_equal(got["M"][fr], st0["M"][fr])
         assert np.array_equal(got["V"][fr], st0["V"][fr])
         a = ~fr
@@ -168,6 +173,6 @@ def test_graph_replayed_batch_step_matches_oracle(tile):
         assert np.all(np.abs(got["V"][a] - Vo[a]) <= 1e-5 * v_scale + 1e-30)
         grp = np.array([0] * 3 + [1] * 3 + [2] * 4 + [3] + [4] * 3 + [5] * 45)
         bc1, bc2 = 1 - b1 ** got["step"], 1 - b2 ** got["step"]
-        step_bound = st0["lr"][grp] * (m_scale / bc1) / (np.sqrt(Vo[a] / bc2) + eps)
+        step_bound = lr[grp] * (m_scale / bc1) / (np.sqrt(Vo[a] / bc2) + eps)
         spacing = np.spacing(np.abs(st0["P"][a]).astype(np.float32)).astype(np.float64)
         assert np.all(np.abs(got["P"][a] - Po[a]) <= 1e-4 * step_bound + 2 * spacing)

@@ -76,7 +76,7 @@ def _pins(k: int) -> subprocess.CompletedProcess:
     files = sorted(f for f in glob.glob(os.path.join(ROOT, "tests", "test_oracle_*.py"))
                    if not f.endswith("test_oracle_mutants.py"))
     files.append(os.path.join(ROOT, "tests", "test_fd_local.py"))
-    env = dict(os.environ, GSTA_ORACLE_PLANT=str(k))
+    env = dict(os.environ, GSTA_ORACLE_PLANT=str(k), OMP_NUM_THREADS="1")  # the children run side by side
     return subprocess.run([sys.executable, "-m", "pytest", *files, "-x", "-q", "-p", "no:cacheprovider",
                            "-m", "not gpu"], env=env, cwd=ROOT, capture_output=True, text=True, timeout=900)
 
