@@ -234,15 +234,19 @@ static int32_t tile_rect(float mx, float my, int32_t r, int32_t tile, int32_t tx
 /* Reading of the tile lists (Sec. 3.1, Eq. 2; 3DGS, which the paper builds
  * on, lists a splat in every tile of its 3-sigma rectangle): a tile of the
  * rectangle lists the splat only if one of its pixel centres inside the image
- * has alpha = o exp(-q/2) >= 1/255, q = d^T Q d with d = pixel - mean and Q
- * the conic. At every other pixel of the rectangle the compositing floor of
- * Eq. 2 skips the splat, so the image and every gradient are those of the
- * full rectangle. Brute force over the tile's pixels in double precision;
- * o exp(-q/2) >= 1/255 is tested in the equivalent form q <= 2 ln(255 o)
- * (no pixel qualifies when 255 o < 1). */
+ * has alpha = o exp(-q/2) >= (1 - LIST_SLACK) / 255, q = d^T Q d with d =
+ * pixel - mean and Q the conic. At every other pixel of the rectangle the
+ * compositing floor of Eq. 2 skips the splat, so the image and every gradient
+ * are those of the full rectangle. The slack lists the splats whose alpha
+ * lies just below the floor, where single precision may take the other
+ * decision: compositing skips them, but it evaluates them and records how
+ * close each decision came (the parity tests' margins). Brute force over the
+ * tile's pixels in double precision; the alpha test is taken in the
+ * equivalent form q <= 2 ln(255 o / (1 - LIST_SLACK)). */
+#define LIST_SLACK 3e-4
 static int tile_lists(double mx, double my, double a, double b, double c, double o, int32_t tile, int32_t x,
                       int32_t y, int32_t W, int32_t H) {
-    double floor_alpha = PLANTED(44) ? 1.0 / 128.0 : 1.0 / 255.0;
+    double floor_alpha = (PLANTED(44) ? 1.0 / 128.0 : 1.0 / 255.0) * (1.0 - LIST_SLACK);
     if (!(o >= floor_alpha)) return 0;
     double tau = 2.0 * log(o / floor_alpha);
     int32_t px1 = x * tile + tile < W ? x * tile + tile : W;

@@ -249,19 +249,23 @@ def test_tiled_render_equals_brute_force(orc, tile):
     assert np.abs(f["image"] - brute).max() < 1e-12
 
 
+SLACK = 3e-4  # the oracle lists splats whose alpha comes within this relative distance of the floor
+
+
 def test_sort_lists_isotropic_closed_form(orc):
     """Isotropic splats (conic a = c = 1/s^2, b = 0): alpha = o exp(-r^2 / (2 s^2))
-    reaches the 1/255 floor of Eq. 2 within the distance R = s sqrt(2 ln(255 o))
-    of the mean, so a tile of the 3-sigma rectangle lists the splat exactly when
-    the pixel centre of the tile (inside the image) nearest to the mean lies
-    within R. Each tile's list is in (float32 depth, index) order."""
+    reaches (1 - SLACK) / 255, the floor of Eq. 2 with the oracle's slack,
+    within the distance R = s sqrt(2 ln(255 o / (1 - SLACK))) of the mean, so a
+    tile of the 3-sigma rectangle lists the splat exactly when the pixel centre
+    of the tile (inside the image) nearest to the mean lies within R. Each
+    tile's list is in (float32 depth, index) order."""
     g = np.random.default_rng(21)
     n, W, H, tile = 700, 150, 93, 16
     mx = g.uniform(-25, W + 25, n)
     my = g.uniform(-25, H + 25, n)
     s = g.uniform(0.7, 14.0, n)
     o = np.exp(g.uniform(np.log(0.002), 0.0, n))
-    o[:20] = 1.0 / 255.0 - 1e-6  # below the floor: listed nowhere
+    o[:20] = (1.0 - SLACK) / 255.0 - 1e-6  # below the floor: listed nowhere
     rad = np.ceil(3 * s).astype(np.int32)
     depth = g.choice(np.array([1.0, 2.5, 4.0], np.float32), n)  # many equal depths: index breaks ties
     m32 = np.stack([mx, my], 1).astype(np.float32)
@@ -277,9 +281,9 @@ def test_sort_lists_isotropic_closed_form(orc):
         x1 = min(int(np.floor((m32[i, 0] + rad[i]) / np.float32(tile))), tx - 1)
         y0 = max(int(np.floor((m32[i, 1] - rad[i]) / np.float32(tile))), 0)
         y1 = min(int(np.floor((m32[i, 1] + rad[i]) / np.float32(tile))), ty - 1)
-        if O[i] * 255.0 < 1.0:
+        if O[i] * 255.0 < 1.0 - SLACK:
             continue
-        R2 = S2[i] * 2.0 * np.log(255.0 * O[i])
+        R2 = S2[i] * 2.0 * np.log(255.0 * O[i] / (1.0 - SLACK))
         for y in range(y0, y1 + 1):
             for x in range(x0, x1 + 1):
                 nx = min(max(round(M[i, 0]), x * tile), min(x * tile + tile, W) - 1)
@@ -298,11 +302,13 @@ def test_sort_lists_isotropic_closed_form(orc):
 
 
 def test_sort_lists_are_minimal(orc):
-    """Every entry of a tile's list blends at some pixel of that tile: on a scene
-    whose rays never reach the transmittance floor (few, faint splats), each
-    listed splat appears in the compositing trace of at least one pixel of the
-    tile. Together with the untiled brute-force render (no contribution
-    missing), this fixes the lists."""
+    """Every entry of a tile's list blends at some pixel of that tile, but for
+    the slack band: on a scene whose rays never reach the transmittance floor
+    (few, faint splats), each listed splat appears in the compositing trace of
+    at least one pixel of the tile, except entries whose largest alpha over
+    the tile's pixel centres lies in [(1 - SLACK) / 255, 1 / 255). Together
+    with the untiled brute-force render (no contribution missing), this fixes
+    the lists."""
     g = np.random.default_rng(5)
     P, cam = _random_view(orc, n=120, W=64, H=48, tile=16, seed=13)
     op = g.uniform(0.004, 0.3, P.shape[0])
@@ -318,7 +324,15 @@ def test_sort_lists_are_minimal(orc):
             t = (py // 16) * tx + px // 16
             seen.update((t, int(vals[ranges[t, 0] + p])) for p in pos)
     listed = {(t, int(i)) for t in range(len(ranges)) for i in vals[ranges[t, 0]:ranges[t, 1]]}
-    assert len(listed) > 100 and listed == seen
+    assert len(listed) > 100 and seen <= listed
+    pr = f["proj"]
+    for t, i in listed - seen:  # the slack band only
+        x0, y0 = (t % tx) * 16, (t // tx) * 16
+        ys, xs = np.mgrid[y0:min(y0 + 16, cam.height), x0:min(x0 + 16, cam.width)]
+        dx, dy = xs - pr["mean2d"][i, 0], ys - pr["mean2d"][i, 1]
+        a, b, c = pr["conic"][i]
+        amax = (pr["opacity"][i] * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))).max()
+        assert (1 - SLACK) / 255 <= amax < 1 / 255, (t, i, amax * 255)
     assert np.abs(f["image"] - orc.render_brute(f["proj"], cam)).max() < 1e-12
 
 
