@@ -325,6 +325,11 @@ static void project_one(const double *p, const or_camera *cam, int sh_degree, in
     if (u < -limx) { g->cux = -limx; g->clampx = 1; }
     if (v > limy) { g->cuy = limy; g->clampy = 1; }
     if (v < -limy) { g->cuy = -limy; g->clampy = 1; }
+    if (!smooth) { /* distance (pixels) of the screen position to the clamp, a decision of the gradient */
+        double mx = cam->fx * fmin(fabs(u - limx), fabs(u + limx)), my = cam->fy * fmin(fabs(v - limy), fabs(v + limy));
+        if (mx < g->margin) g->margin = mx;
+        if (my < g->margin) g->margin = my;
+    }
     double *J = g->J;
     J[0] = cam->fx / tz; J[1] = 0; J[2] = PLANTED(2) ? 0.0 : -cam->fx * g->cux / tz;
     J[3] = 0; J[4] = cam->fy / tz; J[5] = -cam->fy * g->cuy / tz;

@@ -163,9 +163,12 @@ struct PixBwd {
 // with respect to the 2-D mean and conic are dx/dy polynomials; the thread's
 // pixels share dx, so only the dy moments of dL/dpower are summed here
 // (g[0] += dpow, g[1] += dy dpow, g[2] += dy^2 dpow) and geo_grads() turns
-// them into the five gradients once per splat.
+// them into the five gradients once per splat. FRZ: the splat is frozen, so
+// only the pixel's state moves (a separate instantiation, so that a frozen
+// splat issues none of the gradient instructions).
+template <bool FRZ>
 __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row, float dy, const float4 &co,
-                                        float blue, bool frz, float (&g)[9]) {
+                                        float blue, float (&g)[9]) {
     const float power = splat_power(row, dy);
     const float G = __expf(power);
     const float oG = __fmul_rn(co.y, G);
@@ -173,9 +176,9 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row,
     if (!(pos < p.nl && power <= 0.f && alpha >= kAlphaMin)) return false;
     const float om = 1.f - alpha;
     p.T = __fdividef(p.T, om);  // transmittance in front of this splat
-    p.D = p.la * p.ldc + (1.f - p.la) * p.D;
+    p.D = fmaf(p.la, p.ldc - p.D, p.D);
     const float dcc = p.dC0 * co.z + p.dC1 * co.w + p.dC2 * blue;
-    if (!frz) {
+    if (!FRZ) {
         const float dA = p.T * (dcc - p.D) - __fdividef(p.Tf, om) * p.bgdot;
         const float wT = alpha * p.T;
         g[6] += wT * p.dC0;
@@ -281,17 +284,23 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
             const int pos = (int)(bstart - (int64_t)start) + j;  // position in the tile list
             const float4 xa = s_xyab[j], co = s_cocg[j];
             const float blue = s_blue[j];
-            const bool frz = s_frz[j] != 0;
+            const bool frz = s_frz[j] != 0;  // the same for every thread: a uniform branch
             const float dx = __fsub_rn(xa.x, fpx);
             const SplatRow row = splat_row(dx, xa.z, xa.w, co.x);
             float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            bool c = false;
+            if (frz) {
 #pragma unroll
-            for (int k = 0; k < PPT; ++k) c |= pix_bwd(p[k], pos, row, __fsub_rn(xa.y, fpy[k]), co, blue, frz, g);
-            if (!frz && __any_sync(kFull, c)) {
-                geo_grads(g, dx, xa.z, xa.w, co.x);
-                const float tot = warp_sum9(g, lane);
-                if (writer) atomicAdd(&s_acc[slot][j], tot);
+                for (int k = 0; k < PPT; ++k) pix_bwd<true>(p[k], pos, row, __fsub_rn(xa.y, fpy[k]), co, blue, g);
+            } else {
+                bool c = false;
+#pragma unroll
+                for (int k = 0; k < PPT; ++k)
+                    c |= pix_bwd<false>(p[k], pos, row, __fsub_rn(xa.y, fpy[k]), co, blue, g);
+                if (__any_sync(kFull, c)) {
+                    geo_grads(g, dx, xa.z, xa.w, co.x);
+                    const float tot = warp_sum9(g, lane);
+                    if (writer) atomicAdd(&s_acc[slot][j], tot);
+                }
             }
         }
         __syncthreads();

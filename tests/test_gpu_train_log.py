@@ -2,7 +2,6 @@
 (plain arm: it ends at the iteration count; no freezing, no densification yet)."""
 import json
 import math
-from types import SimpleNamespace
 
 import pytest
 
@@ -19,10 +18,9 @@ def test_short_run_writes_the_training_record(tmp_path):
     build.build()
     lib.load()
     p = tmp_path / "train.jsonl"
-    args = SimpleNamespace(arm="plain", n_init=3000, n_gt=4000, views=16, width=160, height=120, iters=40,
-                           eval_every=20, autotune=False, no_calibrate=False, no_densify=False, tune_after=0,
-                           freeze_strategy="gsta", no_abs_opacity=False, abs_moments="rescale", abs_lr="slope",
-                           trick_gs=False, volume_mask=False, significance=False, log_jsonl=str(p), log_every=10)
+    args = train.parser().parse_args(["--arm", "plain", "--n-init", "3000", "--n-gt", "4000", "--views", "16",
+                                      "--width", "160", "--height", "120", "--iters", "40", "--eval-every", "20",
+                                      "--tune-after", "0", "--log-jsonl", str(p), "--log-every", "10"])
     out = train.run(args)
     assert out["iters"] == 40 and out["device_flags"] == 0
     recs = [json.loads(line) for line in p.read_text().splitlines()]
