@@ -195,3 +195,22 @@ def check_lists(vals, ranges, want_vals, want_ranges, rec, tile: int, tiles_x: i
         worst = float(np.max(q - tau - LIST_BAND * (1 + np.abs(tau))))
         assert worst <= 0.0, f"a CUDA-only entry lies outside the band (excess {worst:.3e})"
     return int(xt.size)
+
+
+# The L1 term of Eq. 3 takes the sign of image - target: where the two agree
+# to within this margin, float32 and double may take different signs, and
+# dL/dC of that channel then differs by 2 (1 - lambda) / (3 H W).
+L1_MARGIN = 1e-5
+
+
+def l1_sign_bound(proj, vals, ranges, ocam, image, gt, frozen=None, lam=0.2):
+    """Bound [n][9] on the raster-gradient change that an L1 sign taken the
+    other way may cause: the oracle's raster backward with dL/dC set to the
+    largest change at the ambiguous channels and 0 elsewhere, its terms taken
+    in absolute value. Pixels where image and target are both exactly zero
+    decide alike on both sides (sign 0)."""
+    amb = np.abs(image - gt) <= L1_MARGIN
+    amb &= ~((image == 0) & (gt == 0))
+    dl = np.where(amb, 2.0 * (1.0 - lam) / image.size, 0.0)
+    rb = oracle.render_bwd(proj, vals, ranges, ocam, dl, frozen, amb.any(axis=0).astype(np.uint8))
+    return rb["amb_abs"]

@@ -51,7 +51,9 @@ def test_autograd_gradient_matches_oracle_with_frozen_rows():
     amb = (want["fwd"]["margin"] <= pu.E2E_PIXEL_MARGIN).astype(np.uint8)
     rb = oracle.render_bwd(want["fwd"]["proj"], want["fwd"]["vals"], want["fwd"]["ranges"], ocam, want["dl_dimage"],
                            frozen, amb)
-    bound = pu.param_bound(P, ocam, rb["amb_abs"], frozen)
+    l1 = pu.l1_sign_bound(want["fwd"]["proj"], want["fwd"]["vals"], want["fwd"]["ranges"], ocam, want["fwd"]["image"],
+                          gt, frozen)
+    bound = pu.param_bound(P, ocam, rb["amb_abs"] + l1, frozen)
     assert np.all(G[frozen == 1] == 0)
     act = frozen == 0
     for sl in [slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11), slice(11, 14), slice(14, 59)]:

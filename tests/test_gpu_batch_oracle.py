@@ -16,7 +16,8 @@ written back, so that both sides start from the same float32 state. Then:
 * each view's loss equals the oracle's within 1e-4 relative;
 * the scene's gradient (the sum over its views) equals the oracle's within
   1e-3 relative (floor 1% of the largest magnitude), widened only by what
-  the float32 decisions within 2e-4 of a threshold may change, for every
+  the float32 decisions within 2e-4 of a threshold, and the L1 signs of
+  Eq. 3 where image and target agree within 1e-5, may change, for every
   Gaussian farther than 0.3 from the near plane in all views (nearer, the
   float32 Jacobian terms in 1/z^2 carry per-cent errors; at most 1% of the
   Gaussians);
@@ -138,14 +139,15 @@ def test_graph_replayed_batch_step_matches_oracle(tile):
         amb_rows = np.zeros(n, bool)
         vis = np.zeros(n, bool)
         near = np.zeros(n, bool)
-        for oc, r in zip(o["cams"], w["views"]):
+        for oc, o_gt, r in zip(o["cams"], o["gts"], w["views"]):
             f = r["fwd"]
             amb = f["margin"] <= pu.E2E_PIXEL_MARGIN
             assert amb.mean() < 0.05
             rb = oracle.render_bwd(f["proj"], f["vals"], f["ranges"], oc, r["dl_dimage"], o["frozen"],
                                    amb.astype(np.uint8))
-            bound += pu.param_bound(st0["P"].astype(np.float64), oc, rb["amb_abs"], o["frozen"])
-            amb_rows |= rb["amb_abs"].any(axis=1)
+            l1 = pu.l1_sign_bound(f["proj"], f["vals"], f["ranges"], oc, f["image"], o_gt, o["frozen"])
+            bound += pu.param_bound(st0["P"].astype(np.float64), oc, rb["amb_abs"] + l1, o["frozen"])
+            amb_rows |= rb["amb_abs"].any(axis=1) | l1.any(axis=1)
             vis |= f["proj"]["radius"] > 0
             # within 0.3 of the near plane the Jacobian's 1/z^2 terms leave float32
             # gradients with a few per cent of error: such Gaussians are left out

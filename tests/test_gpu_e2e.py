@@ -84,7 +84,9 @@ def test_full_step_matches_oracle(cam_index):
     # through the projection Jacobian
     rb = oracle.render_bwd(want["fwd"]["proj"], want["fwd"]["vals"], want["fwd"]["ranges"], ocam, want["dl_dimage"],
                            frozen, amb.astype(np.uint8))
-    bound = pu.param_bound(P, ocam, rb["amb_abs"], frozen)
+    l1 = pu.l1_sign_bound(want["fwd"]["proj"], want["fwd"]["vals"], want["fwd"]["ranges"], ocam, want["fwd"]["image"],
+                          gt, frozen)
+    bound = pu.param_bound(P, ocam, rb["amb_abs"] + l1, frozen)
     fr = frozen == 1
     act = ~fr & (want["fwd"]["proj"]["radius"] > 0)
     for sl in [slice(0, 3), slice(3, 6), slice(6, 10), slice(10, 11), slice(11, 14), slice(14, 59)]:
