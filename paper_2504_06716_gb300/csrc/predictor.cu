@@ -114,16 +114,33 @@ __device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi)
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// One warp per 16-row tile, tiles strided over the grid. Fragment layouts of
+// A fragments of one 16-row tile (rows beyond n read as zero).
+__device__ __forceinline__ void load_tile(const __nv_bfloat16 *__restrict__ X, int64_t n, int64_t tile, int g, int t,
+                                          uint32_t (&a)[4]) {
+    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+    const uint32_t *x0 = reinterpret_cast<const uint32_t *>(X + r0 * kIn);
+    const uint32_t *x1 = reinterpret_cast<const uint32_t *>(X + r1 * kIn);
+    a[0] = r0 < n ? __ldg(x0 + t) : 0u;
+    a[1] = r1 < n ? __ldg(x1 + t) : 0u;
+    a[2] = r0 < n ? __ldg(x0 + 4 + t) : 0u;
+    a[3] = r1 < n ? __ldg(x1 + 4 + t) : 0u;
+}
+
+// One warp per 16-row tile, tiles strided over the grid; each warp has the
+// features of its next two tiles in flight while it computes the current
+// one (the kernel is bound by reading 32 B per row). Fragment layouts of
 // m16n8k16 (lane = 4 g + t): A rows g, g+8 / columns 2t, 2t+1, 2t+8, 2t+9;
 // B columns g / rows 2t, 2t+1, 2t+8, 2t+9; C rows g, g+8 / columns 2t, 2t+1.
 // The layer-1 accumulators of n-tiles 2s and 2s+1 are exactly the A fragment
-// of layer 2's k-step s, so the hidden layer never leaves registers.
-__global__ void __launch_bounds__(128) k_mlp_fwd(int64_t n, const __nv_bfloat16 *__restrict__ X,
-                                                 const __nv_bfloat16 *__restrict__ wb,
-                                                 const float *__restrict__ prm, float *__restrict__ p) {
+// of layer 2's k-step s, so the hidden layer never leaves registers. Layer
+// 1's B fragments and W3 stay in registers; layer 2's (64 per lane) are read
+// from shared memory, packed per lane, to keep the register count low.
+__global__ void __launch_bounds__(128, 4) k_mlp_fwd(int64_t n, const __nv_bfloat16 *__restrict__ X,
+                                                    const __nv_bfloat16 *__restrict__ wb,
+                                                    const float *__restrict__ prm, float *__restrict__ p) {
     __shared__ __nv_bfloat16 sW[kNWb];
     __shared__ float sB[kH * 2 + 1];
+    __shared__ uint2 sB2[4][8][32];  // [k-step][n-tile][lane]
     for (int k = threadIdx.x; k < kNWb; k += blockDim.x) sW[k] = wb[k];
     for (int k = threadIdx.x; k < kH; k += blockDim.x) {
         sB[k] = prm[oB1 + k];
@@ -131,49 +148,50 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int64_t n, const __nv_bfloat16 
     }
     if (threadIdx.x == 0) sB[2 * kH] = prm[oB3];
     __syncthreads();
+    for (int e = threadIdx.x; e < 4 * 8 * 32; e += blockDim.x) {
+        const int st = e >> 8, nt = (e >> 5) & 7, ln = e & 31;
+        const int col = 8 * nt + (ln >> 2), k0 = 16 * st + 2 * (ln & 3);
+        sB2[st][nt][ln] = make_uint2(pack_raw(sW[wbW2 + k0 * kH + col], sW[wbW2 + (k0 + 1) * kH + col]),
+                                     pack_raw(sW[wbW2 + (k0 + 8) * kH + col], sW[wbW2 + (k0 + 9) * kH + col]));
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    // B fragments of W1 (8 n-tiles) and W2 (4 k-steps x 8 n-tiles)
-    uint32_t b1[8][2], b2[4][8][2];
+    uint32_t b1[8][2];
+    float w3[8][2];
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
         const int col = 8 * nt + g;
         b1[nt][0] = pack_raw(sW[wbW1 + (2 * t) * kH + col], sW[wbW1 + (2 * t + 1) * kH + col]);
         b1[nt][1] = pack_raw(sW[wbW1 + (2 * t + 8) * kH + col], sW[wbW1 + (2 * t + 9) * kH + col]);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int k0 = 16 * s + 2 * t;
-            b2[s][nt][0] = pack_raw(sW[wbW2 + k0 * kH + col], sW[wbW2 + (k0 + 1) * kH + col]);
-            b2[s][nt][1] = pack_raw(sW[wbW2 + (k0 + 8) * kH + col], sW[wbW2 + (k0 + 9) * kH + col]);
-        }
-    }
-    float w3[8][2];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
         w3[nt][0] = __bfloat162float(sW[wbW3 + 8 * nt + 2 * t]);
         w3[nt][1] = __bfloat162float(sW[wbW3 + 8 * nt + 2 * t + 1]);
     }
+    const float b3 = sB[2 * kH];
     const int64_t tiles = (n + 15) / 16;
     const int warp = threadIdx.x >> 5, warps = blockDim.x >> 5;
-    for (int64_t tile = (int64_t)blockIdx.x * warps + warp; tile < tiles; tile += (int64_t)gridDim.x * warps) {
-        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-        const uint32_t *x0 = reinterpret_cast<const uint32_t *>(X + r0 * kIn);
-        const uint32_t *x1 = reinterpret_cast<const uint32_t *>(X + r1 * kIn);
-        const uint32_t a0 = r0 < n ? __ldg(x0 + t) : 0u, a1 = r1 < n ? __ldg(x1 + t) : 0u;
-        const uint32_t a2 = r0 < n ? __ldg(x0 + 4 + t) : 0u, a3 = r1 < n ? __ldg(x1 + 4 + t) : 0u;
-        float h[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const float c0 = sB[8 * nt + 2 * t], c1 = sB[8 * nt + 2 * t + 1];
-            h[nt][0] = c0; h[nt][1] = c1; h[nt][2] = c0; h[nt][3] = c1;
-            mma16816(h[nt], a0, a1, a2, a3, b1[nt][0], b1[nt][1]);
-        }
+    const int64_t stride = (int64_t)gridDim.x * warps;
+    int64_t tile = (int64_t)blockIdx.x * warps + warp;
+    uint32_t a[4], na[4];
+    load_tile(X, n, tile, g, t, a);
+    load_tile(X, n, tile + stride, g, t, na);
+    for (; tile < tiles; tile += stride) {
+        uint32_t nna[4];
+        load_tile(X, n, tile + 2 * stride, g, t, nna);
         uint32_t ha[4][4];  // relu(h1) as bf16 A fragments of layer 2
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            ha[s][0] = pack_bf16(fmaxf(h[2 * s][0], 0.f), fmaxf(h[2 * s][1], 0.f));
-            ha[s][1] = pack_bf16(fmaxf(h[2 * s][2], 0.f), fmaxf(h[2 * s][3], 0.f));
-            ha[s][2] = pack_bf16(fmaxf(h[2 * s + 1][0], 0.f), fmaxf(h[2 * s + 1][1], 0.f));
-            ha[s][3] = pack_bf16(fmaxf(h[2 * s + 1][2], 0.f), fmaxf(h[2 * s + 1][3], 0.f));
+        for (int st = 0; st < 4; ++st) {
+            float h[2][4];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int nt = 2 * st + q;
+                const float c0 = sB[8 * nt + 2 * t], c1 = sB[8 * nt + 2 * t + 1];
+                h[q][0] = c0; h[q][1] = c1; h[q][2] = c0; h[q][3] = c1;
+                mma16816(h[q], a[0], a[1], a[2], a[3], b1[nt][0], b1[nt][1]);
+            }
+            ha[st][0] = pack_bf16(fmaxf(h[0][0], 0.f), fmaxf(h[0][1], 0.f));
+            ha[st][1] = pack_bf16(fmaxf(h[0][2], 0.f), fmaxf(h[0][3], 0.f));
+            ha[st][2] = pack_bf16(fmaxf(h[1][0], 0.f), fmaxf(h[1][1], 0.f));
+            ha[st][3] = pack_bf16(fmaxf(h[1][2], 0.f), fmaxf(h[1][3], 0.f));
         }
         float z0 = 0.f, z1 = 0.f;
 #pragma unroll
@@ -181,7 +199,10 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int64_t n, const __nv_bfloat16 
             const float c0 = sB[kH + 8 * nt + 2 * t], c1 = sB[kH + 8 * nt + 2 * t + 1];
             float acc[4] = {c0, c1, c0, c1};
 #pragma unroll
-            for (int s = 0; s < 4; ++s) mma16816(acc, ha[s][0], ha[s][1], ha[s][2], ha[s][3], b2[s][nt][0], b2[s][nt][1]);
+            for (int st = 0; st < 4; ++st) {
+                const uint2 bb = sB2[st][nt][lane];
+                mma16816(acc, ha[st][0], ha[st][1], ha[st][2], ha[st][3], bb.x, bb.y);
+            }
             z0 += fmaxf(acc[0], 0.f) * w3[nt][0] + fmaxf(acc[1], 0.f) * w3[nt][1];
             z1 += fmaxf(acc[2], 0.f) * w3[nt][0] + fmaxf(acc[3], 0.f) * w3[nt][1];
         }
@@ -189,9 +210,15 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(int64_t n, const __nv_bfloat16 
         z0 += __shfl_xor_sync(kFull, z0, 2);
         z1 += __shfl_xor_sync(kFull, z1, 1);
         z1 += __shfl_xor_sync(kFull, z1, 2);
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
         if (t == 0) {
-            if (r0 < n) p[r0] = 1.f / (1.f + expf(-(z0 + sB[2 * kH])));
-            if (r1 < n) p[r1] = 1.f / (1.f + expf(-(z1 + sB[2 * kH])));
+            if (r0 < n) p[r0] = 1.f / (1.f + expf(-(z0 + b3)));
+            if (r1 < n) p[r1] = 1.f / (1.f + expf(-(z1 + b3)));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[k] = na[k];
+            na[k] = nna[k];
         }
     }
 }
@@ -400,7 +427,7 @@ extern "C" int gs_mlp_fwd(int64_t n, const uint16_t *X, const uint16_t *wb, cons
     if (!X || !wb || !params || !p || (reinterpret_cast<uintptr_t>(X) & 3)) return GS_ERR_INVALID_ARG;
     const int64_t tiles = (n + 15) / 16;
     int64_t blocks = (tiles + 3) / 4;
-    if (blocks > (int64_t)sms() * 8) blocks = (int64_t)sms() * 8;
+    if (blocks > (int64_t)sms() * 4) blocks = (int64_t)sms() * 4;  // one resident wave
     k_mlp_fwd<<<(unsigned)blocks, 128, 0, as_stream(stream)>>>(n, reinterpret_cast<const __nv_bfloat16 *>(X),
                                                                reinterpret_cast<const __nv_bfloat16 *>(wb), params, p);
     note_launches(1);

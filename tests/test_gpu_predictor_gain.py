@@ -1,14 +1,21 @@
 """What the learned freeze predictor buys on the tiny-scene workload.
 
 The predictor is trained (by its own CUDA kernels) on the freeze decisions
-the gradient-norm rule logs over four tiny-scene runs, then a held-out scene
-is trained twice: with the rule alone and with the predictor applied every 4
-iterations (tau = 0.9). Asserted: the predictor run does measurably less
-work -- at least 5% fewer active-Gaussian iterations, the quantity freezing
-saves in the backward and the optimiser -- for at most 1 dB of held-out PSNR,
-and its false-freeze rate (the share of Gaussians it froze whose unmasked
-gradient norms over the following window would not have passed the rule) is
-measured and reported next to the rule's own.
+the gradient-norm rule logs over four tiny-scene runs; its decision
+threshold is the lowest probability at which its freezes are 90% right on
+the logs of two further runs. Then a held-out scene is trained twice: with
+the rule alone, and with the predictor applied every 4 iterations between
+the rule's updates (the rule keeps running). Asserted, the target this
+component is judged by: the predictor run does at least 5% less work --
+active-Gaussian iterations, the quantity freezing saves in the backward and
+the optimiser -- at a held-out PSNR no more than 0.1 dB below the rule's.
+
+The false-freeze rate (the share of Gaussians frozen by a source whose
+unmasked gradient norms, over the rest of the window they were frozen in,
+would not pass Eq. 4) is compared in a second test that is expected to
+fail: the predictor's rate stays well above the rule's in the rule-only
+run (about 0.85 against 0.25 when measured), i.e. it freezes Gaussians early
+that the rule would have frozen one window later.
 """
 import json
 
@@ -19,36 +26,47 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", autouse=True)
-def _built():
+@pytest.fixture(scope="module")
+def runs():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2504_06716_gb300 import build, lib
-
-    build.build()
-    lib.load()
-
-
-def test_predictor_saves_work_on_a_held_out_scene():
-    from paper_2504_06716_gb300 import synth
+    from paper_2504_06716_gb300 import build, lib, synth
     from paper_2504_06716_gb300.predictor import FreezePredictor, collect, evaluate
     from paper_2504_06716_gb300.schedule import GStaConfig
 
+    build.build()
+    lib.load()
     cfg = GStaConfig.tiny()
-    logs = [collect(synth.tiny_scene(seed=s), cfg, cfg.total_iter) for s in (0, 1, 2, 3)]
-    data = [lg.dataset() for lg in logs]
-    X = torch.cat([d[0] for d in data if d[0] is not None])
-    y = torch.cat([d[1] for d in data if d[1] is not None]).to(X.device)
+
+    def data(seeds):
+        ds = [collect(synth.tiny_scene(seed=s), cfg, cfg.total_iter).dataset() for s in seeds]
+        return torch.cat([d[0] for d in ds if d[0] is not None]), torch.cat([d[1] for d in ds if d[1] is not None])
+
+    X, y = data((0, 1, 2, 3))
     assert 0.02 < float(y.mean()) < 0.98  # both classes present
     pred = FreezePredictor()
-    losses = pred.fit(X, y, epochs=600)
+    losses = pred.fit(X, y.to(X.device), epochs=800)
     assert losses[-1] < losses[0]
+    Xv, yv = data((4, 5))
+    tau = pred.choose_tau(Xv, yv, 0.9)
+    assert tau < 1.0
     scene = synth.tiny_scene(seed=9)
     rule = evaluate(scene, cfg, None, 1.0, 4)
-    withp = evaluate(scene, cfg, pred, 0.9, 4)
-    print(json.dumps(dict(samples=int(X.shape[0]), rule=rule, predictor=withp), default=str))
+    withp = evaluate(scene, cfg, pred, tau, 4)
+    print(json.dumps(dict(samples=int(X.shape[0]), tau=tau, rule=rule, predictor=withp), default=str))
+    return rule, withp
+
+
+def test_predictor_saves_work_at_the_rules_psnr(runs):
+    rule, withp = runs
     assert withp["predicted"] > 0
     assert withp["active_gaussian_iters"] <= 0.95 * rule["active_gaussian_iters"]
-    assert withp["heldout_psnr"] >= rule["heldout_psnr"] - 1.0
-    ff = withp["false_freeze_pred"]
-    assert ff is not None and 0.0 <= ff <= 1.0
+    assert withp["heldout_psnr"] >= rule["heldout_psnr"] - 0.1
+
+
+@pytest.mark.xfail(reason="measured: the predictor's false-freeze rate is about 0.85 against the rule's 0.25",
+                   strict=False)
+def test_predictor_false_freeze_rate_no_worse_than_the_rule(runs):
+    rule, withp = runs
+    assert withp["false_freeze_pred"] is not None and rule["false_freeze_rule"] is not None
+    assert withp["false_freeze_pred"] <= rule["false_freeze_rule"] + 0.05
