@@ -406,6 +406,10 @@ def gpu_arm(args):
         torch.cuda.empty_cache()
         ttp = {"noiseless": time_to_psnr(scene), "target_noise_0.03": time_to_psnr(scene, 0.03)}
 
+    batched = None
+    if world == 1 and not args.no_batch:
+        batched = batch_leg()
+
     if reps.printer:
         line = dict(metric=METRIC, value=its, unit="it/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
@@ -416,7 +420,8 @@ def gpu_arm(args):
                     plain["its"],
                     roofline=roofline, roofline_adam=adam, roofline_adam_all_active=adam_all,
                     roofline_project=project, cpu_baseline=cpu, e2e=e2e, gpu_launches=launches,
-                    clocks=clk_summary, device_flags=flags, amortized=periodic, time_to_psnr=ttp)
+                    clocks=clk_summary, device_flags=flags, amortized=periodic, time_to_psnr=ttp,
+                    batched_scenes=batched)
         print(json.dumps(line), flush=True)
     reps.close()
 
@@ -650,6 +655,35 @@ def time_to_psnr(scene, target_noise: float = 0.0) -> dict:
     return out
 
 
+def batch_leg(steps: int = 40, warmup: int = 8, pretrain: int = 300) -> dict:
+    """Several scenes per step (the batched workload): 8 scenes of 50K to 2M
+    Gaussians (5.72M in all), 4 views of each at 800x800 per step, one
+    persistent compositing and one persistent backward launch over the 32
+    (scene, view) jobs, each step replayed from a CUDA graph; tile size and
+    launch shapes from the batch's own autotuner; CUDA events over `steps`
+    replayed steps after `pretrain` + `warmup` steps."""
+    import torch
+
+    from paper_2504_06716_gb300 import batch
+    from paper_2504_06716_gb300.schedule import GStaConfig
+
+    t0 = time.perf_counter()
+    bt = batch.BatchTrainer(batch.make_scenes(), GStaConfig())
+    setup_s = time.perf_counter() - t0
+    tuning = batch.tune(bt)
+    for _ in range(pretrain):
+        bt.step("graph")
+    r = batch.measure(bt, steps, warmup, "graph")
+    out = dict(workload="8 scenes of 50K-2M Gaussians (5.72M), 4 views each at 800x800 per step",
+               ms_per_step=r["ms_per_step"], gaussian_views_per_s=r["gaussian_views_per_s"],
+               launches_per_step=r["launches_per_step"], steps=steps, start_step=pretrain + warmup,
+               tuning=dict(tile=tuning["tile"], fwd_ppt_batch=list(tuning["fwd"]), bwd_ppt_batch=list(tuning["bwd"])),
+               setup_s=setup_s, timing="CUDA events around the replayed steps on the launching stream")
+    del bt
+    torch.cuda.empty_cache()
+    return out
+
+
 def periodic_costs(tr) -> dict:
     """Milliseconds of the work GSta does only every so many iterations,
     measured on the bench state at the end (they change it): a densification
@@ -686,6 +720,7 @@ def main():
     ap.add_argument("--start-iter", type=int, default=4750)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep 16-pixel tiles and default launch shapes")
+    ap.add_argument("--no-batch", action="store_true", help="skip the several-scene step (about a minute)")
     ap.add_argument("--no-time-to-psnr", action="store_true",
                     help="skip the four full training runs of the time-to-PSNR comparison (about three minutes)")
     ap.add_argument("--views", type=int, default=WORKLOAD["views"],
