@@ -432,9 +432,20 @@ def gpu_arm(args):
 # gives the command). Valid only for the kernel sources it was taken on: the
 # digest of those files is compared at run time and traffic is reported as null
 # once they have changed.
-RASTER_BWD_TRAFFIC = dict(bytes_per_launch=72891853,
-                          sources_sha256="1b09d07e683ea1a70bff1ebf02d655e1f8267a556bc0025ae4a502d9b5810589")
+RASTER_BWD_TRAFFIC = dict(bytes_per_launch=80703232,
+                          sources_sha256="e736c990d5f4ef88ac26f9e7fcfdf434655490df04828070179026041574d070")
 RASTER_BWD_SOURCES = ("paper_2504_06716_gb300/csrc/render.cu", "paper_2504_06716_gb300/csrc/common.cuh")
+# The same for Adam and the projection (profiles/k_adam_traffic_surface-1M-1237x822.md,
+# profiles/k_project_fwd_traffic_surface-1M-1237x822.md):
+# DRAM bytes per launch of three captured launches, with the launch's units
+# (active Gaussians; the projection's algorithmic bytes), so that a run on
+# another state scales the traffic by its own units.
+ADAM_TRAFFIC = dict(bytes_per_launch=54627669, active=52081,
+                    sources_sha256="1c6eb55051c060fe2047d7a99f0b9a63590f4306f660a75f8c3be7cbe99b4d65")
+ADAM_SOURCES = ("paper_2504_06716_gb300/csrc/optim.cu", "paper_2504_06716_gb300/csrc/common.cuh")
+PROJECT_TRAFFIC = dict(bytes_per_launch=281098582, algorithmic_bytes=253242144,
+                       sources_sha256="59e78e87e3cf1cb79297be6b9af183f72676207972492cf49dedd9ec1c0324bd")
+PROJECT_SOURCES = ("paper_2504_06716_gb300/csrc/project.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 
 
 def sources_digest(paths) -> str:
@@ -453,6 +464,22 @@ def raster_bwd_traffic():
     if t["bytes_per_launch"] is None or t["sources_sha256"] != sources_digest(RASTER_BWD_SOURCES):
         return None
     return t["bytes_per_launch"]
+
+
+def adam_traffic(active: int):
+    """Captured Adam DRAM bytes per launch scaled to `active` Gaussians (null
+    once the kernel's sources differ from the captured ones)."""
+    t = ADAM_TRAFFIC
+    if t["sources_sha256"] != sources_digest(ADAM_SOURCES):
+        return None
+    return round(t["bytes_per_launch"] * active / t["active"])
+
+
+def project_traffic(algorithmic_bytes: float):
+    t = PROJECT_TRAFFIC
+    if t["sources_sha256"] != sources_digest(PROJECT_SOURCES):
+        return None
+    return round(t["bytes_per_launch"] * algorithmic_bytes / t["algorithmic_bytes"])
 
 
 # Algorithmic FP32 work of the rasteriser backward per (pixel, splat) pair, counted
@@ -505,6 +532,9 @@ def stage_split(tr, n) -> dict:
         v = tr.order[tr.k + i]
         m.retarget(view, tr.cams[v])
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+        # the device waits ~0.5 ms while the host enqueues the whole sequence, so
+        # each event pair brackets its kernel alone (no host launch gap inside)
+        torch.cuda._sleep(1_000_000)
         ev[0].record()
         lib.gs_project(m.P, m.n, m.sh_degree, view.cam, m.splats)
         ev[1].record()
@@ -537,10 +567,11 @@ def stage_split(tr, n) -> dict:
     return dict(stage_ms=st, fwd_ms=st["project"] + st["sort"] + st["render"],
                 bwd_ms=st["loss"] + st["raster_bwd"] + st["project_bwd"],
                 adam_roofline=dict(bound="hbm", kernel="k_adam", achieved=adam_gbs, peak=peaks["hbm_gbs"],
-                                   unit="GB/s", frac=adam_gbs / peaks["hbm_gbs"], traffic=None,
+                                   unit="GB/s", frac=adam_gbs / peaks["hbm_gbs"], traffic=adam_traffic(n_act),
                                    bytes_per_active_gaussian=15 * 16 * 7, active=n_act, peak_source=kind),
                 project_roofline=dict(bound="hbm", kernel="k_project_fwd", achieved=proj_gbs, peak=peaks["hbm_gbs"],
-                                      unit="GB/s", frac=proj_gbs / peaks["hbm_gbs"], traffic=None,
+                                      unit="GB/s", frac=proj_gbs / peaks["hbm_gbs"],
+                                      traffic=project_traffic(proj_bytes / n),
                                       bytes_per_gaussian=dict(visible=PROJECT_BYTES_VISIBLE,
                                                               culled=PROJECT_BYTES_CULLED),
                                       gaussians=m.n, bytes_per_launch=round(proj_bytes / n), peak_source=kind))
