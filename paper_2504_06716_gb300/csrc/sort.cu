@@ -646,19 +646,21 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
     __shared__ uint32_t hit_mask[2 * kChunk];  // per entry, low and high halves
     __shared__ float4 shape[2 * kChunk];
     __shared__ uint32_t rect[kChunk];
-    __shared__ uint32_t cnt[64];
+    __shared__ uint32_t cnt[kChunk / 32][64];  // per warp and slot: the warp's entries that the slot's tile lists
     const TestScratch sc{hit_mask, shape, rect};
     const uint32_t nc = chunk_base[ns];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
         chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, sc, nullptr, masks);
-        if (threadIdx.x < 64) cnt[threadIdx.x] = 0u;
-        __syncthreads();
-        for (unsigned long long m = cx.mask; m; m &= m - 1ull) atomicAdd(&cnt[__ffsll((long long)m) - 1], 1u);
+        cnt[warp][lane] = (uint32_t)__popc(warp_transpose32((uint32_t)cx.mask, lane));
+        cnt[warp][lane + 32] = (uint32_t)__popc(warp_transpose32((uint32_t)(cx.mask >> 32), lane));
         __syncthreads();
         if (threadIdx.x < 64) {
             const int t = threadIdx.x;
-            const uint32_t n = cnt[t];
+            uint32_t n = 0u;
+#pragma unroll
+            for (int w = 0; w < kChunk / 32; ++w) n += cnt[w][t];
             counts[(int64_t)c * 64 + t] = n;
             if (n) atomicAdd(tile_count + slot_tile(t, cx.sx, cx.sy, cam.tiles_x), n);
         }
