@@ -71,17 +71,25 @@ __device__ __forceinline__ bool splat_visible(const float *splats, int64_t i) {
 }
 
 // ---- stage 1a: compaction of visible Gaussians ----
+// Also zeroes the sort's counters: `zero` [nzero] words and *total_exact.
 __global__ void __launch_bounds__(kScanBlock) k_count_visible(const float *__restrict__ splats, int64_t n,
-                                                             uint32_t *__restrict__ part) {
+                                                             uint32_t *__restrict__ part, uint32_t *__restrict__ zero,
+                                                             int64_t nzero,
+                                                             unsigned long long *__restrict__ total_exact) {
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    for (int64_t z = i; z < nzero; z += (int64_t)gridDim.x * kScanBlock) zero[z] = 0u;
+    if (i == 0) *total_exact = 0ull;
     int f = (i < n) && splat_visible(splats, i);
     int c = __syncthreads_count(f);
     if (threadIdx.x == 0) part[blockIdx.x] = (uint32_t)c;
 }
 
-// Exclusive scan of part[0..nb) in place by one block; total to *total.
+// Exclusive scan of part[0..nb) in place by one block; total to *total. With
+// clip given: *clip = min(total, capacity), and the capacity flag if the
+// total exceeds it (the super-tile entries kept).
 template <typename T>
-__global__ void __launch_bounds__(1024) k_scan_parts(T *__restrict__ part, int nb, T *__restrict__ total) {
+__global__ void __launch_bounds__(1024) k_scan_parts(T *__restrict__ part, int nb, T *__restrict__ total,
+                                                     uint32_t *__restrict__ clip, int64_t capacity) {
     __shared__ T ws[32];
     T carry = 0;
     for (int base = 0; base < nb; base += 1024) {
@@ -91,7 +99,14 @@ __global__ void __launch_bounds__(1024) k_scan_parts(T *__restrict__ part, int n
         if (j < nb) part[j] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0) *total = carry;
+    if (threadIdx.x == 0) {
+        *total = carry;
+        if (clip) {
+            const unsigned long long Q = (unsigned long long)carry;
+            *clip = (uint32_t)(Q > (unsigned long long)capacity ? capacity : Q);
+            if (Q > (unsigned long long)capacity) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_emit_visible(const float *__restrict__ splats, int64_t n,
@@ -157,12 +172,22 @@ __global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t *__restrict__ h
     if (threadIdx.x == 0) digit_total[blockIdx.x] = carry;
 }
 
+// Where a one-pass sort by super-tile id leaves each super-tile's entries:
+// its digit's range of the output. Given (seg_lo non-null), block 0 of the
+// pass writes seg_lo / seg_hi [ns] and the chunk plan -- chunk_base [ns + 1]
+// (exclusive scan of ceil(len / chunk)) and chunk_super (the super-tile of
+// every chunk) -- from the digit totals.
+struct SegPlan {
+    uint32_t *seg_lo, *seg_hi, *chunk_base, *chunk_super;
+    int ns, chunk;
+};
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *__restrict__ kin,
                                                                const uint32_t *__restrict__ vin,
                                                                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                                const uint32_t *__restrict__ count, int shift, int bits,
                                                                const uint32_t *__restrict__ hist,
-                                                               const uint32_t *__restrict__ digit_total) {
+                                                               const uint32_t *__restrict__ digit_total, SegPlan sp) {
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPer = kMaxRadix / kSortThreads;  // buckets per thread (consecutive)
     __shared__ uint32_t run[kMaxRadix];
@@ -170,7 +195,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     __shared__ uint32_t ws[32];
     const uint32_t n = *count;
     const int nbd = radix_blocks(count);
-    if ((int)blockIdx.x >= nbd) return;
+    const bool plan = sp.seg_lo && blockIdx.x == 0;
+    if ((int)blockIdx.x >= nbd && !plan) return;
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
     const int t = threadIdx.x, warp = t >> 5;
@@ -186,6 +212,29 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     dbase[0] = block_scan_excl<uint32_t>(own, ws, &tot);
 #pragma unroll
     for (int q = 1; q < kPer; ++q) dbase[q] = dbase[q - 1] + dtot[q - 1];
+    if (plan) {  // block-uniform
+        uint32_t nc[kPer], ncown = 0u, nctot;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int d = kPer * t + q;
+            nc[q] = d < sp.ns ? (dtot[q] + (uint32_t)sp.chunk - 1u) / (uint32_t)sp.chunk : 0u;
+            ncown += nc[q];
+        }
+        uint32_t cb = block_scan_excl<uint32_t>(ncown, ws, &nctot);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int d = kPer * t + q;
+            if (d < sp.ns) {
+                sp.seg_lo[d] = dbase[q];
+                sp.seg_hi[d] = dbase[q] + dtot[q];
+                sp.chunk_base[d] = cb;
+                for (uint32_t c = 0; c < nc[q]; ++c) sp.chunk_super[cb + c] = (uint32_t)d;
+            }
+            cb += nc[q];
+        }
+        if (t == 0) sp.chunk_base[sp.ns] = nctot;
+        if ((int)blockIdx.x >= nbd) return;
+    }
     for (int b = blockIdx.x; b < nbd; b += gridDim.x) {
         const int64_t base = (int64_t)b * kSortBlock;
 #pragma unroll
@@ -409,16 +458,26 @@ __global__ void __launch_bounds__(kScanBlock) k_count_entries(const float *__res
     if (threadIdx.x == 0) part_s[blockIdx.x] = tot;
 }
 
-// sclip = super-tile entries kept; the flag if they alone exceed the capacity.
-__global__ void k_finish_super(const unsigned long long *__restrict__ total_s, int64_t capacity,
-                               uint32_t *__restrict__ sclip) {
-    const unsigned long long Q = *total_s;
-    *sclip = (uint32_t)(Q > (unsigned long long)capacity ? capacity : Q);
-    if (Q > (unsigned long long)capacity) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
-}
-
 // Only when the super-tile entries alone overflowed the capacity (then the
 // tile counts miss the dropped ones): P counted splat by splat, tile by tile.
+// The tiles that list splat g, counted one by one.
+__device__ __forceinline__ unsigned long long exact_tiles(const float *splats, uint32_t g, const DevCam &cam) {
+    int x0, y0, x1, y1;
+    const SplatShape sh = splat_shape(splats, g);
+    if (sh.tau < 0.f || !cand_rect(splats, g, cam, sh.tau, x0, y0, x1, y1)) return 0ull;
+    unsigned long long m = 0ull;
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) m += tile_hit(sh, cam.tile, x, y) ? 1ull : 0ull;
+    return m;
+}
+
+// A warp's sum of v added to *total (every lane of the warp calls it).
+__device__ __forceinline__ void warp_add_total(unsigned long long v, unsigned long long *total) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
 __global__ void __launch_bounds__(256) k_count_exact(const float *__restrict__ splats,
                                                     const uint32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ n_vis, DevCam cam,
@@ -427,17 +486,9 @@ __global__ void __launch_bounds__(256) k_count_exact(const float *__restrict__ s
     if (*total_s <= (unsigned long long)capacity) return;
     unsigned long long mine = 0ull;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < *n_vis;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t g = order[k];
-        int x0, y0, x1, y1;
-        const SplatShape sh = splat_shape(splats, g);
-        if (sh.tau < 0.f || !cand_rect(splats, g, cam, sh.tau, x0, y0, x1, y1)) continue;
-        for (int y = y0; y < y1; ++y)
-            for (int x = x0; x < x1; ++x) mine += tile_hit(sh, cam.tile, x, y) ? 1ull : 0ull;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(kFull, mine, o);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(total_exact, mine);
+         k += (int64_t)gridDim.x * blockDim.x)
+        mine += exact_tiles(splats, order[k], cam);
+    warp_add_total(mine, total_exact);
 }
 
 // count_dev = P, the number of entries: the sum of the tile counts, or the
@@ -455,8 +506,10 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restri
                                                           const uint32_t *__restrict__ order,
                                                           const uint32_t *__restrict__ n_vis, DevCam cam,
                                                           int supers_x, const unsigned long long *__restrict__ part_s,
+                                                          const unsigned long long *__restrict__ total_s,
                                                           int64_t capacity, uint32_t *__restrict__ skeys,
-                                                          uint32_t *__restrict__ svals) {
+                                                          uint32_t *__restrict__ svals,
+                                                          unsigned long long *__restrict__ total_exact) {
     __shared__ unsigned long long ws[32];
     int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     int sx0 = 0, sy0 = 0, sx1 = 0, sy1 = 0;
@@ -468,6 +521,8 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restri
     }
     unsigned long long tot;
     unsigned long long off = part_s[blockIdx.x] + block_scan_excl<unsigned long long>(c, ws, &tot);
+    if (*total_s > (unsigned long long)capacity)  // the super-tile entries overflowed: P counted tile by tile
+        warp_add_total(c ? exact_tiles(splats, g, cam) : 0ull, total_exact);
     if (c == 0) return;
     for (int y = sy0; y < sy1; ++y)
         for (int x = sx0; x < sx1; ++x) {
@@ -667,33 +722,33 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
     }
 }
 
-// Tile starts (exclusive scan of the tile counts over tile ids) and the
-// ranges, clipped to the capacity: per-block sums, a scan of those, then each
-// block scans its own tiles from its offset.
-__global__ void __launch_bounds__(kScanBlock) k_tile_sums(const uint32_t *__restrict__ tile_count, int64_t tiles,
-                                                         unsigned long long *__restrict__ part) {
+// Tile starts (exclusive scan of the tile counts over tile ids), the ranges
+// clipped to the capacity, and count_dev (as k_finish_count): one block,
+// each thread over a run of consecutive tiles.
+__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *__restrict__ tile_count, int64_t tiles,
+                                                    int64_t capacity, const unsigned long long *__restrict__ total_s,
+                                                    const unsigned long long *__restrict__ total_exact,
+                                                    unsigned long long *__restrict__ tile_start,
+                                                    uint32_t *__restrict__ ranges, int64_t *__restrict__ count_dev) {
     __shared__ unsigned long long ws[32];
-    const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    unsigned long long tot;
-    block_scan_excl<unsigned long long>(j < tiles ? tile_count[j] : 0ull, ws, &tot);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanBlock) k_tile_starts(const uint32_t *__restrict__ tile_count, int64_t tiles,
-                                                           const unsigned long long *__restrict__ part,
-                                                           int64_t capacity, unsigned long long *__restrict__ tile_start,
-                                                           uint32_t *__restrict__ ranges) {
-    __shared__ unsigned long long ws[32];
-    const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    const unsigned long long n = j < tiles ? tile_count[j] : 0ull;
-    unsigned long long tot;
-    const unsigned long long st = part[blockIdx.x] + block_scan_excl<unsigned long long>(n, ws, &tot);
-    if (j < tiles) {
-        const unsigned long long cap = (unsigned long long)capacity, en = st + n;
+    const int64_t per = (tiles + 1023) / 1024;
+    const int64_t j0 = (int64_t)threadIdx.x * per, j1 = j0 + per < tiles ? j0 + per : tiles;
+    unsigned long long sum = 0ull, total;
+    for (int64_t j = j0; j < j1; ++j) sum += tile_count[j];
+    unsigned long long st = block_scan_excl<unsigned long long>(sum, ws, &total);
+    const unsigned long long cap = (unsigned long long)capacity;
+    for (int64_t j = j0; j < j1; ++j) {
+        const unsigned long long n = tile_count[j], en = st + n;
         tile_start[j] = st;
         // an empty tile has the range (0, 0)
         ranges[2 * j] = n ? (uint32_t)(st < cap ? st : cap) : 0u;
         ranges[2 * j + 1] = n ? (uint32_t)(en < cap ? en : cap) : 0u;
+        st = en;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long P = *total_s > cap ? *total_exact : total;
+        *count_dev = (int64_t)P;
+        if (P > cap) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
     }
 }
 
@@ -774,7 +829,6 @@ struct SortWs {
     unsigned long long *tile_start;            // [tiles]
     uint32_t *chunk_counts;                    // [max chunks][64]
     uint32_t *chunk_super;                     // [max chunks]
-    unsigned long long *tile_part;             // [tile blocks]
     size_t bytes;
 };
 
@@ -815,7 +869,6 @@ inline SortWs sort_layout(char *base, int64_t n, int64_t cap, int64_t tiles, int
     w.tile_count = w.seg_lo ? w.seg_lo + 2 * ns : nullptr;
     w.chunk_base = (uint32_t *)take(4 * (size_t)(ns + 1));
     w.chunk_super = (uint32_t *)take(4 * (size_t)max_chunks(cap, ns));
-    w.tile_part = (unsigned long long *)take(8 * (size_t)((tiles + kScanBlock - 1) / kScanBlock));
     w.tile_start = (unsigned long long *)take(8 * (size_t)tiles);
     w.chunk_counts = (uint32_t *)take(4 * 64 * (size_t)max_chunks(cap, ns));
     w.bytes = off;
@@ -838,10 +891,10 @@ inline SuperGrid super_grid(int32_t width, int32_t height, int32_t tile) {
 }
 
 // One full LSD sort of (keys, vals) over *count (bounded by `bound`) on `bits`
-// low bits; buffers ping-pong between index `in` and 1 - in. Returns the
-// index holding the result.
+// low bits; buffers ping-pong between index `in` and 1 - in. The last pass
+// writes the segment plan sp (if given). Returns the index holding the result.
 int radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], int in, const uint32_t *count, int64_t bound,
-               int total_bits, const SortWs &w, cudaStream_t s) {
+               int total_bits, const SortWs &w, cudaStream_t s, SegPlan sp = SegPlan{}) {
     if (total_bits <= 0) return in;
     // 8-bit digits, or one pass of up to kMaxRadixBits when that suffices
     int npass = total_bits <= kMaxRadixBits ? 1 : (total_bits + 7) / 8;
@@ -854,7 +907,8 @@ int radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], int in, const u
         k_radix_hist<<<grid, kSortThreads, 0, s>>>(keys[in], count, shift, bits, w.hist);
         k_radix_rowscan<<<1 << bits, 1024, 0, s>>>(w.hist, count, w.digit_total);
         k_radix_scatter<<<grid, kSortThreads, 0, s>>>(keys[in], vals[in], keys[1 - in], vals[1 - in], count, shift,
-                                                      bits, w.hist, w.digit_total);
+                                                      bits, w.hist, w.digit_total,
+                                                      p == npass - 1 ? sp : SegPlan{});
         note_launches(3);
         in = 1 - in;
         shift += bits;
@@ -909,26 +963,23 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
             return launch_status();
         }
     }
-    k_zero_u32<<<grid_for(2 * sg.ns + tiles, 256), 256, 0, s>>>(w.seg_lo, 2 * sg.ns + tiles);
-    note_launches(1);
-    // stage 1: visible Gaussians by depth
-    k_count_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32);
-    k_scan_parts<uint32_t><<<1, 1024, 0, s>>>(w.part32, nbS, w.n_vis);
+    // stage 1: visible Gaussians by depth (the first kernel also zeroes the
+    // segment bounds, tile counts and exact count)
+    k_count_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, w.seg_lo, 2 * sg.ns + tiles, w.total_exact);
+    k_scan_parts<uint32_t><<<1, 1024, 0, s>>>(w.part32, nbS, w.n_vis, nullptr, 0);
     k_emit_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, w.keys[0], w.vals[0]);
     note_launches(3);
     int cur = radix_sort(w.keys, w.vals, 0, w.n_vis, n, 32, w, s);
     // stage 2: super-tile entries in depth order, stable-sorted by super-tile
     k_count_entries<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.part_s);
-    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.part_s, nbS, w.total_s);
-    k_finish_super<<<1, 1, 0, s>>>(w.total_s, capacity, w.sclip);
-    cudaMemsetAsync(w.total_exact, 0, sizeof(unsigned long long), s);
-    k_count_exact<<<(unsigned)resident_blocks(), 256, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.total_s, capacity,
-                                                              w.total_exact);
-    note_launches(4);
+    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.part_s, nbS, w.total_s, w.sclip, capacity);
+    note_launches(2);
     if (capacity == 0) {
         cudaMemsetAsync(w.total_t, 0, sizeof(unsigned long long), s);
+        k_count_exact<<<(unsigned)resident_blocks(), 256, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.total_s,
+                                                                  capacity, w.total_exact);
         k_finish_count<<<1, 1, 0, s>>>(w.total_t, w.total_s, w.total_exact, capacity, count_dev);
-        note_launches(1);
+        note_launches(2);
         return launch_status();
     }
     const int sbits = ceil_log2(sg.ns);
@@ -936,25 +987,26 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     uint32_t *sk[2] = {w.skeys[0], w.skeys[1]};
     uint32_t *sv[2] = {w.svals1, vals};  // the sorted list must end in svals1: vals is written from it
     const int start = npass % 2;
-    k_emit_super<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s, capacity,
-                                            sk[start], sv[start]);
+    k_emit_super<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s, w.total_s,
+                                            capacity, sk[start], sv[start], w.total_exact);
     note_launches(1);
-    radix_sort(sk, sv, start, w.sclip, capacity, sbits, w, s);  // ends in skeys[0] / svals1
+    // one pass: its digit ranges are the segments, written by the pass itself
+    const SegPlan sp{w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns, kChunk};
+    radix_sort(sk, sv, start, w.sclip, capacity, sbits, w, s, npass == 1 ? sp : SegPlan{});  // ends in skeys[0] / svals1
     // stage 3: per-tile lists
     const int64_t chunks = max_chunks(capacity, sg.ns), resident = resident_blocks();
     const unsigned cgrid = (unsigned)(chunks < resident ? chunks : resident);
-    k_seg_mark<<<(unsigned)resident, 256, 0, s>>>(w.skeys[0], w.sclip, w.seg_lo, w.seg_hi);
-    k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_super);
+    if (npass != 1) {
+        k_seg_mark<<<(unsigned)resident, 256, 0, s>>>(w.skeys[0], w.sclip, w.seg_lo, w.seg_hi);
+        k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_super);
+        note_launches(2);
+    }
     k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
                                             sg.supers_x, dc, w.chunk_counts, w.tile_count, w.masks);
-    const int tb = (int)((tiles + kScanBlock - 1) / kScanBlock);
-    k_tile_sums<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part);
-    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.tile_part, tb, w.total_t);
-    k_finish_count<<<1, 1, 0, s>>>(w.total_t, w.total_s, w.total_exact, capacity, count_dev);
-    k_tile_starts<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part, capacity, w.tile_start, ranges);
+    k_tile_scan<<<1, 1024, 0, s>>>(w.tile_count, tiles, capacity, w.total_s, w.total_exact, w.tile_start, ranges,
+                                   count_dev);
     k_expand<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
                                       sg.supers_x, dc, w.chunk_counts, w.tile_start, capacity, w.masks, vals);
     note_launches(3);
-    note_launches(5);
     return launch_status();
 }

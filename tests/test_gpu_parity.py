@@ -266,6 +266,57 @@ def test_sort_capacity_overflow_is_flagged_and_clipped():
     assert lib.gs_get_device_error() == 0
 
 
+def _random_records(n, W, H, tile, seed):
+    """Isotropic splats scattered over a W x H image, radii 1-40 px, random
+    depths; the tile count field is the 3-sigma rectangle's (the projection's)."""
+    g = np.random.default_rng(seed)
+    rec = np.zeros((n, 12), np.float32)
+    rec[:, 0] = g.uniform(-20, W + 20, n)
+    rec[:, 1] = g.uniform(-20, H + 20, n)
+    rec[:, 9] = g.uniform(0.5, 30.0, n)
+    rad = g.integers(1, 40, n).astype(np.int32)
+    rec[:, 10] = rad.view(np.float32)
+    sig = rad.astype(np.float32) / 3.0
+    rec[:, 2] = rec[:, 4] = 1.0 / (sig * sig)
+    rec[:, 5] = g.uniform(0.02, 0.99, n)
+    tx, ty = (W + tile - 1) // tile, (H + tile - 1) // tile
+    x0 = np.clip(np.floor((rec[:, 0] - rad) / tile), 0, None)
+    x1 = np.clip(np.floor((rec[:, 0] + rad) / tile), None, tx - 1)
+    y0 = np.clip(np.floor((rec[:, 1] - rad) / tile), 0, None)
+    y1 = np.clip(np.floor((rec[:, 1] + rad) / tile), None, ty - 1)
+    rect = np.where((x0 <= x1) & (y0 <= y1), (x1 - x0 + 1) * (y1 - y0 + 1), 0).astype(np.int32)
+    rec[:, 11] = rect.view(np.float32)
+    return rec
+
+
+@pytest.mark.parametrize("W,H,tile", [(1600, 1400, 8), (1024, 1024, 8), (120, 90, 8)])
+def test_sort_super_tile_grids(W, H, tile):
+    """Grids of 550 super-tiles (two radix passes by super-tile id), 256 (one
+    pass, its digit ranges taken as the segments) and 4."""
+    rec = _random_records(12000 if W > 500 else 1500, W, H, tile, seed=W)
+    ocam, gcam = pu.cameras(synth.pinhole(W, H, 60.0, (0, -3, 0.5)), tile=tile)
+    want_vals, want_ranges = _oracle_sort(rec, ocam)
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam)
+    assert flags == 0
+    assert len(want_vals) > 0
+    _check(vals, ranges, Pn, want_vals, want_ranges, rec, gcam)
+
+
+@pytest.mark.parametrize("cap", [0, 5])
+def test_sort_capacity_below_the_super_tile_entries(cap):
+    """A capacity smaller than the super-tile entries themselves: the entry
+    count is then taken tile by tile and must equal the full sort's."""
+    rec = _random_records(3000, 320, 200, 8, seed=3)
+    _, gcam = pu.cameras(synth.pinhole(320, 200, 60.0, (0, -3, 0.5)), tile=8)
+    _, _, P_full, flags_full, _ = _gpu_sort(rec, gcam)
+    assert flags_full == 0 and P_full > 100
+    vals, ranges, Pn, flags, _ = _gpu_sort(rec, gcam, capacity=cap)
+    assert flags & lib.GS_FLAG_CAPACITY
+    assert Pn == P_full
+    assert ranges.max() <= cap
+    assert lib.gs_get_device_error() == 0
+
+
 # ----------------------------------------------------------------------------- A3 render forward
 
 
