@@ -109,21 +109,6 @@ __global__ void __launch_bounds__(1024) k_scan_parts(T *__restrict__ part, int n
     }
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_emit_visible(const float *__restrict__ splats, int64_t n,
-                                                            const uint32_t *__restrict__ part,
-                                                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    __shared__ int ws[32];
-    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    int f = (i < n) && splat_visible(splats, i);
-    int tot;
-    int r = block_scan_excl<int>(f, ws, &tot);
-    if (f) {
-        uint32_t pos = part[blockIdx.x] + (uint32_t)r;
-        keys[pos] = __float_as_uint(__ldg(splats + i * kSplat + 9));
-        vals[pos] = (uint32_t)i;
-    }
-}
-
 // ---- LSD radix pass: histogram, per-digit row scan, stable scatter ----
 // The number of keys lives on the device; the three kernels derive the same
 // block count nbd from it and loop over those blocks with whatever grid the
@@ -434,25 +419,66 @@ __device__ __forceinline__ int cand_rect(const float *splats, uint32_t g, const 
     return 1;
 }
 
+// The tile tests' constants and the candidate rectangle of a visible
+// Gaussian, computed once per sort (k_emit_visible) and read by the
+// depth-ordered passes and the chunk kernels: cull[2 g] = (tau, b / c, b / a,
+// 0), cull[2 g + 1] = (x0 | y0 << 16, x1 | y1 << 16, 0, 0) as integers, the
+// empty rectangle when no tile can list the splat (255 o < 1).
+__device__ __forceinline__ void write_cull(const float *splats, uint32_t g, const DevCam &cam, float4 *cull) {
+    const SplatShape sh = splat_shape(splats, g);
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (!(sh.tau >= 0.f) || !cand_rect(splats, g, cam, sh.tau, x0, y0, x1, y1)) x0 = y0 = x1 = y1 = 0;
+    cull[2 * (int64_t)g] = make_float4(sh.tau, sh.bc, sh.ba, 0.f);
+    reinterpret_cast<uint4 *>(cull)[2 * (int64_t)g + 1] =
+        make_uint4((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16), 0u, 0u);
+}
+
+// Tile coordinates are below 2^16 (images of at most 16384 pixels a side).
+__device__ __forceinline__ bool cull_rect(const float4 *cull, uint32_t g, int &x0, int &y0, int &x1, int &y1) {
+    const uint4 r = __ldg(reinterpret_cast<const uint4 *>(cull) + 2 * (int64_t)g + 1);
+    x0 = (int)(r.x & 0xffffu);
+    y0 = (int)(r.x >> 16);
+    x1 = (int)(r.y & 0xffffu);
+    y1 = (int)(r.y >> 16);
+    return x0 < x1 && y0 < y1;
+}
+
+// The depth keys and indices of the visible Gaussians, ascending index, and
+// their cull records.
+__global__ void __launch_bounds__(kScanBlock) k_emit_visible(const float *__restrict__ splats, int64_t n,
+                                                            const uint32_t *__restrict__ part, DevCam cam,
+                                                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                            float4 *__restrict__ cull) {
+    __shared__ int ws[32];
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int f = (i < n) && splat_visible(splats, i);
+    int tot;
+    int r = block_scan_excl<int>(f, ws, &tot);
+    if (f) {
+        uint32_t pos = part[blockIdx.x] + (uint32_t)r;
+        keys[pos] = __float_as_uint(__ldg(splats + i * kSplat + 9));
+        vals[pos] = (uint32_t)i;
+        write_cull(splats, (uint32_t)i, cam, cull);
+    }
+}
+
 // Per block of depth-ordered Gaussians: its super-tile entries (part_s).
 // Only splats some tile can list (255 o >= 1) get entries.
-__device__ __forceinline__ unsigned long long super_entries(const float *splats, uint32_t g, const DevCam &cam,
-                                                            int &sx0, int &sy0, int &sx1, int &sy1) {
+__device__ __forceinline__ unsigned long long super_entries(const float4 *cull, uint32_t g, int &sx0, int &sy0,
+                                                            int &sx1, int &sy1) {
     int x0, y0, x1, y1;
-    const float tau = tile_tau(__ldg(splats + (int64_t)g * kSplat + 5));
-    if (!(tau >= 0.f)) return 0ull;
-    if (!cand_rect(splats, g, cam, tau, x0, y0, x1, y1)) return 0ull;
+    if (!cull_rect(cull, g, x0, y0, x1, y1)) return 0ull;
     return (unsigned long long)super_rect(x0, y0, x1, y1, sx0, sy0, sx1, sy1);
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_count_entries(const float *__restrict__ splats,
+__global__ void __launch_bounds__(kScanBlock) k_count_entries(const float4 *__restrict__ cull,
                                                              const uint32_t *__restrict__ order,
-                                                             const uint32_t *__restrict__ n_vis, DevCam cam,
+                                                             const uint32_t *__restrict__ n_vis,
                                                              unsigned long long *__restrict__ part_s) {
     __shared__ unsigned long long ws[32];
     int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     int sx0, sy0, sx1, sy1;
-    const unsigned long long cs = k < *n_vis ? super_entries(splats, order[k], cam, sx0, sy0, sx1, sy1) : 0ull;
+    const unsigned long long cs = k < *n_vis ? super_entries(cull, order[k], sx0, sy0, sx1, sy1) : 0ull;
     unsigned long long tot;
     block_scan_excl<unsigned long long>(cs, ws, &tot);
     if (threadIdx.x == 0) part_s[blockIdx.x] = tot;
@@ -503,6 +529,7 @@ __global__ void k_finish_count(const unsigned long long *__restrict__ total_t,
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restrict__ splats,
+                                                          const float4 *__restrict__ cull,
                                                           const uint32_t *__restrict__ order,
                                                           const uint32_t *__restrict__ n_vis, DevCam cam,
                                                           int supers_x, const unsigned long long *__restrict__ part_s,
@@ -517,7 +544,7 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restri
     unsigned long long c = 0ull;
     if (k < *n_vis) {
         g = order[k];
-        c = super_entries(splats, g, cam, sx0, sy0, sx1, sy1);
+        c = super_entries(cull, g, sx0, sy0, sx1, sy1);
     }
     unsigned long long tot;
     unsigned long long off = part_s[blockIdx.x] + block_scan_excl<unsigned long long>(c, ws, &tot);
@@ -588,6 +615,7 @@ struct TestScratch {
 // With masks_in NULL the masks are computed by the tile test (and stored to
 // masks_out when given); else they are read.
 __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float *__restrict__ splats,
+                                           const float4 *__restrict__ cull,
                                            const uint32_t *__restrict__ svals, const uint32_t *__restrict__ seg_lo,
                                            const uint32_t *__restrict__ seg_hi,
                                            const uint32_t *__restrict__ chunk_base,
@@ -613,12 +641,19 @@ __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float
     int lx0 = 0, ly0 = 0, w = 0, h = 0;
     SplatShape sh{};
     int x0, y0, x1, y1;
-    if (valid) sh = splat_shape(splats, cx.g);
-    if (valid && sh.tau >= 0.f && cand_rect(splats, cx.g, cam, sh.tau, x0, y0, x1, y1)) {
-        lx0 = max(x0 - cx.sx * kSuper, 0);
-        ly0 = max(y0 - cx.sy * kSuper, 0);
-        w = max(min(x1 - cx.sx * kSuper, kSuper) - lx0, 0);
-        h = max(min(y1 - cx.sy * kSuper, kSuper) - ly0, 0);
+    if (valid) {  // every listed entry's splat has tau >= 0 and a candidate rectangle
+        const float *r = splats + (int64_t)cx.g * kSplat;
+        const float4 p0 = __ldg(reinterpret_cast<const float4 *>(r));
+        const float4 c0 = __ldg(cull + 2 * (int64_t)cx.g);
+        sh.mx = p0.x; sh.my = p0.y; sh.a = p0.z; sh.b = p0.w;
+        sh.c = __ldg(r + 4);
+        sh.tau = c0.x; sh.bc = c0.y; sh.ba = c0.z;
+        if (cull_rect(cull, cx.g, x0, y0, x1, y1)) {
+            lx0 = max(x0 - cx.sx * kSuper, 0);
+            ly0 = max(y0 - cx.sy * kSuper, 0);
+            w = max(min(x1 - cx.sx * kSuper, kSuper) - lx0, 0);
+            h = max(min(y1 - cx.sy * kSuper, kSuper) - ly0, 0);
+        }
     }
     const int cnt = w * h;
     sc.shape[2 * threadIdx.x] = make_float4(sh.mx, sh.my, sh.a, sh.b);
@@ -690,6 +725,7 @@ __device__ __forceinline__ int slot_tile(int t, int sx, int sy, int tiles_x) {
 }
 
 __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict__ splats,
+                                                        const float4 *__restrict__ cull,
                                                         const uint32_t *__restrict__ svals,
                                                         const uint32_t *__restrict__ seg_lo,
                                                         const uint32_t *__restrict__ seg_hi,
@@ -707,7 +743,8 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
-        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, sc, nullptr, masks);
+        chunk_load(cx, c, splats, cull, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, sc, nullptr,
+                   masks);
         cnt[warp][lane] = (uint32_t)__popc(warp_transpose32((uint32_t)cx.mask, lane));
         cnt[warp][lane + 32] = (uint32_t)__popc(warp_transpose32((uint32_t)(cx.mask >> 32), lane));
         __syncthreads();
@@ -770,8 +807,8 @@ __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ spl
     const unsigned lt = lanemask_lt();
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
-        chunk_load(cx, c, splats, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, TestScratch{}, masks,
-                   nullptr);
+        chunk_load(cx, c, splats, nullptr, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, TestScratch{},
+                   masks, nullptr);
         const uint32_t lo = (uint32_t)cx.mask, hi = (uint32_t)(cx.mask >> 32);
         ballots[warp][lane] = warp_transpose32(lo, lane);
         ballots[warp][lane + 32] = warp_transpose32(hi, lane);
@@ -823,6 +860,7 @@ struct SortWs {
     uint32_t *hist, *digit_total, *part32;
     unsigned long long *part_s, *total_s, *total_t, *total_exact;
     unsigned long long *masks;                 // [capacity] tile mask of each super-tile entry
+    float4 *cull;                              // [2 n] cull record of each visible Gaussian
     uint32_t *n_vis, *sclip;
     uint32_t *seg_lo, *seg_hi, *chunk_base;    // [ns], [ns], [ns + 1]
     uint32_t *tile_count;                      // [tiles]
@@ -861,6 +899,7 @@ inline SortWs sort_layout(char *base, int64_t n, int64_t cap, int64_t tiles, int
     w.total_t = (unsigned long long *)take(8);
     w.total_exact = (unsigned long long *)take(8);
     w.masks = (unsigned long long *)take(8 * (size_t)cap);
+    w.cull = (float4 *)take(32 * (size_t)n);
     w.n_vis = (uint32_t *)take(4);
     w.sclip = (uint32_t *)take(4);
     // zeroed together before each sort: segment bounds, then tile counts
@@ -967,11 +1006,11 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     // segment bounds, tile counts and exact count)
     k_count_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, w.seg_lo, 2 * sg.ns + tiles, w.total_exact);
     k_scan_parts<uint32_t><<<1, 1024, 0, s>>>(w.part32, nbS, w.n_vis, nullptr, 0);
-    k_emit_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, w.keys[0], w.vals[0]);
+    k_emit_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, dc, w.keys[0], w.vals[0], w.cull);
     note_launches(3);
     int cur = radix_sort(w.keys, w.vals, 0, w.n_vis, n, 32, w, s);
     // stage 2: super-tile entries in depth order, stable-sorted by super-tile
-    k_count_entries<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.part_s);
+    k_count_entries<<<nbS, kScanBlock, 0, s>>>(w.cull, w.vals[cur], w.n_vis, w.part_s);
     k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.part_s, nbS, w.total_s, w.sclip, capacity);
     note_launches(2);
     if (capacity == 0) {
@@ -987,7 +1026,7 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     uint32_t *sk[2] = {w.skeys[0], w.skeys[1]};
     uint32_t *sv[2] = {w.svals1, vals};  // the sorted list must end in svals1: vals is written from it
     const int start = npass % 2;
-    k_emit_super<<<nbS, kScanBlock, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s, w.total_s,
+    k_emit_super<<<nbS, kScanBlock, 0, s>>>(splats, w.cull, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s, w.total_s,
                                             capacity, sk[start], sv[start], w.total_exact);
     note_launches(1);
     // one pass: its digit ranges are the segments, written by the pass itself
@@ -1001,7 +1040,7 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
         k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_super);
         note_launches(2);
     }
-    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
+    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.cull, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
                                             sg.supers_x, dc, w.chunk_counts, w.tile_count, w.masks);
     k_tile_scan<<<1, 1024, 0, s>>>(w.tile_count, tiles, capacity, w.total_s, w.total_exact, w.tile_start, ranges,
                                    count_dev);
