@@ -759,31 +759,44 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
     }
 }
 
-// Tile starts (exclusive scan of the tile counts over tile ids), the ranges
-// clipped to the capacity, and count_dev (as k_finish_count): one block,
-// each thread over a run of consecutive tiles.
-__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t *__restrict__ tile_count, int64_t tiles,
-                                                    int64_t capacity, const unsigned long long *__restrict__ total_s,
-                                                    const unsigned long long *__restrict__ total_exact,
-                                                    unsigned long long *__restrict__ tile_start,
-                                                    uint32_t *__restrict__ ranges, int64_t *__restrict__ count_dev) {
+// Tile starts (exclusive scan of the tile counts over tile ids) and the
+// ranges, clipped to the capacity: per-block sums, a scan of those, then each
+// block scans its own tiles from its offset; block 0 of the last step also
+// sets count_dev = P, the sum of the tile counts, or the exact count when the
+// super-tile entries overflowed (and the capacity flag if P exceeds it).
+__global__ void __launch_bounds__(kScanBlock) k_tile_sums(const uint32_t *__restrict__ tile_count, int64_t tiles,
+                                                         unsigned long long *__restrict__ part) {
     __shared__ unsigned long long ws[32];
-    const int64_t per = (tiles + 1023) / 1024;
-    const int64_t j0 = (int64_t)threadIdx.x * per, j1 = j0 + per < tiles ? j0 + per : tiles;
-    unsigned long long sum = 0ull, total;
-    for (int64_t j = j0; j < j1; ++j) sum += tile_count[j];
-    unsigned long long st = block_scan_excl<unsigned long long>(sum, ws, &total);
+    const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    unsigned long long tot;
+    block_scan_excl<unsigned long long>(j < tiles ? tile_count[j] : 0ull, ws, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_tile_starts(const uint32_t *__restrict__ tile_count, int64_t tiles,
+                                                           const unsigned long long *__restrict__ part,
+                                                           int64_t capacity,
+                                                           const unsigned long long *__restrict__ total_t,
+                                                           const unsigned long long *__restrict__ total_s,
+                                                           const unsigned long long *__restrict__ total_exact,
+                                                           unsigned long long *__restrict__ tile_start,
+                                                           uint32_t *__restrict__ ranges,
+                                                           int64_t *__restrict__ count_dev) {
+    __shared__ unsigned long long ws[32];
+    const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    const unsigned long long n = j < tiles ? tile_count[j] : 0ull;
+    unsigned long long tot;
+    const unsigned long long st = part[blockIdx.x] + block_scan_excl<unsigned long long>(n, ws, &tot);
     const unsigned long long cap = (unsigned long long)capacity;
-    for (int64_t j = j0; j < j1; ++j) {
-        const unsigned long long n = tile_count[j], en = st + n;
+    if (j < tiles) {
+        const unsigned long long en = st + n;
         tile_start[j] = st;
         // an empty tile has the range (0, 0)
         ranges[2 * j] = n ? (uint32_t)(st < cap ? st : cap) : 0u;
         ranges[2 * j + 1] = n ? (uint32_t)(en < cap ? en : cap) : 0u;
-        st = en;
     }
-    if (threadIdx.x == 0) {
-        const unsigned long long P = *total_s > cap ? *total_exact : total;
+    if (j == 0) {
+        const unsigned long long P = *total_s > cap ? *total_exact : *total_t;
         *count_dev = (int64_t)P;
         if (P > cap) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
     }
@@ -860,6 +873,7 @@ struct SortWs {
     uint32_t *hist, *digit_total, *part32;
     unsigned long long *part_s, *total_s, *total_t, *total_exact;
     unsigned long long *masks;                 // [capacity] tile mask of each super-tile entry
+    unsigned long long *tile_part;             // [tile blocks]
     float4 *cull;                              // [2 n] cull record of each visible Gaussian
     uint32_t *n_vis, *sclip;
     uint32_t *seg_lo, *seg_hi, *chunk_base;    // [ns], [ns], [ns + 1]
@@ -908,6 +922,7 @@ inline SortWs sort_layout(char *base, int64_t n, int64_t cap, int64_t tiles, int
     w.tile_count = w.seg_lo ? w.seg_lo + 2 * ns : nullptr;
     w.chunk_base = (uint32_t *)take(4 * (size_t)(ns + 1));
     w.chunk_super = (uint32_t *)take(4 * (size_t)max_chunks(cap, ns));
+    w.tile_part = (unsigned long long *)take(8 * (size_t)((tiles + kScanBlock - 1) / kScanBlock));
     w.tile_start = (unsigned long long *)take(8 * (size_t)tiles);
     w.chunk_counts = (uint32_t *)take(4 * 64 * (size_t)max_chunks(cap, ns));
     w.bytes = off;
@@ -1031,7 +1046,8 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     note_launches(1);
     // one pass: its digit ranges are the segments, written by the pass itself
     const SegPlan sp{w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns, kChunk};
-    radix_sort(sk, sv, start, w.sclip, capacity, sbits, w, s, npass == 1 ? sp : SegPlan{});  // ends in skeys[0] / svals1
+    // ends in skeys[0] / svals1
+    radix_sort(sk, sv, start, w.sclip, capacity, sbits, w, s, npass == 1 ? sp : SegPlan{});
     // stage 3: per-tile lists
     const int64_t chunks = max_chunks(capacity, sg.ns), resident = resident_blocks();
     const unsigned cgrid = (unsigned)(chunks < resident ? chunks : resident);
@@ -1040,10 +1056,15 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
         k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_super);
         note_launches(2);
     }
-    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.cull, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
-                                            sg.supers_x, dc, w.chunk_counts, w.tile_count, w.masks);
-    k_tile_scan<<<1, 1024, 0, s>>>(w.tile_count, tiles, capacity, w.total_s, w.total_exact, w.tile_start, ranges,
-                                   count_dev);
+    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.cull, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base,
+                                            w.chunk_super, ns, sg.supers_x, dc, w.chunk_counts, w.tile_count,
+                                            w.masks);
+    const int tb = (int)((tiles + kScanBlock - 1) / kScanBlock);
+    k_tile_sums<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part);
+    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.tile_part, tb, w.total_t, nullptr, 0);
+    k_tile_starts<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part, capacity, w.total_t, w.total_s,
+                                            w.total_exact, w.tile_start, ranges, count_dev);
+    note_launches(2);
     k_expand<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
                                       sg.supers_x, dc, w.chunk_counts, w.tile_start, capacity, w.masks, vals);
     note_launches(3);
