@@ -158,12 +158,14 @@ __global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t *__restrict__ h
 }
 
 // Where a one-pass sort by super-tile id leaves each super-tile's entries:
-// its digit's range of the output. Given (seg_lo non-null), block 0 of the
-// pass writes seg_lo / seg_hi [ns] and the chunk plan -- chunk_base [ns + 1]
-// (exclusive scan of ceil(len / chunk)) and chunk_super (the super-tile of
-// every chunk) -- from the digit totals.
+// its digit's range of the output. Given (chunk_base non-null), block 0 of
+// the pass writes the chunk plan from the digit totals: chunk_base [ns + 1]
+// (exclusive scan of ceil(len / chunk)) and chunk_rec (per chunk: its
+// super-tile, first entry, the segment's end and the super-tile's first
+// chunk).
 struct SegPlan {
-    uint32_t *seg_lo, *seg_hi, *chunk_base, *chunk_super;
+    uint32_t *chunk_base;
+    uint4 *chunk_rec;
     int ns, chunk;
 };
 
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     __shared__ uint32_t ws[32];
     const uint32_t n = *count;
     const int nbd = radix_blocks(count);
-    const bool plan = sp.seg_lo && blockIdx.x == 0;
+    const bool plan = sp.chunk_base && blockIdx.x == 0;
     if ((int)blockIdx.x >= nbd && !plan) return;
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
@@ -210,10 +212,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
         for (int q = 0; q < kPer; ++q) {
             const int d = kPer * t + q;
             if (d < sp.ns) {
-                sp.seg_lo[d] = dbase[q];
-                sp.seg_hi[d] = dbase[q] + dtot[q];
                 sp.chunk_base[d] = cb;
-                for (uint32_t c = 0; c < nc[q]; ++c) sp.chunk_super[cb + c] = (uint32_t)d;
+                for (uint32_t c = 0; c < nc[q]; ++c)
+                    sp.chunk_rec[cb + c] = make_uint4((uint32_t)d, dbase[q] + c * (uint32_t)sp.chunk,
+                                                      dbase[q] + dtot[q], cb);
             }
             cb += nc[q];
         }
@@ -574,11 +576,12 @@ __global__ void __launch_bounds__(256) k_seg_mark(const uint32_t *__restrict__ s
 }
 
 // One block: chunk bases, chunk_base [ns + 1] (exclusive scan of
-// ceil(len / kChunk)), and the super-tile of every chunk, chunk_super [chunks].
+// ceil(len / kChunk)), and the record of every chunk, chunk_rec [chunks] (as
+// the one-pass radix writes them).
 __global__ void __launch_bounds__(1024) k_super_plan(const uint32_t *__restrict__ seg_lo,
                                                      const uint32_t *__restrict__ seg_hi, int ns,
                                                      uint32_t *__restrict__ chunk_base,
-                                                     uint32_t *__restrict__ chunk_super) {
+                                                     uint4 *__restrict__ chunk_rec) {
     __shared__ uint32_t ws[32];
     uint32_t carry = 0;
     for (int base = 0; base < ns; base += 1024) {
@@ -588,7 +591,8 @@ __global__ void __launch_bounds__(1024) k_super_plan(const uint32_t *__restrict_
         const uint32_t ex = block_scan_excl<uint32_t>(nc, ws, &tot);
         if (j < ns) {
             chunk_base[j] = carry + ex;
-            for (uint32_t c = 0; c < nc; ++c) chunk_super[carry + ex + c] = (uint32_t)j;
+            for (uint32_t c = 0; c < nc; ++c)
+                chunk_rec[carry + ex + c] = make_uint4((uint32_t)j, seg_lo[j] + c * kChunk, seg_hi[j], carry + ex);
         }
         carry += tot;
     }
@@ -599,6 +603,7 @@ __global__ void __launch_bounds__(1024) k_super_plan(const uint32_t *__restrict_
 // mask of the tiles of the super-tile that list it.
 struct ChunkCtx {
     int s, sx, sy;
+    uint32_t first;  // the super-tile's first chunk
     uint32_t g;
     unsigned long long mask;
 };
@@ -616,19 +621,19 @@ struct TestScratch {
 // masks_out when given); else they are read.
 __device__ __forceinline__ void chunk_load(ChunkCtx &cx, uint32_t c, const float *__restrict__ splats,
                                            const float4 *__restrict__ cull,
-                                           const uint32_t *__restrict__ svals, const uint32_t *__restrict__ seg_lo,
-                                           const uint32_t *__restrict__ seg_hi,
-                                           const uint32_t *__restrict__ chunk_base,
-                                           const uint32_t *__restrict__ chunk_super, int supers_x,
+                                           const uint32_t *__restrict__ svals,
+                                           const uint4 *__restrict__ chunk_rec, int supers_x,
                                            const DevCam &cam, const TestScratch &sc,
                                            const unsigned long long *__restrict__ masks_in,
                                            unsigned long long *__restrict__ masks_out) {
     __syncthreads();  // the previous chunk's shared data is no longer read
-    cx.s = (int)chunk_super[c];
+    const uint4 cr = chunk_rec[c];
+    cx.s = (int)cr.x;
+    cx.first = cr.w;
     cx.sx = cx.s % supers_x;
     cx.sy = cx.s / supers_x;
-    const uint32_t e = seg_lo[cx.s] + (c - chunk_base[cx.s]) * kChunk + threadIdx.x;
-    const bool valid = e < seg_hi[cx.s];
+    const uint32_t e = cr.y + threadIdx.x;
+    const bool valid = e < cr.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     cx.mask = 0ull;
     cx.g = valid ? svals[e] : 0u;
@@ -727,10 +732,8 @@ __device__ __forceinline__ int slot_tile(int t, int sx, int sy, int tiles_x) {
 __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict__ splats,
                                                         const float4 *__restrict__ cull,
                                                         const uint32_t *__restrict__ svals,
-                                                        const uint32_t *__restrict__ seg_lo,
-                                                        const uint32_t *__restrict__ seg_hi,
                                                         const uint32_t *__restrict__ chunk_base,
-                                                        const uint32_t *__restrict__ chunk_super, int ns,
+                                                        const uint4 *__restrict__ chunk_rec, int ns,
                                                         int supers_x, DevCam cam, uint32_t *__restrict__ counts,
                                                         uint32_t *__restrict__ tile_count,
                                                         unsigned long long *__restrict__ masks) {
@@ -743,8 +746,7 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
-        chunk_load(cx, c, splats, cull, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, sc, nullptr,
-                   masks);
+        chunk_load(cx, c, splats, cull, svals, chunk_rec, supers_x, cam, sc, nullptr, masks);
         cnt[warp][lane] = (uint32_t)__popc(warp_transpose32((uint32_t)cx.mask, lane));
         cnt[warp][lane + 32] = (uint32_t)__popc(warp_transpose32((uint32_t)(cx.mask >> 32), lane));
         __syncthreads();
@@ -803,10 +805,8 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_starts(const uint32_t *__re
 }
 
 __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ splats, const uint32_t *__restrict__ svals,
-                                                  const uint32_t *__restrict__ seg_lo,
-                                                  const uint32_t *__restrict__ seg_hi,
                                                   const uint32_t *__restrict__ chunk_base,
-                                                  const uint32_t *__restrict__ chunk_super, int ns, int supers_x,
+                                                  const uint4 *__restrict__ chunk_rec, int ns, int supers_x,
                                                   DevCam cam, const uint32_t *__restrict__ counts,
                                                   const unsigned long long *__restrict__ tile_start, int64_t capacity,
                                                   const unsigned long long *__restrict__ masks,
@@ -820,16 +820,24 @@ __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ spl
     const unsigned lt = lanemask_lt();
     for (uint32_t c = blockIdx.x; c < nc; c += gridDim.x) {
         ChunkCtx cx;
-        chunk_load(cx, c, splats, nullptr, svals, seg_lo, seg_hi, chunk_base, chunk_super, supers_x, cam, TestScratch{},
-                   masks, nullptr);
+        chunk_load(cx, c, splats, nullptr, svals, chunk_rec, supers_x, cam, TestScratch{}, masks, nullptr);
         const uint32_t lo = (uint32_t)cx.mask, hi = (uint32_t)(cx.mask >> 32);
         ballots[warp][lane] = warp_transpose32(lo, lane);
         ballots[warp][lane + 32] = warp_transpose32(hi, lane);
-        {   // entries of each slot in the super-tile's earlier chunks: 4 threads per slot
+        {   // entries of each slot in the super-tile's earlier chunks: 4 threads per slot,
+            // four independent sums so that the loads overlap
+            constexpr int kQ = kChunk / 64;
             const int t = threadIdx.x & 63, q = threadIdx.x >> 6;
-            uint32_t n = 0;
-            for (uint32_t c2 = chunk_base[cx.s] + q; c2 < c; c2 += kChunk / 64) n += counts[(int64_t)c2 * 64 + t];
-            before[q][t] = n;
+            uint32_t n0 = 0u, n1 = 0u, n2 = 0u, n3 = 0u;
+            uint32_t c2 = cx.first + q;
+            for (; c2 + 3 * kQ < c; c2 += 4 * kQ) {
+                n0 += counts[(int64_t)c2 * 64 + t];
+                n1 += counts[(int64_t)(c2 + kQ) * 64 + t];
+                n2 += counts[(int64_t)(c2 + 2 * kQ) * 64 + t];
+                n3 += counts[(int64_t)(c2 + 3 * kQ) * 64 + t];
+            }
+            for (; c2 < c; c2 += kQ) n0 += counts[(int64_t)c2 * 64 + t];
+            before[q][t] = (n0 + n1) + (n2 + n3);
         }
         __syncthreads();
         if (threadIdx.x < 64) {
@@ -880,7 +888,7 @@ struct SortWs {
     uint32_t *tile_count;                      // [tiles]
     unsigned long long *tile_start;            // [tiles]
     uint32_t *chunk_counts;                    // [max chunks][64]
-    uint32_t *chunk_super;                     // [max chunks]
+    uint4 *chunk_rec;                          // [max chunks]
     size_t bytes;
 };
 
@@ -921,7 +929,7 @@ inline SortWs sort_layout(char *base, int64_t n, int64_t cap, int64_t tiles, int
     w.seg_hi = w.seg_lo ? w.seg_lo + ns : nullptr;
     w.tile_count = w.seg_lo ? w.seg_lo + 2 * ns : nullptr;
     w.chunk_base = (uint32_t *)take(4 * (size_t)(ns + 1));
-    w.chunk_super = (uint32_t *)take(4 * (size_t)max_chunks(cap, ns));
+    w.chunk_rec = (uint4 *)take(16 * (size_t)max_chunks(cap, ns));
     w.tile_part = (unsigned long long *)take(8 * (size_t)((tiles + kScanBlock - 1) / kScanBlock));
     w.tile_start = (unsigned long long *)take(8 * (size_t)tiles);
     w.chunk_counts = (uint32_t *)take(4 * 64 * (size_t)max_chunks(cap, ns));
@@ -1045,7 +1053,7 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
                                             capacity, sk[start], sv[start], w.total_exact);
     note_launches(1);
     // one pass: its digit ranges are the segments, written by the pass itself
-    const SegPlan sp{w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns, kChunk};
+    const SegPlan sp{w.chunk_base, w.chunk_rec, ns, kChunk};
     // ends in skeys[0] / svals1
     radix_sort(sk, sv, start, w.sclip, capacity, sbits, w, s, npass == 1 ? sp : SegPlan{});
     // stage 3: per-tile lists
@@ -1053,20 +1061,19 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     const unsigned cgrid = (unsigned)(chunks < resident ? chunks : resident);
     if (npass != 1) {
         k_seg_mark<<<(unsigned)resident, 256, 0, s>>>(w.skeys[0], w.sclip, w.seg_lo, w.seg_hi);
-        k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_super);
+        k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_rec);
         note_launches(2);
     }
-    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.cull, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base,
-                                            w.chunk_super, ns, sg.supers_x, dc, w.chunk_counts, w.tile_count,
-                                            w.masks);
+    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.cull, w.svals1, w.chunk_base, w.chunk_rec, ns, sg.supers_x, dc,
+                                            w.chunk_counts, w.tile_count, w.masks);
     const int tb = (int)((tiles + kScanBlock - 1) / kScanBlock);
     k_tile_sums<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part);
     k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.tile_part, tb, w.total_t, nullptr, 0);
     k_tile_starts<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part, capacity, w.total_t, w.total_s,
                                             w.total_exact, w.tile_start, ranges, count_dev);
     note_launches(2);
-    k_expand<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.seg_lo, w.seg_hi, w.chunk_base, w.chunk_super, ns,
-                                      sg.supers_x, dc, w.chunk_counts, w.tile_start, capacity, w.masks, vals);
+    k_expand<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.chunk_base, w.chunk_rec, ns, sg.supers_x, dc, w.chunk_counts,
+                                      w.tile_start, capacity, w.masks, vals);
     note_launches(3);
     return launch_status();
 }
