@@ -21,14 +21,11 @@ constexpr int kT = 32;            // output tile edge
 constexpr int kR = 5;             // window radius
 constexpr int kE = kT + 2 * kR;   // tile edge with halo
 constexpr int kLossThreads = 256;
+constexpr int kLoadRows = kLossThreads / kE;  // haloed rows loaded per round (6; threads 252-255 idle)
 
 struct Win {
     float w[11];
 };
-
-__device__ __forceinline__ float ld_or_zero(const float *p, int y, int x, int H, int W) {
-    return (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(p + (int64_t)y * W + x) : 0.f;
-}
 
 // Each pass gives a thread kV = 4 consecutive outputs, so that it reads the
 // kV + 10 inputs of their windows once from shared memory instead of
@@ -84,13 +81,19 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
     const int64_t HW = (int64_t)H * W;
     const float *x = img + ch * HW, *y = gt + ch * HW;
     const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
+    {   // thread t loads column t % kE of rows t / kE, + kLoadRows, ...: all its loads in flight together
+        const int c = (int)threadIdx.x % kE, r0 = (int)threadIdx.x / kE;
+        const int gx = ox + c;
+        const bool col_in = gx >= 0 && gx < W;
+        if (r0 < kLoadRows) {
 #pragma unroll
-    for (int k0 = 0; k0 < kE * kE; k0 += kLossThreads) {  // all loads of a thread in flight together
-        const int k = k0 + (int)threadIdx.x;
-        if (k < kE * kE) {
-            int r = k / kE, c = k % kE;
-            sx[r][c] = ld_or_zero(x, oy + r, ox + c, H, W);
-            sy[r][c] = ld_or_zero(y, oy + r, ox + c, H, W);
+            for (int r = r0; r < kE; r += kLoadRows) {
+                const int gy = oy + r;
+                const bool in = col_in && gy >= 0 && gy < H;
+                const int64_t o = (int64_t)gy * W + gx;
+                sx[r][c] = in ? __ldg(x + o) : 0.f;
+                sy[r][c] = in ? __ldg(y + o) : 0.f;
+            }
         }
     }
     __syncthreads();
@@ -152,15 +155,16 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
             // d1 >= C1 and d2 >= C2 (up to rounding of the variances): the map
             // and its partials are formed without dividing by n1 or n2, which
             // may be zero (m / n2 = n1 / (d1 d2), m / n1 = n2 / (d1 d2))
-            const float qd = 1.f / (d1 * d2);
+            const float rd1 = __fdividef(1.f, d1), rd2 = __fdividef(1.f, d2);  // d1, d2 in [1e-4, 3]
+            const float qd = rd1 * rd2;
             const float m_n1 = n2 * qd, m_n2 = n1 * qd;
             const float m = n1 * m_n1;
             ss += m;
             l1 += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
             // partials of the map value w.r.t. the window means of x, x^2 and x*y
             const int64_t p = ch * HW + (int64_t)gy * W + gx;
-            mapA[p] = 2.f * my[v] * (m_n1 - m_n2) + 2.f * mx[v] * m * (1.f / d2 - 1.f / d1);
-            mapB[p] = -m / d2;
+            mapA[p] = 2.f * my[v] * (m_n1 - m_n2) + 2.f * mx[v] * m * (rd2 - rd1);
+            mapB[p] = -m * rd2;
             mapC[p] = 2.f * m_n2;
         }
     }
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
     }
 }
 
-__global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restrict__ img,
+__global__ void __launch_bounds__(kLossThreads, 5) k_ssim_bwd(const float *__restrict__ img,
                                                           const float *__restrict__ gt, int H, int W, Win win,
                                                           float lambda, const float *__restrict__ mapA,
                                                           const float *__restrict__ mapB,
@@ -199,14 +203,20 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_bwd(const float *__restri
     const int64_t HW = (int64_t)H * W;
     const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
     const float *a = mapA + ch * HW, *b = mapB + ch * HW, *c = mapC + ch * HW;
+    {
+        const int q = (int)threadIdx.x % kE, r0 = (int)threadIdx.x / kE;
+        const int gx = ox + q;
+        const bool col_in = gx >= 0 && gx < W;
+        if (r0 < kLoadRows) {
 #pragma unroll
-    for (int k0 = 0; k0 < kE * kE; k0 += kLossThreads) {
-        const int k = k0 + (int)threadIdx.x;
-        if (k < kE * kE) {
-            int r = k / kE, q = k % kE;
-            sm[0][r][q] = ld_or_zero(a, oy + r, ox + q, H, W);
-            sm[1][r][q] = ld_or_zero(b, oy + r, ox + q, H, W);
-            sm[2][r][q] = ld_or_zero(c, oy + r, ox + q, H, W);
+            for (int r = r0; r < kE; r += kLoadRows) {
+                const int gy = oy + r;
+                const bool in = col_in && gy >= 0 && gy < H;
+                const int64_t o = (int64_t)gy * W + gx;
+                sm[0][r][q] = in ? __ldg(a + o) : 0.f;
+                sm[1][r][q] = in ? __ldg(b + o) : 0.f;
+                sm[2][r][q] = in ? __ldg(c + o) : 0.f;
+            }
         }
     }
     __syncthreads();
