@@ -58,6 +58,29 @@ void note_launches(int k);
 
 inline int launch_status() { return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 
+// Programmatic dependent launch: a kernel started by launch_chained may be
+// scheduled while the kernel before it in the stream is still finishing, so
+// that its launch overlaps that kernel's last blocks. It must call
+// wait_prior_grid() before anything else: griddepcontrol.wait returns once
+// the grids it depends on have completed and their memory operations are
+// visible (at once when it was launched without a dependency).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // Tile rectangle of a splat, decided in float32 with explicitly rounded

@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kScanBlock) k_count_visible(const float *__res
                                                              uint32_t *__restrict__ part, uint32_t *__restrict__ zero,
                                                              int64_t nzero,
                                                              unsigned long long *__restrict__ total_exact) {
+    wait_prior_grid();
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     for (int64_t z = i; z < nzero; z += (int64_t)gridDim.x * kScanBlock) zero[z] = 0u;
     if (i == 0) *total_exact = 0ull;
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kScanBlock) k_count_visible(const float *__res
 template <typename T>
 __global__ void __launch_bounds__(1024) k_scan_parts(T *__restrict__ part, int nb, T *__restrict__ total,
                                                      uint32_t *__restrict__ clip, int64_t capacity) {
+    wait_prior_grid();
     __shared__ T ws[32];
     T carry = 0;
     for (int base = 0; base < nb; base += 1024) {
@@ -121,6 +123,7 @@ __device__ __forceinline__ int radix_blocks(const uint32_t *count) {
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__restrict__ keys,
                                                             const uint32_t *__restrict__ count, int shift, int bits,
                                                             uint32_t *__restrict__ hist) {
+    wait_prior_grid();
     __shared__ uint32_t h[kMaxRadix];
     const int radix = 1 << bits;
     const uint32_t mask = (uint32_t)radix - 1u;
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *__r
 
 __global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t *__restrict__ hist, const uint32_t *__restrict__ count,
                                                         uint32_t *__restrict__ digit_total) {
+    wait_prior_grid();
     __shared__ uint32_t ws[32];
     const int nb = radix_blocks(count);
     uint32_t *row = hist + (int64_t)blockIdx.x * nb;
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
                                                                const uint32_t *__restrict__ count, int shift, int bits,
                                                                const uint32_t *__restrict__ hist,
                                                                const uint32_t *__restrict__ digit_total, SegPlan sp) {
+    wait_prior_grid();
     constexpr int kWarps = kSortThreads / 32;
     constexpr int kPer = kMaxRadix / kSortThreads;  // buckets per thread (consecutive)
     __shared__ uint32_t run[kMaxRadix];
@@ -283,6 +288,7 @@ int64_t resident_blocks() {
 }
 
 __global__ void k_zero_u32(uint32_t *__restrict__ p, int64_t n) {
+    wait_prior_grid();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = 0u;
 }
@@ -451,6 +457,7 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_visible(const float *__rest
                                                             const uint32_t *__restrict__ part, DevCam cam,
                                                             uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                                             float4 *__restrict__ cull) {
+    wait_prior_grid();
     __shared__ int ws[32];
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     int f = (i < n) && splat_visible(splats, i);
@@ -477,6 +484,7 @@ __global__ void __launch_bounds__(kScanBlock) k_count_entries(const float4 *__re
                                                              const uint32_t *__restrict__ order,
                                                              const uint32_t *__restrict__ n_vis,
                                                              unsigned long long *__restrict__ part_s) {
+    wait_prior_grid();
     __shared__ unsigned long long ws[32];
     int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     int sx0, sy0, sx1, sy1;
@@ -511,6 +519,7 @@ __global__ void __launch_bounds__(256) k_count_exact(const float *__restrict__ s
                                                     const uint32_t *__restrict__ n_vis, DevCam cam,
                                                     const unsigned long long *__restrict__ total_s, int64_t capacity,
                                                     unsigned long long *__restrict__ total_exact) {
+    wait_prior_grid();
     if (*total_s <= (unsigned long long)capacity) return;
     unsigned long long mine = 0ull;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < *n_vis;
@@ -525,6 +534,7 @@ __global__ void k_finish_count(const unsigned long long *__restrict__ total_t,
                                const unsigned long long *__restrict__ total_s,
                                const unsigned long long *__restrict__ total_exact, int64_t capacity,
                                int64_t *__restrict__ count_dev) {
+    wait_prior_grid();
     const unsigned long long P = *total_s > (unsigned long long)capacity ? *total_exact : *total_t;
     *count_dev = (int64_t)P;
     if (P > (unsigned long long)capacity) atomicOr(&g_sort_flags, GS_FLAG_CAPACITY);
@@ -539,6 +549,7 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restri
                                                           int64_t capacity, uint32_t *__restrict__ skeys,
                                                           uint32_t *__restrict__ svals,
                                                           unsigned long long *__restrict__ total_exact) {
+    wait_prior_grid();
     __shared__ unsigned long long ws[32];
     int64_t k = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     int sx0 = 0, sy0 = 0, sx1 = 0, sy1 = 0;
@@ -567,6 +578,7 @@ __global__ void __launch_bounds__(kScanBlock) k_emit_super(const float *__restri
 __global__ void __launch_bounds__(256) k_seg_mark(const uint32_t *__restrict__ skeys,
                                                  const uint32_t *__restrict__ count, uint32_t *__restrict__ seg_lo,
                                                  uint32_t *__restrict__ seg_hi) {
+    wait_prior_grid();
     const uint32_t n = *count;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = skeys[e];
@@ -582,6 +594,7 @@ __global__ void __launch_bounds__(1024) k_super_plan(const uint32_t *__restrict_
                                                      const uint32_t *__restrict__ seg_hi, int ns,
                                                      uint32_t *__restrict__ chunk_base,
                                                      uint4 *__restrict__ chunk_rec) {
+    wait_prior_grid();
     __shared__ uint32_t ws[32];
     uint32_t carry = 0;
     for (int base = 0; base < ns; base += 1024) {
@@ -737,6 +750,7 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
                                                         int supers_x, DevCam cam, uint32_t *__restrict__ counts,
                                                         uint32_t *__restrict__ tile_count,
                                                         unsigned long long *__restrict__ masks) {
+    wait_prior_grid();
     __shared__ uint32_t hit_mask[2 * kChunk];  // per entry, low and high halves
     __shared__ float4 shape[2 * kChunk];
     __shared__ uint32_t rect[kChunk];
@@ -768,6 +782,7 @@ __global__ void __launch_bounds__(kChunk) k_chunk_counts(const float *__restrict
 // super-tile entries overflowed (and the capacity flag if P exceeds it).
 __global__ void __launch_bounds__(kScanBlock) k_tile_sums(const uint32_t *__restrict__ tile_count, int64_t tiles,
                                                          unsigned long long *__restrict__ part) {
+    wait_prior_grid();
     __shared__ unsigned long long ws[32];
     const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     unsigned long long tot;
@@ -784,6 +799,7 @@ __global__ void __launch_bounds__(kScanBlock) k_tile_starts(const uint32_t *__re
                                                            unsigned long long *__restrict__ tile_start,
                                                            uint32_t *__restrict__ ranges,
                                                            int64_t *__restrict__ count_dev) {
+    wait_prior_grid();
     __shared__ unsigned long long ws[32];
     const int64_t j = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     const unsigned long long n = j < tiles ? tile_count[j] : 0ull;
@@ -811,6 +827,7 @@ __global__ void __launch_bounds__(kChunk) k_expand(const float *__restrict__ spl
                                                   const unsigned long long *__restrict__ tile_start, int64_t capacity,
                                                   const unsigned long long *__restrict__ masks,
                                                   uint32_t *__restrict__ vals) {
+    wait_prior_grid();
     constexpr int kW = kChunk / 32;
     __shared__ uint32_t ballots[kW][64];                 // per (warp, slot): lanes whose entry the tile lists
     __shared__ uint32_t before[kChunk / 64][64];         // partial sums of earlier chunks' counts
@@ -966,11 +983,10 @@ int radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], int in, const u
     int shift = 0;
     for (int p = 0; p < npass; ++p) {
         int bits = per < total_bits - shift ? per : total_bits - shift;
-        k_radix_hist<<<grid, kSortThreads, 0, s>>>(keys[in], count, shift, bits, w.hist);
-        k_radix_rowscan<<<1 << bits, 1024, 0, s>>>(w.hist, count, w.digit_total);
-        k_radix_scatter<<<grid, kSortThreads, 0, s>>>(keys[in], vals[in], keys[1 - in], vals[1 - in], count, shift,
-                                                      bits, w.hist, w.digit_total,
-                                                      p == npass - 1 ? sp : SegPlan{});
+        launch_chained(k_radix_hist, grid, kSortThreads, s, keys[in], count, shift, bits, w.hist);
+        launch_chained(k_radix_rowscan, 1 << bits, 1024, s, w.hist, count, w.digit_total);
+        launch_chained(k_radix_scatter, grid, kSortThreads, s, keys[in], vals[in], keys[1 - in], vals[1 - in], count,
+                       shift, bits, w.hist, w.digit_total, p == npass - 1 ? sp : SegPlan{});
         note_launches(3);
         in = 1 - in;
         shift += bits;
@@ -1027,20 +1043,21 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     }
     // stage 1: visible Gaussians by depth (the first kernel also zeroes the
     // segment bounds, tile counts and exact count)
-    k_count_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, w.seg_lo, 2 * sg.ns + tiles, w.total_exact);
-    k_scan_parts<uint32_t><<<1, 1024, 0, s>>>(w.part32, nbS, w.n_vis, nullptr, 0);
-    k_emit_visible<<<nbS, kScanBlock, 0, s>>>(splats, n, w.part32, dc, w.keys[0], w.vals[0], w.cull);
+    launch_chained(k_count_visible, nbS, kScanBlock, s, splats, n, w.part32, w.seg_lo, 2 * sg.ns + tiles,
+                   w.total_exact);
+    launch_chained(k_scan_parts<uint32_t>, 1, 1024, s, w.part32, nbS, w.n_vis, nullptr, 0);
+    launch_chained(k_emit_visible, nbS, kScanBlock, s, splats, n, w.part32, dc, w.keys[0], w.vals[0], w.cull);
     note_launches(3);
     int cur = radix_sort(w.keys, w.vals, 0, w.n_vis, n, 32, w, s);
     // stage 2: super-tile entries in depth order, stable-sorted by super-tile
-    k_count_entries<<<nbS, kScanBlock, 0, s>>>(w.cull, w.vals[cur], w.n_vis, w.part_s);
-    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.part_s, nbS, w.total_s, w.sclip, capacity);
+    launch_chained(k_count_entries, nbS, kScanBlock, s, w.cull, w.vals[cur], w.n_vis, w.part_s);
+    launch_chained(k_scan_parts<unsigned long long>, 1, 1024, s, w.part_s, nbS, w.total_s, w.sclip, capacity);
     note_launches(2);
     if (capacity == 0) {
         cudaMemsetAsync(w.total_t, 0, sizeof(unsigned long long), s);
-        k_count_exact<<<(unsigned)resident_blocks(), 256, 0, s>>>(splats, w.vals[cur], w.n_vis, dc, w.total_s,
-                                                                  capacity, w.total_exact);
-        k_finish_count<<<1, 1, 0, s>>>(w.total_t, w.total_s, w.total_exact, capacity, count_dev);
+        launch_chained(k_count_exact, (unsigned)resident_blocks(), 256, s, splats, w.vals[cur], w.n_vis, dc, w.total_s,
+                       capacity, w.total_exact);
+        launch_chained(k_finish_count, 1, 1, s, w.total_t, w.total_s, w.total_exact, capacity, count_dev);
         note_launches(2);
         return launch_status();
     }
@@ -1049,8 +1066,8 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     uint32_t *sk[2] = {w.skeys[0], w.skeys[1]};
     uint32_t *sv[2] = {w.svals1, vals};  // the sorted list must end in svals1: vals is written from it
     const int start = npass % 2;
-    k_emit_super<<<nbS, kScanBlock, 0, s>>>(splats, w.cull, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s, w.total_s,
-                                            capacity, sk[start], sv[start], w.total_exact);
+    launch_chained(k_emit_super, nbS, kScanBlock, s, splats, w.cull, w.vals[cur], w.n_vis, dc, sg.supers_x, w.part_s,
+                   w.total_s, capacity, sk[start], sv[start], w.total_exact);
     note_launches(1);
     // one pass: its digit ranges are the segments, written by the pass itself
     const SegPlan sp{w.chunk_base, w.chunk_rec, ns, kChunk};
@@ -1060,20 +1077,20 @@ extern "C" int gs_sort(const float *splats, int64_t n, const gs_camera *cam, voi
     const int64_t chunks = max_chunks(capacity, sg.ns), resident = resident_blocks();
     const unsigned cgrid = (unsigned)(chunks < resident ? chunks : resident);
     if (npass != 1) {
-        k_seg_mark<<<(unsigned)resident, 256, 0, s>>>(w.skeys[0], w.sclip, w.seg_lo, w.seg_hi);
-        k_super_plan<<<1, 1024, 0, s>>>(w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_rec);
+        launch_chained(k_seg_mark, (unsigned)resident, 256, s, w.skeys[0], w.sclip, w.seg_lo, w.seg_hi);
+        launch_chained(k_super_plan, 1, 1024, s, w.seg_lo, w.seg_hi, ns, w.chunk_base, w.chunk_rec);
         note_launches(2);
     }
-    k_chunk_counts<<<cgrid, kChunk, 0, s>>>(splats, w.cull, w.svals1, w.chunk_base, w.chunk_rec, ns, sg.supers_x, dc,
-                                            w.chunk_counts, w.tile_count, w.masks);
+    launch_chained(k_chunk_counts, cgrid, kChunk, s, splats, w.cull, w.svals1, w.chunk_base, w.chunk_rec, ns,
+                   sg.supers_x, dc, w.chunk_counts, w.tile_count, w.masks);
     const int tb = (int)((tiles + kScanBlock - 1) / kScanBlock);
-    k_tile_sums<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part);
-    k_scan_parts<unsigned long long><<<1, 1024, 0, s>>>(w.tile_part, tb, w.total_t, nullptr, 0);
-    k_tile_starts<<<tb, kScanBlock, 0, s>>>(w.tile_count, tiles, w.tile_part, capacity, w.total_t, w.total_s,
-                                            w.total_exact, w.tile_start, ranges, count_dev);
+    launch_chained(k_tile_sums, tb, kScanBlock, s, w.tile_count, tiles, w.tile_part);
+    launch_chained(k_scan_parts<unsigned long long>, 1, 1024, s, w.tile_part, tb, w.total_t, nullptr, 0);
+    launch_chained(k_tile_starts, tb, kScanBlock, s, w.tile_count, tiles, w.tile_part, capacity, w.total_t, w.total_s,
+                   w.total_exact, w.tile_start, ranges, count_dev);
     note_launches(2);
-    k_expand<<<cgrid, kChunk, 0, s>>>(splats, w.svals1, w.chunk_base, w.chunk_rec, ns, sg.supers_x, dc, w.chunk_counts,
-                                      w.tile_start, capacity, w.masks, vals);
+    launch_chained(k_expand, cgrid, kChunk, s, splats, w.svals1, w.chunk_base, w.chunk_rec, ns, sg.supers_x, dc,
+                   w.chunk_counts, w.tile_start, capacity, w.masks, vals);
     note_launches(3);
     return launch_status();
 }
