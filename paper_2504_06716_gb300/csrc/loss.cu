@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_fwd(const float *__restri
     __shared__ float red[2][kLossThreads / 32];
     __shared__ bool last;
     static_assert(sizeof(h) >= 2 * kLossThreads * sizeof(double), "scratch fits");
+    wait_prior_grid();
     const int ch = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const float *x = img + ch * HW, *y = gt + ch * HW;
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(kLossThreads, 5) k_ssim_bwd(const float *__res
                                                           const float *__restrict__ mapC, float *__restrict__ dl) {
     __shared__ float sm[3][kE][kE + 1];
     __shared__ float h[3][kE][kT + 1];
+    wait_prior_grid();
     const int ch = blockIdx.z;
     const int64_t HW = (int64_t)H * W;
     const int oy = blockIdx.y * kT - kR, ox = blockIdx.x * kT - kR;
@@ -368,8 +370,9 @@ extern "C" int gs_loss(const float *image, const float *gt, int32_t H, int32_t W
                                                           align256(sizeof(float2) * (size_t)g.nparts));
     Win win = make_window();
     if (cudaMemsetAsync(done, 0, sizeof(unsigned int), s) != cudaSuccess) return GS_ERR_CUDA;
-    k_ssim_fwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, mapA, mapB, mapC, part, done, lambda, loss_dev);
-    k_ssim_bwd<<<g.grid, kLossThreads, 0, s>>>(image, gt, H, W, win, lambda, mapA, mapB, mapC, dl_dimage);
+    launch_chained(k_ssim_fwd, g.grid, kLossThreads, s, image, gt, H, W, win, mapA, mapB, mapC, part, done, lambda,
+                   loss_dev);
+    launch_chained(k_ssim_bwd, g.grid, kLossThreads, s, image, gt, H, W, win, lambda, mapA, mapB, mapC, dl_dimage);
     note_launches(2);
     return launch_status();
 }

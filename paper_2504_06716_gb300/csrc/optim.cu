@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(256) k_adam(float *__restrict__ P, const float
                                               const int32_t *__restrict__ act, const int32_t *__restrict__ n_active,
                                               AdamArgs a, const float *__restrict__ scales,
                                               const float *__restrict__ lr_dev) {
+    wait_prior_grid();
     const float step_size_scale = scales ? scales[0] : a.step_size_scale;
     const float inv_sqrt_bc2 = scales ? scales[1] : a.inv_sqrt_bc2;
     float l0 = a.lr[0], l1 = a.lr[1], l2 = a.lr[2], l3 = a.lr[3], l4 = a.lr[4], l5 = a.lr[5], l6 = a.lr[6];
@@ -534,7 +535,8 @@ extern "C" int gs_adam_masked_groups(float *P, const float *G, float *m, float *
     a.step_size_scale = (float)(1.0 / bc1);
     a.inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
     const int64_t blocks = adam_grid(n);
-    k_adam<<<(unsigned)blocks, 256, 0, as_stream(stream)>>>(P, G, m, v, act, n_active_dev, a, nullptr, nullptr);
+    launch_chained(k_adam, (unsigned)blocks, 256, as_stream(stream), P, G, m, v, act, n_active_dev, a,
+                   static_cast<float *>(nullptr), static_cast<float *>(nullptr));
     note_launches(1);
     return launch_status();
 }

@@ -188,6 +188,7 @@ __device__ __forceinline__ bool masked_off(const float *__restrict__ P, int64_t 
 
 __global__ void __launch_bounds__(256) k_project_fwd(const float *__restrict__ P, int64_t n, int deg, int flags,
                                                      DevCam cam, float *__restrict__ out) {
+    wait_prior_grid();
     const int abs_act = flags & GS_OPACITY_ABS;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -462,6 +463,7 @@ __global__ void __launch_bounds__(128, 4) k_project_bwd(const float *__restrict_
                                                      const int32_t *__restrict__ act,
                                                      const int32_t *__restrict__ n_active, float *__restrict__ grad2d,
                                                      float *__restrict__ G, StatSets st, int ACC) {
+    wait_prior_grid();
     const int64_t na = *n_active;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < na; k += (int64_t)gridDim.x * blockDim.x)
         project_bwd_one(k, P, deg, flags, mask_loss, cam, splats, act, grad2d, G, st, ACC);
@@ -481,8 +483,8 @@ extern "C" int gs_project_ex(const float *P, int64_t n, int32_t sh_degree, int32
     if (n == 0) return GS_OK;
     if (!P || !splats) return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(P) | reinterpret_cast<uintptr_t>(splats)) & 15) return GS_ERR_INVALID_ARG;
-    k_project_fwd<<<grid_for(n, 256), 256, 0, as_stream(stream)>>>(P, n, sh_degree, opacity_act, make_cam(cam),
-                                                                    splats);
+    launch_chained(k_project_fwd, grid_for(n, 256), 256, as_stream(stream), P, n, sh_degree, opacity_act, make_cam(cam),
+                   splats);
     note_launches(1);
     return launch_status();
 }
@@ -526,8 +528,8 @@ static int project_bwd(bool acc, const float *P, int64_t n, int32_t sh_degree, i
         per_sm = v;
     }
     const unsigned grid = std::min<unsigned>(grid_for(n, 128), (unsigned)(sms > 0 ? sms : 152) * (unsigned)per_sm);
-    k_project_bwd<<<grid, 128, 0, as_stream(stream)>>>(P, sh_degree, opacity_act, mask_loss, dc, splats, act,
-                                                        n_active_dev, grad2d, G, st, acc ? 1 : 0);
+    launch_chained(k_project_bwd, grid, 128, as_stream(stream), P, sh_degree, opacity_act, mask_loss, dc, splats, act,
+                   n_active_dev, grad2d, G, st, acc ? 1 : 0);
     note_launches(1);
     return launch_status();
 }

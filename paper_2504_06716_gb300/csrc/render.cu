@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const float *__res
                                                               const uint32_t *__restrict__ ranges, DevCam cam,
                                                               float *__restrict__ image, float *__restrict__ t_final,
                                                               int32_t *__restrict__ n_last) {
+    wait_prior_grid();
     render_tile<TS, PPT, B>(splats, vals, ranges, cam, image, t_final, n_last, blockIdx.x);
 }
 
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__res
                                                               const float *__restrict__ dl_dimage,
                                                               const uint8_t *__restrict__ frozen,
                                                               float *__restrict__ grad2d) {
+    wait_prior_grid();
     raster_bwd_tile<TS, PPT, B>(splats, vals, ranges, cam, t_final, n_last, dl_dimage, frozen, grad2d, blockIdx.x);
 }
 
@@ -486,14 +488,14 @@ struct BwdArgs {
 
 template <int TS, int PPT, int B>
 void launch(const FwdArgs &a, cudaStream_t s) {
-    k_render_fwd<TS, PPT, B><<<a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, 0, s>>>(a.splats, a.vals, a.ranges, a.cam,
-                                                                                    a.image, a.t_final, a.n_last);
+    launch_chained(k_render_fwd<TS, PPT, B>, a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, s, a.splats, a.vals,
+                   a.ranges, a.cam, a.image, a.t_final, a.n_last);
 }
 
 template <int TS, int PPT, int B>
 void launch(const BwdArgs &a, cudaStream_t s) {
-    k_raster_bwd<TS, PPT, B><<<a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, 0, s>>>(
-        a.splats, a.vals, a.ranges, a.cam, a.t_final, a.n_last, a.dl, a.frozen, a.grad2d);
+    launch_chained(k_raster_bwd<TS, PPT, B>, a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, s, a.splats, a.vals,
+                   a.ranges, a.cam, a.t_final, a.n_last, a.dl, a.frozen, a.grad2d);
 }
 
 struct BatchArgs {
