@@ -432,19 +432,19 @@ def gpu_arm(args):
 # gives the command). Valid only for the kernel sources it was taken on: the
 # digest of those files is compared at run time and traffic is reported as null
 # once they have changed.
-RASTER_BWD_TRAFFIC = dict(bytes_per_launch=80703232,
-                          sources_sha256="e736c990d5f4ef88ac26f9e7fcfdf434655490df04828070179026041574d070")
+RASTER_BWD_TRAFFIC = dict(bytes_per_launch=77951147,
+                          sources_sha256="2fc405011f464c5a6b8ead47ae04a112cee2bd8919cd61e50bbf2d7e49e32eb9")
 RASTER_BWD_SOURCES = ("paper_2504_06716_gb300/csrc/render.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 # The same for Adam and the projection (profiles/k_adam_traffic_surface-1M-1237x822.md,
 # profiles/k_project_fwd_traffic_surface-1M-1237x822.md):
 # DRAM bytes per launch of three captured launches, with the launch's units
 # (active Gaussians; the projection's algorithmic bytes), so that a run on
 # another state scales the traffic by its own units.
-ADAM_TRAFFIC = dict(bytes_per_launch=54627669, active=52081,
-                    sources_sha256="1c6eb55051c060fe2047d7a99f0b9a63590f4306f660a75f8c3be7cbe99b4d65")
+ADAM_TRAFFIC = dict(bytes_per_launch=54905941, active=51957,
+                    sources_sha256="f4427d4d6e48285976e19cf4f231892ddbf9b135e5266f21d5773d65ae72834c")
 ADAM_SOURCES = ("paper_2504_06716_gb300/csrc/optim.cu", "paper_2504_06716_gb300/csrc/common.cuh")
-PROJECT_TRAFFIC = dict(bytes_per_launch=281098582, algorithmic_bytes=253242144,
-                       sources_sha256="59e78e87e3cf1cb79297be6b9af183f72676207972492cf49dedd9ec1c0324bd")
+PROJECT_TRAFFIC = dict(bytes_per_launch=281083136, algorithmic_bytes=253244083,
+                       sources_sha256="ea098f45eebc9a528634cb8691bb351e975e2e63371b2853b3c1b65eb2594e69")
 PROJECT_SOURCES = ("paper_2504_06716_gb300/csrc/project.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 
 
