@@ -57,9 +57,14 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
         if (__syncthreads_count(all) == NT) break;
         for (int q = threadIdx.x; q < B; q += NT) {
             if (base + q < end) {
+                // staged with -a/2 and -c/2 in place of a and c: the row coefficients of
+                // splat_row, rounded once here instead of once per thread
                 const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)vals[base + q] * kSplat);
-                s_xyab[q] = __ldg(r);
-                s_cocg[q] = __ldg(r + 1);
+                float4 xa = __ldg(r), co = __ldg(r + 1);
+                xa.z = __fmul_rn(-0.5f, xa.z);
+                co.x = __fmul_rn(-0.5f, co.x);
+                s_xyab[q] = xa;
+                s_cocg[q] = co;
                 s_blue[q] = __ldg(reinterpret_cast<const float *>(r + 2));
             }
         }
@@ -68,7 +73,11 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
         for (int j = 0; j < cnt; ++j) {
             const float4 xa = s_xyab[j], co = s_cocg[j];
             const float blue = s_blue[j];
-            const SplatRow row = splat_row(__fsub_rn(xa.x, fpx), xa.z, xa.w, co.x);
+            const float dx = __fsub_rn(xa.x, fpx);
+            SplatRow row;  // splat_row's coefficients from the staged halves
+            row.c0 = __fmul_rn(xa.z, __fmul_rn(dx, dx));
+            row.c1 = __fmul_rn(-xa.w, dx);
+            row.c2 = co.x;
             bool alive = false;
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
@@ -271,8 +280,13 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
             if (q < cnt) {
                 const uint32_t g = vals[bstart + q];
                 const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
-                s_xyab[q] = __ldg(r);
-                s_cocg[q] = __ldg(r + 1);
+                // -a/2 and -c/2 in place of a and c, as in the forward (exact halves;
+                // geo_grads gets a and c back by an exact doubling)
+                float4 xa = __ldg(r), co = __ldg(r + 1);
+                xa.z = __fmul_rn(-0.5f, xa.z);
+                co.x = __fmul_rn(-0.5f, co.x);
+                s_xyab[q] = xa;
+                s_cocg[q] = co;
                 s_blue[q] = __ldg(reinterpret_cast<const float *>(r + 2));
                 s_gid[q] = g;
                 s_frz[q] = frozen ? (int)frozen[g] : 0;
@@ -287,7 +301,10 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
             const float blue = s_blue[j];
             const bool frz = s_frz[j] != 0;  // the same for every thread: a uniform branch
             const float dx = __fsub_rn(xa.x, fpx);
-            const SplatRow row = splat_row(dx, xa.z, xa.w, co.x);
+            SplatRow row;  // splat_row's coefficients from the staged halves
+            row.c0 = __fmul_rn(xa.z, __fmul_rn(dx, dx));
+            row.c1 = __fmul_rn(-xa.w, dx);
+            row.c2 = co.x;
             float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (frz) {
 #pragma unroll
@@ -298,7 +315,7 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
                 for (int k = 0; k < PPT; ++k)
                     c |= pix_bwd<false>(p[k], pos, row, __fsub_rn(xa.y, fpy[k]), co, blue, g);
                 if (__any_sync(kFull, c)) {
-                    geo_grads(g, dx, xa.z, xa.w, co.x);
+                    geo_grads(g, dx, -2.f * xa.z, xa.w, -2.f * co.x);
                     const float tot = warp_sum9(g, lane);
                     if (writer) atomicAdd(&s_acc[slot][j], tot);
                 }
