@@ -540,13 +540,11 @@ def stage_split(tr, n) -> dict:
         ev[1].record()
         lib.gs_sort(m.splats, m.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count)
         ev[2].record()
-        lib.gs_render_fwd_cfg(m.splats, view.vals, view.ranges, view.cam, m.fwd_cfg, view.image, view.t_final,
-                              view.n_last)
+        m.render_fwd(view)
         ev[3].record()
         m.loss(view, tr.targets[v])
         ev[4].record()
-        lib.gs_raster_bwd_cfg(m.splats, view.vals, view.ranges, view.cam, m.bwd_cfg, view.t_final, view.n_last,
-                              view.dl, m.frozen, m.grad2d)
+        m.raster_bwd(view)
         ev[5].record()
         lib.gs_project_bwd(m.P, m.n, m.sh_degree, view.cam, m.splats, m.act, m.n_active, m.grad2d, m.G, m.acc_xyz,
                            m.acc_rgb, m.cnt)

@@ -206,6 +206,30 @@ int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t 
                       const gs_raster_config *cfg, const float *t_final, const int32_t *n_last,
                       const float *dl_dimage, const uint8_t *frozen, float *grad2d, gs_stream_t stream);
 
+/* Sec. 3.1 and Sec. 3.2.4 with the frozen splats behind a tile's last
+ * unfrozen one left out of the backward. A frozen Gaussian takes no
+ * gradient (Sec. 3.2.4); the backward visits the splats behind an unfrozen
+ * one only to rebuild the transmittance in front of it and the colour
+ * blended behind it, so the forward records those: gs_render_fwd_resume is
+ * gs_render_fwd_cfg that also writes, for each tile, resume_pos [tiles]
+ * (int32) = 1 + the list position of the last splat with frozen[i] == 0 the
+ * tile's walk passed (0 if none; frozen may be NULL: nothing frozen), and
+ * for each pixel resume [H][W][4] (float, 16-byte aligned) = (T after that
+ * splat, the colour blended behind it). gs_raster_bwd_resume is
+ * gs_raster_bwd_cfg that starts each tile's walk there from that state,
+ * given the buffers of the forward of the same lists and freeze map; its
+ * gradients equal gs_raster_bwd_cfg's up to float32 rounding (the state is
+ * carried forward instead of recovered backward). resume and resume_pos are
+ * both NULL (no record: the plain calls) or both given. Errors: INVALID_ARG
+ * (also one of the two NULL, resume misaligned), CUDA. */
+int gs_render_fwd_resume(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                         const gs_raster_config *cfg, const uint8_t *frozen, float *image, float *t_final,
+                         int32_t *n_last, float *resume, int32_t *resume_pos, gs_stream_t stream);
+int gs_raster_bwd_resume(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
+                         const gs_raster_config *cfg, const float *t_final, const int32_t *n_last,
+                         const float *dl_dimage, const uint8_t *frozen, const float *resume,
+                         const int32_t *resume_pos, float *grad2d, gs_stream_t stream);
+
 /* Several scenes in one launch. The paper trains one scene at a time and
  * has no counterpart; each job computes what gs_render_fwd (Sec. 3.1,
  * Eq. 2) or gs_raster_bwd (Sec. 3.2.4) computes for one view.
@@ -300,7 +324,7 @@ int gs_render_bwd(const float *P, int64_t n, int32_t sh_degree, const gs_camera 
                   float *grad2d, float *G, float *acc_xyz, float *acc_rgb, int32_t *cnt, gs_stream_t stream);
 
 /* One iteration of Algorithm 1's inner body for one view, in one call:
- * gs_project_ex, gs_sort, gs_render_fwd_cfg, gs_loss, gs_raster_bwd_cfg,
+ * gs_project_ex, gs_sort, gs_render_fwd_resume, gs_loss, gs_raster_bwd_resume,
  * gs_project_bwd_ex (statistics windows `stats`), gs_adam_masked -- the
  * same kernels, enqueued from native code instead of one binding call
  * each. Everything the step touches is described by gs_step (device
@@ -340,6 +364,10 @@ typedef struct {
     /* optional cudaEvent_t pair (NULL: none) recorded on the stream just
      * before and just after the rasteriser backward, to time it in place */
     void *bwd_events[2];
+    /* optional: the view's resume record ([H][W][4] float, [tiles] int32,
+     * see gs_render_fwd_resume); both NULL runs the plain rasteriser calls */
+    float *resume;
+    int32_t *resume_pos;
 } gs_step;
 
 int gs_train_step(const gs_step *s, const gs_camera *cam, const float *gt, const float *lr, int64_t step,

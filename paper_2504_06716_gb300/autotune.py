@@ -70,15 +70,13 @@ def tune(model, cams, targets, tiles=(8, 16, 32), ppts=(1, 2, 4), batches=(32, 6
                 for b in batches:
                     cfg = lib.raster_config(ppt, b)
                     fwd_times[(ppt, b)] = fwd_times.get((ppt, b), 0.0) + _time(
-                        lambda: lib.gs_render_fwd_cfg(model.splats, v.vals, v.ranges, v.cam, cfg, v.image, v.t_final,
-                                                      v.n_last), reps)
+                        lambda: model.render_fwd(v, cfg), reps)
             model.loss(v, gt)
             for ppt in ppts:
                 for b in batches:
                     cfg = lib.raster_config(ppt, b)
                     bwd_times[(ppt, b)] = bwd_times.get((ppt, b), 0.0) + _time(
-                        lambda: lib.gs_raster_bwd_cfg(model.splats, v.vals, v.ranges, v.cam, cfg, v.t_final, v.n_last,
-                                                      v.dl, model.frozen, model.grad2d), reps)
+                        lambda: model.raster_bwd(v, cfg), reps)
         model.grad2d.zero_()
         bf = min(fwd_times, key=fwd_times.get)
         bb = min(bwd_times, key=bwd_times.get)

@@ -34,7 +34,8 @@ extern "C" int gs_train_step(const gs_step *s, const gs_camera *cam, const float
         st = gs_sort(s->splats, s->n, cam, s->sort_ws, s->sort_ws_bytes, s->capacity, s->vals, s->ranges,
                      s->count_dev, stream);
     if (st == GS_OK)
-        st = gs_render_fwd_cfg(s->splats, s->vals, s->ranges, cam, fwd, s->image, s->t_final, s->n_last, stream);
+        st = gs_render_fwd_resume(s->splats, s->vals, s->ranges, cam, fwd, s->frozen, s->image, s->t_final, s->n_last,
+                                  s->resume, s->resume_pos, stream);
     if (st == GS_OK)
         st = gs_loss(s->image, gt, cam->height, cam->width, s->lambda_ssim, s->loss_ws, s->loss_ws_bytes, s->loss_dev,
                      s->dl_dimage, stream);
@@ -42,8 +43,8 @@ extern "C" int gs_train_step(const gs_step *s, const gs_camera *cam, const float
     if (st == GS_OK && s->bwd_events[0] && cudaEventRecord(static_cast<cudaEvent_t>(s->bwd_events[0]), cs) != cudaSuccess)
         st = GS_ERR_CUDA;
     if (st == GS_OK)
-        st = gs_raster_bwd_cfg(s->splats, s->vals, s->ranges, cam, bwd, s->t_final, s->n_last, s->dl_dimage,
-                               s->frozen, s->grad2d, stream);
+        st = gs_raster_bwd_resume(s->splats, s->vals, s->ranges, cam, bwd, s->t_final, s->n_last, s->dl_dimage,
+                                  s->frozen, s->resume, s->resume_pos, s->grad2d, stream);
     if (st == GS_OK && s->bwd_events[1] && cudaEventRecord(static_cast<cudaEvent_t>(s->bwd_events[1]), cs) != cudaSuccess)
         st = GS_ERR_CUDA;
     if (st == GS_OK)

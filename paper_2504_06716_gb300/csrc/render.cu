@@ -25,15 +25,27 @@ namespace {
 // splat staged in shared memory is loaded once per PPT evaluations, and the
 // per-pixel update is written with selects instead of branches so the PPT
 // independent chains interleave.
+//
+// With resume given, the walk also records where the backward may start:
+// resume_pos[tile] = 1 + the list position of the last unfrozen splat it
+// passed (0 if none), and per pixel resume = (T after that splat, the colour
+// blended behind it), so that the backward skips the frozen splats behind
+// every unfrozen one: they carry no gradient, and the state they would
+// rebuild is this one.
 template <int TS, int PPT, int B>
 __device__ __forceinline__ void render_tile(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
                                             const uint32_t *__restrict__ ranges, const DevCam &cam,
                                             float *__restrict__ image, float *__restrict__ t_final,
-                                            int32_t *__restrict__ n_last, int tile) {
+                                            int32_t *__restrict__ n_last, int tile,
+                                            const uint8_t *__restrict__ frozen = nullptr,
+                                            float4 *__restrict__ resume = nullptr,
+                                            int32_t *__restrict__ resume_pos = nullptr) {
     constexpr int NT = TS * TS / PPT;  // threads; B = splats per staged batch
     __shared__ float4 s_xyab[B];
     __shared__ float4 s_cocg[B];
     __shared__ float s_blue[B];
+    __shared__ int s_lu;  // the batch's last unfrozen splat (-1: none)
+    __shared__ int s_upos;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int px = tx * TS + (int)(threadIdx.x % TS);
     const uint32_t start = ranges[2 * tile], end = ranges[2 * tile + 1];
@@ -41,6 +53,8 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
     float fpy[PPT], T[PPT], c0[PPT], c1[PPT], c2[PPT];
     int last[PPT], py[PPT];
     bool done[PPT];
+    float uT[PPT], u0[PPT], u1[PPT], u2[PPT];  // T and colour after the last unfrozen splat passed
+    int upos = 0;
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
         py[k] = ty * TS + (int)(threadIdx.x / TS) + k * (TS / PPT);
@@ -49,7 +63,14 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
         c0[k] = c1[k] = c2[k] = 0.f;
         last[k] = 0;
         done[k] = !(px < cam.W && py[k] < cam.H);
+        uT[k] = 1.f;
+        u0[k] = u1[k] = u2[k] = 0.f;
     }
+    if (resume) {  // a uniform branch
+        if (threadIdx.x == 0) s_upos = 0;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s_lu = -1;  // ordered before the staging's atomics by the loop's first barrier
     for (uint32_t base = start; base < end; base += B) {
         bool all = true;
 #pragma unroll
@@ -59,18 +80,21 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
             if (base + q < end) {
                 // staged with -a/2 and -c/2 in place of a and c: the row coefficients of
                 // splat_row, rounded once here instead of once per thread
-                const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)vals[base + q] * kSplat);
+                const uint32_t g = vals[base + q];
+                const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
                 float4 xa = __ldg(r), co = __ldg(r + 1);
                 xa.z = __fmul_rn(-0.5f, xa.z);
                 co.x = __fmul_rn(-0.5f, co.x);
                 s_xyab[q] = xa;
                 s_cocg[q] = co;
                 s_blue[q] = __ldg(reinterpret_cast<const float *>(r + 2));
+                if (resume && !(frozen && frozen[g])) atomicMax(&s_lu, q);
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)B, end - base);
-        for (int j = 0; j < cnt; ++j) {
+        // One splat of the batch for this thread's pixels; false once they are all done.
+        auto blend = [&](int j) -> bool {
             const float4 xa = s_xyab[j], co = s_cocg[j];
             const float blue = s_blue[j];
             const float dx = __fsub_rn(xa.x, fpx);
@@ -97,9 +121,47 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
                 done[k] = done[k] || stop;
                 alive = alive || !done[k];
             }
-            if (!alive) break;
+            return alive;
+        };
+        // with resume, the loop runs in two parts around the batch's last unfrozen
+        // splat, recording the state after it; no test per splat
+        const int lu = resume ? s_lu : -1;
+        int j = 0;
+        bool alive = true;
+        if (lu >= 0) {
+            for (; j <= lu && alive; ++j) alive = blend(j);
+            if (alive || j == lu + 1) {  // reached the state after splat lu
+#pragma unroll
+                for (int k = 0; k < PPT; ++k) {
+                    uT[k] = T[k];
+                    u0[k] = c0[k];
+                    u1[k] = c1[k];
+                    u2[k] = c2[k];
+                }
+                upos = (int)(base - start) + lu + 1;
+            }
         }
+        for (; j < cnt && alive; ++j) alive = blend(j);
         __syncthreads();
+        if (threadIdx.x == 0) s_lu = -1;  // read by every thread before the barrier above
+    }
+    if (resume) {
+        // A thread leaves the splat loop once its own pixels are done, so it may
+        // have stopped before the tile's last unfrozen splat: its pixels are then
+        // done at that position too, with their final T and nothing blended behind.
+        if (upos > 0) atomicMax(&s_upos, upos);
+        __syncthreads();
+        const int umax = s_upos;
+        if (upos < umax) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                uT[k] = T[k];
+                u0[k] = c0[k];
+                u1[k] = c1[k];
+                u2[k] = c2[k];
+            }
+        }
+        upos = umax;
     }
     const int64_t HW = (int64_t)cam.W * cam.H;
 #pragma unroll
@@ -111,8 +173,12 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
             image[2 * HW + pix] = c2[k] + T[k] * cam.bg[2];
             t_final[pix] = T[k];
             n_last[pix] = last[k];
+            if (resume)
+                resume[pix] = make_float4(uT[k], __fsub_rn(c0[k], u0[k]), __fsub_rn(c1[k], u1[k]),
+                                          __fsub_rn(c2[k], u2[k]));
         }
     }
+    if (resume && threadIdx.x == 0) resume_pos[tile] = upos;
 }
 
 template <int TS, int PPT, int B>
@@ -120,9 +186,13 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_render_fwd(const float *__res
                                                               const uint32_t *__restrict__ vals,
                                                               const uint32_t *__restrict__ ranges, DevCam cam,
                                                               float *__restrict__ image, float *__restrict__ t_final,
-                                                              int32_t *__restrict__ n_last) {
+                                                              int32_t *__restrict__ n_last,
+                                                              const uint8_t *__restrict__ frozen,
+                                                              float4 *__restrict__ resume,
+                                                              int32_t *__restrict__ resume_pos) {
     wait_prior_grid();
-    render_tile<TS, PPT, B>(splats, vals, ranges, cam, image, t_final, n_last, blockIdx.x);
+    render_tile<TS, PPT, B>(splats, vals, ranges, cam, image, t_final, n_last, blockIdx.x, frozen, resume,
+                            resume_pos);
 }
 
 // Sum of nine per-lane values over a warp by recursive halving: at each of
@@ -160,12 +230,13 @@ __device__ __forceinline__ float warp_sum9(const float (&g)[9], int lane) {
 }
 
 // Backward state of one pixel: recovered transmittance T, dL/dC, and the
-// colour blended behind the current splat, S, kept only as D = dL/dC . S
-// (all dL/dalpha needs): with la and ldc = dL/dC . c of the last splat
-// blended behind, S' = la c + (1 - la) S becomes D' = la ldc + (1 - la) D.
+// colour blended behind the current splat, kept only as G = dL/dC . sum over
+// the splats k behind it of c_k alpha_k T_k (all dL/dalpha needs): a splat
+// with alpha and T in front of it has dL/dalpha = T dL/dC . c - (G + T_final
+// dL/dC . bg) / (1 - alpha), and adds dL/dC . c alpha T to G.
 struct PixBwd {
     float T, Tf, dC0, dC1, dC2, bgdot;
-    float D, la, ldc;
+    float G;
     int nl;
 };
 
@@ -186,10 +257,9 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row,
     if (!(pos < p.nl && power <= 0.f && alpha >= kAlphaMin)) return false;
     const float om = 1.f - alpha;
     p.T = __fdividef(p.T, om);  // transmittance in front of this splat
-    p.D = fmaf(p.la, p.ldc - p.D, p.D);
     const float dcc = p.dC0 * co.z + p.dC1 * co.w + p.dC2 * blue;
     if (!FRZ) {
-        const float dA = p.T * (dcc - p.D) - __fdividef(p.Tf, om) * p.bgdot;
+        const float dA = p.T * dcc - __fdividef(fmaf(p.Tf, p.bgdot, p.G), om);
         const float wT = alpha * p.T;
         g[6] += wT * p.dC0;
         g[7] += wT * p.dC1;
@@ -203,8 +273,7 @@ __device__ __forceinline__ bool pix_bwd(PixBwd &p, int pos, const SplatRow &row,
             g[2] += dy * ydp;
         }
     }
-    p.la = alpha;
-    p.ldc = dcc;
+    p.G = fmaf(dcc * alpha, p.T, p.G);
     return true;
 }
 
@@ -220,9 +289,14 @@ __device__ __forceinline__ void geo_grads(float (&g)[9], float dx, float a, floa
     g[4] = -0.5f * s2;
 }
 
+// The walk starts from the pixel's final state (T = T_final, nothing behind),
+// or, with resume, from the state the forward recorded after the tile's last
+// unfrozen splat (T there, and the colour blended behind it).
 __device__ __forceinline__ void pix_load(PixBwd &p, bool inside, int64_t pix, int64_t HW, const float *t_final,
-                                         const int32_t *n_last, const float *dl, const DevCam &cam) {
+                                         const int32_t *n_last, const float *dl, const float4 *resume,
+                                         const DevCam &cam) {
     p.T = 1.f; p.dC0 = p.dC1 = p.dC2 = 0.f; p.nl = 0;
+    p.G = 0.f;
     if (inside) {
         p.T = t_final[pix];
         p.nl = n_last[pix];
@@ -232,7 +306,11 @@ __device__ __forceinline__ void pix_load(PixBwd &p, bool inside, int64_t pix, in
     }
     p.Tf = p.T;
     p.bgdot = cam.bg[0] * p.dC0 + cam.bg[1] * p.dC1 + cam.bg[2] * p.dC2;
-    p.D = p.la = p.ldc = 0.f;
+    if (inside && resume) {
+        const float4 r = resume[pix];
+        p.T = r.x;
+        p.G = p.dC0 * r.y + p.dC1 * r.z + p.dC2 * r.w;
+    }
 }
 
 template <int TS, int PPT, int B>
@@ -240,7 +318,9 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
                                                 const uint32_t *__restrict__ ranges, const DevCam &cam,
                                                 const float *__restrict__ t_final, const int32_t *__restrict__ n_last,
                                                 const float *__restrict__ dl_dimage, const uint8_t *__restrict__ frozen,
-                                                float *__restrict__ grad2d, int tile) {
+                                                float *__restrict__ grad2d, int tile,
+                                                const float4 *__restrict__ resume = nullptr,
+                                                const int32_t *__restrict__ resume_pos = nullptr) {
     constexpr int NT = TS * TS / PPT;
     __shared__ float4 s_xyab[B];
     __shared__ float4 s_cocg[B];
@@ -261,14 +341,16 @@ __device__ __forceinline__ void raster_bwd_tile(const float *__restrict__ splats
     for (int k = 0; k < PPT; ++k) {
         const int py = ty * TS + (int)(threadIdx.x / TS) + k * (TS / PPT);
         fpy[k] = (float)py;
-        pix_load(p[k], px < cam.W && py < cam.H, (int64_t)py * cam.W + px, HW, t_final, n_last, dl_dimage, cam);
+        pix_load(p[k], px < cam.W && py < cam.H, (int64_t)py * cam.W + px, HW, t_final, n_last, dl_dimage, resume,
+                 cam);
         nlmax = max(nlmax, p[k].nl);
     }
     if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
     if (nlmax > 0) atomicMax(&s_maxlast, nlmax);
     __syncthreads();
-    const uint32_t rend = start + (uint32_t)s_maxlast;
+    // with resume, the frozen splats behind the last unfrozen one are skipped
+    const uint32_t rend = start + (uint32_t)(resume ? min(s_maxlast, resume_pos[tile]) : s_maxlast);
     const int lane = threadIdx.x & 31;
     const int slot = kSlotOf[(lane >> 1) & 15];
     const bool writer = slot >= 0 && !(lane & 1);
@@ -344,9 +426,12 @@ __global__ void __launch_bounds__(TS * TS / PPT) k_raster_bwd(const float *__res
                                                               const int32_t *__restrict__ n_last,
                                                               const float *__restrict__ dl_dimage,
                                                               const uint8_t *__restrict__ frozen,
-                                                              float *__restrict__ grad2d) {
+                                                              float *__restrict__ grad2d,
+                                                              const float4 *__restrict__ resume,
+                                                              const int32_t *__restrict__ resume_pos) {
     wait_prior_grid();
-    raster_bwd_tile<TS, PPT, B>(splats, vals, ranges, cam, t_final, n_last, dl_dimage, frozen, grad2d, blockIdx.x);
+    raster_bwd_tile<TS, PPT, B>(splats, vals, ranges, cam, t_final, n_last, dl_dimage, frozen, grad2d, blockIdx.x,
+                                resume, resume_pos);
 }
 
 // ---- measurement support: the (pixel, splat) pairs the backward visits ----
@@ -490,6 +575,9 @@ struct FwdArgs {
     DevCam cam;
     float *image, *t_final;
     int32_t *n_last;
+    const uint8_t *frozen;
+    float4 *resume;
+    int32_t *resume_pos;
 };
 
 struct BwdArgs {
@@ -501,18 +589,20 @@ struct BwdArgs {
     const float *dl;
     const uint8_t *frozen;
     float *grad2d;
+    const float4 *resume;
+    const int32_t *resume_pos;
 };
 
 template <int TS, int PPT, int B>
 void launch(const FwdArgs &a, cudaStream_t s) {
     launch_chained(k_render_fwd<TS, PPT, B>, a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, s, a.splats, a.vals,
-                   a.ranges, a.cam, a.image, a.t_final, a.n_last);
+                   a.ranges, a.cam, a.image, a.t_final, a.n_last, a.frozen, a.resume, a.resume_pos);
 }
 
 template <int TS, int PPT, int B>
 void launch(const BwdArgs &a, cudaStream_t s) {
     launch_chained(k_raster_bwd<TS, PPT, B>, a.cam.tiles_x * a.cam.tiles_y, TS * TS / PPT, s, a.splats, a.vals,
-                   a.ranges, a.cam, a.t_final, a.n_last, a.dl, a.frozen, a.grad2d);
+                   a.ranges, a.cam, a.t_final, a.n_last, a.dl, a.frozen, a.grad2d, a.resume, a.resume_pos);
 }
 
 struct BatchArgs {
@@ -582,17 +672,27 @@ inline bool config_ok(const gs_raster_config *c, int tile) {
 
 using namespace gs;
 
-extern "C" int gs_render_fwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
-                                 const gs_camera *cam, const gs_raster_config *cfg, float *image, float *t_final,
-                                 int32_t *n_last, gs_stream_t stream) {
+extern "C" int gs_render_fwd_resume(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                    const gs_camera *cam, const gs_raster_config *cfg, const uint8_t *frozen,
+                                    float *image, float *t_final, int32_t *n_last, float *resume,
+                                    int32_t *resume_pos, gs_stream_t stream) {
     if (!camera_ok(cam) || !config_ok(cfg, cam->tile) || !ranges || !image || !t_final || !n_last)
         return GS_ERR_INVALID_ARG;
-    if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
-    FwdArgs a{splats, vals, ranges, make_cam(cam), image, t_final, n_last};
+    if ((resume == nullptr) != (resume_pos == nullptr)) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats) | reinterpret_cast<uintptr_t>(resume)) & 15) return GS_ERR_INVALID_ARG;
+    FwdArgs a{splats, vals, ranges, make_cam(cam), image, t_final, n_last, frozen, reinterpret_cast<float4 *>(resume),
+              resume_pos};
     int ppt, batch;
     default_config(a.cam.tile, false, ppt, batch);
     if (cfg) { ppt = cfg->pixels_per_thread; batch = cfg->batch; }
     return dispatch(a.cam.tile, ppt, batch, a, as_stream(stream));
+}
+
+extern "C" int gs_render_fwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                 const gs_camera *cam, const gs_raster_config *cfg, float *image, float *t_final,
+                                 int32_t *n_last, gs_stream_t stream) {
+    return gs_render_fwd_resume(splats, vals, ranges, cam, cfg, nullptr, image, t_final, n_last, nullptr, nullptr,
+                                stream);
 }
 
 extern "C" int gs_render_fwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
@@ -600,18 +700,29 @@ extern "C" int gs_render_fwd(const float *splats, const uint32_t *vals, const ui
     return gs_render_fwd_cfg(splats, vals, ranges, cam, nullptr, image, t_final, n_last, stream);
 }
 
-extern "C" int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
-                                 const gs_camera *cam, const gs_raster_config *cfg, const float *t_final,
-                                 const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen, float *grad2d,
-                                 gs_stream_t stream) {
+extern "C" int gs_raster_bwd_resume(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                    const gs_camera *cam, const gs_raster_config *cfg, const float *t_final,
+                                    const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen,
+                                    const float *resume, const int32_t *resume_pos, float *grad2d,
+                                    gs_stream_t stream) {
     if (!camera_ok(cam) || !config_ok(cfg, cam->tile) || !ranges || !t_final || !n_last || !dl_dimage || !grad2d)
         return GS_ERR_INVALID_ARG;
-    if (reinterpret_cast<uintptr_t>(splats) & 15) return GS_ERR_INVALID_ARG;
-    BwdArgs a{splats, vals, ranges, make_cam(cam), t_final, n_last, dl_dimage, frozen, grad2d};
+    if ((resume == nullptr) != (resume_pos == nullptr)) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(splats) | reinterpret_cast<uintptr_t>(resume)) & 15) return GS_ERR_INVALID_ARG;
+    BwdArgs a{splats, vals, ranges, make_cam(cam), t_final, n_last, dl_dimage, frozen, grad2d,
+              reinterpret_cast<const float4 *>(resume), resume_pos};
     int ppt, batch;
     default_config(a.cam.tile, true, ppt, batch);
     if (cfg) { ppt = cfg->pixels_per_thread; batch = cfg->batch; }
     return dispatch(a.cam.tile, ppt, batch, a, as_stream(stream));
+}
+
+extern "C" int gs_raster_bwd_cfg(const float *splats, const uint32_t *vals, const uint32_t *ranges,
+                                 const gs_camera *cam, const gs_raster_config *cfg, const float *t_final,
+                                 const int32_t *n_last, const float *dl_dimage, const uint8_t *frozen, float *grad2d,
+                                 gs_stream_t stream) {
+    return gs_raster_bwd_resume(splats, vals, ranges, cam, cfg, t_final, n_last, dl_dimage, frozen, nullptr, nullptr,
+                                grad2d, stream);
 }
 
 extern "C" int gs_raster_bwd(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,

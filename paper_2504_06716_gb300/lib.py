@@ -82,6 +82,9 @@ _SIGS = {
     "gs_render_fwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P], _I32),
     "gs_render_fwd_cfg": ([_P, _P, _P, _CAM, ctypes.POINTER(GsRasterConfig), _P, _P, _P, _P], _I32),
     "gs_raster_bwd_cfg": ([_P, _P, _P, _CAM, ctypes.POINTER(GsRasterConfig), _P, _P, _P, _P, _P, _P], _I32),
+    "gs_render_fwd_resume": ([_P, _P, _P, _CAM, ctypes.POINTER(GsRasterConfig), _P, _P, _P, _P, _P, _P, _P], _I32),
+    "gs_raster_bwd_resume": ([_P, _P, _P, _CAM, ctypes.POINTER(GsRasterConfig), _P, _P, _P, _P, _P, _P, _P, _P],
+                             _I32),
     "gs_loss_workspace_bytes": ([_I32, _I32], _SZ),
     "gs_loss": ([_P, _P, _I32, _I32, _F32, _P, _SZ, _P, _P, _P], _I32),
     "gs_raster_bwd": ([_P, _P, _P, _CAM, _P, _P, _P, _P, _P, _P], _I32),
@@ -232,6 +235,30 @@ def gs_render_fwd_cfg(splats, vals, ranges, cam: GsCamera, cfg, image, t_final, 
         _ptr(t_final, torch.float32, "t_final"), _ptr(n_last, torch.int32, "n_last"), _stream(stream)))
 
 
+def gs_render_fwd_resume(splats, vals, ranges, cam: GsCamera, cfg, frozen, image, t_final, n_last, resume,
+                         resume_pos, stream=None):
+    import torch
+
+    _check("gs_render_fwd_resume", load().gs_render_fwd_resume(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), None if cfg is None else ctypes.byref(cfg), _ptr(frozen, torch.uint8, "frozen"),
+        _ptr(image, torch.float32, "image"), _ptr(t_final, torch.float32, "t_final"),
+        _ptr(n_last, torch.int32, "n_last"), _ptr(resume, torch.float32, "resume"),
+        _ptr(resume_pos, torch.int32, "resume_pos"), _stream(stream)))
+
+
+def gs_raster_bwd_resume(splats, vals, ranges, cam: GsCamera, cfg, t_final, n_last, dl_dimage, frozen, resume,
+                         resume_pos, grad2d, stream=None):
+    import torch
+
+    _check("gs_raster_bwd_resume", load().gs_raster_bwd_resume(
+        _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
+        ctypes.byref(cam), None if cfg is None else ctypes.byref(cfg), _ptr(t_final, torch.float32, "t_final"),
+        _ptr(n_last, torch.int32, "n_last"), _ptr(dl_dimage, torch.float32, "dl_dimage"),
+        _ptr(frozen, torch.uint8, "frozen"), _ptr(resume, torch.float32, "resume"),
+        _ptr(resume_pos, torch.int32, "resume_pos"), _ptr(grad2d, torch.float32, "grad2d"), _stream(stream)))
+
+
 def gs_raster_bwd_cfg(splats, vals, ranges, cam: GsCamera, cfg, t_final, n_last, dl_dimage, frozen, grad2d,
                       stream=None):
     import torch
@@ -307,14 +334,15 @@ class GsStep(ctypes.Structure):
         ("n_last", ctypes.c_void_p), ("dl_dimage", ctypes.c_void_p), ("loss_ws", ctypes.c_void_p),
         ("loss_ws_bytes", ctypes.c_size_t), ("loss_dev", ctypes.c_void_p), ("lambda_ssim", ctypes.c_float),
         ("fwd", GsRasterConfig), ("bwd", GsRasterConfig), ("b1", ctypes.c_float), ("b2", ctypes.c_float),
-        ("eps", ctypes.c_float), ("bwd_events", ctypes.c_void_p * 2),
+        ("eps", ctypes.c_float), ("bwd_events", ctypes.c_void_p * 2), ("resume", ctypes.c_void_p),
+        ("resume_pos", ctypes.c_void_p),
     ]
 
 
 def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: int, frozen, act, n_active, stats,
               sort_ws, capacity: int, vals, ranges, count, image, t_final, n_last, dl, loss_ws, loss, lam: float = 0.2,
               fwd=None, bwd=None, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-15, mask_loss: float = 0.0,
-              n_lr: int = 6) -> GsStep:
+              n_lr: int = 6, resume=None, resume_pos=None) -> GsStep:
     """A gs_step for gs_train_step (tensors checked here once; the caller keeps them alive)."""
     import torch
 
@@ -340,6 +368,9 @@ def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: i
     s.fwd = fwd if fwd is not None else GsRasterConfig(0, 0)
     s.bwd = bwd if bwd is not None else GsRasterConfig(0, 0)
     s.b1, s.b2, s.eps = b1, b2, eps
+    if (resume is None) != (resume_pos is None):
+        raise ValueError("resume and resume_pos go together")
+    s.resume, s.resume_pos = _ptr(resume, f32, "resume"), _ptr(resume_pos, i32, "resume_pos")
     return s
 
 

@@ -57,6 +57,10 @@ class View:
     count: torch.Tensor
     sort_ws: torch.Tensor
     capacity: int
+    # the forward's record of where the backward resumes (trainable views;
+    # gs_render_fwd_resume): [H W 4] float, [tiles] int32
+    resume: torch.Tensor | None = None
+    resume_pos: torch.Tensor | None = None
 
 
 class Model:
@@ -266,6 +270,8 @@ class Model:
             count=torch.zeros(1, dtype=torch.int64, device=dev),
             sort_ws=torch.zeros(lib.gs_sort_workspace_bytes(self.cap, capacity, cam), dtype=torch.uint8, device=dev),
             capacity=capacity,
+            resume=torch.zeros(H * W * 4, dtype=torch.float32, device=dev) if trainable else None,
+            resume_pos=torch.zeros(cam.tiles, dtype=torch.int32, device=dev) if trainable else None,
         )
 
     def retarget(self, view: View, cam: lib.GsCamera) -> View:
@@ -282,16 +288,36 @@ class Model:
         lib.gs_project_ex(self.P, self.n, self.sh_degree, self.opacity_act, view.cam, self.splats, stream)
         lib.gs_sort(self.splats, self.n, view.cam, view.sort_ws, view.capacity, view.vals, view.ranges, view.count,
                     stream)
-        lib.gs_render_fwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.fwd_cfg, view.image, view.t_final,
-                              view.n_last, stream)
+        self.render_fwd(view, stream)
+
+    def render_fwd(self, view: View, cfg=None, stream=None):
+        """The compositing forward; on a trainable view it also records where
+        the backward resumes (gs_render_fwd_resume)."""
+        cfg = self.fwd_cfg if cfg is None else cfg
+        if view.resume is not None:
+            lib.gs_render_fwd_resume(self.splats, view.vals, view.ranges, view.cam, cfg, self.frozen, view.image,
+                                     view.t_final, view.n_last, view.resume, view.resume_pos, stream)
+        else:
+            lib.gs_render_fwd_cfg(self.splats, view.vals, view.ranges, view.cam, cfg, view.image, view.t_final,
+                                  view.n_last, stream)
+
+    def raster_bwd(self, view: View, cfg=None, stream=None):
+        """The rasteriser backward, from the forward's resume record when the
+        view has one (the frozen splats behind a tile's last unfrozen one skipped)."""
+        cfg = self.bwd_cfg if cfg is None else cfg
+        if view.resume is not None:
+            lib.gs_raster_bwd_resume(self.splats, view.vals, view.ranges, view.cam, cfg, view.t_final, view.n_last,
+                                     view.dl, self.frozen, view.resume, view.resume_pos, self.grad2d, stream)
+        else:
+            lib.gs_raster_bwd_cfg(self.splats, view.vals, view.ranges, view.cam, cfg, view.t_final, view.n_last,
+                                  view.dl, self.frozen, self.grad2d, stream)
 
     def loss(self, view: View, gt: torch.Tensor, lam: float = 0.2, stream=None):
         lib.gs_loss(view.image, gt, view.cam.height, view.cam.width, lam, view.loss_ws, view.loss, view.dl, stream)
 
     def backward(self, view: View, stats: bool = True, stream=None):
         """gs_render_bwd, as its two halves so that the tuned launch shape applies."""
-        lib.gs_raster_bwd_cfg(self.splats, view.vals, view.ranges, view.cam, self.bwd_cfg, view.t_final, view.n_last,
-                              view.dl, self.frozen, self.grad2d, stream)
+        self.raster_bwd(view, stream=stream)
         self.project_backward(view, stats, stream)
 
     def project_backward(self, view: View, stats: bool = True, stream=None):
@@ -351,7 +377,8 @@ class Model:
                                        self.sh_degree, self.opacity_act, self.frozen, self.act, self.n_active, stats,
                                        view.sort_ws, view.capacity, view.vals, view.ranges, view.count, view.image,
                                        view.t_final, view.n_last, view.dl, view.loss_ws, view.loss, 0.2, self.fwd_cfg,
-                                       self.bwd_cfg, mask_loss=self.mask_loss, n_lr=7 if self.mask_lr else 6)
+                                       self.bwd_cfg, mask_loss=self.mask_loss, n_lr=7 if self.mask_lr else 6,
+                                       resume=view.resume, resume_pos=view.resume_pos)
             self._step_key = key
         return self._step
 
