@@ -370,8 +370,10 @@ def gpu_arm(args):
     achieved = ops / (rb_mean / 1e3) / 1e12
     roofline = dict(bound="alu", kernel="k_raster_bwd", achieved=achieved, peak=alu_peak, unit="TFLOP/s",
                     frac=achieved / alu_peak, traffic=raster_bwd_traffic(),
-                    work_per_unit=f"FP32 lane-instructions per (pixel, splat) pair over each pixel's list up to its"
-                                  f" last contributor: {OPS_BLENDED_ACTIVE} blended by an unfrozen splat,"
+                    work_per_unit=f"FP32 lane-instructions per (pixel, splat) pair the backward walks: each"
+                                  f" pixel's list up to its last contributor or to just behind the tile's last"
+                                  f" unfrozen entry (the frozen splats behind it are skipped): {OPS_BLENDED_ACTIVE}"
+                                  f" blended by an unfrozen splat,"
                                   f" {OPS_BLENDED_FROZEN} by a frozen one, {OPS_SKIPPED} skipped; per launch"
                                   f" {pc[0]:.3e} / {pc[1]:.3e} / {pc[2]:.3e} pairs (gs_raster_pair_counts,"
                                   f" freeze map at the end of the timed region)",
@@ -432,8 +434,8 @@ def gpu_arm(args):
 # gives the command). Valid only for the kernel sources it was taken on: the
 # digest of those files is compared at run time and traffic is reported as null
 # once they have changed.
-RASTER_BWD_TRAFFIC = dict(bytes_per_launch=77951147,
-                          sources_sha256="2fc405011f464c5a6b8ead47ae04a112cee2bd8919cd61e50bbf2d7e49e32eb9")
+RASTER_BWD_TRAFFIC = dict(bytes_per_launch=85856427,
+                          sources_sha256="734913ff3a9cf2b58b7dcb785d805fae371dcb1c19e8b7588f3a3bc26313ffc4")
 RASTER_BWD_SOURCES = ("paper_2504_06716_gb300/csrc/render.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 # The same for Adam and the projection (profiles/k_adam_traffic_surface-1M-1237x822.md,
 # profiles/k_project_fwd_traffic_surface-1M-1237x822.md):
@@ -483,13 +485,16 @@ def project_traffic(algorithmic_bytes: float):
 
 
 # Algorithmic FP32 work of the rasteriser backward per (pixel, splat) pair, counted
-# from its formula. Every pair: offset (2), exponent (8), exp and opacity (3),
-# alpha floor/cap tests (3) = 16, all a skipped pair costs. A blended pair adds the
-# transmittance recovery (2) and the colour-behind update (9) = 27, all a frozen
-# splat's pair costs (no gradient, Sec. 3.2.4); an unfrozen splat's pair adds
-# dL/dalpha (10), colour gradient (4), opacity/exponent gradient (3), conic and
-# mean gradients (12) = 56.
-OPS_SKIPPED, OPS_BLENDED_FROZEN, OPS_BLENDED_ACTIVE = 16, 27, 56
+# from its formula (an FMA as two). Every pair: offset (2), exponent (8), exp and
+# opacity (3), alpha floor/cap tests (3) = 16, all a skipped pair costs. A blended
+# pair adds the transmittance recovery (2) and the colour-behind sum (dL/dC . c: 5,
+# times alpha and T into the sum: 3) = 26, all a frozen splat's pair costs (no
+# gradient, Sec. 3.2.4); an unfrozen splat's pair adds dL/dalpha (6), the colour
+# gradient (7), the opacity and exponent moments (8) and its share of the conic
+# and mean gradients formed from those moments (6) = 53. The pairs counted are the
+# ones the resuming backward walks: each pixel's list up to its last contributor or
+# to just behind the tile's last unfrozen entry, whichever comes first.
+OPS_SKIPPED, OPS_BLENDED_FROZEN, OPS_BLENDED_ACTIVE = 16, 26, 53
 
 
 def pair_counts(tr, views) -> list[float]:

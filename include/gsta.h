@@ -571,14 +571,16 @@ int gs_adam_masked_devstep(float *P, const float *G, float *m, float *v, int64_t
                            int64_t *step_dev, float *scratch_dev, gs_stream_t stream);
 
 /* Measurement support (the paper has no counterpart): classifies the
- * (pixel, splat) pairs of every pixel's tile list up to its last contributor
- * (n_last, as left by gs_render_fwd) with the forward's own decisions, and
- * ADDS the counts to counts_dev [3] (uint64, device): [0] blended by an
- * unfrozen splat, [1] blended by a frozen splat, [2] skipped (positive
- * exponent or alpha < 1/255). These are the pairs the rasteriser backward
- * evaluates; a benchmark weighs them by their arithmetic to state the
- * backward's algorithmic work. frozen may be NULL. Errors: INVALID_ARG,
- * CUDA. */
+ * (pixel, splat) pairs of every pixel's tile list with the forward's own
+ * decisions, up to its last contributor (n_last, as left by gs_render_fwd)
+ * or, if that is less, 1 + the tile's last unfrozen entry among the first
+ * max(n_last over the tile) -- the pairs gs_raster_bwd_resume walks, or a
+ * lower bound of them; with frozen NULL, every pair up to the last
+ * contributor (gs_raster_bwd's walk) -- and ADDS the counts to counts_dev
+ * [3] (uint64, device): [0] blended by an unfrozen splat, [1] blended by a
+ * frozen splat, [2] skipped (positive exponent or alpha < 1/255). A
+ * benchmark weighs them by their arithmetic to state the backward's
+ * algorithmic work. Errors: INVALID_ARG, CUDA. */
 int gs_raster_pair_counts(const float *splats, const uint32_t *vals, const uint32_t *ranges, const gs_camera *cam,
                           const int32_t *n_last, const uint8_t *frozen, uint64_t *counts_dev, gs_stream_t stream);
 

@@ -471,33 +471,50 @@ __global__ void k_hit_counts(const float *__restrict__ splats, const uint32_t *_
     }
 }
 
-// One CTA per tile, one thread per pixel, walking the pixel's list up to its
-// last contributor with the forward's own decisions.
+// One CTA per tile, one thread per pixel, walking the pixel's list with the
+// forward's own decisions up to where the resuming backward walks it: the
+// pixel's last contributor, or with a freeze map 1 + the tile's last unfrozen
+// entry among those the tile's deepest contributor reaches, if that is less
+// (a lower bound of the backward's walk, which may go on to the deepest
+// contributor when an unfrozen entry lies further on in the list).
+__device__ __forceinline__ bool pair_blended(const float *__restrict__ splats, uint32_t g, float fpx, float fpy) {
+    const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
+    const float4 xa = __ldg(r), co = __ldg(r + 1);
+    const float power = splat_power(splat_row(__fsub_rn(xa.x, fpx), xa.z, xa.w, co.x), __fsub_rn(xa.y, fpy));
+    const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
+    return power <= 0.f && alpha >= kAlphaMin;
+}
+
 __global__ void k_pair_counts(const float *__restrict__ splats, const uint32_t *__restrict__ vals,
                               const uint32_t *__restrict__ ranges, DevCam cam, const int32_t *__restrict__ n_last,
                               const uint8_t *__restrict__ frozen, unsigned long long *__restrict__ counts) {
     __shared__ unsigned long long s_c[3];
+    __shared__ int s_maxnl, s_lu;
     if (threadIdx.x < 3) s_c[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) { s_maxnl = 0; s_lu = -1; }
     __syncthreads();
     const int tile = blockIdx.x, TS = cam.tile;
     const int px = (tile % cam.tiles_x) * TS + (int)(threadIdx.x % TS);
     const int py = (tile / cam.tiles_x) * TS + (int)(threadIdx.x / TS);
+    const bool inside = px < cam.W && py < cam.H;
+    const int nl = inside ? n_last[(int64_t)py * cam.W + px] : 0;
+    const uint32_t start = ranges[2 * tile];
+    if (nl > 0) atomicMax(&s_maxnl, nl);
+    __syncthreads();
+    if (frozen) {
+        for (int j = (int)threadIdx.x; j < s_maxnl; j += (int)blockDim.x)
+            if (!frozen[vals[start + j]]) atomicMax(&s_lu, j);
+        __syncthreads();
+    }
+    const int upto = frozen ? min(nl, s_lu + 1) : nl;
     uint32_t c[3] = {0u, 0u, 0u};
-    if (px < cam.W && py < cam.H) {
-        const uint32_t start = ranges[2 * tile];
-        const int nl = n_last[(int64_t)py * cam.W + px];
-        const float fpx = (float)px, fpy = (float)py;
-        for (int j = 0; j < nl; ++j) {
-            const uint32_t g = vals[start + j];
-            const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
-            const float4 xa = __ldg(r), co = __ldg(r + 1);
-            const float power = splat_power(splat_row(__fsub_rn(xa.x, fpx), xa.z, xa.w, co.x), __fsub_rn(xa.y, fpy));
-            const float alpha = fminf(kAlphaMax, __fmul_rn(co.y, __expf(power)));
-            if (power <= 0.f && alpha >= kAlphaMin)
-                ++c[frozen && frozen[g] ? 1 : 0];
-            else
-                ++c[2];
-        }
+    const float fpx = (float)px, fpy = (float)py;
+    for (int j = 0; j < upto; ++j) {
+        const uint32_t g = vals[start + j];
+        if (pair_blended(splats, g, fpx, fpy))
+            ++c[frozen && frozen[g] ? 1 : 0];
+        else
+            ++c[2];
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

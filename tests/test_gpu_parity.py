@@ -344,7 +344,10 @@ def test_render_forward_matches_oracle(kind, tile, bg):
 @pytest.mark.parametrize("kind,tile", [("tiny", 16), ("surface", 8)])
 def test_pair_counts_match_oracle_decisions(kind, tile):
     """gs_raster_pair_counts (measurement support) against the oracle's own
-    record of every decision up to each pixel's last contributor."""
+    record of every decision, over the pairs the resuming backward walks:
+    each pixel's list up to its last contributor or 1 + the tile's last
+    unfrozen entry among the first (deepest contributor) ones, whichever is
+    less; with no freeze map, up to the last contributor."""
     P, cams = _scene(kind)
     ocam, gcam = pu.cameras(cams[0], tile=tile)
     rec = pu.records_from_oracle(oracle.project(P, ocam))
@@ -367,13 +370,28 @@ def test_pair_counts_match_oracle_decisions(kind, tile):
     inside = pos < nlo[:, None]
     g = vals[np.minimum(starts[:, None] + pos, max(Pn - 1, 0))]
     blended = inside & ((dec == 1) | (dec == 2))
-    want_c = np.array([(blended & (frozen[g] == 0)).sum(), (blended & (frozen[g] == 1)).sum(),
-                       (inside & (dec == 0)).sum()])
+    # walked: up to min(n_last, 1 + the tile's last unfrozen entry below its deepest n_last)
+    tl = tiles.ravel()
+    maxnl = np.zeros(int(tl.max()) + 1, np.int64)
+    np.maximum.at(maxnl, tl, nlo)
+    lu = np.full(maxnl.shape[0], -1, np.int64)
+    for t in np.nonzero(maxnl)[0]:
+        e = frozen[vals[ranges[t, 0]:ranges[t, 0] + maxnl[t]]] == 0
+        if e.any():
+            lu[t] = int(np.nonzero(e)[0][-1])
+    upto = np.minimum(nlo, lu[tl] + 1)
+    need = pos < upto[:, None]
+    want_c = np.array([(need & blended & (frozen[g] == 0)).sum(), (need & blended & (frozen[g] == 1)).sum(),
+                       (need & inside & (dec == 0)).sum()])
     # pixels whose decisions are within float32 reach may count either way
     amb = (want["margin"] <= pu.PIXEL_MARGIN).ravel()
     slack = int(nlo[amb].sum() + nl.ravel()[amb].sum())
     assert np.abs(got - want_c).sum() <= slack, (got, want_c, slack)
-    assert got.sum() == nl.astype(np.int64).sum()
+    assert want_c.sum() < inside.sum()  # the freeze map leaves pairs out
+    # with no freeze map: every pair up to each pixel's last contributor
+    counts.zero_()
+    lib.gs_raster_pair_counts(spl, vt, rt, gcam, torch.from_numpy(nl).to(DEV), None, counts)
+    assert int(counts.sum().item()) == nl.astype(np.int64).sum()
 
 
 # ----------------------------------------------------------------------------- A4 loss
