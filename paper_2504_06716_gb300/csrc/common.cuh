@@ -58,6 +58,40 @@ void note_launches(int k);
 
 inline int launch_status() { return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
 
+// Two float32 values in one 64-bit register pair, and the packed FP32
+// instructions of sm_100 and later (add/sub/mul/fma .rn .f32x2): each half is
+// rounded exactly as the scalar __fadd_rn / __fsub_rn / __fmul_rn / __fmaf_rn
+// of the same operands, and one instruction issues both.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Programmatic dependent launch: a kernel started by launch_chained may be
 // scheduled while the kernel before it in the stream is still finishing, so
 // that its launch overlaps that kernel's last blocks. It must call

@@ -41,9 +41,16 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
                                             float4 *__restrict__ resume = nullptr,
                                             int32_t *__restrict__ resume_pos = nullptr) {
     constexpr int NT = TS * TS / PPT;  // threads; B = splats per staged batch
-    __shared__ float4 s_xyab[B];
-    __shared__ float4 s_cocg[B];
-    __shared__ float s_blue[B];
+    // With an even number of pixels per thread, the pixels go in pairs through
+    // the packed FP32 instructions (f2_*), and each splat is staged with every
+    // value duplicated into both halves of a 64-bit pair.
+    constexpr bool kPair = PPT % 2 == 0;
+    constexpr int NP = kPair ? PPT / 2 : 1;
+    __shared__ float4 s_xyab[kPair ? 1 : B];
+    __shared__ float4 s_cocg[kPair ? 1 : B];
+    __shared__ float s_blue[kPair ? 1 : B];
+    __shared__ ulonglong2 s_pk[kPair ? 4 * B : 1];  // (mx, my), (-a/2, -b), (-c/2, o), (r, g), each duplicated
+    __shared__ f32x2 s_pb[kPair ? B : 1];           // (blue, blue)
     __shared__ int s_lu;  // the batch's last unfrozen splat (-1: none)
     __shared__ int s_upos;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
@@ -66,6 +73,27 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
         uT[k] = 1.f;
         u0[k] = u1[k] = u2[k] = 0.f;
     }
+    // packed state of pixel pairs (2h, 2h + 1); the scalar arrays are brought up
+    // to date from it where they are read (the resume record and the end)
+    f32x2 T2[NP], r2[NP], g2[NP], b2[NP], fpy2[NP];
+    const f32x2 fpx2 = f2_pack(fpx, fpx), one2 = f2_pack(1.f, 1.f);
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        T2[h] = one2;
+        r2[h] = g2[h] = b2[h] = f2_pack(0.f, 0.f);
+        fpy2[h] = kPair ? f2_pack(fpy[2 * h], fpy[(2 * h + 1) % PPT]) : 0ull;
+    }
+    auto to_scalar = [&]() {
+        if constexpr (kPair) {
+#pragma unroll
+            for (int h = 0; h < NP; ++h) {
+                f2_unpack(T2[h], T[2 * h], T[2 * h + 1]);
+                f2_unpack(r2[h], c0[2 * h], c0[2 * h + 1]);
+                f2_unpack(g2[h], c1[2 * h], c1[2 * h + 1]);
+                f2_unpack(b2[h], c2[2 * h], c2[2 * h + 1]);
+            }
+        }
+    };
     if (resume) {  // a uniform branch
         if (threadIdx.x == 0) s_upos = 0;
         __syncthreads();
@@ -83,11 +111,20 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
                 const uint32_t g = vals[base + q];
                 const float4 *r = reinterpret_cast<const float4 *>(splats + (int64_t)g * kSplat);
                 float4 xa = __ldg(r), co = __ldg(r + 1);
+                const float blue = __ldg(reinterpret_cast<const float *>(r + 2));
                 xa.z = __fmul_rn(-0.5f, xa.z);
                 co.x = __fmul_rn(-0.5f, co.x);
-                s_xyab[q] = xa;
-                s_cocg[q] = co;
-                s_blue[q] = __ldg(reinterpret_cast<const float *>(r + 2));
+                if constexpr (kPair) {
+                    s_pk[4 * q] = make_ulonglong2(f2_pack(xa.x, xa.x), f2_pack(xa.y, xa.y));
+                    s_pk[4 * q + 1] = make_ulonglong2(f2_pack(xa.z, xa.z), f2_pack(-xa.w, -xa.w));
+                    s_pk[4 * q + 2] = make_ulonglong2(f2_pack(co.x, co.x), f2_pack(co.y, co.y));
+                    s_pk[4 * q + 3] = make_ulonglong2(f2_pack(co.z, co.z), f2_pack(co.w, co.w));
+                    s_pb[q] = f2_pack(blue, blue);
+                } else {
+                    s_xyab[q] = xa;
+                    s_cocg[q] = co;
+                    s_blue[q] = blue;
+                }
                 if (resume && !(frozen && frozen[g])) atomicMax(&s_lu, q);
             }
         }
@@ -123,14 +160,61 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
             }
             return alive;
         };
+        // The same for a pair of pixels per packed instruction: every rounded
+        // operation is the scalar one's, so the results are bit for bit those of
+        // blend (the exponential stays scalar).
+        auto blend2 = [&](int j) -> bool {
+            const ulonglong2 q0 = s_pk[4 * j], q1 = s_pk[4 * j + 1], q2 = s_pk[4 * j + 2], q3 = s_pk[4 * j + 3];
+            const f32x2 qb = s_pb[j];
+            const f32x2 dx2 = f2_sub(q0.x, fpx2);
+            const f32x2 rc0 = f2_mul(q1.x, f2_mul(dx2, dx2)), rc1 = f2_mul(q1.y, dx2);
+            bool alive = false;
+#pragma unroll
+            for (int h = 0; h < NP; ++h) {
+                const int ka = 2 * h, kb = (2 * h + 1) % PPT;
+                const f32x2 dy2 = f2_sub(q0.y, fpy2[h]);
+                const f32x2 pw2 = f2_fma(f2_fma(q2.x, dy2, rc1), dy2, rc0);
+                float pa, pb;
+                f2_unpack(pw2, pa, pb);
+                float oa, ob;
+                f2_unpack(f2_mul(q2.y, f2_pack(__expf(pa), __expf(pb))), oa, ob);
+                const float aa = fminf(kAlphaMax, oa), ab = fminf(kAlphaMax, ob);
+                const f32x2 al2 = f2_pack(aa, ab);
+                float tna, tnb, ata, atb, Ta, Tb;
+                f2_unpack(f2_mul(T2[h], f2_sub(one2, al2)), tna, tnb);
+                f2_unpack(f2_mul(al2, T2[h]), ata, atb);
+                f2_unpack(T2[h], Ta, Tb);
+                const bool usea = !done[ka] && pa <= 0.f && aa >= kAlphaMin;
+                const bool useb = !done[kb] && pb <= 0.f && ab >= kAlphaMin;
+                const bool stopa = usea && tna < kTMin, stopb = useb && tnb < kTMin;
+                const bool adda = usea && !stopa, addb = useb && !stopb;
+                const f32x2 w2 = f2_pack(adda ? ata : 0.f, addb ? atb : 0.f);
+                r2[h] = f2_fma(q3.x, w2, r2[h]);
+                g2[h] = f2_fma(q3.y, w2, g2[h]);
+                b2[h] = f2_fma(qb, w2, b2[h]);
+                T2[h] = f2_pack(adda ? tna : Ta, addb ? tnb : Tb);
+                const int idx = (int)(base - start) + j + 1;
+                last[ka] = adda ? idx : last[ka];
+                last[kb] = addb ? idx : last[kb];
+                done[ka] = done[ka] || stopa;
+                done[kb] = done[kb] || stopb;
+                alive = alive || !done[ka] || !done[kb];
+            }
+            return alive;
+        };
+        auto step = [&](int jj) -> bool {
+            if constexpr (kPair) return blend2(jj);
+            else return blend(jj);
+        };
         // with resume, the loop runs in two parts around the batch's last unfrozen
         // splat, recording the state after it; no test per splat
         const int lu = resume ? s_lu : -1;
         int j = 0;
         bool alive = true;
         if (lu >= 0) {
-            for (; j <= lu && alive; ++j) alive = blend(j);
+            for (; j <= lu && alive; ++j) alive = step(j);
             if (alive || j == lu + 1) {  // reached the state after splat lu
+                to_scalar();
 #pragma unroll
                 for (int k = 0; k < PPT; ++k) {
                     uT[k] = T[k];
@@ -141,10 +225,11 @@ __device__ __forceinline__ void render_tile(const float *__restrict__ splats, co
                 upos = (int)(base - start) + lu + 1;
             }
         }
-        for (; j < cnt && alive; ++j) alive = blend(j);
+        for (; j < cnt && alive; ++j) alive = step(j);
         __syncthreads();
         if (threadIdx.x == 0) s_lu = -1;  // read by every thread before the barrier above
     }
+    to_scalar();
     if (resume) {
         // A thread leaves the splat loop once its own pixels are done, so it may
         // have stopped before the tile's last unfrozen splat: its pixels are then
