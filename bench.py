@@ -434,19 +434,19 @@ def gpu_arm(args):
 # gives the command). Valid only for the kernel sources it was taken on: the
 # digest of those files is compared at run time and traffic is reported as null
 # once they have changed.
-RASTER_BWD_TRAFFIC = dict(bytes_per_launch=85856427,
-                          sources_sha256="734913ff3a9cf2b58b7dcb785d805fae371dcb1c19e8b7588f3a3bc26313ffc4")
+RASTER_BWD_TRAFFIC = dict(bytes_per_launch=86249472,
+                          sources_sha256="bc6c9ed3d5d8c517458d919f3c4d49d3f942f36aafcd9879d92b9a0f869007bb")
 RASTER_BWD_SOURCES = ("paper_2504_06716_gb300/csrc/render.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 # The same for Adam and the projection (profiles/k_adam_traffic_surface-1M-1237x822.md,
 # profiles/k_project_fwd_traffic_surface-1M-1237x822.md):
 # DRAM bytes per launch of three captured launches, with the launch's units
 # (active Gaussians; the projection's algorithmic bytes), so that a run on
 # another state scales the traffic by its own units.
-ADAM_TRAFFIC = dict(bytes_per_launch=54905941, active=51957,
-                    sources_sha256="f4427d4d6e48285976e19cf4f231892ddbf9b135e5266f21d5773d65ae72834c")
+ADAM_TRAFFIC = dict(bytes_per_launch=54777856, active=52186,
+                    sources_sha256="9d8ebeb61c1b3774cceebad5438ced7db05608feaa78eef00845ec0860717c55")
 ADAM_SOURCES = ("paper_2504_06716_gb300/csrc/optim.cu", "paper_2504_06716_gb300/csrc/common.cuh")
-PROJECT_TRAFFIC = dict(bytes_per_launch=281083136, algorithmic_bytes=253244083,
-                       sources_sha256="ea098f45eebc9a528634cb8691bb351e975e2e63371b2853b3c1b65eb2594e69")
+PROJECT_TRAFFIC = dict(bytes_per_launch=280659627, algorithmic_bytes=252735533,
+                       sources_sha256="ebe0ce4ab160cf25a187e3a33c2d647e92ac4bb162f39343f6b5a945f363c0aa")
 PROJECT_SOURCES = ("paper_2504_06716_gb300/csrc/project.cu", "paper_2504_06716_gb300/csrc/common.cuh")
 
 

@@ -41,7 +41,7 @@ def _built():
     lib.load()
 
 
-def _run(st, resume: bool):
+def _run(st, resume: bool, cfg=None):
     """Forward and backward of one staged view, plain or with the resume record."""
     gcam = st["gcam"]
     n = st["P"].shape[0]
@@ -57,11 +57,11 @@ def _run(st, resume: bool):
     dl = torch.from_numpy(st["dl"].astype(np.float32)).to(DEV)
     g2 = torch.zeros((n, 12), device=DEV)
     if resume:
-        lib.gs_render_fwd_resume(st["spl"], vals, ranges, gcam, None, fr, img, tf, nl, rs, rp)
-        lib.gs_raster_bwd_resume(st["spl"], vals, ranges, gcam, None, tf, nl, dl, fr, rs, rp, g2)
+        lib.gs_render_fwd_resume(st["spl"], vals, ranges, gcam, cfg, fr, img, tf, nl, rs, rp)
+        lib.gs_raster_bwd_resume(st["spl"], vals, ranges, gcam, cfg, tf, nl, dl, fr, rs, rp, g2)
     else:
-        lib.gs_render_fwd_cfg(st["spl"], vals, ranges, gcam, None, img, tf, nl)
-        lib.gs_raster_bwd_cfg(st["spl"], vals, ranges, gcam, None, tf, nl, dl, fr, g2)
+        lib.gs_render_fwd_cfg(st["spl"], vals, ranges, gcam, cfg, img, tf, nl)
+        lib.gs_raster_bwd_cfg(st["spl"], vals, ranges, gcam, cfg, tf, nl, dl, fr, g2)
     torch.cuda.synchronize()
     assert lib.gs_get_device_error() == 0
     out = dict(img=img.cpu().numpy(), tf=tf.cpu().numpy(), nl=nl.cpu().numpy(), g2=g2.cpu().numpy())
@@ -147,3 +147,22 @@ def test_resume_buffers_go_together():
     rs = torch.zeros(H * W * 4, device=DEV)
     with pytest.raises(lib.GsError):
         lib.gs_render_fwd_resume(st["spl"], vals, ranges, gcam, None, None, img, tf, nl, rs, None)
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_resume_record_is_the_same_for_every_launch_shape(tile):
+    """Pixels per thread (the packed two-pixel forward included) and batch size
+    change only the launch shape: the record and the forward are bit-identical
+    across them, the gradients equal up to atomic reordering."""
+    st = tp._stage_inputs("surface", tile, frozen_frac=0.9, seed=6)
+    ref = None
+    for ppt in (1, 2, 4) if tile >= 16 else (1, 2):
+        for batch in (32, 64, 128, 256):
+            out = _run(st, True, lib.raster_config(ppt, batch))
+            if ref is None:
+                ref = out
+                continue
+            for key in ("img", "tf", "nl", "rp", "rs"):
+                assert np.array_equal(out[key], ref[key]), (ppt, batch, key)
+            good, worst = pu.close(out["g2"], ref["g2"], 1e-4, 1e-3 * np.abs(ref["g2"]).max())
+            assert good, (ppt, batch, worst)
