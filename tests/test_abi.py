@@ -89,6 +89,33 @@ def test_host_validation_rejects_bad_arguments_without_launching(cdll):
     assert L.gs_loss_workspace_bytes(8, 8) > 0
 
 
+def test_host_validation_of_the_resume_calls(cdll):
+    """The resume record's two buffers go together and the per-pixel one is
+    16-byte aligned; both are checked on the host before any launch (the
+    addresses below are host stand-ins that a passing call would never get)."""
+    from paper_2504_06716_gb300 import lib
+
+    lib.load()
+    L = lib._lib
+    cam = lib.GsCamera()
+    cam.width, cam.height, cam.tile, cam.fx, cam.fy = 64, 64, 16, 50.0, 50.0
+    buf = ctypes.create_string_buffer(4096)
+    a = (ctypes.addressof(buf) + 255) & ~255  # 256-byte aligned stand-in
+    p = ctypes.c_void_p
+    # resume without resume_pos, resume_pos without resume
+    assert L.gs_render_fwd_resume(p(a), p(a), p(a), ctypes.byref(cam), None, None, p(a), p(a), p(a), p(a), None,
+                                  None) == 1
+    assert L.gs_render_fwd_resume(p(a), p(a), p(a), ctypes.byref(cam), None, None, p(a), p(a), p(a), None, p(a),
+                                  None) == 1
+    assert L.gs_raster_bwd_resume(p(a), p(a), p(a), ctypes.byref(cam), None, p(a), p(a), p(a), None, p(a), None,
+                                  p(a), None) == 1
+    # a resume record that is not 16-byte aligned
+    assert L.gs_render_fwd_resume(p(a), p(a), p(a), ctypes.byref(cam), None, None, p(a), p(a), p(a), p(a + 4),
+                                  p(a), None) == 1
+    assert L.gs_raster_bwd_resume(p(a), p(a), p(a), ctypes.byref(cam), None, p(a), p(a), p(a), None, p(a + 4),
+                                  p(a), p(a), None) == 1
+
+
 def test_host_validation_of_the_update_loss_and_metric_calls(cdll):
     """More argument checks that return GS_ERR_INVALID_ARG (1) on the host
     before any CUDA call: bad modes, sizes, optimiser constants, workspace
