@@ -235,10 +235,19 @@ def gs_render_fwd_cfg(splats, vals, ranges, cam: GsCamera, cfg, image, t_final, 
         _ptr(t_final, torch.float32, "t_final"), _ptr(n_last, torch.int32, "n_last"), _stream(stream)))
 
 
+def _resume_sizes(cam: GsCamera, resume, resume_pos):
+    """The resume record's sizes: [H][W][4] float and [tiles] int32."""
+    if resume is not None and resume.numel() < 4 * cam.width * cam.height:
+        raise ValueError("resume holds fewer than H * W * 4 floats")
+    if resume_pos is not None and resume_pos.numel() < cam.tiles:
+        raise ValueError("resume_pos holds fewer than tiles entries")
+
+
 def gs_render_fwd_resume(splats, vals, ranges, cam: GsCamera, cfg, frozen, image, t_final, n_last, resume,
                          resume_pos, stream=None):
     import torch
 
+    _resume_sizes(cam, resume, resume_pos)
     _check("gs_render_fwd_resume", load().gs_render_fwd_resume(
         _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
         ctypes.byref(cam), None if cfg is None else ctypes.byref(cfg), _ptr(frozen, torch.uint8, "frozen"),
@@ -251,6 +260,7 @@ def gs_raster_bwd_resume(splats, vals, ranges, cam: GsCamera, cfg, t_final, n_la
                          resume_pos, grad2d, stream=None):
     import torch
 
+    _resume_sizes(cam, resume, resume_pos)
     _check("gs_raster_bwd_resume", load().gs_raster_bwd_resume(
         _ptr(splats, torch.float32, "splats"), _ptr(vals, torch.int32, "vals"), _ptr(ranges, torch.int32, "ranges"),
         ctypes.byref(cam), None if cfg is None else ctypes.byref(cfg), _ptr(t_final, torch.float32, "t_final"),
@@ -370,6 +380,8 @@ def step_args(P, G, m, v, splats, grad2d, n: int, sh_degree: int, opacity_act: i
     s.b1, s.b2, s.eps = b1, b2, eps
     if (resume is None) != (resume_pos is None):
         raise ValueError("resume and resume_pos go together")
+    if resume is not None and (resume.numel() < 4 * t_final.numel() or 2 * resume_pos.numel() < ranges.numel()):
+        raise ValueError("the resume record is [H][W][4] float and [tiles] int32")
     s.resume, s.resume_pos = _ptr(resume, f32, "resume"), _ptr(resume_pos, i32, "resume_pos")
     return s
 

@@ -116,6 +116,23 @@ def test_host_validation_of_the_resume_calls(cdll):
                                   p(a), p(a), None) == 1
 
 
+def test_resume_record_sizes_are_checked_by_the_binding():
+    """The binding refuses a resume record smaller than [H][W][4] floats and
+    [tiles] int32 before it calls the library (tensors on the host)."""
+    import torch
+
+    from paper_2504_06716_gb300 import lib
+
+    cam = lib.GsCamera()
+    cam.width, cam.height, cam.tile = 40, 24, 16  # 3 x 2 tiles
+    lib._resume_sizes(cam, torch.zeros(40 * 24 * 4), torch.zeros(6, dtype=torch.int32))
+    lib._resume_sizes(cam, None, None)
+    with pytest.raises(ValueError):
+        lib._resume_sizes(cam, torch.zeros(40 * 24 * 4), torch.zeros(5, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        lib._resume_sizes(cam, torch.zeros(40 * 24 * 4 - 1), torch.zeros(6, dtype=torch.int32))
+
+
 def test_host_validation_of_the_update_loss_and_metric_calls(cdll):
     """More argument checks that return GS_ERR_INVALID_ARG (1) on the host
     before any CUDA call: bad modes, sizes, optimiser constants, workspace
