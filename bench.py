@@ -377,8 +377,9 @@ def gpu_arm(args):
                                   f" {OPS_BLENDED_FROZEN} by a frozen one, {OPS_SKIPPED} skipped; per launch"
                                   f" {pc[0]:.3e} / {pc[1]:.3e} / {pc[2]:.3e} pairs (gs_raster_pair_counts,"
                                   f" freeze map at the end of the timed region)",
-                    peak_source=f"{sms} SMs (device) x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock of "
-                                f"{peak_kind} peaks file)",
+                    peak_source=f"{sms} SMs (device) x 128 FP32 lanes x {sm_max:.0f} MHz (max SM clock, "
+                                + ("measured peaks file)" if peak_kind == "measured" else
+                                   "fallback figure: no measured peaks file)"),
                     mean_launch_ms=rb_mean)
     adam = stages.get("adam_roofline")
     project = stages.get("project_roofline")
